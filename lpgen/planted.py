@@ -1,0 +1,280 @@
+"""Planted-optimum LP generators (seeded, synthetic).
+
+Every instance is drawn from ``numpy.random.default_rng(seed)`` in a fixed
+order, so a (generator, sizes, seed) triple names one problem exactly.
+
+The shapes follow the tall/wide regime the paper targets (m << n, Section 1)
+and stand in for its l1-SVM data sets, which are not available here.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# storage rounding
+# ---------------------------------------------------------------------------
+
+def bf16_bits(a: np.ndarray) -> np.ndarray:
+    """Round FP64/FP32 values to bfloat16 (round to nearest even); uint16 bits."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    # NaN is not produced by the generators; plain RNE on the upper 16 bits.
+    rounding = 0x7FFF + ((u >> 16) & 1)
+    return ((u + rounding) >> 16).astype(np.uint16)
+
+
+def round_bf16(a: np.ndarray) -> np.ndarray:
+    """Values of ``a`` after bfloat16 storage, as FP64."""
+    bits = bf16_bits(a).astype(np.uint32) << 16
+    return bits.view(np.float32).astype(np.float64)
+
+
+def _round_storage(a: np.ndarray, storage: str) -> np.ndarray:
+    if storage == "f64":
+        return np.asarray(a, dtype=np.float64)
+    if storage == "f32":
+        return np.asarray(a, dtype=np.float32).astype(np.float64)
+    if storage == "bf16":
+        return round_bf16(a)
+    raise ValueError(f"unknown storage {storage!r}")
+
+
+# ---------------------------------------------------------------------------
+# planted problems
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PlantedLP:
+    """A planted LP.  ``A`` holds the stored (rounded) values in FP64.
+
+    Dense problems keep ``A`` as an (m, n) array; sparse problems keep CSC
+    arrays (``col_ptr``, ``row_idx``, ``val``) and ``A`` is None unless
+    requested with ``dense()``.
+    """
+
+    m: int
+    n: int
+    b: np.ndarray
+    c: np.ndarray
+    x_star: np.ndarray
+    y_star: np.ndarray
+    s_star: np.ndarray
+    basis: np.ndarray
+    storage: str = "f64"
+    A: Optional[np.ndarray] = None
+    col_ptr: Optional[np.ndarray] = None
+    row_idx: Optional[np.ndarray] = None
+    val: Optional[np.ndarray] = None
+
+    @property
+    def sparse(self) -> bool:
+        return self.col_ptr is not None
+
+    @property
+    def objective(self) -> float:
+        """c^T x* (= b^T y*): the planted optimal value."""
+        return float(self.c @ self.x_star)
+
+    def dense(self) -> np.ndarray:
+        if self.A is not None:
+            return self.A
+        A = np.zeros((self.m, self.n))
+        for j in range(self.n):
+            lo, hi = self.col_ptr[j], self.col_ptr[j + 1]
+            A[self.row_idx[lo:hi], j] = self.val[lo:hi]
+        return A
+
+    def scipy_csc(self):
+        import scipy.sparse as sp
+        return sp.csc_matrix((self.val, self.row_idx, self.col_ptr), shape=(self.m, self.n))
+
+    def storage_array(self) -> np.ndarray:
+        """Column-major storage of dense A in its storage dtype.
+
+        Returned as an (n, m) C-contiguous array (row j = column a_j), i.e. the
+        column-major layout with leading dimension m; bf16 is returned as its
+        uint16 bit pattern.
+        """
+        assert self.A is not None
+        At = np.ascontiguousarray(self.A.T)
+        if self.storage == "f64":
+            return At
+        if self.storage == "f32":
+            return At.astype(np.float32)
+        return bf16_bits(At)
+
+
+def _plant(rng: np.random.Generator, m: int, n: int):
+    basis = np.sort(rng.choice(n, size=m, replace=False))
+    x_star = np.zeros(n)
+    x_star[basis] = rng.uniform(1.0, 2.0, size=m)
+    s_star = rng.uniform(1.0, 2.0, size=n)
+    s_star[basis] = 0.0
+    y_star = rng.standard_normal(m)
+    return basis, x_star, y_star, s_star
+
+
+def planted_dense(m: int, n: int, seed: int = 0, storage: str = "f64",
+                  col_scale_log10: Optional[tuple] = None) -> PlantedLP:
+    """Dense planted LP with iid N(0,1) entries.
+
+    ``col_scale_log10=(lo, hi)`` multiplies column j by 10**U(lo, hi)
+    (log-uniform column scaling).  A is rounded to ``storage`` first, then
+    b = A x*, c = A^T y* + s* are formed in FP64 from the rounded A.
+    """
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n))
+    if col_scale_log10 is not None:
+        lo, hi = col_scale_log10
+        A *= 10.0 ** rng.uniform(lo, hi, size=n)
+    A = _round_storage(A, storage)
+    basis, x_star, y_star, s_star = _plant(rng, m, n)
+    b = A @ x_star
+    c = A.T @ y_star + s_star
+    return PlantedLP(m=m, n=n, b=b, c=c, x_star=x_star, y_star=y_star,
+                     s_star=s_star, basis=basis, storage=storage, A=A)
+
+
+def planted_sparse(m: int, n: int, nnz_per_col: int = 8, seed: int = 0,
+                   zipf_frac: float = 0.2, zipf_a: float = 1.2,
+                   storage: str = "f32") -> PlantedLP:
+    """Sparse planted LP in CSC form.
+
+    Each column has ``nnz_per_col`` distinct rows: a fraction ``1-zipf_frac``
+    uniform over rows, the rest drawn from a Zipf(zipf_a) rank distribution
+    mapped through a random row permutation (heavy-tailed row counts).
+    Values are N(0,1), rounded to ``storage``.
+    """
+    rng = np.random.default_rng(seed)
+    k = nnz_per_col
+    if k > m:
+        raise ValueError("nnz_per_col > m")
+    perm = rng.permutation(m)
+    rows = rng.integers(0, m, size=(n, k))
+    zipf_mask = rng.random((n, k)) < zipf_frac
+
+    def zipf_rows(cnt):
+        out = np.empty(cnt, dtype=np.int64)
+        filled = 0
+        while filled < cnt:
+            z = rng.zipf(zipf_a, size=2 * (cnt - filled) + 16)
+            z = z[z <= m]
+            take = min(len(z), cnt - filled)
+            out[filled:filled + take] = perm[z[:take] - 1]
+            filled += take
+        return out
+
+    rows[zipf_mask] = zipf_rows(int(zipf_mask.sum()))
+    # resample repeated rows within a column (uniformly) until all distinct
+    while True:
+        srt = np.sort(rows, axis=1)
+        dup_cols = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+        if dup_cols.size == 0:
+            break
+        sub = rows[dup_cols]
+        for t in range(1, k):
+            clash = (sub[:, t:t + 1] == sub[:, :t]).any(axis=1)
+            sub[clash, t] = rng.integers(0, m, size=int(clash.sum()))
+        rows[dup_cols] = sub
+    rows.sort(axis=1)
+    vals = rng.standard_normal((n, k))
+    vals = _round_storage(vals, storage)
+    col_ptr = np.arange(0, n * k + 1, k, dtype=np.int64)
+    row_idx = rows.reshape(-1).astype(np.int32)
+    val = vals.reshape(-1)
+    basis, x_star, y_star, s_star = _plant(rng, m, n)
+    # b = A x*, c = A^T y* + s* in FP64 from the stored values
+    b = np.zeros(m)
+    np.add.at(b, row_idx, val * np.repeat(x_star, k))
+    c = (val * y_star[row_idx]).reshape(n, k).sum(axis=1) + s_star
+    return PlantedLP(m=m, n=n, b=b, c=c, x_star=x_star, y_star=y_star,
+                     s_star=s_star, basis=basis, storage=storage,
+                     col_ptr=col_ptr, row_idx=row_idx, val=val)
+
+
+# ---------------------------------------------------------------------------
+# strictly feasible start for planted problems
+# ---------------------------------------------------------------------------
+
+def feasible_start(lp: PlantedLP, gamma: float, shrink: float = 0.5):
+    """A strictly feasible (x0, y0, s0) with x0 o s0 >= (1-gamma) mu0.
+
+    With B the planted support (|B| = m, A_B nonsingular):
+      primal: delta_N = 1, A_B delta_B = -A_N 1, x0 = x* + t delta  (A x0 = b)
+      dual:   A_B^T u = 1, y0 = y* - t u, s0 = c - A^T y0 = s* + t A^T u
+              (so s0_B = t).
+    t starts at ``shrink`` times the largest value keeping (x0, s0) > 0 and
+    is halved until the neighbourhood condition holds.
+    """
+    A = lp.dense()
+    B = lp.basis
+    N = np.setdiff1d(np.arange(lp.n), B)
+    AB = A[:, B]
+    delta = np.ones(lp.n)
+    delta[B] = np.linalg.solve(AB, -A[:, N].sum(axis=1))
+    u = np.linalg.solve(AB.T, np.ones(lp.m))
+    g = A.T @ u
+    # largest t with x* + t delta > 0 and s* + t g > 0
+    tmax = np.inf
+    neg = delta < 0
+    if neg.any():
+        tmax = min(tmax, np.min(lp.x_star[neg] / -delta[neg]))
+    neg = g < 0
+    if neg.any():
+        tmax = min(tmax, np.min(lp.s_star[neg] / -g[neg]))
+    t = shrink * (tmax if np.isfinite(tmax) else 1.0)
+    for _ in range(200):
+        x0 = lp.x_star + t * delta
+        y0 = lp.y_star - t * u
+        s0 = lp.c - A.T @ y0
+        if (x0 > 0).all() and (s0 > 0).all():
+            mu0 = x0 @ s0 / lp.n
+            if np.min(x0 * s0) >= (1.0 - gamma) * mu0:
+                return x0, y0, s0
+        t *= 0.5
+    raise RuntimeError("no strictly feasible start found")
+
+
+# ---------------------------------------------------------------------------
+# the five workload shapes
+# ---------------------------------------------------------------------------
+
+CONFIGS = {
+    # feasible-start IPM, FP64, dense 64 x 4096, CountSketch w=4m, s=2
+    "c1": dict(kind="dense", m=64, n=4096, storage="f64", col_scale=None,
+               mode="feasible", w_factor=4.0, s=2, seed=0),
+    # infeasible-start IPM, FP32 storage, dense 512 x 131072,
+    # columns scaled by 10**U(-2, 2), CountSketch w=4m, s=4
+    "c2": dict(kind="dense", m=512, n=131072, storage="f32", col_scale=(-2.0, 2.0),
+               mode="infeasible", w_factor=4.0, s=4, seed=0),
+    # infeasible-start IPM, sparse CSC 4096 x 2,000,000, 8 nnz per column,
+    # 20% Zipf(1.2) rows, CountSketch w=3m, s=2
+    "c3": dict(kind="sparse", m=4096, n=2_000_000, storage="f32", nnz_per_col=8,
+               mode="infeasible", w_factor=3.0, s=2, seed=0),
+    # BF16 storage, dense 2048 x 524288, CountSketch w=4m, s=2
+    "c4": dict(kind="dense", m=2048, n=524288, storage="bf16", col_scale=None,
+               mode="infeasible", w_factor=4.0, s=2, seed=0),
+}
+
+
+def make(cfg: dict, m: Optional[int] = None, n: Optional[int] = None,
+         seed: Optional[int] = None) -> PlantedLP:
+    m = cfg["m"] if m is None else m
+    n = cfg["n"] if n is None else n
+    seed = cfg["seed"] if seed is None else seed
+    if cfg["kind"] == "dense":
+        return planted_dense(m, n, seed=seed, storage=cfg["storage"],
+                             col_scale_log10=cfg.get("col_scale"))
+    return planted_sparse(m, n, nnz_per_col=cfg.get("nnz_per_col", 8), seed=seed,
+                          storage=cfg["storage"])
+
+
+def config_small(name: str, div: int = 8, seed: Optional[int] = None) -> PlantedLP:
+    """The named workload with m and n divided by ``div`` (CI-sized)."""
+    cfg = CONFIGS[name]
+    return make(cfg, m=max(4, cfg["m"] // div), n=max(16, cfg["n"] // div), seed=seed)

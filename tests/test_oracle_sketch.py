@@ -1,0 +1,108 @@
+"""Pins for oracle.sketch: the counter-based generator and the sketches."""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import sketch
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+
+
+def _golden():
+    rows = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        vals = [int(t) for t in line.split()]
+        rows.append((vals[0], vals[1:]))
+    return rows
+
+
+def test_splitmix64_reference_outputs():
+    for seed, outs in _golden():
+        got = sketch.splitmix64_stream(seed, len(outs))
+        assert [int(v) for v in got] == outs
+
+
+def test_counter_draw_equals_stream_position():
+    # draw(seed, t-1) is output t of the sequential stream
+    seq = sketch.splitmix64_stream(1234567, 50)
+    ctr = sketch.draw(1234567, np.arange(50, dtype=np.uint64))
+    assert np.array_equal(seq, ctr)
+
+
+def test_mix64_is_bijective_on_sample():
+    # invert the three xorshift-multiply steps; a wrong shift breaks this
+    def inv_xorshift(z, k):
+        out = z.copy()
+        for _ in range(64 // k + 1):
+            out = z ^ (out >> np.uint64(k))
+        return out
+
+    z = np.random.default_rng(1).integers(0, 2**63, size=1000, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    y = sketch.mix64(z)
+    c2 = pow(0x94D049BB133111EB, -1, 2**64)
+    c1 = pow(0xBF58476D1CE4E5B9, -1, 2**64)
+    with np.errstate(over="ignore"):
+        t = inv_xorshift(y, 31) * np.uint64(c2)
+        t = inv_xorshift(t, 27) * np.uint64(c1)
+        t = inv_xorshift(t, 30)
+    assert np.array_equal(t, z)
+
+
+@pytest.mark.parametrize("w,s", [(64, 1), (64, 2), (96, 3), (128, 4)])
+def test_countsketch_structure(w, s):
+    n = 500
+    W = sketch.countsketch_matrix(7, 3, 0, n, w, s).toarray()
+    wb = w // s
+    for b in range(s):
+        blk = W[:, b * wb:(b + 1) * wb]
+        # exactly one nonzero per row per block, value +-1/sqrt(s)
+        assert np.array_equal((blk != 0).sum(axis=1), np.ones(n))
+        assert np.allclose(np.abs(blk[blk != 0]), 1.0 / np.sqrt(s))
+    # squared row norms are exactly 1 (E[W W^T] = I on the diagonal)
+    assert np.allclose((W * W).sum(axis=1), 1.0)
+
+
+def test_countsketch_buckets_uniform_and_signs_balanced():
+    n, w, s = 200_000, 64, 2
+    cols, signs = sketch.countsketch_hash(11, 0, 0, n, w, s)
+    for b in range(s):
+        counts = np.bincount(cols[b] - b * (w // s), minlength=w // s)
+        expected = n / (w // s)
+        chi2 = ((counts - expected) ** 2 / expected).sum()
+        # 31 degrees of freedom: P(chi2 > 70) < 1e-4
+        assert chi2 < 70.0
+        assert abs(signs[b].mean()) < 5.0 / np.sqrt(n)
+
+
+def test_countsketch_redraw_changes_hash():
+    a = sketch.countsketch_hash(5, 2, 0, 1000, 64, 2)[0]
+    b = sketch.countsketch_hash(5, 2, 1, 1000, 64, 2)[0]
+    c = sketch.countsketch_hash(5, 3, 0, 1000, 64, 2)[0]
+    assert (a != b).mean() > 0.8 and (a != c).mean() > 0.8
+
+
+def test_sparse_embedding_approximates_gram():
+    # eq. pdprec with Z = V^T (orthonormal rows): ||Z W W^T Z^T - I|| small for large w
+    rng = np.random.default_rng(0)
+    m, n = 4, 4000
+    V, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    W = sketch.countsketch_matrix(3, 0, 0, n, 4096, 4)
+    ZW = (W.T @ V).T
+    err = np.linalg.norm(ZW @ ZW.T - np.eye(m), 2)
+    assert err < 0.25
+
+
+def test_gaussian_sketch_moments():
+    n, w = 400, 256
+    G = sketch.gaussian_matrix(9, 1, 0, n, w) * np.sqrt(w)
+    assert abs(G.mean()) < 0.02
+    assert abs(G.var() - 1.0) < 0.03
+    # fourth moment of N(0,1) is 3
+    assert abs((G ** 4).mean() - 3.0) < 0.15
+    G2 = sketch.gaussian_matrix(9, 2, 0, n, w)
+    assert not np.allclose(G / np.sqrt(w), G2)
