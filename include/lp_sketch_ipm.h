@@ -1,0 +1,228 @@
+/*
+ * lp_sketch_ipm.h -- C ABI of the GB300 sketched inexact interior-point LP solver.
+ *
+ * Problem (arXiv 2209.08722, Section 1, eq. primal / eq. dual):
+ *     min c^T x  s.t.  A x = b, x >= 0        max b^T y  s.t.  A^T y + s = c, s >= 0
+ * with A in R^{m x n}, m << n, full row rank (Section 1).
+ *
+ * Every outer iteration solves the normal equations A D^2 A^T dy = p (eq. normal,
+ * D = X^{1/2} S^{-1/2}) inexactly: a sparse-embedding (CountSketch) sketch A D W
+ * (Section 2, eq. pdprec), a factorisation of that sketch giving the
+ * preconditioner Q = A D W W^T D A^T (eq. pdprecond, Algorithm 1 steps 1-2),
+ * preconditioned CG or Chebyshev iteration run to the inexactness bound
+ * (Algorithm 1 step 3, Lemma 4.4), and the correction vector v of eq. (compv).
+ * The outer loop is Algorithm 2 (feasible start) or Algorithm 3 (infeasible start).
+ *
+ * Conventions for every entry point:
+ *   - Return value: 0 = LP_OK; negative = error (LP_ERR_*); positive = a
+ *     completed call with a warning status (LP_STATUS_*, LP_WARN_*).  After an
+ *     error, lp_last_error(h) gives a one-line message.
+ *   - Ownership: the handle owns all device memory it allocates.  Caller
+ *     buffers are never retained: lp_create copies A, b, c; outputs are written
+ *     into caller-allocated buffers.
+ *   - Host or device pointers: calls that take an `on_device` flag accept host
+ *     pointers (0) or device pointers on the handle's device (1).  Calls in the
+ *     "kernel-level" section take DEVICE pointers only.
+ *   - All vectors are FP64 unless stated.  A handle is not thread-safe; calls on
+ *     one handle are ordered on its stream and every call returns after its
+ *     work completed (the host synchronises the stream).
+ */
+#ifndef LP_SKETCH_IPM_H
+#define LP_SKETCH_IPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque solver handle: owns the device copy of A, b, c and every workspace. */
+typedef struct lp_handle lp_handle;
+
+/* ---- status codes ------------------------------------------------------- */
+#define LP_OK                   0
+#define LP_ERR_ARG             -1  /* invalid argument (sizes, pointers, options) */
+#define LP_ERR_CUDA            -2  /* a CUDA runtime / cuBLAS / cuSOLVER call failed */
+#define LP_ERR_OOM             -3  /* device allocation failed */
+#define LP_ERR_SKETCH_RANK     -4  /* A D W rank deficient after every redraw (Lemma 4.1) */
+#define LP_ERR_NOT_FEASIBLE    -5  /* feasible mode: start not strictly feasible / not in N(gamma) */
+#define LP_ERR_NUMERICAL       -6  /* NaN/Inf or a breakdown in a reduction */
+#define LP_ERR_DEVICE_TIMEOUT  -7  /* a bounded device-side wait gave up */
+#define LP_ERR_UNSUPPORTED     -8  /* valid request this build does not implement */
+#define LP_STATUS_MAX_ITER      1  /* lp_solve: k_max outer iterations reached */
+#define LP_WARN_INNER_MAXIT     2  /* an inner solve stopped at t_max */
+#define LP_STATUS_STALLED       3  /* lp_solve: step length reached zero */
+
+/* ---- matrix description -------------------------------------------------- */
+typedef enum { LP_DENSE_COLMAJOR = 0, LP_CSC = 1 } lp_format;
+typedef enum { LP_F64 = 0, LP_F32 = 1, LP_BF16 = 2 } lp_dtype;
+
+typedef struct {
+    int32_t m;            /* rows (constraints) */
+    int64_t n;            /* columns (variables) */
+    int32_t fmt;          /* lp_format */
+    int32_t dtype;        /* lp_dtype of the stored values; the LP solved is the one
+                             with these (rounded) values */
+    const void* val;      /* dense: column j at val + j*ld; CSC: nnz values */
+    int64_t ld;           /* dense: leading dimension (>= m); ignored for CSC */
+    const int64_t* ptr;   /* CSC: n+1 column pointers (ptr[0] = 0) */
+    const int32_t* idx;   /* CSC: nnz row indices in [0, m) */
+    int64_t nnz;          /* CSC: number of stored entries */
+    int32_t on_device;    /* 1: val/ptr/idx are device pointers */
+} lp_matrix;
+
+/* ---- options -------------------------------------------------------------- */
+enum { LP_SKETCH_COUNT = 0, LP_SKETCH_GAUSS = 1 };
+enum { LP_INNER_CG = 0, LP_INNER_CHEBYSHEV = 1 };
+enum { LP_RULE_THEORY = 0, LP_RULE_RELATIVE = 1 };
+enum { LP_FEASIBLE = 0, LP_INFEASIBLE = 1 };
+
+typedef struct {
+    double sigma;          /* centering parameter, (0, 4/5) (Algorithms 2, 3); 0.5 */
+    double gamma;          /* neighbourhood N(gamma) width, (0, 1) (eq. neigh); 0.999 */
+    double tol_cg;         /* relative inner tolerance for LP_RULE_RELATIVE (Section 7); 1e-5 */
+    int32_t inner_rule;    /* LP_RULE_THEORY: ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(3n)) (Lemmas 4.2, 4.4) */
+    int32_t sketch;        /* LP_SKETCH_COUNT (Section 2) or LP_SKETCH_GAUSS (Section 6) */
+    int32_t s;             /* nonzeros per row of a CountSketch W (1..16); 2 */
+    int32_t inner;         /* LP_INNER_CG or LP_INNER_CHEBYSHEV (Section 3) */
+    int32_t refine_every;  /* FP64 true-residual refresh every k inner steps; 8 */
+    int32_t k_max;         /* outer iteration limit; 200 */
+    int32_t t_max;         /* inner iteration limit per outer iteration; 500 */
+    int32_t v_correction;  /* 1: apply eq. (compv); 0: v = 0 (Table 2 ablation) */
+    int32_t cheb_lanczos;  /* CG steps used to estimate the Chebyshev interval; 10 */
+    int32_t profile;       /* 1: time the hot product kernel with CUDA events */
+    double w_factor;       /* sketch width w = w_factor * m when w == 0; 4.0 */
+    int64_t w;             /* explicit sketch width (multiple of s), or 0 */
+    uint64_t seed;         /* seed of the sketch generator; 0 */
+    void* stream;          /* cudaStream_t to run on, or NULL for a private stream */
+} lp_options;
+
+/* ---- results -------------------------------------------------------------- */
+typedef struct {
+    int32_t status;             /* LP_OK (optimal to tol), LP_STATUS_*, or an error */
+    int32_t outer_iterations;
+    int64_t inner_total;        /* sum of inner iterations */
+    int32_t inner_max;          /* max inner iterations of one outer iteration */
+    int32_t sketch_retries;     /* total redraws after a rank failure */
+    double primal_obj;          /* c^T x */
+    double dual_obj;            /* b^T y */
+    double rel_gap;             /* |c^T x - b^T y| / (1 + |c^T x|) */
+    double rp_rel;              /* ||A x - b|| / (1 + ||b||) */
+    double rd_rel;              /* ||A^T y + s - c|| / (1 + ||c||) */
+    double mu;                  /* final x^T s / n */
+    double ms_total;            /* wall time of the call */
+    double ms_residual, ms_sketch, ms_factor, ms_inner, ms_correction, ms_step;
+} lp_result;
+
+typedef struct {
+    int32_t inner_iterations;   /* CG / Chebyshev iterations taken */
+    int32_t retries;            /* sketch redraws (rank failures) */
+    double f_norm;              /* ||f^(t)|| = sqrt(r^T Q^{-1} r), r = p - A D^2 A^T dy (FP64) */
+    double f0_norm;             /* ||Q^{-1/2} p|| */
+    double v_norm;              /* ||v|| (0 when v was not requested) */
+    double lam_min, lam_max;    /* Chebyshev interval used (0 for CG) */
+} lp_nsolve_info;
+
+typedef struct {
+    int64_t launches;           /* hot product kernel launches timed since the last reset */
+    double ms;                  /* their summed CUDA-event duration */
+    int64_t bytes_per_launch;   /* algorithmic bytes of one launch (A + d^2 + in/out vectors) */
+    int64_t all_launches;       /* every kernel this library launched since the last reset
+                                   (library-wide counter; cuSOLVER's kernels not included) */
+} lp_kernel_stats;
+
+/* ---- lifecycle -------------------------------------------------------------- */
+
+/* Fills `opt` with the defaults listed above. */
+void lp_options_default(lp_options* opt);
+
+/* Copies A (dense column-major or CSC), b (m) and c (n) to the device in the
+ * handle's layout and allocates every workspace the solver needs.  `bc_on_device`
+ * says where b and c live.  Errors: LP_ERR_ARG (sizes, m > n, bad CSC, bad
+ * options), LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_UNSUPPORTED (shape outside this
+ * build's kernels).  On error *h is NULL. */
+int lp_create(lp_handle** h, const lp_matrix* A, const double* b, const double* c,
+              int32_t bc_on_device, const lp_options* opt);
+
+/* Frees the handle and everything it owns.  NULL is accepted. */
+int lp_destroy(lp_handle* h);
+
+/* Message of the last error on `h` (empty string if none); valid until the next call. */
+const char* lp_last_error(const lp_handle* h);
+
+/* Message of the last lp_create failure in this process. */
+const char* lp_create_error(void);
+
+/* ---- solver ---------------------------------------------------------------- */
+
+/* Runs Algorithm 3 (mode LP_INFEASIBLE) or Algorithm 2 (LP_FEASIBLE) until
+ * |c^T x - b^T y|/(1+|c^T x|), ||r_p||/(1+||b||), ||r_d||/(1+||c||) are all <= tol
+ * or k_max iterations.  x0, y0, s0 may be NULL: infeasible mode then starts from
+ * x0 = s0 = 1, y0 = 0; feasible mode requires a start that is strictly feasible
+ * and in N(gamma) (else LP_ERR_NOT_FEASIBLE).  x (n), y (m), s (n) receive the
+ * final iterate (NULL to skip).  `io_on_device` applies to x0..s0 and x..s.
+ * Returns LP_OK, LP_STATUS_MAX_ITER, LP_STATUS_STALLED or an error; `info`
+ * (nullable) receives the summary. */
+int lp_solve(lp_handle* h, double tol, int32_t mode,
+             const double* x0, const double* y0, const double* s0, int32_t io_on_device,
+             double* x, double* y, double* s, lp_result* info);
+
+/* One inexact normal-equation solve A D^2 A^T dy = p (Algorithm 1 + eq. compv)
+ * with the sketch drawn for outer-iteration index k.  D (n) is the diagonal of
+ * D; p (m) the right-hand side.  tol_f > 0: stop when ||f^(t)|| <= tol_f;
+ * tol_f <= 0: stop when ||f^(t)|| <= tol_cg * ||f^(0)||.  If xs (n, x o s) and
+ * v (n) are both non-NULL, v = (XS)^{1/2} W (ADW)^+ (A D^2 A^T dy - p) is
+ * returned too (requires D^2 = x/s for the invariant of eq. addl to hold).
+ * Returns LP_OK, LP_WARN_INNER_MAXIT or an error. */
+int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double* xs,
+                    int64_t k, double tol_f, int32_t io_on_device,
+                    double* dy, double* v, lp_nsolve_info* info);
+
+/* ---- kernel-level entry points (DEVICE pointers; the handle's resident A) ---- */
+
+/* u = A diag(d2) A^T v  (the product inside every CG step, eq. normal).
+ * d2 (n), v (m), u (m).  precision 0: products in FP32 with FP32 accumulation
+ * (FP32/BF16 storage; FP64 storage always computes in FP64); 1: FP64. */
+int lp_adat(lp_handle* h, const double* d2, const double* v, double* u, int32_t precision);
+
+/* Residuals and right-hand side of Algorithm 3 step 3 (Section 5) or eq. pdef:
+ * r_p = A x - b (m), r_d = A^T y + s - c (n), mu = x^T s / n, and
+ *   infeasible: p = -r_p - sigma mu A S^{-1} 1 + A x - A D^2 r_d
+ *   feasible:   p = -sigma mu A S^{-1} 1 + A x.
+ * out5 (host, 5 doubles) receives {mu, c^T x, b^T y, ||r_p||, ||r_d||}. */
+int lp_residual_rhs(lp_handle* h, const double* x, const double* y, const double* s,
+                    int32_t mode, double* r_p, double* r_d, double* p, double* out5);
+
+/* A D W for the CountSketch of (seed, k, retry): adw is m x w, row-major
+ * (adw[i*w + j]).  D (n).  Returns the width w through *w_out (nullable). */
+int lp_sketch(lp_handle* h, const double* D, uint64_t seed, int64_t k, int32_t retry,
+              double* adw, int64_t* w_out);
+
+/* Factors an m x w row-major sketch (QR of its transpose) and keeps the
+ * preconditioner in the handle; then z = Q^{-1} r with Q = adw adw^T.
+ * Returns LP_ERR_SKETCH_RANK if adw is numerically rank deficient. */
+int lp_precond_apply(lp_handle* h, const double* adw, const double* r, double* z);
+
+/* Directions of eqs. (delshat)/(delshat_i) and (delxhat):
+ *   ds = -A^T dy (feasible) or -r_d - A^T dy (infeasible);
+ *   dx = -x + sigma mu / s - (x/s) o ds - v / s.   rd may be NULL in feasible mode. */
+int lp_directions(lp_handle* h, const double* x, const double* s, const double* rd,
+                  const double* dy, const double* v, double mu, int32_t mode,
+                  double* dx, double* ds);
+
+/* Step lengths of Algorithm 2 steps 5-6 / Algorithm 3 steps 6-7: alpha_max is the
+ * first exit from N(gamma) along (dx, ds) in [0, 1] (res_ratio = ||r||/||r^0||
+ * and mu0 enter the infeasible condition), alpha_bar minimises the gap on
+ * [0, alpha_max].  out2 (host) = {alpha_max, alpha_bar}. */
+int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double* dx,
+                    const double* ds, int32_t mode, double res_ratio, double mu0,
+                    double* out2);
+
+/* Statistics of the hot product kernel (requires opt.profile = 1). */
+int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);
+int lp_reset_kernel_stats(lp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LP_SKETCH_IPM_H */

@@ -1,0 +1,64 @@
+// Declarations shared by the translation units of the CUDA library.
+#pragma once
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "stream.cuh"
+
+namespace lpk {
+
+// kernels launched by this library since load (cuSOLVER's own kernels excluded)
+extern std::atomic<long long> g_launches;
+
+struct StreamPlan {
+  int nb = 0, ntiles = 0, stages = 0, grid = 0, smem = 0, smem8 = 0;
+  bool ok = false;
+};
+
+StreamPlan make_stream_plan(int m, long long n, int lda, int esz, int num_sms, int tc_bytes);
+int fused_vpl(int lda, int esz);
+cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
+                          const StreamPlan& p, cudaStream_t st);
+cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
+
+cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
+                               const double* dvec, int is_d2, uint64_t seed, long long k,
+                               int retry, int s_blocks, int w, double* adw, int num_sms,
+                               cudaStream_t st);
+cudaError_t launch_v_gather(long long n, const double* x, const double* s, const double* u,
+                            uint64_t seed, long long k, int retry, int s_blocks, int w, double scale,
+                            double* v, int num_sms, cudaStream_t st);
+
+enum GemvEpiHost : int {
+  GH_NONE = 0, GH_PCG_INIT = 1, GH_PCG_B = 2, GH_REFRESH = 3, GH_CHEB_INIT = 4, GH_CHEB_B = 5,
+  GH_CHEB_REFRESH = 6
+};
+cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
+                            int skip_level, double* r, double* p, double* dy, DevScalars* sc,
+                            unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_cheb_pre(int m, double* dy, const double* dir, DevScalars* sc, cudaStream_t st);
+cudaError_t launch_adwt(const double* adw, int m, int w, const double* g, double* part, int max_parts,
+                        double* out, int num_sms, cudaStream_t st);
+cudaError_t launch_dot(long long n, const double* x, const double* y, double scale, double* part,
+                       unsigned* ticket, double* out, int num_sms, cudaStream_t st);
+cudaError_t launch_step(long long n, const double* x, const double* s, const double* dx,
+                        const double* ds, double gamma, int feasible, double res_ratio, double mu0,
+                        double* part, unsigned* ticket, DevScalars* sc, int num_sms, cudaStream_t st);
+cudaError_t launch_update(long long n, int m, double* x, double* s, double* y, const double* dx,
+                          const double* ds, const double* dy, DevScalars* sc, double* part,
+                          unsigned* ticket, int num_sms, cudaStream_t st);
+cudaError_t launch_fill(long long n, double* x, double v, int num_sms, cudaStream_t st);
+cudaError_t launch_min_prod(long long n, const double* x, const double* y, double* part,
+                            unsigned* ticket, double* out, int num_sms, cudaStream_t st);
+cudaError_t launch_to_f32(long long n, const double* x, float* y, int square, int num_sms,
+                          cudaStream_t st);
+cudaError_t launch_square(long long n, const double* x, double* y, int num_sms, cudaStream_t st);
+cudaError_t launch_factor_utils(int which, const double* a, int w, int m, double* b, DevScalars* sc,
+                                double rank_tol, int num_sms, cudaStream_t st);
+
+}  // namespace lpk

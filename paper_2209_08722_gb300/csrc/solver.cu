@@ -1,0 +1,920 @@
+// Host driver of the GB300 sketched inexact IPM: the C ABI of lp_sketch_ipm.h.
+//
+// Outer iteration (Algorithm 3 step numbers; Algorithm 2 is the same with
+// r_d = 0 and p from eq. pdef):
+//   step 3   one FP64 A-pass: r_p = A x - b, r_d = A^T y + s - c, p, d^2
+//   step 2   CountSketch A D W (sketch.cu)
+//   Alg. 1   QR of (ADW)^T (cuSOLVER geqrf) and R^{-1} (cuSOLVER trtri):
+//            Q = A D W W^T D A^T = R^T R, Q^{-1} = R^{-1} R^{-T}
+//   step 4   PCG on eq. (precond) with preconditioner Q^{-1}: FP32 products
+//            (k_adat_fused), FP64 true-residual refresh every `refine_every`
+//            steps, stop at ||f|| = sqrt(r^T Q^{-1} r) <= tol (Lemma 4.4)
+//   step 5   v of eq. (compv) = (XS)^{1/2} W (ADW)^T Q^{-1} (M dy - p)
+//            (using (ADW)^+ = (ADW)^T Q^{-1} for full row rank), the
+//            directions (one FP64 A^T-pass), then the step lengths (steps 6-7)
+//            and the update (step 8).
+// The host synchronises a few times per outer iteration (stopping test, rank
+// check, inner-solve chunks); everything else is stream-ordered.
+#include <cusolverDn.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lp_sketch_ipm.h"
+#include "internal.h"
+
+using namespace lpk;
+
+namespace {
+std::string g_create_error;
+
+long long round_up_ll(long long x, long long a) { return (x + a - 1) / a * a; }
+
+struct EvPair {
+  cudaEvent_t a, b;
+};
+}  // namespace
+
+struct lp_handle {
+  int dev = 0, num_sms = 1;
+  int m = 0;
+  long long n = 0, npad = 0;
+  int lda = 0, dtype = 0, esz = 0, fmt = 0;
+  void* A = nullptr;
+  lp_options opt{};
+  int w = 0, s_blocks = 2;
+  double bnorm = 0.0, cnorm = 0.0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  cusolverDnHandle_t sol = nullptr;
+  // n-vectors (padded)
+  double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
+         *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
+  float* d2f = nullptr;
+  // m-vectors
+  double *b = nullptr, *rp = nullptr, *p = nullptr, *dy = nullptr, *r = nullptr, *z = nullptr,
+         *pdir = nullptr, *q = nullptr, *wv = nullptr, *mb0 = nullptr, *mb1 = nullptr;
+  double* coef = nullptr;  // CG coefficients for the Lanczos interval
+  // sketch and factor
+  double *adw = nullptr, *qr = nullptr, *tau = nullptr, *rinv_cm = nullptr, *rinv_rm = nullptr,
+         *uw = nullptr, *adwt_part = nullptr;
+  int adwt_parts = 64;
+  void* dwork = nullptr;
+  size_t dwork_bytes = 0;
+  void* hwork = nullptr;
+  size_t hwork_bytes = 0;
+  int lwork_geqrf = 0;
+  int* dinfo = nullptr;
+  // scratch
+  void* partials = nullptr;
+  double* red_partials = nullptr;
+  unsigned* tickets = nullptr;
+  double* vpart = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* hsc = nullptr;  // pinned host copy
+  int* hinfo = nullptr;       // pinned
+  double* hval = nullptr;     // pinned staging for scalars
+  StreamPlan plan;
+  std::string err;
+  // profiling of the hot product kernel
+  std::vector<EvPair> ev_pool;
+  size_t ev_used = 0;
+  long long k1_launches = 0;
+  double k1_ms = 0.0;
+  long long launch_base = 0;
+  std::vector<void*> allocs;
+
+  int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  template <typename T>
+  int alloc(T** ptr, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *ptr = nullptr;
+      return fail(LP_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    allocs.push_back(p);
+    cudaMemsetAsync(p, 0, bytes, st);
+    *ptr = static_cast<T*>(p);
+    return LP_OK;
+  }
+  cudaStream_t stream() const { return st; }
+};
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess) return h->fail(LP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+#define CS(call)                                                                       \
+  do {                                                                                 \
+    cusolverStatus_t _s = (call);                                                      \
+    if (_s != CUSOLVER_STATUS_SUCCESS) return h->fail(LP_ERR_CUDA, "%s: status %d", #call, (int)_s); \
+  } while (0)
+#define RET(call)              \
+  do {                         \
+    int _r = (call);           \
+    if (_r < 0) return _r;     \
+  } while (0)
+
+namespace {
+
+int sync_read(lp_handle* h) {
+  CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->hsc->err == ERR_TIMEOUT) return h->fail(LP_ERR_DEVICE_TIMEOUT, "device wait timed out");
+  if (h->hsc->err == ERR_NUMERICAL) return h->fail(LP_ERR_NUMERICAL, "non-finite value in a reduction");
+  return LP_OK;
+}
+
+int set_scalar(lp_handle* h, double* dev_field, double value) {
+  CK(cudaStreamSynchronize(h->st));
+  *h->hval = value;
+  CK(cudaMemcpyAsync(dev_field, h->hval, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return LP_OK;
+}
+
+StreamArgs base_args(lp_handle* h) {
+  StreamArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.A = h->A;
+  a.lda = h->lda;
+  a.m = h->m;
+  a.n = h->n;
+  a.nb = h->plan.nb;
+  a.ntiles = h->plan.ntiles;
+  a.stages = h->plan.stages;
+  a.sigma = h->opt.sigma;
+  a.partials = h->partials;
+  a.ticket = h->tickets + 0;
+  a.sc = h->sc;
+  a.err = &h->sc->err;
+  return a;
+}
+
+// ---- profiling of the hot product (opt.profile) ----
+EvPair* ev_next(lp_handle* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    EvPair e;
+    if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return &h->ev_pool[h->ev_used++];
+}
+
+void ev_flush(lp_handle* h) {
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[i].a, h->ev_pool[i].b) == cudaSuccess) {
+      h->k1_ms += ms;
+      h->k1_launches += 1;
+    }
+  }
+  h->ev_used = 0;
+}
+
+// u = A diag(d2) A^T v with FP32 products (the hot kernel) or FP64
+int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int skip_level,
+                double* out_m0) {
+  StreamArgs a = base_args(h);
+  const bool use64 = fp64 || h->dtype == LP_F64;
+  a.cv[0] = use64 ? (const void*)h->d2d : (const void*)h->d2f;
+  a.cv_esz[0] = use64 ? 8 : 4;
+  a.ncv = 1;
+  a.vin = vin;
+  a.epilogue = epilogue;
+  a.skip_level = skip_level;
+  a.out_m0 = out_m0;
+  a.pcg_p = h->pdir;
+  a.pcg_r = h->r;
+  a.pcg_dy = h->dy;
+  a.bvec = h->p;
+  a.coef = h->coef;
+  EvPair* ev = nullptr;
+  if (h->opt.profile && !use64) {
+    ev = ev_next(h);
+    if (ev) cudaEventRecord(ev->a, h->st);
+  }
+  cudaError_t e = use64 ? launch_stream(h->dtype, true, M_ADAT, a, h->plan, h->st)
+                        : launch_adat_fused(h->dtype, a, h->plan, h->st);
+  if (ev) cudaEventRecord(ev->b, h->st);
+  if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "adat launch: %s", cudaGetErrorString(e));
+  return LP_OK;
+}
+
+int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_level) {
+  cudaError_t e = launch_gemv_tri(h->rinv_cm, h->m, 1, r, h->wv, GH_NONE, skip_level, nullptr,
+                                  nullptr, nullptr, h->sc, h->tickets + 1, &h->sc->err, 0, nullptr,
+                                  h->num_sms, h->st);
+  if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
+  e = launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, z, epi, skip_level, h->r, h->pdir, h->dy, h->sc,
+                      h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st);
+  if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
+  return LP_OK;
+}
+
+// QR of (ADW)^T and R^{-1}; LP_ERR_SKETCH_RANK on a rank failure.
+int factor(lp_handle* h) {
+  const int m = h->m, w = h->w;
+  CK(cudaMemcpyAsync(h->qr, h->adw, sizeof(double) * (size_t)m * w, cudaMemcpyDeviceToDevice, h->st));
+  CS(cusolverDnDgeqrf(h->sol, w, m, h->qr, w, h->tau, static_cast<double*>(h->dwork),
+                      h->lwork_geqrf, h->dinfo));
+  CK(launch_factor_utils(0, h->qr, w, m, h->rinv_cm, h->sc, 0.0, h->num_sms, h->st));
+  CK(launch_factor_utils(1, h->rinv_cm, w, m, nullptr, h->sc, 1e-13, h->num_sms, h->st));
+  CS(cusolverDnXtrtri(h->sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, m, CUDA_R_64F,
+                      h->rinv_cm, m, h->dwork, h->dwork_bytes, h->hwork, h->hwork_bytes,
+                      h->dinfo + 1));
+  CK(launch_factor_utils(2, h->rinv_cm, w, m, h->rinv_rm, h->sc, 0.0, h->num_sms, h->st));
+  CK(cudaMemcpyAsync(h->hinfo, h->dinfo, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  RET(sync_read(h));
+  if (h->hsc->rank_bad || h->hinfo[0] != 0 || h->hinfo[1] != 0)
+    return h->fail(LP_ERR_SKETCH_RANK, "A D W is numerically rank deficient (|R_ii| range %.3e..%.3e)",
+                   h->hsc->diag_min, h->hsc->diag_max);
+  return LP_OK;
+}
+
+// sketch for (k, retry) + factor, redrawing on a rank failure (Lemma 4.1)
+int sketch_and_factor(lp_handle* h, const double* dvec, int is_d2, long long k, int* retries) {
+  int rc = LP_ERR_SKETCH_RANK;
+  for (int retry = 0; retry < kMaxRetry; ++retry) {
+    CK(launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, h->opt.seed, k, retry,
+                          h->s_blocks, h->w, h->adw, h->num_sms, h->st));
+    rc = factor(h);
+    if (rc != LP_ERR_SKETCH_RANK) {
+      if (retries) *retries = retry;
+      return rc;
+    }
+  }
+  return rc;
+}
+
+// Symmetric tridiagonal eigenvalue bounds by bisection on Sturm counts.
+void tridiag_extremes(const std::vector<double>& dg, const std::vector<double>& off, double* lo,
+                      double* hi) {
+  const int k = (int)dg.size();
+  double gl = 1e300, gu = -1e300;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? fabs(off[i - 1]) : 0.0) + (i + 1 < k ? fabs(off[i]) : 0.0);
+    gl = std::min(gl, dg[i] - r);
+    gu = std::max(gu, dg[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < k; ++i) {
+      const double o2 = i > 0 ? off[i - 1] * off[i - 1] : 0.0;
+      q = dg[i] - x - (i > 0 ? o2 / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  auto kth = [&](int idx) {  // idx-th smallest eigenvalue (0-based)
+    double a = gl, b = gu;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (count_below(mid) > idx) b = mid;
+      else a = mid;
+    }
+    return 0.5 * (a + b);
+  };
+  *lo = kth(0);
+  *hi = kth(k - 1);
+}
+
+// The inner solve on the current factor: dy ~ M^{-1} p.  Returns LP_OK or
+// LP_WARN_INNER_MAXIT.  tol_f > 0: absolute ||f|| target; else relative tol_cg.
+int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
+  const int m = h->m;
+  const int inner = h->opt.inner;
+  CK(cudaMemsetAsync(h->dy, 0, sizeof(double) * m, h->st));
+  CK(cudaMemcpyAsync(h->r, h->p, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
+  RET(set_scalar(h, &h->sc->tol_f, tol_f > 0 ? tol_f : 0.0));
+  const int refine = std::max(1, h->opt.refine_every);
+  int total_iters = 0;
+  if (inner == LP_INNER_CHEBYSHEV) {
+    // interval from a few CG (Lanczos) steps on the same system
+    RET(precond_gemvs(h, h->r, h->z, GH_PCG_INIT, 0));
+    const int kl = std::max(2, h->opt.cheb_lanczos);
+    RET(set_scalar(h, &h->sc->tol_f, 0.0));
+    for (int j = 0; j < kl; ++j) {
+      RET(launch_adat(h, h->pdir, E_PCG_A, false, 0, h->q));
+      RET(precond_gemvs(h, h->r, h->z, GH_PCG_B, 0));
+    }
+    RET(sync_read(h));
+    std::vector<double> coef(2 * kl);
+    CK(cudaMemcpy(coef.data(), h->coef, sizeof(double) * 2 * kl, cudaMemcpyDeviceToHost));
+    const int kk = std::min(kl, h->hsc->inner_iters);
+    std::vector<double> dg(kk), off(std::max(0, kk - 1));
+    for (int j = 0; j < kk; ++j) {
+      const double al = coef[2 * j], be_prev = j > 0 ? coef[2 * (j - 1) + 1] : 0.0;
+      const double al_prev = j > 0 ? coef[2 * (j - 1)] : 1.0;
+      dg[j] = 1.0 / al + (j > 0 ? be_prev / al_prev : 0.0);
+      if (j + 1 < kk) off[j] = sqrt(coef[2 * j + 1]) / al;
+    }
+    double tmin = 0.5, tmax = 2.0;
+    if (kk > 0) tridiag_extremes(dg, off, &tmin, &tmax);
+    total_iters += kk;
+    // restart from dy = 0 with the Chebyshev recurrence
+    CK(cudaMemsetAsync(h->dy, 0, sizeof(double) * m, h->st));
+    CK(cudaMemcpyAsync(h->r, h->p, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
+    RET(set_scalar(h, &h->sc->lam_min, 0.5 * tmin));
+    RET(set_scalar(h, &h->sc->lam_max, 1.05 * tmax));
+    RET(set_scalar(h, &h->sc->tol_f, tol_f > 0 ? tol_f : 0.0));
+    RET(precond_gemvs(h, h->r, h->z, GH_CHEB_INIT, 0));
+  } else {
+    RET(precond_gemvs(h, h->r, h->z, GH_PCG_INIT, 0));
+  }
+  RET(sync_read(h));
+  if (tol_f <= 0) {
+    const double f0 = sqrt(std::max(h->hsc->rho0, 0.0));
+    RET(set_scalar(h, &h->sc->tol_f, h->opt.tol_cg * f0));
+    if (h->opt.tol_cg * f0 >= f0) {
+      *iters_out = total_iters;
+      return LP_OK;
+    }
+  } else if (h->hsc->inner_done == 2) {
+    *iters_out = total_iters;
+    return LP_OK;
+  }
+  int status = LP_OK;
+  while (true) {
+    for (int j = 0; j < refine; ++j) {
+      if (inner == LP_INNER_CHEBYSHEV) {
+        CK(launch_cheb_pre(m, h->dy, h->pdir, h->sc, h->st));
+        RET(launch_adat(h, h->pdir, E_CHEB, false, 1, h->q));
+        RET(precond_gemvs(h, h->r, h->z, GH_CHEB_B, 1));
+      } else {
+        RET(launch_adat(h, h->pdir, E_PCG_A, false, 1, h->q));
+        RET(precond_gemvs(h, h->r, h->z, GH_PCG_B, 1));
+      }
+    }
+    // FP64 true residual r = p - M dy, ||f|| = sqrt(r^T Q^{-1} r)
+    RET(launch_adat(h, h->dy, E_TRUE_RES, true, 2, nullptr));
+    RET(precond_gemvs(h, h->r, h->z, inner == LP_INNER_CHEBYSHEV ? GH_CHEB_REFRESH : GH_REFRESH, 2));
+    RET(sync_read(h));
+    if (h->opt.profile) ev_flush(h);
+    if (h->hsc->inner_done == 2) break;
+    if (h->hsc->inner_iters >= h->opt.t_max) {
+      status = LP_WARN_INNER_MAXIT;
+      break;
+    }
+  }
+  *iters_out = total_iters + h->hsc->inner_iters;
+  return status;
+}
+
+// v = (XS)^{1/2} W (ADW)^T Q^{-1} (M dy - p); the last refresh left r = p - M dy
+// and z = Q^{-1} r, so (ADW)^+ (M dy - p) = -(ADW)^T z.
+int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k, int retry) {
+  if (!h->opt.v_correction) {
+    CK(cudaMemsetAsync(h->v, 0, sizeof(double) * h->npad, h->st));
+    return LP_OK;
+  }
+  CK(launch_adwt(h->adw, h->m, h->w, h->z, h->adwt_part, h->adwt_parts, h->uw, h->num_sms, h->st));
+  CK(launch_v_gather(h->n, xs_x, xs_s, h->uw, h->opt.seed, k, retry, h->s_blocks, h->w, -1.0, h->v,
+                     h->num_sms, h->st));
+  return LP_OK;
+}
+
+int copy_in(lp_handle* h, double* dst, const double* src, size_t count, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, sizeof(double) * count,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  return LP_OK;
+}
+
+int copy_out(lp_handle* h, double* dst, const double* src, size_t count, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, sizeof(double) * count,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+  return LP_OK;
+}
+
+int residual_pass(lp_handle* h, bool feasible) {
+  StreamArgs a = base_args(h);
+  a.feasible = feasible ? 1 : 0;
+  a.cv[0] = h->x;
+  a.cv[1] = h->s;
+  a.cv[2] = h->c;
+  a.cv_esz[0] = a.cv_esz[1] = a.cv_esz[2] = 8;
+  a.ncv = 3;
+  a.vin = h->y;
+  a.out_col[0] = h->rd;
+  a.out_col[1] = h->d2d;
+  a.out_colf = h->d2f;
+  a.red_partials = h->red_partials;
+  a.epilogue = E_RESID;
+  a.out_m0 = h->rp;
+  a.out_m1 = h->p;
+  a.bvec = h->b;
+  CK(launch_stream(h->dtype, true, M_RESID, a, h->plan, h->st));
+  return LP_OK;
+}
+
+int direction_pass(lp_handle* h, bool feasible) {
+  StreamArgs a = base_args(h);
+  a.feasible = feasible ? 1 : 0;
+  a.cv[0] = h->x;
+  a.cv[1] = h->s;
+  a.cv[2] = h->v;
+  a.cv[3] = h->rd;
+  a.cv_esz[0] = a.cv_esz[1] = a.cv_esz[2] = a.cv_esz[3] = 8;
+  a.ncv = feasible ? 3 : 4;
+  a.vin = h->dy;
+  a.out_col[0] = h->dx;
+  a.out_col[1] = h->ds;
+  a.red_partials = h->red_partials;
+  a.epilogue = E_DIR;
+  CK(launch_stream(h->dtype, true, M_DIR, a, h->plan, h->st));
+  return LP_OK;
+}
+
+int compute_mu(lp_handle* h) {
+  CK(launch_dot(h->n, h->x, h->s, 1.0 / (double)h->n, h->vpart, h->tickets + 3, &h->sc->mu,
+                h->num_sms, h->st));
+  return LP_OK;
+}
+
+void options_check(const lp_options* o, std::string* why) {
+  if (!(o->sigma > 0 && o->sigma < 1)) *why = "sigma must be in (0, 1)";
+  else if (!(o->gamma > 0 && o->gamma < 1)) *why = "gamma must be in (0, 1)";
+  else if (o->s < 1 || o->s > kMaxBlocks) *why = "s must be in [1, 16]";
+  else if (o->sketch != LP_SKETCH_COUNT) *why = "only the CountSketch sketch is built";
+  else if (o->inner != LP_INNER_CG && o->inner != LP_INNER_CHEBYSHEV) *why = "inner must be CG or Chebyshev";
+  else if (o->t_max < 1 || o->k_max < 0) *why = "t_max >= 1 and k_max >= 0 required";
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void lp_options_default(lp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->sigma = 0.5;
+  o->gamma = 0.999;
+  o->tol_cg = 1e-5;
+  o->inner_rule = LP_RULE_THEORY;
+  o->sketch = LP_SKETCH_COUNT;
+  o->s = 2;
+  o->inner = LP_INNER_CG;
+  o->refine_every = 8;
+  o->k_max = 200;
+  o->t_max = 500;
+  o->v_correction = 1;
+  o->cheb_lanczos = 10;
+  o->profile = 0;
+  o->w_factor = 4.0;
+  o->w = 0;
+  o->seed = 0;
+  o->stream = nullptr;
+}
+
+const char* lp_create_error(void) { return g_create_error.c_str(); }
+
+const char* lp_last_error(const lp_handle* h) { return h ? h->err.c_str() : ""; }
+
+int lp_destroy(lp_handle* h) {
+  if (!h) return LP_OK;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (auto& e : h->ev_pool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->hsc) cudaFreeHost(h->hsc);
+  if (h->hinfo) cudaFreeHost(h->hinfo);
+  if (h->hval) cudaFreeHost(h->hval);
+  if (h->hwork) free(h->hwork);
+  if (h->sol) cusolverDnDestroy(h->sol);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  delete h;
+  return LP_OK;
+}
+
+static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const double* c,
+                       int bc_on_device, const lp_options* opt) {
+  if (!A || !b || !c) return h->fail(LP_ERR_ARG, "A, b and c are required");
+  if (A->m < 1 || A->n < A->m) return h->fail(LP_ERR_ARG, "need 1 <= m <= n (m=%d n=%lld)", A->m, (long long)A->n);
+  if (A->fmt != LP_DENSE_COLMAJOR)
+    return h->fail(LP_ERR_UNSUPPORTED, "sparse (CSC) storage is not built in this version");
+  if (A->dtype < LP_F64 || A->dtype > LP_BF16) return h->fail(LP_ERR_ARG, "bad dtype");
+  if (!A->val || A->ld < A->m) return h->fail(LP_ERR_ARG, "dense A needs val and ld >= m");
+  lp_options_default(&h->opt);
+  if (opt) h->opt = *opt;
+  std::string why;
+  options_check(&h->opt, &why);
+  if (!why.empty()) return h->fail(LP_ERR_ARG, "%s", why.c_str());
+  CK(cudaGetDevice(&h->dev));
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
+  if (h->opt.stream) {
+    h->st = static_cast<cudaStream_t>(h->opt.stream);
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  h->m = A->m;
+  h->n = A->n;
+  h->dtype = A->dtype;
+  h->fmt = A->fmt;
+  h->esz = A->dtype == LP_F64 ? 8 : (A->dtype == LP_F32 ? 4 : 2);
+  const int vec = 16 / h->esz;
+  h->lda = (int)round_up_ll(h->m, vec);
+  h->npad = round_up_ll(h->n, 64);
+  h->s_blocks = h->opt.s;
+  long long w = h->opt.w > 0 ? h->opt.w : (long long)llround(h->opt.w_factor * h->m);
+  w = round_up_ll(std::max<long long>(w, h->s_blocks), h->s_blocks);
+  if (w < h->m) return h->fail(LP_ERR_ARG, "sketch width w=%lld < m=%d: A D W cannot have rank m", w, h->m);
+  if (w > (1 << 30)) return h->fail(LP_ERR_ARG, "sketch width too large");
+  h->w = (int)w;
+  // kernel shape limits
+  h->plan = make_stream_plan(h->m, h->n, h->lda, h->esz, h->num_sms, 4);
+  if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
+  if (h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0)
+    return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the fused product kernel", h->m);
+  if (h->lda / vec > 4 * kThreads)
+    return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the FP64 streaming kernel", h->m);
+  // device memory
+  const size_t n = (size_t)h->npad, m = (size_t)h->lda;
+  RET(h->alloc(reinterpret_cast<char**>(&h->A), (size_t)h->lda * h->n * h->esz));
+  CK(cudaMemcpy2DAsync(h->A, (size_t)h->lda * h->esz, A->val, (size_t)A->ld * h->esz,
+                       (size_t)h->m * h->esz, (size_t)h->n,
+                       A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  double** nvecs[] = {&h->c, &h->x, &h->y, &h->s, &h->rd, &h->d2d, &h->dx, &h->ds, &h->v,
+                      &h->nb0, &h->nb1, &h->nb2};
+  for (double** p : nvecs) RET(h->alloc(p, n));
+  RET(h->alloc(&h->d2f, n));
+  double** mvecs[] = {&h->b, &h->rp, &h->p, &h->dy, &h->r, &h->z, &h->pdir, &h->q, &h->wv,
+                      &h->mb0, &h->mb1};
+  for (double** p : mvecs) RET(h->alloc(p, m + 64));
+  RET(h->alloc(&h->coef, std::max<size_t>(2 * (size_t)h->opt.t_max, 2048) + 64));
+  CK(cudaMemcpyAsync(h->b, b, sizeof(double) * h->m,
+                     bc_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->c, c, sizeof(double) * h->n,
+                     bc_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  const size_t mw = (size_t)h->m * h->w;
+  RET(h->alloc(&h->adw, mw));
+  RET(h->alloc(&h->qr, mw));
+  RET(h->alloc(&h->tau, (size_t)h->m));
+  RET(h->alloc(&h->rinv_cm, (size_t)h->m * h->m));
+  RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
+  RET(h->alloc(&h->uw, (size_t)h->w));
+  RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
+  RET(h->alloc(&h->dinfo, 4));
+  RET(h->alloc(reinterpret_cast<char**>(&h->partials), (size_t)h->plan.grid * 2 * h->lda * 8));
+  RET(h->alloc(&h->red_partials, (size_t)h->plan.grid * 2 + 2));
+  RET(h->alloc(&h->tickets, 16));
+  RET(h->alloc(&h->vpart, (size_t)h->num_sms * 8 + 64));
+  RET(h->alloc(&h->sc, 1));
+  CK(cudaMallocHost(&h->hsc, sizeof(DevScalars)));
+  CK(cudaMallocHost(&h->hinfo, 4 * sizeof(int)));
+  CK(cudaMallocHost(&h->hval, sizeof(double)));
+  // cuSOLVER
+  if (cusolverDnCreate(&h->sol) != CUSOLVER_STATUS_SUCCESS)
+    return h->fail(LP_ERR_CUDA, "cusolverDnCreate failed");
+  CS(cusolverDnSetStream(h->sol, h->st));
+  CS(cusolverDnDgeqrf_bufferSize(h->sol, h->w, h->m, h->qr, h->w, &h->lwork_geqrf));
+  size_t dtr = 0, htr = 0;
+  CS(cusolverDnXtrtri_bufferSize(h->sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, h->m,
+                                 CUDA_R_64F, h->rinv_cm, h->m, &dtr, &htr));
+  h->dwork_bytes = std::max<size_t>((size_t)h->lwork_geqrf * sizeof(double), dtr) + 256;
+  RET(h->alloc(reinterpret_cast<char**>(&h->dwork), h->dwork_bytes));
+  h->hwork_bytes = std::max<size_t>(htr, 8);
+  h->hwork = malloc(h->hwork_bytes);
+  if (!h->hwork) return h->fail(LP_ERR_OOM, "host workspace");
+  // norms of b and c for the stopping test
+  CK(launch_dot(h->m, h->b, h->b, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[0], h->num_sms, h->st));
+  CK(launch_dot(h->n, h->c, h->c, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[1], h->num_sms, h->st));
+  RET(sync_read(h));
+  h->bnorm = sqrt(h->hsc->pad[0]);
+  h->cnorm = sqrt(h->hsc->pad[1]);
+  if (!std::isfinite(h->bnorm) || !std::isfinite(h->cnorm))
+    return h->fail(LP_ERR_ARG, "b or c contains NaN/Inf");
+  return LP_OK;
+}
+
+int lp_create(lp_handle** out, const lp_matrix* A, const double* b, const double* c,
+              int32_t bc_on_device, const lp_options* opt) {
+  if (!out) return LP_ERR_ARG;
+  *out = nullptr;
+  lp_handle* h = new lp_handle();
+  const int rc = create_impl(h, A, b, c, bc_on_device, opt);
+  if (rc != LP_OK) {
+    g_create_error = h->err;
+    lp_destroy(h);
+    return rc;
+  }
+  g_create_error.clear();
+  *out = h;
+  return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel-level entry points
+// ---------------------------------------------------------------------------
+int lp_adat(lp_handle* h, const double* d2, const double* v, double* u, int32_t precision) {
+  if (!h || !d2 || !v || !u) return LP_ERR_ARG;
+  h->err.clear();
+  CK(cudaMemcpyAsync(h->d2d, d2, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+  CK(launch_to_f32(h->n, h->d2d, h->d2f, 0, h->num_sms, h->st));
+  CK(cudaMemcpyAsync(h->mb0, v, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
+  RET(launch_adat(h, h->mb0, E_PLAIN, precision != 0, 0, h->mb1));
+  CK(cudaMemcpyAsync(u, h->mb1, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
+  RET(sync_read(h));
+  if (h->opt.profile) ev_flush(h);
+  return LP_OK;
+}
+
+int lp_residual_rhs(lp_handle* h, const double* x, const double* y, const double* s, int32_t mode,
+                    double* r_p, double* r_d, double* p, double* out5) {
+  if (!h || !x || !y || !s) return LP_ERR_ARG;
+  h->err.clear();
+  RET(copy_in(h, h->x, x, h->n, 1));
+  RET(copy_in(h, h->s, s, h->n, 1));
+  RET(copy_in(h, h->y, y, h->m, 1));
+  RET(compute_mu(h));
+  RET(residual_pass(h, mode == LP_FEASIBLE));
+  if (r_p) RET(copy_out(h, r_p, h->rp, h->m, 1));
+  if (r_d) RET(copy_out(h, r_d, h->rd, h->n, 1));
+  if (p) RET(copy_out(h, p, h->p, h->m, 1));
+  RET(sync_read(h));
+  if (out5) {
+    out5[0] = h->hsc->mu;
+    out5[1] = h->hsc->cx;
+    out5[2] = h->hsc->by;
+    out5[3] = sqrt(h->hsc->rp2);
+    out5[4] = sqrt(h->hsc->rd2);
+  }
+  return LP_OK;
+}
+
+int lp_sketch(lp_handle* h, const double* D, uint64_t seed, int64_t k, int32_t retry, double* adw,
+              int64_t* w_out) {
+  if (!h || !D || !adw || retry < 0 || retry >= kMaxRetry || k < 0) return LP_ERR_ARG;
+  h->err.clear();
+  RET(copy_in(h, h->nb0, D, h->n, 1));
+  CK(launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, h->nb0, 0, seed, k, retry, h->s_blocks,
+                        h->w, h->adw, h->num_sms, h->st));
+  CK(cudaMemcpyAsync(adw, h->adw, sizeof(double) * (size_t)h->m * h->w, cudaMemcpyDeviceToDevice, h->st));
+  RET(sync_read(h));
+  if (w_out) *w_out = h->w;
+  return LP_OK;
+}
+
+int lp_precond_apply(lp_handle* h, const double* adw, const double* r, double* z) {
+  if (!h || !adw || !r || !z) return LP_ERR_ARG;
+  h->err.clear();
+  CK(cudaMemcpyAsync(h->adw, adw, sizeof(double) * (size_t)h->m * h->w, cudaMemcpyDeviceToDevice, h->st));
+  RET(factor(h));
+  RET(copy_in(h, h->mb0, r, h->m, 1));
+  RET(precond_gemvs(h, h->mb0, h->mb1, GH_NONE, 0));
+  RET(copy_out(h, z, h->mb1, h->m, 1));
+  RET(sync_read(h));
+  return LP_OK;
+}
+
+int lp_directions(lp_handle* h, const double* x, const double* s, const double* rd, const double* dy,
+                  const double* v, double mu, int32_t mode, double* dx, double* ds) {
+  if (!h || !x || !s || !dy || !v || !dx || !ds) return LP_ERR_ARG;
+  const bool feasible = mode == LP_FEASIBLE;
+  if (!feasible && !rd) return LP_ERR_ARG;
+  h->err.clear();
+  RET(copy_in(h, h->x, x, h->n, 1));
+  RET(copy_in(h, h->s, s, h->n, 1));
+  RET(copy_in(h, h->v, v, h->n, 1));
+  if (!feasible) RET(copy_in(h, h->rd, rd, h->n, 1));
+  RET(copy_in(h, h->dy, dy, h->m, 1));
+  RET(set_scalar(h, &h->sc->mu, mu));
+  RET(direction_pass(h, feasible));
+  RET(copy_out(h, dx, h->dx, h->n, 1));
+  RET(copy_out(h, ds, h->ds, h->n, 1));
+  RET(sync_read(h));
+  return LP_OK;
+}
+
+int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double* dx, const double* ds,
+                    int32_t mode, double res_ratio, double mu0, double* out2) {
+  if (!h || !x || !s || !dx || !ds || !out2) return LP_ERR_ARG;
+  h->err.clear();
+  RET(copy_in(h, h->x, x, h->n, 1));
+  RET(copy_in(h, h->s, s, h->n, 1));
+  RET(copy_in(h, h->dx, dx, h->n, 1));
+  RET(copy_in(h, h->ds, ds, h->n, 1));
+  const double inv_n = 1.0 / (double)h->n;
+  CK(launch_dot(h->n, h->x, h->s, inv_n, h->vpart, h->tickets + 3, &h->sc->mu, h->num_sms, h->st));
+  CK(launch_dot(h->n, h->x, h->ds, inv_n, h->vpart, h->tickets + 3, &h->sc->pad[0], h->num_sms, h->st));
+  CK(launch_dot(h->n, h->s, h->dx, inv_n, h->vpart, h->tickets + 3, &h->sc->pad[1], h->num_sms, h->st));
+  CK(launch_dot(h->n, h->dx, h->ds, inv_n, h->vpart, h->tickets + 3, &h->sc->c2, h->num_sms, h->st));
+  RET(sync_read(h));
+  RET(set_scalar(h, &h->sc->c1, h->hsc->pad[0] + h->hsc->pad[1]));
+  CK(launch_step(h->n, h->x, h->s, h->dx, h->ds, h->opt.gamma, mode == LP_FEASIBLE, res_ratio, mu0,
+                 h->vpart, h->tickets + 4, h->sc, h->num_sms, h->st));
+  RET(sync_read(h));
+  out2[0] = h->hsc->alpha_max;
+  out2[1] = h->hsc->alpha_bar;
+  return LP_OK;
+}
+
+int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st) {
+  if (!h || !st) return LP_ERR_ARG;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return LP_ERR_CUDA;
+  ev_flush(h);
+  st->launches = h->k1_launches;
+  st->ms = h->k1_ms;
+  st->bytes_per_launch = (int64_t)h->m * h->n * h->esz + 4 * h->n + 2 * 8 * (int64_t)h->m;
+  st->all_launches = g_launches.load() - h->launch_base;
+  return LP_OK;
+}
+
+int lp_reset_kernel_stats(lp_handle* h) {
+  if (!h) return LP_ERR_ARG;
+  cudaStreamSynchronize(h->st);
+  ev_flush(h);
+  h->k1_launches = 0;
+  h->k1_ms = 0.0;
+  h->launch_base = g_launches.load();
+  return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// normal-equation solve (Algorithm 1 + eq. compv)
+// ---------------------------------------------------------------------------
+int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double* xs, int64_t k,
+                    double tol_f, int32_t io_on_device, double* dy, double* v, lp_nsolve_info* info) {
+  if (!h || !D || !p || !dy || k < 0) return LP_ERR_ARG;
+  h->err.clear();
+  RET(copy_in(h, h->nb0, D, h->n, io_on_device));
+  RET(copy_in(h, h->p, p, h->m, io_on_device));
+  CK(launch_square(h->n, h->nb0, h->d2d, h->num_sms, h->st));
+  CK(launch_to_f32(h->n, h->nb0, h->d2f, 1, h->num_sms, h->st));
+  int retry = 0;
+  RET(sketch_and_factor(h, h->nb0, 0, k, &retry));
+  int iters = 0;
+  const int status = inner_solve(h, tol_f, &iters);
+  if (status < 0) return status;
+  const double f_true = h->hsc->f_true, f0 = sqrt(std::max(h->hsc->rho0, 0.0));
+  double vnorm = 0.0;
+  if (xs && v) {
+    RET(copy_in(h, h->nb1, xs, h->n, io_on_device));
+    RET(correction(h, h->nb1, nullptr, k, retry));  // nb1 holds x o s
+    CK(launch_dot(h->n, h->v, h->v, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[2], h->num_sms, h->st));
+    RET(copy_out(h, v, h->v, h->n, io_on_device));
+  }
+  RET(copy_out(h, dy, h->dy, h->m, io_on_device));
+  RET(sync_read(h));
+  if (xs && v) vnorm = sqrt(h->hsc->pad[2]);
+  if (info) {
+    info->inner_iterations = iters;
+    info->retries = retry;
+    info->f_norm = f_true;
+    info->f0_norm = f0;
+    info->v_norm = vnorm;
+    info->lam_min = h->hsc->lam_min;
+    info->lam_max = h->hsc->lam_max;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// the IPM (Algorithm 2 / Algorithm 3)
+// ---------------------------------------------------------------------------
+int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const double* y0,
+             const double* s0, int32_t io_on_device, double* x, double* y, double* s,
+             lp_result* info) {
+  if (!h || !(tol > 0)) return LP_ERR_ARG;
+  if (mode != LP_FEASIBLE && mode != LP_INFEASIBLE) return LP_ERR_ARG;
+  h->err.clear();
+  const auto t_start = std::chrono::steady_clock::now();
+  const bool feasible = mode == LP_FEASIBLE;
+  lp_result res;
+  std::memset(&res, 0, sizeof res);
+  const long long n = h->n;
+  const int m = h->m;
+  // start point
+  if (x0) RET(copy_in(h, h->x, x0, n, io_on_device));
+  else CK(launch_fill(n, h->x, 1.0, h->num_sms, h->st));
+  if (s0) RET(copy_in(h, h->s, s0, n, io_on_device));
+  else CK(launch_fill(n, h->s, 1.0, h->num_sms, h->st));
+  if (y0) RET(copy_in(h, h->y, y0, m, io_on_device));
+  else CK(cudaMemsetAsync(h->y, 0, sizeof(double) * m, h->st));
+  if (feasible && (!x0 || !y0 || !s0))
+    return h->fail(LP_ERR_NOT_FEASIBLE, "feasible mode needs x0, y0, s0");
+  CK(cudaMemsetAsync(&h->sc->err, 0, sizeof(int), h->st));
+  RET(compute_mu(h));
+  CK(launch_min_prod(n, h->x, h->s, h->vpart, h->tickets + 5, &h->sc->pad[3], h->num_sms, h->st));
+  RET(sync_read(h));
+  const double mu0 = h->hsc->mu;
+  if (!(mu0 > 0) || !(h->hsc->pad[3] > 0)) return h->fail(LP_ERR_ARG, "start needs x0 > 0 and s0 > 0");
+  if (feasible && h->hsc->pad[3] < (1.0 - h->opt.gamma) * mu0 * (1.0 - 1e-9))
+    return h->fail(LP_ERR_NOT_FEASIBLE, "start is not in N(gamma)");
+  double r0 = 0.0;
+  int status = LP_STATUS_MAX_ITER;
+  double ms_res = 0, ms_sk = 0, ms_fac = 0, ms_in = 0, ms_cor = 0, ms_step = 0;
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  auto ms_since = [](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+  };
+  for (int k = 0; k <= h->opt.k_max; ++k) {
+    auto t0 = now();
+    // ---- step 3: residuals, mu, right-hand side, d^2 ----
+    RET(residual_pass(h, feasible));
+    RET(sync_read(h));
+    ms_res += ms_since(t0);
+    const DevScalars& S = *h->hsc;
+    const double rp = sqrt(S.rp2), rd = sqrt(S.rd2);
+    const double gap = fabs(S.cx - S.by) / (1.0 + fabs(S.cx));
+    const double rp_rel = rp / (1.0 + h->bnorm), rd_rel = rd / (1.0 + h->cnorm);
+    if (k == 0) {
+      r0 = sqrt(S.rp2 + S.rd2);
+      if (feasible && (rp_rel > 1e-8 || rd_rel > 1e-8))
+        return h->fail(LP_ERR_NOT_FEASIBLE, "start is not feasible (rel residuals %.2e, %.2e)", rp_rel, rd_rel);
+    } else if (S.alpha_bar <= 0.0) {
+      status = LP_STATUS_STALLED;
+      res.outer_iterations = k;
+      break;
+    }
+    res.outer_iterations = k;
+    res.primal_obj = S.cx;
+    res.dual_obj = S.by;
+    res.rel_gap = gap;
+    res.rp_rel = rp_rel;
+    res.rd_rel = rd_rel;
+    res.mu = S.mu;
+    if (!std::isfinite(gap) || !std::isfinite(rp) || !std::isfinite(rd))
+      return h->fail(LP_ERR_NUMERICAL, "non-finite residuals at iteration %d", k);
+    if (gap <= tol && rp_rel <= tol && rd_rel <= tol) {
+      status = LP_OK;
+      break;
+    }
+    if (k == h->opt.k_max) break;
+    const double mu = S.mu;
+    const double res_ratio = feasible ? 0.0 : sqrt(S.rp2 + S.rd2) / r0;
+    // ---- step 2 + Algorithm 1 steps 1-2: sketch and factor ----
+    t0 = now();
+    int retry = 0;
+    RET(sketch_and_factor(h, h->d2d, 1, k, &retry));
+    res.sketch_retries += retry;
+    ms_fac += ms_since(t0);
+    // ---- Algorithm 1 step 3: inner solve to the Lemma 4.4 level ----
+    t0 = now();
+    const double tol_f = h->opt.inner_rule == LP_RULE_THEORY
+                             ? h->opt.gamma * h->opt.sigma * sqrt(mu) / (4.0 * sqrt(3.0 * (double)n))
+                             : 0.0;
+    int iters = 0;
+    const int ist = inner_solve(h, tol_f, &iters);
+    if (ist < 0) return ist;
+    res.inner_total += iters;
+    res.inner_max = std::max(res.inner_max, iters);
+    ms_in += ms_since(t0);
+    // ---- step 5: correction v, directions ----
+    t0 = now();
+    RET(correction(h, h->x, h->s, k, retry));
+    RET(direction_pass(h, feasible));
+    CK(cudaStreamSynchronize(h->st));
+    ms_cor += ms_since(t0);
+    // ---- steps 6-8: step lengths and update ----
+    t0 = now();
+    CK(launch_step(n, h->x, h->s, h->dx, h->ds, h->opt.gamma, feasible ? 1 : 0, res_ratio, mu0,
+                   h->vpart, h->tickets + 4, h->sc, h->num_sms, h->st));
+    CK(launch_update(n, m, h->x, h->s, h->y, h->dx, h->ds, h->dy, h->sc, h->vpart, h->tickets + 6,
+                     h->num_sms, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    ms_step += ms_since(t0);
+  }
+  if (x) RET(copy_out(h, x, h->x, n, io_on_device));
+  if (y) RET(copy_out(h, y, h->y, m, io_on_device));
+  if (s) RET(copy_out(h, s, h->s, n, io_on_device));
+  CK(cudaStreamSynchronize(h->st));
+  res.status = status;
+  res.ms_total = ms_since(t_start);
+  res.ms_residual = ms_res;
+  res.ms_sketch = ms_sk;
+  res.ms_factor = ms_fac;
+  res.ms_inner = ms_in;
+  res.ms_correction = ms_cor;
+  res.ms_step = ms_step;
+  if (info) *info = res;
+  return status;
+}
+
+}  // extern "C"

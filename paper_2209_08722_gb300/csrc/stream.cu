@@ -1,0 +1,572 @@
+// Column-streaming kernels over a dense column-major A: the fused
+// A diag(d2) A^T v product and the FP64 passes of the outer iteration.
+// See stream.cuh for the design.
+#include <algorithm>
+#include <cstdio>
+
+#include "internal.h"
+#include "stream.cuh"
+
+namespace lpk {
+
+// ---------------------------------------------------------------------------
+// tile producer (one thread)
+// ---------------------------------------------------------------------------
+template <typename TA>
+__device__ __forceinline__ void issue_tile(const StreamArgs& a, const SmemLayout& L, char* smem,
+                                           uint64_t* bars, int stage, int tile) {
+  const long long j0 = (long long)tile * a.nb;
+  const int ncols = (int)min((long long)a.nb, a.n - j0);
+  char* st = smem + (size_t)stage * L.stage_bytes;
+  const uint32_t abytes = (uint32_t)ncols * (uint32_t)a.lda * (uint32_t)sizeof(TA);
+  uint32_t total = abytes;
+  uint32_t cvb[kMaxColVecs];
+#pragma unroll
+  for (int q = 0; q < kMaxColVecs; ++q) {
+    cvb[q] = (q < a.ncv) ? (uint32_t)align_up_i(ncols * a.cv_esz[q], 16) : 0u;
+    total += cvb[q];
+  }
+  mbar_arrive_expect_tx(&bars[stage], total);
+  bulk_g2s(st, static_cast<const char*>(a.A) + (size_t)j0 * a.lda * sizeof(TA), abytes,
+           &bars[stage]);
+#pragma unroll
+  for (int q = 0; q < kMaxColVecs; ++q)
+    if (q < a.ncv)
+      bulk_g2s(st + L.cv_off[q], static_cast<const char*>(a.cv[q]) + (size_t)j0 * a.cv_esz[q],
+               cvb[q], &bars[stage]);
+}
+
+__device__ __forceinline__ double cv_at(const char* stage, const SmemLayout& L, const StreamArgs& a,
+                                        int q, int jj) {
+  const char* p = stage + L.cv_off[q];
+  return a.cv_esz[q] == 8 ? reinterpret_cast<const double*>(p)[jj]
+                          : (double)reinterpret_cast<const float*>(p)[jj];
+}
+
+// Waits (bounded) on every stage still holding an issued copy; used when aborting.
+template <typename TA>
+__device__ void drain_stages(uint64_t* bars, int consumed, int my_tiles, int S, int* err) {
+  for (int i = consumed; i < my_tiles && i < consumed + S; ++i)
+    mbar_wait(&bars[i % S], (i / S) & 1, err);
+}
+
+// ---------------------------------------------------------------------------
+// epilogue run by the last CTA: FP64 reduction of the per-CTA partials in a
+// fixed order, then the mode-specific vector work on m-vectors.
+// ---------------------------------------------------------------------------
+template <typename TC>
+__device__ void stream_epilogue(const StreamArgs& a, int nacc, double* red) {
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const TC* part = static_cast<const TC*>(a.partials);
+  const size_t pstride = (size_t)2 * a.lda;
+  if (*a.err != ERR_NONE) return;
+  auto acc_row = [&](int k, int i) -> double {
+    double s = 0.0;
+    for (int b = 0; b < G; ++b) s += (double)__ldcg(part + (size_t)b * pstride + (size_t)k * a.lda + i);
+    return s;
+  };
+  // column reductions (two FP64 sums over columns)
+  double cr0 = 0.0, cr1 = 0.0;
+  if (a.red_partials) {
+    if (tid == 0) {
+      for (int b = 0; b < G; ++b) {
+        cr0 += __ldcg(a.red_partials + 2 * b);
+        cr1 += __ldcg(a.red_partials + 2 * b + 1);
+      }
+    }
+  }
+  switch (a.epilogue) {
+    case E_PLAIN:
+      for (int i = tid; i < a.m; i += blockDim.x) {
+        a.out_m0[i] = acc_row(0, i);
+        if (nacc > 1) a.out_m1[i] = acc_row(1, i);
+      }
+      break;
+    case E_TRUE_RES:
+      for (int i = tid; i < a.m; i += blockDim.x) a.pcg_r[i] = a.bvec[i] - acc_row(0, i);
+      break;
+    case E_PCG_A: {
+      double pq = 0.0;
+      for (int i = tid; i < a.m; i += blockDim.x) {
+        const double q = acc_row(0, i);
+        a.out_m0[i] = q;
+        pq += a.pcg_p[i] * q;
+      }
+      pq = block_sum(pq, red);
+      const double alpha = a.sc->rho / pq;
+      if (!(pq > 0.0) || !isfinite(alpha)) {
+        if (tid == 0) atomicExch(a.err, ERR_NUMERICAL);
+        return;
+      }
+      for (int i = tid; i < a.m; i += blockDim.x) {
+        a.pcg_dy[i] += alpha * a.pcg_p[i];
+        a.pcg_r[i] -= alpha * a.out_m0[i];
+      }
+      if (tid == 0) {
+        a.sc->pq = pq;
+        const int it = a.sc->inner_iters;
+        if (a.coef && it < 1024) a.coef[2 * it] = alpha;
+      }
+      break;
+    }
+    case E_CHEB:
+      for (int i = tid; i < a.m; i += blockDim.x) a.pcg_r[i] -= acc_row(0, i);
+      break;
+    case E_RESID: {
+      double rp2 = 0.0, by = 0.0;
+      for (int i = tid; i < a.m; i += blockDim.x) {
+        const double rp = acc_row(0, i) - a.bvec[i];
+        const double ap = acc_row(1, i);
+        a.out_m0[i] = rp;
+        a.out_m1[i] = a.feasible ? ap : ap - rp;
+        rp2 += rp * rp;
+        by += a.bvec[i] * a.vin[i];
+      }
+      rp2 = block_sum(rp2, red);
+      by = block_sum(by, red);
+      if (tid == 0) {
+        a.sc->rp2 = rp2;
+        a.sc->by = by;
+        a.sc->rd2 = cr0;
+        a.sc->cx = cr1;
+      }
+      break;
+    }
+    case E_DIR:
+      if (tid == 0) {
+        a.sc->c1 = cr0 / (double)a.n;
+        a.sc->c2 = cr1 / (double)a.n;
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_stream: phase 1 per-column scalars (warp per column), phase 2 row-owned
+// accumulation.  MAXRPT = row vectors per thread (compile-time maximum).
+// ---------------------------------------------------------------------------
+template <typename TA, typename TC, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
+  constexpr int VEC = VecOf<TA>::N;
+  constexpr int MAXRPT = 4;
+  constexpr int NACC = (MODE == M_RESID) ? 2 : ((MODE == M_ADAT || MODE == M_AX) ? 1 : 0);
+  constexpr bool DOT = (MODE != M_AX);
+  extern __shared__ __align__(128) char smem[];
+  const SmemLayout L = make_layout(a.lda, (int)sizeof(TA), a.nb, a.stages, (int)sizeof(TC));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  TC* v_s = reinterpret_cast<TC*>(smem + L.v_off);
+  double* t_s = reinterpret_cast<double*>(smem + L.t_off);
+  double* red = reinterpret_cast<double*>(smem + L.red_off);
+  __shared__ int s_flag;
+  if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int RV = a.lda / VEC;
+  const int S = a.stages;
+  const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const double sigma_mu = a.sigma * a.sc->mu;
+
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  if (DOT)
+    for (int i = tid; i < a.lda; i += blockDim.x) v_s[i] = (i < a.m) ? (TC)a.vin[i] : (TC)0;
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 0; i < my_tiles && i < S; ++i)
+      issue_tile<TA>(a, L, smem, bars, i, (int)blockIdx.x + i * (int)gridDim.x);
+
+  // phase-2 thread mapping
+  int groups, rpt, g, rv0;
+  if (RV >= kThreads) {
+    groups = 1;
+    rpt = (RV + kThreads - 1) / kThreads;
+    g = 0;
+    rv0 = tid;
+  } else {
+    groups = kThreads / RV;
+    rpt = 1;
+    g = tid / RV;
+    rv0 = tid % RV;
+  }
+  const bool p2_active = (g < groups);
+
+  TC acc0[MAXRPT][VEC], acc1[MAXRPT][VEC];
+#pragma unroll
+  for (int q = 0; q < MAXRPT; ++q)
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc0[q][e] = acc1[q][e] = (TC)0;
+  double cred0 = 0.0, cred1 = 0.0;  // column reductions (lane 0 of each warp)
+
+  int consumed = 0;
+  bool aborted = false;
+  for (int i = 0; i < my_tiles; ++i) {
+    const int st = i % S;
+    const bool ok = mbar_wait(&bars[st], (uint32_t)((i / S) & 1), a.err);
+    if (!__syncthreads_and(ok)) {
+      aborted = true;
+      break;
+    }
+    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+    const long long j0 = (long long)tile * a.nb;
+    const int ncols = (int)min((long long)a.nb, a.n - j0);
+    const char* stage = smem + (size_t)st * L.stage_bytes;
+    const TA* At = reinterpret_cast<const TA*>(stage);
+
+    // ---- phase 1: per-column scalars ----
+    for (int jj = warp; jj < ncols; jj += kWarps) {
+      double dot = 0.0;
+      if (DOT) {
+        TC d = (TC)0;
+        const TA* col = At + (size_t)jj * a.lda;
+        for (int rv = lane; rv < RV; rv += 32) {
+          TC av[VEC];
+          ld16<TC>(col + rv * VEC, av);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) d += av[e] * v_s[rv * VEC + e];
+        }
+        dot = (double)warp_sum(d);
+      }
+      if (lane == 0) {
+        const long long j = j0 + jj;
+        double t0 = 0.0, t1 = 0.0;
+        if (MODE == M_ADAT) {
+          t0 = cv_at(stage, L, a, 0, jj) * dot;
+        } else if (MODE == M_AX) {
+          t0 = cv_at(stage, L, a, 0, jj);
+        } else if (MODE == M_ATY) {
+          a.out_col[0][j] = dot;
+        } else if (MODE == M_RESID) {
+          const double x = cv_at(stage, L, a, 0, jj);
+          const double s = cv_at(stage, L, a, 1, jj);
+          const double c = cv_at(stage, L, a, 2, jj);
+          const double rd = dot + s - c;
+          const double d2 = x / s;
+          a.out_col[0][j] = rd;
+          a.out_col[1][j] = d2;
+          a.out_colf[j] = (float)d2;
+          t0 = x;
+          t1 = a.feasible ? (x - sigma_mu / s) : (x - sigma_mu / s - d2 * rd);
+          cred0 += rd * rd;
+          cred1 += c * x;
+        } else if (MODE == M_DIR) {
+          const double x = cv_at(stage, L, a, 0, jj);
+          const double s = cv_at(stage, L, a, 1, jj);
+          const double v = cv_at(stage, L, a, 2, jj);
+          const double rd = a.feasible ? 0.0 : cv_at(stage, L, a, 3, jj);
+          const double ds = -rd - dot;
+          const double dx = -x + sigma_mu / s - (x / s) * ds - v / s;
+          a.out_col[0][j] = dx;
+          a.out_col[1][j] = ds;
+          cred0 += x * ds + s * dx;
+          cred1 += dx * ds;
+        }
+        t_s[jj] = t0;
+        t_s[a.nb + jj] = t1;
+      }
+    }
+    if (NACC > 0) {
+      __syncthreads();
+      // ---- phase 2: acc += A_tile * t ----
+      if (p2_active) {
+        for (int jj = g; jj < ncols; jj += groups) {
+          const TC t0 = (TC)t_s[jj];
+          const TC t1 = (TC)t_s[a.nb + jj];
+          const TA* col = At + (size_t)jj * a.lda;
+#pragma unroll
+          for (int q = 0; q < MAXRPT; ++q) {
+            const int rv = rv0 + q * kThreads;
+            if (q < rpt && rv < RV) {
+              TC av[VEC];
+              ld16<TC>(col + rv * VEC, av);
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) {
+                acc0[q][e] += av[e] * t0;
+                if (NACC > 1) acc1[q][e] += av[e] * t1;
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    consumed = i + 1;
+    if (tid == 0 && i + S < my_tiles) {
+      fence_proxy_async_smem();
+      issue_tile<TA>(a, L, smem, bars, st, (int)blockIdx.x + (i + S) * (int)gridDim.x);
+    }
+  }
+  if (aborted && tid == 0) drain_stages<TA>(bars, consumed, my_tiles, S, a.err);
+  __syncthreads();
+
+  // ---- per-CTA partials ----
+  if (NACC > 0) {
+    // combine the column groups through shared memory (stage area is free now)
+    TC* buf = reinterpret_cast<TC*>(smem);
+    for (int k = 0; k < NACC; ++k) {
+      if (p2_active) {
+#pragma unroll
+        for (int q = 0; q < MAXRPT; ++q) {
+          const int rv = rv0 + q * kThreads;
+          if (q < rpt && rv < RV)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+              buf[(size_t)g * a.lda + rv * VEC + e] = (k == 0) ? acc0[q][e] : acc1[q][e];
+        }
+      }
+      __syncthreads();
+      TC* part = static_cast<TC*>(a.partials) + (size_t)blockIdx.x * 2 * a.lda + (size_t)k * a.lda;
+      for (int i = tid; i < a.lda; i += blockDim.x) {
+        TC s = (TC)0;
+        for (int gg = 0; gg < groups; ++gg) s += buf[(size_t)gg * a.lda + i];
+        part[i] = aborted ? (TC)0 : s;
+      }
+      __syncthreads();
+    }
+  }
+  if (a.red_partials) {
+    const double r0 = block_sum(lane == 0 ? cred0 : 0.0, red);
+    const double r1 = block_sum(lane == 0 ? cred1 : 0.0, red);
+    if (tid == 0) {
+      a.red_partials[2 * blockIdx.x] = r0;
+      a.red_partials[2 * blockIdx.x + 1] = r1;
+    }
+  }
+  if (a.epilogue == E_NONE) return;
+  if (last_block_ticket(a.ticket, &s_flag)) stream_epilogue<TC>(a, NACC, red);
+}
+
+// ---------------------------------------------------------------------------
+// k_adat_fused: u = A diag(d2) A^T v in FP32, warp-per-column, one smem read
+// per element, per-lane accumulators over all rows.  VPL = 16-byte vectors
+// per lane per column (lda <= 32 * VPL * VEC).
+// ---------------------------------------------------------------------------
+template <typename TA, int VPL>
+__global__ void __launch_bounds__(kThreads, 1) k_adat_fused(const StreamArgs a) {
+  constexpr int VEC = VecOf<TA>::N;
+  constexpr bool VREG = (VPL * VEC <= 32);
+  extern __shared__ __align__(128) char smem[];
+  const SmemLayout L = make_layout(a.lda, (int)sizeof(TA), a.nb, a.stages, 4);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  float* v_s = reinterpret_cast<float*>(smem + L.v_off);
+  double* red = reinterpret_cast<double*>(smem + L.red_off);
+  __shared__ int s_flag;
+  if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int RV = a.lda / VEC;
+  const int S = a.stages;
+  const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < a.lda; i += blockDim.x) v_s[i] = (i < a.m) ? (float)a.vin[i] : 0.0f;
+  __syncthreads();
+  if (tid == 0)
+    for (int i = 0; i < my_tiles && i < S; ++i)
+      issue_tile<TA>(a, L, smem, bars, i, (int)blockIdx.x + i * (int)gridDim.x);
+
+  float vr[VREG ? VPL : 1][VREG ? VEC : 1];
+  if (VREG) {
+#pragma unroll
+    for (int c = 0; c < VPL; ++c)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const int rv = c * 32 + lane;
+        vr[c][e] = (rv < RV) ? v_s[rv * VEC + e] : 0.0f;
+      }
+  }
+  float acc[VPL][VEC];
+#pragma unroll
+  for (int c = 0; c < VPL; ++c)
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[c][e] = 0.0f;
+
+  int consumed = 0;
+  bool aborted = false;
+  for (int i = 0; i < my_tiles; ++i) {
+    const int st = i % S;
+    const bool ok = mbar_wait(&bars[st], (uint32_t)((i / S) & 1), a.err);
+    if (!__syncthreads_and(ok)) {
+      aborted = true;
+      break;
+    }
+    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+    const long long j0 = (long long)tile * a.nb;
+    const int ncols = (int)min((long long)a.nb, a.n - j0);
+    const char* stage = smem + (size_t)st * L.stage_bytes;
+    const TA* At = reinterpret_cast<const TA*>(stage);
+    const float* d2t = reinterpret_cast<const float*>(stage + L.cv_off[0]);
+    for (int jj = warp; jj < ncols; jj += kWarps) {
+      const TA* col = At + (size_t)jj * a.lda;
+      float av[VPL][VEC];
+      float d = 0.0f;
+#pragma unroll
+      for (int c = 0; c < VPL; ++c) {
+        const int rv = c * 32 + lane;
+        if (rv < RV) {
+          ld16<float>(col + rv * VEC, av[c]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) av[c][e] = 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const float vv = VREG ? vr[VREG ? c : 0][VREG ? e : 0]
+                                : ((rv < RV) ? v_s[rv * VEC + e] : 0.0f);
+          d = fmaf(av[c][e], vv, d);
+        }
+      }
+      d = warp_sum(d);
+      const float t = d2t[jj] * d;
+#pragma unroll
+      for (int c = 0; c < VPL; ++c)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[c][e] = fmaf(av[c][e], t, acc[c][e]);
+    }
+    __syncthreads();
+    consumed = i + 1;
+    if (tid == 0 && i + S < my_tiles) {
+      fence_proxy_async_smem();
+      issue_tile<TA>(a, L, smem, bars, st, (int)blockIdx.x + (i + S) * (int)gridDim.x);
+    }
+  }
+  if (aborted && tid == 0) drain_stages<TA>(bars, consumed, my_tiles, S, a.err);
+  __syncthreads();
+  // cross-warp reduction through shared memory: buf[warp][lda]
+  float* buf = reinterpret_cast<float*>(smem);
+#pragma unroll
+  for (int c = 0; c < VPL; ++c) {
+    const int rv = c * 32 + lane;
+    if (rv < RV)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) buf[(size_t)warp * a.lda + rv * VEC + e] = acc[c][e];
+  }
+  __syncthreads();
+  float* part = static_cast<float*>(a.partials) + (size_t)blockIdx.x * 2 * a.lda;
+  for (int r = tid; r < a.lda; r += blockDim.x) {
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += buf[(size_t)w * a.lda + r];
+    part[r] = aborted ? 0.0f : s;
+  }
+  if (a.epilogue == E_NONE) return;
+  if (last_block_ticket(a.ticket, &s_flag)) stream_epilogue<float>(a, 1, red);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename TA, typename TC, int MODE>
+cudaError_t launch_stream_t(const StreamArgs& a, int grid, int smem, cudaStream_t st) {
+  auto k = k_stream<TA, TC, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename TA, int VPL>
+cudaError_t launch_fused_t(const StreamArgs& a, int grid, int smem, cudaStream_t st) {
+  auto k = k_adat_fused<TA, VPL>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename TA, typename TC>
+cudaError_t dispatch_mode(int mode, const StreamArgs& a, int grid, int smem, cudaStream_t st) {
+  switch (mode) {
+    case M_ADAT: return launch_stream_t<TA, TC, M_ADAT>(a, grid, smem, st);
+    case M_AX: return launch_stream_t<TA, TC, M_AX>(a, grid, smem, st);
+    case M_RESID: return launch_stream_t<TA, TC, M_RESID>(a, grid, smem, st);
+    case M_DIR: return launch_stream_t<TA, TC, M_DIR>(a, grid, smem, st);
+    case M_ATY: return launch_stream_t<TA, TC, M_ATY>(a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename TA>
+cudaError_t dispatch_fused(int vpl, const StreamArgs& a, int grid, int smem, cudaStream_t st) {
+  switch (vpl) {
+    case 1: return launch_fused_t<TA, 1>(a, grid, smem, st);
+    case 2: return launch_fused_t<TA, 2>(a, grid, smem, st);
+    case 4: return launch_fused_t<TA, 4>(a, grid, smem, st);
+    case 8: return launch_fused_t<TA, 8>(a, grid, smem, st);
+    case 16: return launch_fused_t<TA, 16>(a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+StreamPlan make_stream_plan(int m, long long n, int lda, int esz, int num_sms, int tc_bytes) {
+  StreamPlan p;
+  const int col_bytes = lda * esz;
+  const int target = 32 * 1024;
+  int nb = target / col_bytes;
+  nb = std::max(4, std::min(64, nb));
+  nb = nb / 4 * 4;
+  p.nb = nb;
+  p.ntiles = (int)((n + nb - 1) / nb);
+  const int budget = 220 * 1024;
+  int stages = kMaxStages;
+  for (; stages >= 2; --stages) {
+    SmemLayout L = make_layout(lda, esz, nb, stages, 8);
+    // the end-of-kernel reduction buffer reuses the stage area
+    const int redbuf = std::max(kWarps * lda * 4, kThreads / std::max(1, lda / (16 / esz)) * lda * 8);
+    if (L.total <= budget && stages * L.stage_bytes >= redbuf) break;
+  }
+  if (stages < 2) stages = 2;
+  p.stages = stages;
+  p.grid = std::max(1, std::min(p.ntiles, num_sms));
+  p.smem = make_layout(lda, esz, nb, stages, tc_bytes).total;
+  p.smem8 = make_layout(lda, esz, nb, stages, 8).total;
+  p.ok = (p.smem8 <= 227 * 1024);
+  (void)m;
+  return p;
+}
+
+int fused_vpl(int lda, int esz) {
+  const int vec = 16 / esz;
+  const int rv = lda / vec;
+  const int need = (rv + 31) / 32;
+  for (int v : {1, 2, 4, 8, 16})
+    if (need <= v) return v;
+  return 0;
+}
+
+cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
+                          const StreamPlan& p, cudaStream_t st) {
+  const int smem = fp64_acc ? p.smem8 : p.smem;
+  if (dtype == 0) return dispatch_mode<double, double>(mode, a, p.grid, p.smem8, st);
+  if (dtype == 1) {
+    if (fp64_acc) return dispatch_mode<float, double>(mode, a, p.grid, smem, st);
+    return dispatch_mode<float, float>(mode, a, p.grid, smem, st);
+  }
+  if (fp64_acc) return dispatch_mode<bf16raw, double>(mode, a, p.grid, smem, st);
+  return dispatch_mode<bf16raw, float>(mode, a, p.grid, smem, st);
+}
+
+cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p,
+                              cudaStream_t st) {
+  const int esz = dtype == 1 ? 4 : 2;
+  const int vpl = fused_vpl(a.lda, esz);
+  if (vpl == 0) return cudaErrorInvalidValue;
+  if (dtype == 1) return dispatch_fused<float>(vpl, a, p.grid, p.smem, st);
+  if (dtype == 2) return dispatch_fused<bf16raw>(vpl, a, p.grid, p.smem, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lpk

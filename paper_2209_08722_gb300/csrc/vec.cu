@@ -1,0 +1,488 @@
+// m-vector and n-vector kernels of the outer iteration:
+//   - the preconditioner application z = Q^{-1} r = R^{-1} R^{-T} r through two
+//     triangular GEMVs with the explicit inverse of the R factor of (ADW)^T,
+//     with the CG / Chebyshev scalar updates fused into the second GEMV's
+//     last-CTA epilogue (Algorithm 1 step 3);
+//   - (ADW)^T g for the correction vector (eq. compv);
+//   - the step lengths of Algorithms 2-3 (first exit from N(gamma), closed-form
+//     minimiser of the gap) and the iterate update;
+//   - small utilities (dot products, FP32 copies, R extraction, rank check).
+// All arithmetic here is FP64.
+#include "internal.h"
+
+namespace lpk {
+
+std::atomic<long long> g_launches{0};
+
+// ---------------------------------------------------------------------------
+// triangular GEMV with a fused epilogue
+// ---------------------------------------------------------------------------
+enum GemvEpi : int {
+  G_NONE = 0,
+  G_PCG_INIT = 1,   // rho = r.z, p = z, f_rec = sqrt(rho)
+  G_PCG_B = 2,      // rho' = r.z; beta = rho'/rho; p = z + beta p; done if sqrt(rho') <= 0.5 tol
+  G_REFRESH = 3,    // true residual: rho' = r.z; converged if sqrt(rho') <= tol; else residual replacement
+  G_CHEB_INIT = 4,  // rho = r.z; dir = z / theta; cheb_rho = 1/s1
+  G_CHEB_B = 5,     // cheb recurrence on dir; f_rec = sqrt(r.z)
+  G_CHEB_REFRESH = 6,  // true residual: converged if sqrt(r.z) <= tol; direction untouched
+};
+
+struct GemvArgs {
+  const double* M;   // m x m, row i contiguous (ld = m)
+  int m;
+  int lower;         // 1: row i uses columns [0, i]; 0: columns [i, m)
+  const double* x;
+  double* y;
+  int epi;
+  int skip_level;    // return immediately if sc->inner_done >= skip_level (0: never)
+  double* r;
+  double* p;         // CG search direction / Chebyshev update direction
+  double* dy;
+  DevScalars* sc;
+  unsigned* ticket;
+  int* err;
+  int t_max;
+  double* coef;      // G_PCG_B: beta of CG step j stored at coef[2j+1]
+};
+
+__global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
+  __shared__ int s_flag;
+  __shared__ double red[32];
+  if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
+  const int lane = threadIdx.x & 31;
+  const int warps_per_block = blockDim.x >> 5;
+  const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+  const int nw = gridDim.x * warps_per_block;
+  for (int i = gw; i < a.m; i += nw) {
+    const int lo = a.lower ? 0 : i;
+    const int hi = a.lower ? i + 1 : a.m;
+    const double* row = a.M + (size_t)i * a.m;
+    double acc = 0.0;
+    for (int j = lo + lane; j < hi; j += 32) acc = fma(row[j], a.x[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) a.y[i] = acc;
+  }
+  if (a.epi == G_NONE) return;
+  if (!last_block_ticket(a.ticket, &s_flag)) return;
+  // ---- epilogue (one CTA): m-vector CG / Chebyshev updates ----
+  DevScalars* sc = a.sc;
+  const double* z = a.y;
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < a.m; i += blockDim.x) rz += a.r[i] * __ldcg(z + i);
+  rz = block_sum(rz, red);
+  if (!isfinite(rz)) {
+    if (threadIdx.x == 0) atomicExch(a.err, ERR_NUMERICAL);
+    return;
+  }
+  const double f = sqrt(fmax(rz, 0.0));
+  if (a.epi == G_PCG_INIT) {
+    for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i);
+    if (threadIdx.x == 0) {
+      sc->rho = rz;
+      sc->rho0 = rz;
+      sc->f_rec = f;
+      sc->f_true = f;
+      sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
+    }
+  } else if (a.epi == G_PCG_B || a.epi == G_REFRESH) {
+    const double beta = rz / sc->rho;
+    bool stop;
+    if (a.epi == G_PCG_B) {
+      stop = f <= 0.5 * sc->tol_f;
+    } else {
+      stop = f <= sc->tol_f;
+    }
+    if (!stop)
+      for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) + beta * a.p[i];
+    if (threadIdx.x == 0) {
+      sc->rho = rz;
+      if (a.epi == G_PCG_B) {
+        if (a.coef && sc->inner_iters < 1024) a.coef[2 * sc->inner_iters + 1] = beta;
+        sc->f_rec = f;
+        sc->inner_iters += 1;
+        if (stop) sc->inner_done = 1;
+        else if (sc->inner_iters >= a.t_max) sc->inner_done = 1;
+      } else {
+        sc->f_true = f;
+        sc->inner_done = stop ? 2 : 0;
+      }
+    }
+  } else if (a.epi == G_CHEB_INIT) {
+    const double theta = 0.5 * (sc->lam_max + sc->lam_min);
+    const double delta = 0.5 * (sc->lam_max - sc->lam_min);
+    for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) / theta;
+    if (threadIdx.x == 0) {
+      sc->cheb_rho = delta / theta;
+      sc->rho0 = rz;
+      sc->f_rec = f;
+      sc->f_true = f;
+      sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
+    }
+  } else if (a.epi == G_CHEB_REFRESH) {
+    if (threadIdx.x == 0) {
+      sc->f_true = f;
+      sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
+    }
+  } else if (a.epi == G_CHEB_B) {
+    const double theta = 0.5 * (sc->lam_max + sc->lam_min);
+    const double delta = 0.5 * (sc->lam_max - sc->lam_min);
+    const double s1 = theta / delta;
+    const double rho = sc->cheb_rho;
+    const double rho_new = 1.0 / (2.0 * s1 - rho);
+    for (int i = threadIdx.x; i < a.m; i += blockDim.x)
+      a.p[i] = rho_new * rho * a.p[i] + (2.0 * rho_new / delta) * __ldcg(z + i);
+    if (threadIdx.x == 0) {
+      sc->cheb_rho = rho_new;
+      sc->f_rec = f;
+      sc->inner_iters += 1;
+      if (f <= 0.5 * sc->tol_f || sc->inner_iters >= a.t_max) sc->inner_done = 1;
+    }
+  }
+}
+
+cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
+                            int skip_level, double* r, double* p, double* dy, DevScalars* sc,
+                            unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
+                            cudaStream_t st) {
+  GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef};
+  const int warps = 8;
+  int grid = (m + warps - 1) / warps;
+  grid = std::max(1, std::min(grid, num_sms * 4));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_gemv_tri<<<grid, warps * 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Chebyshev / residual helpers on m-vectors (one CTA)
+__global__ void k_cheb_pre(int m, double* dy, const double* dir, DevScalars* sc) {
+  if (sc->inner_done >= 1) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) dy[i] += dir[i];
+}
+
+cudaError_t launch_cheb_pre(int m, double* dy, const double* dir, DevScalars* sc, cudaStream_t st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_cheb_pre<<<1, 256, 0, st>>>(m, dy, dir, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// u = (ADW)^T g, adw row-major m x w: partial sums over row slices, then a sum
+// ---------------------------------------------------------------------------
+__global__ void k_adwt_partial(const double* __restrict__ adw, int m, int w,
+                               const double* __restrict__ g, int rows_per, double* part) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = blockIdx.y * rows_per;
+  const int i1 = min(m, i0 + rows_per);
+  if (k >= w) return;
+  double acc = 0.0;
+  for (int i = i0; i < i1; ++i) acc = fma(adw[(size_t)i * w + k], g[i], acc);
+  part[(size_t)blockIdx.y * w + k] = acc;
+}
+
+__global__ void k_sum_rows(const double* __restrict__ part, int nparts, int w, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= w) return;
+  double acc = 0.0;
+  for (int q = 0; q < nparts; ++q) acc += part[(size_t)q * w + k];
+  out[k] = acc;
+}
+
+cudaError_t launch_adwt(const double* adw, int m, int w, const double* g, double* part, int max_parts,
+                        double* out, int num_sms, cudaStream_t st) {
+  const int bx = (w + 255) / 256;
+  int ny = std::max(1, std::min(max_parts, (num_sms * 2 + bx - 1) / bx));
+  ny = std::min(ny, m);
+  const int rows_per = (m + ny - 1) / ny;
+  ny = (m + rows_per - 1) / rows_per;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_adwt_partial<<<dim3(bx, ny), 256, 0, st>>>(adw, m, w, g, rows_per, part);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_sum_rows<<<bx, 256, 0, st>>>(part, ny, w, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// dot over n with a last-CTA finish: *out = scale * sum x_i y_i
+// ---------------------------------------------------------------------------
+__global__ void k_dot(long long n, const double* __restrict__ x, const double* __restrict__ y,
+                      double scale, double* part, unsigned* ticket, double* out) {
+  __shared__ double red[32];
+  __shared__ int s_flag;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (!last_block_ticket(ticket, &s_flag)) return;
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + b);
+    *out = scale * t;
+  }
+}
+
+cudaError_t launch_dot(long long n, const double* x, const double* y, double scale, double* part,
+                       unsigned* ticket, double* out, int num_sms, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 2));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_dot<<<grid, 256, 0, st>>>(n, x, y, scale, part, ticket, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// step lengths (Algorithm 2 steps 5-6, Algorithm 3 steps 6-7)
+// ---------------------------------------------------------------------------
+// First alpha > 0 where g(t) = qa t^2 + qb t + qc crosses from >= 0 to < 0;
+// +inf if it never does; 0 if g < 0 on all of (0, inf).
+__device__ __forceinline__ double first_exit(double qa, double qb, double qc) {
+  if (qa == 0.0) {
+    if (qb < 0.0) return fmax(-qc / qb, 0.0);
+    return INFINITY;
+  }
+  const double disc = qb * qb - 4.0 * qa * qc;
+  if (disc < 0.0) return qa < 0.0 ? 0.0 : INFINITY;
+  const double sq = sqrt(disc);
+  const double qq = -0.5 * (qb + (qb >= 0.0 ? sq : -sq));
+  double r1 = 0.0, r2 = 0.0;
+  if (qq != 0.0) {
+    r1 = qq / qa;
+    r2 = qc / qq;
+  }
+  const double lo = fmin(r1, r2), hi = fmax(r1, r2);
+  if (qa > 0.0) return lo > 0.0 ? lo : INFINITY;
+  return hi > 0.0 ? hi : 0.0;
+}
+
+struct StepArgs {
+  long long n;
+  const double *x, *s, *dx, *ds;
+  double gamma;
+  int feasible;
+  double res_ratio;  // ||r|| / ||r^0||
+  double mu0;
+  double* part;      // [grid][2]: min over elements of the N(gamma) exit and the positivity exit
+  unsigned* ticket;
+  DevScalars* sc;
+};
+
+__global__ void __launch_bounds__(256) k_step(const StepArgs a) {
+  __shared__ double red[32];
+  __shared__ int s_flag;
+  const double mu = a.sc->mu;
+  const double c1 = a.sc->c1, c2 = a.sc->c2;
+  const double g = 1.0 - a.gamma;
+  double ex = INFINITY, pos = INFINITY;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double x = a.x[i], s = a.s[i], dx = a.dx[i], ds = a.ds[i];
+    ex = fmin(ex, first_exit(dx * ds - g * c2, x * ds + s * dx - g * c1, x * s - g * mu));
+    if (dx < 0.0) pos = fmin(pos, -x / dx);
+    if (ds < 0.0) pos = fmin(pos, -s / ds);
+  }
+  ex = block_min(ex, red);
+  pos = block_min(pos, red);
+  if (threadIdx.x == 0) {
+    a.part[2 * blockIdx.x] = ex;
+    a.part[2 * blockIdx.x + 1] = pos;
+  }
+  if (!last_block_ticket(a.ticket, &s_flag)) return;
+  if (threadIdx.x != 0) return;
+  double e = INFINITY, p = INFINITY;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    e = fmin(e, __ldcg(a.part + 2 * b));
+    p = fmin(p, __ldcg(a.part + 2 * b + 1));
+  }
+  double alpha = fmin(1.0, e);
+  alpha = fmin(alpha, first_exit(c2, c1, mu));  // mu(alpha) > 0
+  if (!a.feasible)
+    alpha = fmin(alpha, first_exit(c2 / a.mu0, c1 / a.mu0 + a.res_ratio, mu / a.mu0 - a.res_ratio));
+  if (p <= alpha) alpha = p * (1.0 - 1e-12);
+  const double amax = fmax(alpha, 0.0);
+  double abar = amax;
+  if (c2 > 0.0) abar = fmin(fmax(-c1 / (2.0 * c2), 0.0), amax);
+  a.sc->alpha_max = amax;
+  a.sc->alpha_bar = abar;
+}
+
+cudaError_t launch_step(long long n, const double* x, const double* s, const double* dx,
+                        const double* ds, double gamma, int feasible, double res_ratio, double mu0,
+                        double* part, unsigned* ticket, DevScalars* sc, int num_sms,
+                        cudaStream_t st) {
+  StepArgs a{n, x, s, dx, ds, gamma, feasible, res_ratio, mu0, part, ticket, sc};
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 2));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_step<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// x += a dx, s += a ds (n), y += a dy (m); sc->mu = x^T s / n afterwards
+__global__ void k_update(long long n, int m, double* x, double* s, double* y, const double* dx,
+                         const double* ds, const double* dy, DevScalars* sc, double* part,
+                         unsigned* ticket) {
+  __shared__ double red[32];
+  __shared__ int s_flag;
+  const double al = sc->alpha_bar;
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long i = t0; i < n; i += stride) {
+    const double xi = x[i] + al * dx[i];
+    const double si = s[i] + al * ds[i];
+    x[i] = xi;
+    s[i] = si;
+    acc = fma(xi, si, acc);
+  }
+  for (long long i = t0; i < m; i += stride) y[i] += al * dy[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (!last_block_ticket(ticket, &s_flag)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + b);
+    sc->xs_next = t;
+    sc->mu = t / (double)n;
+  }
+}
+
+cudaError_t launch_update(long long n, int m, double* x, double* s, double* y, const double* dx,
+                          const double* ds, const double* dy, DevScalars* sc, double* part,
+                          unsigned* ticket, int num_sms, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 2));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_update<<<grid, 256, 0, st>>>(n, m, x, s, y, dx, ds, dy, sc, part, ticket);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// utilities
+// ---------------------------------------------------------------------------
+__global__ void k_fill(long long n, double* x, double v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+cudaError_t launch_fill(long long n, double* x, double v, int num_sms, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 4));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_fill<<<grid, 256, 0, st>>>(n, x, v);
+  return cudaGetLastError();
+}
+
+// *out = min_i x_i y_i
+__global__ void k_min_prod(long long n, const double* __restrict__ x, const double* __restrict__ y,
+                           double* part, unsigned* ticket, double* out) {
+  __shared__ double red[32];
+  __shared__ int s_flag;
+  double mn = INFINITY;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    mn = fmin(mn, x[i] * y[i]);
+  mn = block_min(mn, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = mn;
+  if (!last_block_ticket(ticket, &s_flag)) return;
+  if (threadIdx.x == 0) {
+    double t = INFINITY;
+    for (int b = 0; b < (int)gridDim.x; ++b) t = fmin(t, __ldcg(part + b));
+    *out = t;
+  }
+}
+
+cudaError_t launch_min_prod(long long n, const double* x, const double* y, double* part,
+                            unsigned* ticket, double* out, int num_sms, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 2));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_min_prod<<<grid, 256, 0, st>>>(n, x, y, part, ticket, out);
+  return cudaGetLastError();
+}
+__global__ void k_to_f32(long long n, const double* __restrict__ x, float* __restrict__ y, int square) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    y[i] = (float)(square ? v * v : v);
+  }
+}
+
+__global__ void k_square(long long n, const double* __restrict__ x, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * x[i];
+}
+
+cudaError_t launch_to_f32(long long n, const double* x, float* y, int square, int num_sms,
+                          cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 4));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_to_f32<<<grid, 256, 0, st>>>(n, x, y, square);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_square(long long n, const double* x, double* y, int num_sms, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, num_sms * 4));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_square<<<grid, 256, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+
+// R (upper m x m of a column-major w x m array, ld = w) -> dst column-major m x m,
+// zero below the diagonal; diagonal extremes into sc for the rank check.
+__global__ void k_extract_r(const double* __restrict__ qr, int w, int m, double* __restrict__ dst) {
+  const long long total = (long long)m * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / m), i = (int)(e % m);  // column j, row i
+    dst[e] = (i <= j) ? qr[(size_t)j * w + i] : 0.0;
+  }
+}
+
+__global__ void k_diag_range(const double* __restrict__ r, int m, DevScalars* sc, double rank_tol) {
+  __shared__ double red[32];
+  double mn = INFINITY, mx = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double d = fabs(r[(size_t)i * m + i]);
+    mn = fmin(mn, d);
+    mx = fmax(mx, d);
+  }
+  mn = block_min(mn, red);
+  mx = -block_min(-mx, red);
+  if (threadIdx.x == 0) {
+    sc->diag_min = mn;
+    sc->diag_max = mx;
+    sc->rank_bad = (!(mn > rank_tol * mx) || !isfinite(mx)) ? 1 : 0;
+  }
+}
+
+__global__ void k_transpose(const double* __restrict__ src, int m, double* __restrict__ dst) {
+  __shared__ double tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = by + k, c = bx + threadIdx.x;
+    if (r < m && c < m) tile[k][threadIdx.x] = src[(size_t)r * m + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = bx + k, c = by + threadIdx.x;
+    if (r < m && c < m) dst[(size_t)r * m + c] = tile[threadIdx.x][k];
+  }
+}
+
+cudaError_t launch_factor_utils(int which, const double* a, int w, int m, double* b, DevScalars* sc,
+                                double rank_tol, int num_sms, cudaStream_t st) {
+  if (which == 0) {
+    const long long total = (long long)m * m;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, num_sms * 4));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    k_extract_r<<<grid, 256, 0, st>>>(a, w, m, b);
+  } else if (which == 1) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    k_diag_range<<<1, 256, 0, st>>>(a, m, sc, rank_tol);
+  } else {
+    dim3 grid((m + 31) / 32, (m + 31) / 32);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(a, m, b);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lpk

@@ -1,0 +1,263 @@
+"""Thin Python front-end of the CUDA library (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only turns
+NumPy arrays / torch CUDA tensors into pointers and sizes and reports errors.
+
+Entry points mirror the C ABI names (include/lp_sketch_ipm.h):
+  LPSolver(...)            -> lp_create / lp_destroy
+  .solve(...)              -> lp_solve           (Algorithm 2 or 3)
+  .normal_solve(...)       -> lp_normal_solve    (Algorithm 1 + eq. compv)
+  .adat / .residual_rhs / .sketch / .precond_apply / .directions / .step_lengths
+                           -> the kernel-level entry points (device tensors)
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _native as nat
+
+_DTYPES = {"f64": nat.LP_F64, "f32": nat.LP_F32, "bf16": nat.LP_BF16}
+_NP_DT = {"f64": np.float64, "f32": np.float32, "bf16": np.uint16}
+
+
+class LPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{nat.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _on_device(x) -> bool:
+    return _is_torch(x) and x.is_cuda
+
+
+def _check_dev_f64(*xs):
+    for x in xs:
+        if x is None:
+            continue
+        if not (_is_torch(x) and x.is_cuda and str(x.dtype) == "torch.float64" and x.is_contiguous()):
+            raise TypeError("kernel-level calls take contiguous float64 CUDA tensors")
+
+
+class LPSolver:
+    """An LP  min c^T x, A x = b, x >= 0  resident on the GPU.
+
+    ``A`` is column-major: an (n, m) C-contiguous array whose row j is column
+    a_j (NumPy on the host, or a torch CUDA tensor), in the storage dtype
+    ``dtype`` ("f64", "f32" or "bf16"; bf16 given as uint16 bit patterns or a
+    torch.bfloat16 tensor).
+    """
+
+    def __init__(self, A, b, c, m: int, n: int, dtype: str = "f32", stream=None, **options):
+        self._lib = nat.load()
+        self._h = ctypes.c_void_p()
+        self.m, self.n, self.dtype = int(m), int(n), dtype
+        opt = nat.LpOptions()
+        self._lib.lp_options_default(ctypes.byref(opt))
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, v)
+        if stream is not None:
+            opt.stream = stream
+        self.options = opt
+        if _is_torch(A):
+            if tuple(A.shape) != (self.n, self.m):
+                raise ValueError("A must have shape (n, m) (column-major)")
+        else:
+            A = np.ascontiguousarray(A, dtype=_NP_DT[dtype])
+            if A.shape != (self.n, self.m):
+                raise ValueError("A must have shape (n, m) (column-major)")
+        mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype],
+                           val=_ptr(A), ld=self.m, ptr=None, idx=None, nnz=0,
+                           on_device=1 if _on_device(A) else 0)
+        bc_dev = _on_device(b)
+        if not bc_dev:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            c = np.ascontiguousarray(c, dtype=np.float64)
+        self._keep = (A, b, c)
+        rc = self._lib.lp_create(ctypes.byref(self._h), ctypes.byref(mat), _ptr(b), _ptr(c),
+                                 1 if bc_dev else 0, ctypes.byref(opt))
+        self._keep = None
+        if rc != nat.LP_OK:
+            raise LPError(rc, self._lib.lp_create_error().decode())
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if self._h:
+            self._lib.lp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int, allow=(nat.LP_OK,)):
+        if rc < 0 or rc not in allow and rc < 0:
+            raise LPError(rc, self._lib.lp_last_error(self._h).decode())
+        return rc
+
+    # -- solver ------------------------------------------------------------
+    def solve(self, tol: float = 1e-8, mode: str = "infeasible", x0=None, y0=None, s0=None,
+              out=None):
+        """lp_solve.  Host (NumPy) or device (torch CUDA) start/outputs."""
+        m, n = self.m, self.n
+        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+        dev = any(_on_device(v) for v in (x0, y0, s0) if v is not None) or (
+            out is not None and _on_device(out[0]))
+        if out is None:
+            if dev:
+                import torch
+                out = (torch.empty(n, dtype=torch.float64, device="cuda"),
+                       torch.empty(m, dtype=torch.float64, device="cuda"),
+                       torch.empty(n, dtype=torch.float64, device="cuda"))
+            else:
+                out = (np.empty(n), np.empty(m), np.empty(n))
+        if not dev:
+            x0, y0, s0 = [None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+                          for v in (x0, y0, s0)]
+        res = nat.LpResult()
+        rc = self._lib.lp_solve(self._h, float(tol), mode_c, _ptr(x0), _ptr(y0), _ptr(s0),
+                                1 if dev else 0, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
+                                ctypes.byref(res))
+        if rc < 0:
+            raise LPError(rc, self._lib.lp_last_error(self._h).decode())
+        info = res.as_dict()
+        info["status_name"] = nat.STATUS_NAMES.get(rc, str(rc))
+        return out[0], out[1], out[2], info
+
+    def normal_solve(self, D, p, xs=None, k: int = 0, tol_f: float = 0.0, want_v: bool = True):
+        """lp_normal_solve: returns (dy, v or None, info dict)."""
+        dev = _on_device(D)
+        if dev:
+            import torch
+            dy = torch.empty(self.m, dtype=torch.float64, device="cuda")
+            v = torch.empty(self.n, dtype=torch.float64, device="cuda") if (want_v and xs is not None) else None
+        else:
+            D = np.ascontiguousarray(D, dtype=np.float64)
+            p = np.ascontiguousarray(p, dtype=np.float64)
+            xs = None if xs is None else np.ascontiguousarray(xs, dtype=np.float64)
+            dy = np.empty(self.m)
+            v = np.empty(self.n) if (want_v and xs is not None) else None
+        info = nat.LpNsolveInfo()
+        rc = self._lib.lp_normal_solve(self._h, _ptr(D), _ptr(p), _ptr(xs), int(k), float(tol_f),
+                                       1 if dev else 0, _ptr(dy), _ptr(v), ctypes.byref(info))
+        if rc < 0:
+            raise LPError(rc, self._lib.lp_last_error(self._h).decode())
+        d = info.as_dict()
+        d["status"] = rc
+        return dy, v, d
+
+    # -- kernel-level (device tensors) ---------------------------------------
+    def adat(self, d2, v, precision: int = 0):
+        import torch
+        _check_dev_f64(d2, v)
+        u = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lp_adat(self._h, _ptr(d2), _ptr(v), _ptr(u), int(precision)))
+        return u
+
+    def residual_rhs(self, x, y, s, mode: str = "infeasible"):
+        import torch
+        _check_dev_f64(x, y, s)
+        rp = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        rd = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        p = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        out5 = (ctypes.c_double * 5)()
+        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+        self._check(self._lib.lp_residual_rhs(self._h, _ptr(x), _ptr(y), _ptr(s), mode_c,
+                                              _ptr(rp), _ptr(rd), _ptr(p), out5))
+        keys = ("mu", "cx", "by", "rp_norm", "rd_norm")
+        return rp, rd, p, dict(zip(keys, list(out5)))
+
+    def sketch(self, D, seed: int, k: int, retry: int = 0):
+        import torch
+        _check_dev_f64(D)
+        w = self.sketch_width
+        adw = torch.empty(self.m * w, dtype=torch.float64, device="cuda")
+        wout = ctypes.c_int64()
+        self._check(self._lib.lp_sketch(self._h, _ptr(D), int(seed), int(k), int(retry), _ptr(adw),
+                                        ctypes.byref(wout)))
+        return adw.view(self.m, w)
+
+    @property
+    def sketch_width(self) -> int:
+        s = self.options.s
+        w = self.options.w if self.options.w > 0 else int(round(self.options.w_factor * self.m))
+        w = max(w, s)
+        return (w + s - 1) // s * s
+
+    def precond_apply(self, adw, r):
+        import torch
+        _check_dev_f64(adw, r)
+        z = torch.empty(self.m, dtype=torch.float64, device="cuda")
+        self._check(self._lib.lp_precond_apply(self._h, _ptr(adw), _ptr(r), _ptr(z)))
+        return z
+
+    def directions(self, x, s, rd, dy, v, mu: float, mode: str = "infeasible"):
+        import torch
+        _check_dev_f64(x, s, rd, dy, v)
+        dx = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        ds = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+        self._check(self._lib.lp_directions(self._h, _ptr(x), _ptr(s), _ptr(rd), _ptr(dy), _ptr(v),
+                                            float(mu), mode_c, _ptr(dx), _ptr(ds)))
+        return dx, ds
+
+    def step_lengths(self, x, s, dx, ds, mode: str = "infeasible", res_ratio: float = 0.0,
+                     mu0: float = 1.0):
+        _check_dev_f64(x, s, dx, ds)
+        out2 = (ctypes.c_double * 2)()
+        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+        self._check(self._lib.lp_step_lengths(self._h, _ptr(x), _ptr(s), _ptr(dx), _ptr(ds), mode_c,
+                                              float(res_ratio), float(mu0), out2))
+        return out2[0], out2[1]
+
+    def kernel_stats(self) -> dict:
+        st = nat.LpKernelStats()
+        self._check(self._lib.lp_get_kernel_stats(self._h, ctypes.byref(st)))
+        return {"launches": st.launches, "ms": st.ms, "bytes_per_launch": st.bytes_per_launch,
+                "all_launches": st.all_launches}
+
+    def reset_kernel_stats(self):
+        self._check(self._lib.lp_reset_kernel_stats(self._h))
+
+
+def from_planted(lp, device: bool = False, **options) -> LPSolver:
+    """An LPSolver for an ``lpgen.PlantedLP`` (dense)."""
+    A = lp.storage_array()
+    b, c = lp.b, lp.c
+    if device:
+        import torch
+        A = torch.from_numpy(A).cuda()
+        b = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        c = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+    return LPSolver(A, b, c, lp.m, lp.n, dtype=lp.storage, **options)

@@ -1,0 +1,109 @@
+"""End-to-end parity of lp_solve (Algorithms 2 and 3 on the GPU) with the CPU
+oracle and the planted closed-form optimum.
+
+Bar (BASELINE the benchmark spec): relative duality gap <= 1e-8 and FP64 objective
+agreement <= 1e-7 with the oracle and with c^T x*.
+"""
+
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import ipm
+from tests.gpu_helpers import dev, host, solver_for, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(lp, x, y, s, info, ref=None):
+    assert info["status"] == 0, info
+    assert info["rel_gap"] <= 1e-8
+    obj = float(lp.c @ x)
+    assert abs(obj - lp.objective) <= 1e-7 * (1 + abs(lp.objective)), (obj, lp.objective)
+    assert abs(obj - float(lp.b @ y)) <= 1e-8 * (1 + abs(obj)) * 1.01
+    assert (x > 0).all() and (s > 0).all()
+    A = lp.dense()
+    assert np.linalg.norm(A @ x - lp.b) <= 1e-8 * (1 + np.linalg.norm(lp.b)) * 1.01
+    assert np.linalg.norm(A.T @ y + s - lp.c) <= 1e-8 * (1 + np.linalg.norm(lp.c)) * 1.01
+    if ref is not None:
+        assert abs(obj - float(lp.c @ ref.x)) <= 1e-7 * (1 + abs(obj))
+
+
+@pytest.mark.parametrize("name,div", [("c2", 8), ("c2", 32), ("c4", 16), ("c1", 1)])
+def test_infeasible_solve_small_configs(name, div):
+    lp = lpgen.config_small(name, div)
+    cfg = lpgen.CONFIGS[name]
+    ref = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(mode="infeasible"))
+    with solver_for(lp, s=cfg["s"], w_factor=cfg["w_factor"]) as S:
+        x, y, s, info = S.solve(tol=1e-8, mode="infeasible")
+    _check(lp, x, y, s, info, ref)
+    # outer iterations close to the exact-solve oracle (inexact solve + v)
+    assert abs(info["outer_iterations"] - ref.iterations) <= max(3, 0.2 * ref.iterations)
+
+
+def test_feasible_solve_c1_fp64():
+    lp = lpgen.planted_dense(64, 4096, seed=0, storage="f64")
+    x0, y0, s0 = lpgen.feasible_start(lp, gamma=0.999)
+    ref = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(mode="feasible"), x0, y0, s0)
+    with solver_for(lp, s=2) as S:
+        x, y, s, info = S.solve(tol=1e-8, mode="feasible", x0=x0, y0=y0, s0=s0)
+    _check(lp, x, y, s, info, ref)
+
+
+def test_solve_with_device_buffers_and_chebyshev():
+    torch = torch_cuda()
+    lp = lpgen.planted_dense(96, 12000, seed=3, storage="f32", col_scale_log10=(-1, 1))
+    with solver_for(lp, s=2, inner=1) as S:
+        x, y, s, info = S.solve(tol=1e-8, x0=dev(torch, np.ones(lp.n)),
+                                y0=dev(torch, np.zeros(lp.m)), s0=dev(torch, np.ones(lp.n)))
+    _check(lp, host(x), host(y), host(s), info)
+
+
+def test_solve_without_v_correction_converges():
+    lp = lpgen.planted_dense(64, 8000, seed=5, storage="f32")
+    with solver_for(lp, s=2, v_correction=0) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+    _check(lp, x, y, s, info)
+
+
+def test_solve_is_deterministic():
+    lp = lpgen.planted_dense(128, 10000, seed=6, storage="f32", col_scale_log10=(-1, 1))
+    with solver_for(lp, s=2) as S:
+        x1, y1, _, i1 = S.solve(tol=1e-8)
+        x2, y2, _, i2 = S.solve(tol=1e-8)
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+    assert i1["inner_total"] == i2["inner_total"]
+
+
+def test_feasible_mode_rejects_infeasible_start():
+    from paper_2209_08722_gb300.solver import LPError
+    lp = lpgen.planted_dense(16, 500, seed=7, storage="f64")
+    with solver_for(lp) as S:
+        with pytest.raises(LPError) as ei:
+            S.solve(mode="feasible", x0=np.ones(lp.n), y0=np.zeros(lp.m), s0=np.ones(lp.n))
+        assert "NOT_FEASIBLE" in str(ei.value)
+
+
+def test_create_rejects_bad_arguments():
+    from paper_2209_08722_gb300 import LPSolver
+    from paper_2209_08722_gb300.solver import LPError
+    lp = lpgen.planted_dense(16, 500, seed=8, storage="f32")
+    with pytest.raises(LPError) as ei:   # sketch narrower than m
+        LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", w=8)
+    assert "LP_ERR_ARG" in str(ei.value)
+    b = lp.b.copy()
+    b[0] = np.nan
+    with pytest.raises(LPError):
+        LPSolver(lp.storage_array(), b, lp.c, lp.m, lp.n, dtype="f32")
+    with pytest.raises(LPError):          # m > n
+        LPSolver(np.ones((4, 8), dtype=np.float32), np.ones(8), np.ones(4), 8, 4, dtype="f32")
+
+
+def test_tiny_lp_matches_vertex_enumeration():
+    from oracle import vertex
+    lp = lpgen.planted_dense(3, 10, seed=5, storage="f64")
+    best, _, _ = vertex.enumerate_vertices(lp.A, lp.b, lp.c)
+    with solver_for(lp, s=1) as S:
+        x, y, s, info = S.solve(tol=1e-9)
+    assert info["status"] == 0
+    assert abs(lp.c @ x - best) <= 1e-7 * (1 + abs(best))
