@@ -166,6 +166,36 @@ def run_reference(args):
     return 0
 
 
+def run_kernel(args):
+    """Microbenchmark of the fused FP32 product on the bench's A (used for the
+    ncu captures in profiles/): W warm-up launches, then K timed launches."""
+    import torch
+    from paper_2209_08722_gb300 import LPSolver
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lp = make_lp(0)
+    stream = torch.cuda.current_stream()
+    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=S_BLOCKS,
+                      w_factor=W_FACTOR, profile=1, stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    d2 = torch.from_numpy(np.exp(rng.uniform(-5, 5, lp.n))).cuda()
+    v = torch.from_numpy(rng.standard_normal(lp.m)).cuda()
+    for _ in range(args.warmup):
+        solver.adat(d2, v, 0)
+    solver.reset_kernel_stats()
+    for _ in range(args.steps):
+        solver.adat(d2, v, 0)
+    st = solver.kernel_stats()
+    peak, kind = load_peaks()
+    ms = st["ms"] / max(1, st["launches"])
+    gbs = st["bytes_per_launch"] / (ms * 1e-3) / 1e9
+    print(json.dumps({"kernel": "k_adat_fused", "workload": WORKLOAD, "launches": st["launches"],
+                      "mean_ms": ms, "bytes_per_launch": st["bytes_per_launch"],
+                      "achieved_gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
+                      "frac": gbs / peak}), flush=True)
+    solver.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,9 +203,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", choices=["adat"], default=None,
+                    help="time only the hot product kernel (lp_adat, FP32) on the same A")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel:
+        return run_kernel(args)
 
     import torch
     from paper_2209_08722_gb300 import LPSolver

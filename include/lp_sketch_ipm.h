@@ -131,6 +131,19 @@ typedef struct {
                                    (library-wide counter; cuSOLVER's kernels not included) */
 } lp_kernel_stats;
 
+/* One record per outer iteration of the last lp_solve (iteration log). */
+typedef struct {
+    int32_t k;                  /* outer iteration index */
+    int32_t inner_iterations;   /* inner iterations of this outer iteration */
+    int32_t retries;            /* sketch redraws */
+    int32_t inner_status;       /* LP_OK or LP_WARN_INNER_MAXIT */
+    double mu, rel_gap, rp_rel, rd_rel;   /* at the start of the iteration */
+    double f_norm;              /* final ||f|| of the inner solve */
+    double f0_norm;             /* ||Q^{-1/2} p|| */
+    double tol_f;               /* the inner target used */
+    double alpha_max, alpha_bar;
+} lp_iter_record;
+
 /* ---- lifecycle -------------------------------------------------------------- */
 
 /* Fills `opt` with the defaults listed above. */
@@ -217,6 +230,11 @@ int lp_directions(lp_handle* h, const double* x, const double* s, const double* 
 int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double* dx,
                     const double* ds, int32_t mode, double res_ratio, double mu0,
                     double* out2);
+
+/* Copies up to `max_records` records of the last lp_solve into `recs` (host
+ * memory, nullable when max_records == 0); returns the number of records
+ * available (>= 0) or LP_ERR_ARG. */
+int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
 
 /* Statistics of the hot product kernel (requires opt.profile = 1). */
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);

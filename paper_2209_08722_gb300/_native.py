@@ -76,6 +76,17 @@ class LpNsolveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class LpIterRecord(ctypes.Structure):
+    _fields_ = [("k", c_int32), ("inner_iterations", c_int32), ("retries", c_int32),
+                ("inner_status", c_int32), ("mu", c_double), ("rel_gap", c_double),
+                ("rp_rel", c_double), ("rd_rel", c_double), ("f_norm", c_double),
+                ("f0_norm", c_double), ("tol_f", c_double), ("alpha_max", c_double),
+                ("alpha_bar", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LpKernelStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("ms", c_double), ("bytes_per_launch", c_int64),
                 ("all_launches", c_int64)]
@@ -98,6 +109,7 @@ SIGNATURES = {
     "lp_precond_apply": (c_int32, [P, P, P, P]),
     "lp_directions": (c_int32, [P, P, P, P, P, P, c_double, c_int32, P, P]),
     "lp_step_lengths": (c_int32, [P, P, P, P, P, c_int32, c_double, c_double, P]),
+    "lp_get_history": (c_int32, [P, POINTER(LpIterRecord), c_int32]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }

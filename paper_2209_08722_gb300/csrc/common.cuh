@@ -15,7 +15,11 @@ namespace lpk {
 
 constexpr int kThreads = 256;          // threads per CTA for the streaming kernels
 constexpr int kWarps = kThreads / 32;
+constexpr int kConsumerWarps = 16;     // consumer warps of the fused product kernel
+constexpr int kFusedThreads = (kConsumerWarps + 1) * 32;  // + one producer warp
 constexpr int kMaxStages = 4;
+constexpr int kGroup = 8;              // CTAs per first-level reduction group
+constexpr int kMaxGroups = 64;         // group tickets; slot kMaxGroups is the global one
 constexpr int kMaxColVecs = 4;         // per-column input vectors staged with a tile
 constexpr long long kSpinCycles = 1LL << 31;
 
@@ -86,6 +90,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {

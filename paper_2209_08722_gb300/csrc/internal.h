@@ -40,7 +40,9 @@ enum GemvEpiHost : int {
 cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
-                            cudaStream_t st);
+                            cudaStream_t st, const double* y_add = nullptr);
+cudaError_t launch_gemv_rows(const double* M, int rows, int cols, const double* x, const double* y0,
+                             double alpha, double beta, double* y, int num_sms, cudaStream_t st);
 cudaError_t launch_cheb_pre(int m, double* dy, const double* dir, DevScalars* sc, cudaStream_t st);
 cudaError_t launch_adwt(const double* adw, int m, int w, const double* g, double* part, int max_parts,
                         double* out, int num_sms, cudaStream_t st);

@@ -15,6 +15,7 @@
 //            and the update (step 8).
 // The host synchronises a few times per outer iteration (stopping test, rank
 // check, inner-solve chunks); everything else is stream-ordered.
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <chrono>
@@ -52,6 +53,10 @@ struct lp_handle {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   cusolverDnHandle_t sol = nullptr;
+  cublasHandle_t blas = nullptr;
+  int lwork_potrf = 0;
+  long long qr_fallbacks = 0;
+  long long cheb_fallbacks = 0;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -72,6 +77,8 @@ struct lp_handle {
   int* dinfo = nullptr;
   // scratch
   void* partials = nullptr;
+  double* gpart = nullptr;
+  unsigned* gtickets = nullptr;
   double* red_partials = nullptr;
   unsigned* tickets = nullptr;
   double* vpart = nullptr;
@@ -87,6 +94,7 @@ struct lp_handle {
   long long k1_launches = 0;
   double k1_ms = 0.0;
   long long launch_base = 0;
+  std::vector<lp_iter_record> history;
   std::vector<void*> allocs;
 
   int fail(int code, const char* fmt, ...) {
@@ -161,6 +169,8 @@ StreamArgs base_args(lp_handle* h) {
   a.stages = h->plan.stages;
   a.sigma = h->opt.sigma;
   a.partials = h->partials;
+  a.gpart = h->gpart;
+  a.gtickets = h->gtickets;
   a.ticket = h->tickets + 0;
   a.sc = h->sc;
   a.err = &h->sc->err;
@@ -229,7 +239,40 @@ int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_le
 }
 
 // QR of (ADW)^T and R^{-1}; LP_ERR_SKETCH_RANK on a rank failure.
+int factor_qr(lp_handle* h);
+
+// Q = (ADW)(ADW)^T = R^T R by an FP64 Gram (cuBLAS DSYRK) and Cholesky; the
+// Gram squares kappa(ADW), which stays far below 1/eps_64 on the IPM path; if
+// the Cholesky breaks down the QR of (ADW)^T is used instead.
 int factor(lp_handle* h) {
+  const int m = h->m, w = h->w;
+  if (h->blas) {
+    const double one = 1.0, zero = 0.0;
+    if (cublasDsyrk(h->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, m, w, &one, h->adw, w, &zero,
+                    h->rinv_cm, m) != CUBLAS_STATUS_SUCCESS)
+      return h->fail(LP_ERR_CUDA, "cublasDsyrk failed");
+    CS(cusolverDnDpotrf(h->sol, CUBLAS_FILL_MODE_UPPER, m, h->rinv_cm, m,
+                        static_cast<double*>(h->dwork), h->lwork_potrf, h->dinfo));
+    CK(launch_factor_utils(0, h->rinv_cm, m, m, h->rinv_cm, h->sc, 0.0, h->num_sms, h->st));
+    CK(launch_factor_utils(1, h->rinv_cm, m, m, nullptr, h->sc, 1e-13, h->num_sms, h->st));
+    CK(cudaMemcpyAsync(h->hinfo, h->dinfo, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    RET(sync_read(h));
+    if (h->hinfo[0] == 0 && !h->hsc->rank_bad) {
+      CS(cusolverDnXtrtri(h->sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, m, CUDA_R_64F,
+                          h->rinv_cm, m, h->dwork, h->dwork_bytes, h->hwork, h->hwork_bytes,
+                          h->dinfo + 1));
+      CK(launch_factor_utils(2, h->rinv_cm, w, m, h->rinv_rm, h->sc, 0.0, h->num_sms, h->st));
+      CK(cudaMemcpyAsync(h->hinfo + 1, h->dinfo + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+      RET(sync_read(h));
+      if (h->hinfo[1] == 0) return LP_OK;
+    }
+    h->qr_fallbacks += 1;
+  }
+  return factor_qr(h);
+}
+
+// Q = R^T R from the QR of (ADW)^T (cuSOLVER geqrf), R^{-1} by trtri.
+int factor_qr(lp_handle* h) {
   const int m = h->m, w = h->w;
   CK(cudaMemcpyAsync(h->qr, h->adw, sizeof(double) * (size_t)m * w, cudaMemcpyDeviceToDevice, h->st));
   CS(cusolverDnDgeqrf(h->sol, w, m, h->qr, w, h->tau, static_cast<double*>(h->dwork),
@@ -301,7 +344,7 @@ void tridiag_extremes(const std::vector<double>& dg, const std::vector<double>& 
 // LP_WARN_INNER_MAXIT.  tol_f > 0: absolute ||f|| target; else relative tol_cg.
 int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
   const int m = h->m;
-  const int inner = h->opt.inner;
+  int inner = h->opt.inner;
   CK(cudaMemsetAsync(h->dy, 0, sizeof(double) * m, h->st));
   CK(cudaMemcpyAsync(h->r, h->p, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
@@ -355,14 +398,18 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
     return LP_OK;
   }
   int status = LP_OK;
+  // FP32 products until a refresh shows the true residual stalled (the FP32
+  // product's precision floor); then FP64 products for the rest of this solve.
+  bool use64 = false;
+  double f_prev = h->hsc->f_true;
   while (true) {
     for (int j = 0; j < refine; ++j) {
       if (inner == LP_INNER_CHEBYSHEV) {
         CK(launch_cheb_pre(m, h->dy, h->pdir, h->sc, h->st));
-        RET(launch_adat(h, h->pdir, E_CHEB, false, 1, h->q));
+        RET(launch_adat(h, h->pdir, E_CHEB, use64, 1, h->q));
         RET(precond_gemvs(h, h->r, h->z, GH_CHEB_B, 1));
       } else {
-        RET(launch_adat(h, h->pdir, E_PCG_A, false, 1, h->q));
+        RET(launch_adat(h, h->pdir, E_PCG_A, use64, 1, h->q));
         RET(precond_gemvs(h, h->r, h->z, GH_PCG_B, 1));
       }
     }
@@ -376,6 +423,18 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
       status = LP_WARN_INNER_MAXIT;
       break;
     }
+    if (inner == LP_INNER_CHEBYSHEV && h->hsc->f_true > f_prev) {
+      // The residual grew: the interval from the Lanczos estimate misses part
+      // of the spectrum.  Continue with CG from the current iterate and the
+      // refreshed residual (p = z, rho = r^T z).
+      inner = LP_INNER_CG;
+      RET(set_scalar(h, &h->sc->rho, h->hsc->f_true * h->hsc->f_true));
+      CK(cudaMemcpyAsync(h->pdir, h->z, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+      h->cheb_fallbacks += 1;
+    } else if (!use64 && h->hsc->f_true > 0.5 * f_prev) {
+      use64 = true;
+    }
+    f_prev = h->hsc->f_true;
   }
   *iters_out = total_iters + h->hsc->inner_iters;
   return status;
@@ -388,6 +447,15 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
     CK(cudaMemsetAsync(h->v, 0, sizeof(double) * h->npad, h->st));
     return LP_OK;
   }
+  // One FP64 refinement step of z ~ Q^{-1} r with Q z = ADW (ADW^T z), so that
+  // A S^{-1} v = A D^2 A^T dy - p (eq. addl) holds to FP64 accuracy whatever
+  // the precision of the factor: e = r - Q z, z += R^{-1} R^{-T} e.
+  CK(launch_adwt(h->adw, h->m, h->w, h->z, h->adwt_part, h->adwt_parts, h->uw, h->num_sms, h->st));
+  CK(launch_gemv_rows(h->adw, h->m, h->w, h->uw, h->r, 1.0, -1.0, h->mb0, h->num_sms, h->st));
+  CK(launch_gemv_tri(h->rinv_cm, h->m, 1, h->mb0, h->wv, GH_NONE, 0, nullptr, nullptr, nullptr,
+                     h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st));
+  CK(launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, h->z, GH_NONE, 0, nullptr, nullptr, nullptr,
+                     h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z));
   CK(launch_adwt(h->adw, h->m, h->w, h->z, h->adwt_part, h->adwt_parts, h->uw, h->num_sms, h->st));
   CK(launch_v_gather(h->n, xs_x, xs_s, h->uw, h->opt.seed, k, retry, h->s_blocks, h->w, -1.0, h->v,
                      h->num_sms, h->st));
@@ -506,6 +574,7 @@ int lp_destroy(lp_handle* h) {
   if (h->hval) cudaFreeHost(h->hval);
   if (h->hwork) free(h->hwork);
   if (h->sol) cusolverDnDestroy(h->sol);
+  if (h->blas) cublasDestroy(h->blas);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
   return LP_OK;
@@ -581,6 +650,8 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));
   RET(h->alloc(reinterpret_cast<char**>(&h->partials), (size_t)h->plan.grid * 2 * h->lda * 8));
+  RET(h->alloc(&h->gpart, (size_t)((h->plan.grid + kGroup - 1) / kGroup) * 2 * h->lda));
+  RET(h->alloc(&h->gtickets, kMaxGroups + 1));
   RET(h->alloc(&h->red_partials, (size_t)h->plan.grid * 2 + 2));
   RET(h->alloc(&h->tickets, 16));
   RET(h->alloc(&h->vpart, (size_t)h->num_sms * 8 + 64));
@@ -593,10 +664,13 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
     return h->fail(LP_ERR_CUDA, "cusolverDnCreate failed");
   CS(cusolverDnSetStream(h->sol, h->st));
   CS(cusolverDnDgeqrf_bufferSize(h->sol, h->w, h->m, h->qr, h->w, &h->lwork_geqrf));
+  CS(cusolverDnDpotrf_bufferSize(h->sol, CUBLAS_FILL_MODE_UPPER, h->m, h->rinv_cm, h->m, &h->lwork_potrf));
+  if (cublasCreate(&h->blas) != CUBLAS_STATUS_SUCCESS) return h->fail(LP_ERR_CUDA, "cublasCreate failed");
+  if (cublasSetStream(h->blas, h->st) != CUBLAS_STATUS_SUCCESS) return h->fail(LP_ERR_CUDA, "cublasSetStream failed");
   size_t dtr = 0, htr = 0;
   CS(cusolverDnXtrtri_bufferSize(h->sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, h->m,
                                  CUDA_R_64F, h->rinv_cm, h->m, &dtr, &htr));
-  h->dwork_bytes = std::max<size_t>((size_t)h->lwork_geqrf * sizeof(double), dtr) + 256;
+  h->dwork_bytes = std::max<size_t>(std::max<size_t>((size_t)h->lwork_geqrf, (size_t)h->lwork_potrf) * sizeof(double), dtr) + 256;
   RET(h->alloc(reinterpret_cast<char**>(&h->dwork), h->dwork_bytes));
   h->hwork_bytes = std::max<size_t>(htr, 8);
   h->hwork = malloc(h->hwork_bytes);
@@ -735,6 +809,13 @@ int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double
   return LP_OK;
 }
 
+int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records) {
+  if (!h || max_records < 0 || (max_records > 0 && !recs)) return LP_ERR_ARG;
+  const int cnt = (int)h->history.size();
+  for (int i = 0; i < std::min(cnt, (int)max_records); ++i) recs[i] = h->history[i];
+  return cnt;
+}
+
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st) {
   if (!h || !st) return LP_ERR_ARG;
   if (cudaStreamSynchronize(h->st) != cudaSuccess) return LP_ERR_CUDA;
@@ -806,6 +887,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   h->err.clear();
   const auto t_start = std::chrono::steady_clock::now();
   const bool feasible = mode == LP_FEASIBLE;
+  h->history.clear();
   lp_result res;
   std::memset(&res, 0, sizeof res);
   const long long n = h->n;
@@ -844,6 +926,18 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
     const double rp = sqrt(S.rp2), rd = sqrt(S.rd2);
     const double gap = fabs(S.cx - S.by) / (1.0 + fabs(S.cx));
     const double rp_rel = rp / (1.0 + h->bnorm), rd_rel = rd / (1.0 + h->cnorm);
+    if (k > 0 && !h->history.empty()) {
+      h->history.back().alpha_max = S.alpha_max;
+      h->history.back().alpha_bar = S.alpha_bar;
+    }
+    lp_iter_record rec;
+    std::memset(&rec, 0, sizeof rec);
+    rec.k = k;
+    rec.mu = S.mu;
+    rec.rel_gap = gap;
+    rec.rp_rel = rp_rel;
+    rec.rd_rel = rd_rel;
+    h->history.push_back(rec);
     if (k == 0) {
       r0 = sqrt(S.rp2 + S.rd2);
       if (feasible && (rp_rel > 1e-8 || rd_rel > 1e-8))
@@ -883,6 +977,15 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
     int iters = 0;
     const int ist = inner_solve(h, tol_f, &iters);
     if (ist < 0) return ist;
+    {
+      lp_iter_record& hr = h->history.back();
+      hr.inner_iterations = iters;
+      hr.retries = retry;
+      hr.inner_status = ist;
+      hr.f_norm = h->hsc->f_true;
+      hr.f0_norm = sqrt(std::max(h->hsc->rho0, 0.0));
+      hr.tol_f = tol_f > 0 ? tol_f : h->opt.tol_cg * hr.f0_norm;
+    }
     res.inner_total += iters;
     res.inner_max = std::max(res.inner_max, iters);
     ms_in += ms_since(t0);

@@ -54,27 +54,77 @@ __device__ void drain_stages(uint64_t* bars, int consumed, int my_tiles, int S, 
 // epilogue run by the last CTA: FP64 reduction of the per-CTA partials in a
 // fixed order, then the mode-specific vector work on m-vectors.
 // ---------------------------------------------------------------------------
+// Two-level deterministic reduction of the per-CTA partial vectors.  CTAs form
+// groups of kGroup consecutive blocks; the last CTA of a group to finish (group
+// ticket) sums that group's partials in FP64 in block order into gpart[group],
+// then takes the global ticket; the last group reducer returns true and its
+// CTA then holds every group sum.  Group sums overlap the other CTAs' streaming.
+template <typename TC>
+__device__ bool tree_reduce(const StreamArgs& a, int nacc, int* s_flag) {
+  const int G = gridDim.x;
+  const int ngroups = (G + kGroup - 1) / kGroup;
+  const int grp = blockIdx.x / kGroup;
+  const int b0 = grp * kGroup;
+  const int gsize = min(kGroup, G - b0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(a.gtickets + grp, 1u);
+    const bool last = (t == (unsigned)gsize - 1u);
+    if (last) a.gtickets[grp] = 0u;
+    *s_flag = last ? 1 : 0;
+  }
+  __syncthreads();
+  if (*s_flag == 0) return false;
+  __threadfence();
+  const TC* part = static_cast<const TC*>(a.partials);
+  const size_t pstride = (size_t)2 * a.lda;
+  for (int k = 0; k < nacc; ++k)
+    for (int i = threadIdx.x; i < a.lda; i += blockDim.x) {
+      TC v[kGroup];
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q)
+        v[q] = (q < gsize) ? __ldcg(part + (size_t)(b0 + q) * pstride + (size_t)k * a.lda + i) : (TC)0;
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q) s += (double)v[q];
+      a.gpart[((size_t)grp * 2 + k) * a.lda + i] = s;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(a.gtickets + kMaxGroups, 1u);
+    const bool last = (t == (unsigned)ngroups - 1u);
+    if (last) a.gtickets[kMaxGroups] = 0u;
+    *s_flag = last ? 1 : 0;
+  }
+  __syncthreads();
+  if (*s_flag == 0) return false;
+  __threadfence();
+  return true;
+}
+
 template <typename TC>
 __device__ void stream_epilogue(const StreamArgs& a, int nacc, double* red) {
   const int tid = threadIdx.x;
   const int G = gridDim.x;
-  const TC* part = static_cast<const TC*>(a.partials);
-  const size_t pstride = (size_t)2 * a.lda;
+  const int ngroups = (G + kGroup - 1) / kGroup;
   if (*a.err != ERR_NONE) return;
   auto acc_row = [&](int k, int i) -> double {
     double s = 0.0;
-    for (int b = 0; b < G; ++b) s += (double)__ldcg(part + (size_t)b * pstride + (size_t)k * a.lda + i);
+    for (int g = 0; g < ngroups; ++g) s += __ldcg(a.gpart + ((size_t)g * 2 + k) * a.lda + i);
     return s;
   };
-  // column reductions (two FP64 sums over columns)
+  // column reductions (two FP64 sums over columns), block-parallel in a fixed order
   double cr0 = 0.0, cr1 = 0.0;
   if (a.red_partials) {
-    if (tid == 0) {
-      for (int b = 0; b < G; ++b) {
-        cr0 += __ldcg(a.red_partials + 2 * b);
-        cr1 += __ldcg(a.red_partials + 2 * b + 1);
-      }
+    double t0 = 0.0, t1 = 0.0;
+    for (int b = tid; b < G; b += blockDim.x) {
+      t0 += __ldcg(a.red_partials + 2 * b);
+      t1 += __ldcg(a.red_partials + 2 * b + 1);
     }
+    cr0 = block_sum(t0, red);
+    cr1 = block_sum(t1, red);
   }
   switch (a.epilogue) {
     case E_PLAIN:
@@ -337,21 +387,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream(const StreamArgs a) {
     }
   }
   if (a.epilogue == E_NONE) return;
-  if (last_block_ticket(a.ticket, &s_flag)) stream_epilogue<TC>(a, NACC, red);
+  if (tree_reduce<TC>(a, NACC, &s_flag)) stream_epilogue<TC>(a, NACC, red);
 }
 
 // ---------------------------------------------------------------------------
-// k_adat_fused: u = A diag(d2) A^T v in FP32, warp-per-column, one smem read
-// per element, per-lane accumulators over all rows.  VPL = 16-byte vectors
-// per lane per column (lda <= 32 * VPL * VEC).
+// k_adat_fused: u = A diag(d2) A^T v in FP32 (the product inside every CG
+// step).  Warp-specialised: warp kConsumerWarps is the producer (one lane
+// issues the bulk copies of tile i into stage i % S once the consumers have
+// released it on empty[i % S]); the kConsumerWarps consumer warps each take
+// whole columns of a tile (column jj goes to warp jj % kConsumerWarps): load
+// the column slice from shared memory into registers once, form d2_j (a_j^T v)
+// (four independent partial sums, then a warp reduction) and accumulate
+// a_j t_j into per-lane registers covering all rows.  No CTA-wide barrier
+// inside the stream.  VPL = 16-byte vectors per lane per column.
 // ---------------------------------------------------------------------------
 template <typename TA, int VPL>
-__global__ void __launch_bounds__(kThreads, 1) k_adat_fused(const StreamArgs a) {
+__global__ void __launch_bounds__(kFusedThreads, 1) k_adat_fused(const StreamArgs a) {
   constexpr int VEC = VecOf<TA>::N;
   constexpr bool VREG = (VPL * VEC <= 32);
   extern __shared__ __align__(128) char smem[];
   const SmemLayout L = make_layout(a.lda, (int)sizeof(TA), a.nb, a.stages, 4);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+  uint64_t* empty = full + a.stages;
   float* v_s = reinterpret_cast<float*>(smem + L.v_off);
   double* red = reinterpret_cast<double*>(smem + L.red_off);
   __shared__ int s_flag;
@@ -363,101 +420,120 @@ __global__ void __launch_bounds__(kThreads, 1) k_adat_fused(const StreamArgs a) 
   const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
   if (tid == 0) {
-    for (int st = 0; st < S; ++st) mbar_init(&bars[st], 1);
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kConsumerWarps);
+    }
     fence_mbar_init();
   }
   for (int i = tid; i < a.lda; i += blockDim.x) v_s[i] = (i < a.m) ? (float)a.vin[i] : 0.0f;
   __syncthreads();
-  if (tid == 0)
-    for (int i = 0; i < my_tiles && i < S; ++i)
-      issue_tile<TA>(a, L, smem, bars, i, (int)blockIdx.x + i * (int)gridDim.x);
 
-  float vr[VREG ? VPL : 1][VREG ? VEC : 1];
-  if (VREG) {
-#pragma unroll
-    for (int c = 0; c < VPL; ++c)
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) {
-        const int rv = c * 32 + lane;
-        vr[c][e] = (rv < RV) ? v_s[rv * VEC + e] : 0.0f;
-      }
-  }
   float acc[VPL][VEC];
 #pragma unroll
   for (int c = 0; c < VPL; ++c)
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[c][e] = 0.0f;
-
-  int consumed = 0;
   bool aborted = false;
-  for (int i = 0; i < my_tiles; ++i) {
-    const int st = i % S;
-    const bool ok = mbar_wait(&bars[st], (uint32_t)((i / S) & 1), a.err);
-    if (!__syncthreads_and(ok)) {
-      aborted = true;
-      break;
-    }
-    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-    const long long j0 = (long long)tile * a.nb;
-    const int ncols = (int)min((long long)a.nb, a.n - j0);
-    const char* stage = smem + (size_t)st * L.stage_bytes;
-    const TA* At = reinterpret_cast<const TA*>(stage);
-    const float* d2t = reinterpret_cast<const float*>(stage + L.cv_off[0]);
-    for (int jj = warp; jj < ncols; jj += kWarps) {
-      const TA* col = At + (size_t)jj * a.lda;
-      float av[VPL][VEC];
-      float d = 0.0f;
-#pragma unroll
-      for (int c = 0; c < VPL; ++c) {
-        const int rv = c * 32 + lane;
-        if (rv < RV) {
-          ld16<float>(col + rv * VEC, av[c]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) av[c][e] = 0.0f;
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < my_tiles; ++i) {
+        const int st = i % S;
+        if (i >= S && !mbar_wait(&empty[st], (uint32_t)(((i / S) - 1) & 1), a.err)) {
+          aborted = true;
+          break;
         }
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-          const float vv = VREG ? vr[VREG ? c : 0][VREG ? e : 0]
-                                : ((rv < RV) ? v_s[rv * VEC + e] : 0.0f);
-          d = fmaf(av[c][e], vv, d);
-        }
+        fence_proxy_async_smem();
+        issue_tile<TA>(a, L, smem, full, st, (int)blockIdx.x + i * (int)gridDim.x);
+        issued = i + 1;
       }
-      d = warp_sum(d);
-      const float t = d2t[jj] * d;
+      if (aborted || *a.err != ERR_NONE) {
+        // make sure no copy is still landing in shared memory before exit
+        for (int j = (issued > S ? issued - S : 0); j < issued; ++j)
+          mbar_wait(&full[j % S], (uint32_t)((j / S) & 1), a.err);
+      }
+    }
+  } else {
+    // ---------------- consumers ----------------
+    float vr[VREG ? VPL : 1][VREG ? VEC : 1];
+    if (VREG) {
 #pragma unroll
       for (int c = 0; c < VPL; ++c)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[c][e] = fmaf(av[c][e], t, acc[c][e]);
+        for (int e = 0; e < VEC; ++e) {
+          const int rv = c * 32 + lane;
+          vr[c][e] = (rv < RV) ? v_s[rv * VEC + e] : 0.0f;
+        }
     }
-    __syncthreads();
-    consumed = i + 1;
-    if (tid == 0 && i + S < my_tiles) {
-      fence_proxy_async_smem();
-      issue_tile<TA>(a, L, smem, bars, st, (int)blockIdx.x + (i + S) * (int)gridDim.x);
+    for (int i = 0; i < my_tiles; ++i) {
+      const int st = i % S;
+      if (!mbar_wait(&full[st], (uint32_t)((i / S) & 1), a.err)) {
+        aborted = true;
+        break;
+      }
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const long long j0 = (long long)tile * a.nb;
+      const int ncols = (int)min((long long)a.nb, a.n - j0);
+      const char* stage = smem + (size_t)st * L.stage_bytes;
+      const TA* At = reinterpret_cast<const TA*>(stage);
+      const float* d2t = reinterpret_cast<const float*>(stage + L.cv_off[0]);
+      for (int jj = warp; jj < ncols; jj += kConsumerWarps) {
+        const TA* col = At + (size_t)jj * a.lda;
+        float av[VPL][VEC];
+        float dp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < VPL; ++c) {
+          const int rv = c * 32 + lane;
+          if (rv < RV) {
+            ld16<float>(col + rv * VEC, av[c]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) av[c][e] = 0.0f;
+          }
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            const float vv = VREG ? vr[VREG ? c : 0][VREG ? e : 0]
+                                  : ((rv < RV) ? v_s[rv * VEC + e] : 0.0f);
+            dp[(c * VEC + e) & 3] = fmaf(av[c][e], vv, dp[(c * VEC + e) & 3]);
+          }
+        }
+        float d = (dp[0] + dp[1]) + (dp[2] + dp[3]);
+        d = warp_sum(d);
+        const float t = d2t[jj] * d;
+#pragma unroll
+        for (int c = 0; c < VPL; ++c)
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) acc[c][e] = fmaf(av[c][e], t, acc[c][e]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
     }
   }
-  if (aborted && tid == 0) drain_stages<TA>(bars, consumed, my_tiles, S, a.err);
-  __syncthreads();
-  // cross-warp reduction through shared memory: buf[warp][lda]
+  aborted = __syncthreads_or(aborted) != 0;
+  // cross-warp reduction through shared memory: buf[consumer warp][lda]
   float* buf = reinterpret_cast<float*>(smem);
+  if (warp < kConsumerWarps) {
 #pragma unroll
-  for (int c = 0; c < VPL; ++c) {
-    const int rv = c * 32 + lane;
-    if (rv < RV)
+    for (int c = 0; c < VPL; ++c) {
+      const int rv = c * 32 + lane;
+      if (rv < RV)
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) buf[(size_t)warp * a.lda + rv * VEC + e] = acc[c][e];
+        for (int e = 0; e < VEC; ++e) buf[(size_t)warp * a.lda + rv * VEC + e] = acc[c][e];
+    }
   }
   __syncthreads();
   float* part = static_cast<float*>(a.partials) + (size_t)blockIdx.x * 2 * a.lda;
   for (int r = tid; r < a.lda; r += blockDim.x) {
     float s = 0.0f;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) s += buf[(size_t)w * a.lda + r];
+    for (int w = 0; w < kConsumerWarps; ++w) s += buf[(size_t)w * a.lda + r];
     part[r] = aborted ? 0.0f : s;
   }
   if (a.epilogue == E_NONE) return;
-  if (last_block_ticket(a.ticket, &s_flag)) stream_epilogue<float>(a, 1, red);
+  if (tree_reduce<float>(a, 1, &s_flag)) stream_epilogue<float>(a, 1, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -481,7 +557,7 @@ cudaError_t launch_fused_t(const StreamArgs& a, int grid, int smem, cudaStream_t
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  k<<<grid, kThreads, smem, st>>>(a);
+  k<<<grid, kFusedThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -525,12 +601,12 @@ StreamPlan make_stream_plan(int m, long long n, int lda, int esz, int num_sms, i
   for (; stages >= 2; --stages) {
     SmemLayout L = make_layout(lda, esz, nb, stages, 8);
     // the end-of-kernel reduction buffer reuses the stage area
-    const int redbuf = std::max(kWarps * lda * 4, kThreads / std::max(1, lda / (16 / esz)) * lda * 8);
+    const int redbuf = std::max(kConsumerWarps * lda * 4, kThreads / std::max(1, lda / (16 / esz)) * lda * 8);
     if (L.total <= budget && stages * L.stage_bytes >= redbuf) break;
   }
   if (stages < 2) stages = 2;
   p.stages = stages;
-  p.grid = std::max(1, std::min(p.ntiles, num_sms));
+  p.grid = std::max(1, std::min(std::min(p.ntiles, num_sms), kGroup * kMaxGroups));
   p.smem = make_layout(lda, esz, nb, stages, tc_bytes).total;
   p.smem8 = make_layout(lda, esz, nb, stages, 8).total;
   p.ok = (p.smem8 <= 227 * 1024);

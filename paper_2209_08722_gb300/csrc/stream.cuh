@@ -75,6 +75,8 @@ struct StreamArgs {
   int* err;
   int skip_level;      // return at once if sc->inner_done >= skip_level (0: never)
   double* coef;        // E_PCG_A: alpha of CG step j stored at coef[2j] (Lanczos interval)
+  double* gpart;       // [ceil(grid/kGroup)][2][lda] FP64 group sums of the partials
+  unsigned* gtickets;  // [kMaxGroups + 1] self-resetting tickets of the two-level reduction
 };
 
 // Shared-memory layout shared by host and device.
@@ -103,7 +105,7 @@ __host__ __device__ inline SmemLayout make_layout(int lda, int esz, int nb, int 
   L.stage_bytes = off;
   off = stages * L.stage_bytes;
   L.bar_off = off;
-  off += align_up_i(stages * 8, 128);
+  off += align_up_i(2 * stages * 8, 128);  // full[] and empty[] barriers
   L.v_off = off;
   off += align_up_i(lda * tc_bytes, 128);
   L.t_off = off;

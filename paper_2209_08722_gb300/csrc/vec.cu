@@ -43,6 +43,7 @@ struct GemvArgs {
   int* err;
   int t_max;
   double* coef;      // G_PCG_B: beta of CG step j stored at coef[2j+1]
+  const double* y_add;  // G_NONE: y = y_add + M x when non-null
 };
 
 __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
     double acc = 0.0;
     for (int j = lo + lane; j < hi; j += 32) acc = fma(row[j], a.x[j], acc);
     acc = warp_sum(acc);
-    if (lane == 0) a.y[i] = acc;
+    if (lane == 0) a.y[i] = a.y_add ? a.y_add[i] + acc : acc;
   }
   if (a.epi == G_NONE) return;
   if (!last_block_ticket(a.ticket, &s_flag)) return;
@@ -85,12 +86,16 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
       sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
     }
   } else if (a.epi == G_PCG_B || a.epi == G_REFRESH) {
-    const double beta = rz / sc->rho;
+    double beta = rz / sc->rho;
     bool stop;
     if (a.epi == G_PCG_B) {
       stop = f <= 0.5 * sc->tol_f;
     } else {
       stop = f <= sc->tol_f;
+      // The recursion drifted far from the FP64 residual (FP32 products):
+      // restart CG from the current iterate (iterative refinement) instead of
+      // residual replacement.
+      if (f > 4.0 * sc->f_rec) beta = 0.0;
     }
     if (!stop)
       for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) + beta * a.p[i];
@@ -143,13 +148,38 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
 cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
-                            cudaStream_t st) {
-  GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef};
+                            cudaStream_t st, const double* y_add) {
+  GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef, y_add};
   const int warps = 8;
   int grid = (m + warps - 1) / warps;
   grid = std::max(1, std::min(grid, num_sms * 4));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_gemv_tri<<<grid, warps * 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// y_i = alpha y0_i + beta (M x)_i for a rows x cols row-major M (warp per row)
+__global__ void __launch_bounds__(256) k_gemv_rows(const double* __restrict__ M, int rows, int cols,
+                                                   const double* __restrict__ x,
+                                                   const double* __restrict__ y0, double alpha,
+                                                   double beta, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int i = gw; i < rows; i += nw) {
+    const double* row = M + (size_t)i * cols;
+    double acc = 0.0;
+    for (int j = lane; j < cols; j += 32) acc = fma(row[j], x[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[i] = (y0 ? alpha * y0[i] : 0.0) + beta * acc;
+  }
+}
+
+cudaError_t launch_gemv_rows(const double* M, int rows, int cols, const double* x, const double* y0,
+                             double alpha, double beta, double* y, int num_sms, cudaStream_t st) {
+  const int grid = std::max(1, std::min((rows + 7) / 8, num_sms * 4));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_gemv_rows<<<grid, 256, 0, st>>>(M, rows, cols, x, y0, alpha, beta, y);
   return cudaGetLastError();
 }
 

@@ -241,6 +241,15 @@ class LPSolver:
                                               float(res_ratio), float(mu0), out2))
         return out2[0], out2[1]
 
+    def history(self) -> list:
+        """lp_get_history: per-outer-iteration records of the last solve."""
+        cnt = self._lib.lp_get_history(self._h, None, 0)
+        if cnt < 0:
+            raise LPError(cnt, "lp_get_history failed")
+        recs = (nat.LpIterRecord * max(cnt, 1))()
+        self._lib.lp_get_history(self._h, recs, cnt)
+        return [recs[i].as_dict() for i in range(cnt)]
+
     def kernel_stats(self) -> dict:
         st = nat.LpKernelStats()
         self._check(self._lib.lp_get_kernel_stats(self._h, ctypes.byref(st)))
