@@ -236,6 +236,28 @@ int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double
  * available (>= 0) or LP_ERR_ARG. */
 int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
 
+/* u = A diag(d2) A^T v without any device allocation, for callers that own all
+ * device memory themselves (a pre-sized arena, a serving loop with a fixed
+ * memory budget, code that must not call the driver's allocator after start-up)
+ * and therefore cannot create a handle.  The paper has no counterpart: this is
+ * the FP32 product of the solver's inner loop offered outside a handle.
+ *   A   device pointer, column-major, leading dimension ld (elements) with
+ *       ld * element size a multiple of 16 bytes, 16-byte aligned, holding
+ *       n * ld elements; dtype LP_F32 or LP_BF16.
+ *   d2 (n), v (m), u (m): FP64 device vectors owned by the caller.
+ *   stream: cudaStream_t or NULL.  The call returns after the product is done.
+ * Scratch lives in one fixed 4 MiB __device__ array inside the library, kept by
+ * every device that used it until the library is unloaded; its address is
+ * looked up on the first call on a device, so make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Sizes whose scratch would not fit (about ld > 5000) and m beyond the
+ * kernel's register tile (2048 rows in FP32, 4096 in BF16) return LP_ERR_ARG;
+ * nothing is allocated in any case.  Returns LP_OK, LP_ERR_ARG, LP_ERR_CUDA or
+ * LP_ERR_DEVICE_TIMEOUT. */
+int lp_adat_noalloc(const void* A, int32_t dtype, int32_t m, int64_t n, int64_t ld,
+                    const double* d2, const double* v, double* u, void* stream);
+
 /* Statistics of the hot product kernel (requires opt.profile = 1). */
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);
 int lp_reset_kernel_stats(lp_handle* h);

@@ -110,6 +110,7 @@ SIGNATURES = {
     "lp_directions": (c_int32, [P, P, P, P, P, P, c_double, c_int32, P, P]),
     "lp_step_lengths": (c_int32, [P, P, P, P, P, c_int32, c_double, c_double, P]),
     "lp_get_history": (c_int32, [P, POINTER(LpIterRecord), c_int32]),
+    "lp_adat_noalloc": (c_int32, [P, c_int32, c_int32, c_int64, c_int64, P, P, P, P]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }
