@@ -24,6 +24,8 @@ int fused_vpl(int lda, int esz);
 cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
                           const StreamPlan& p, cudaStream_t st);
 cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
+cudaError_t launch_adat_df(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
+bool adat_df_supported(int lda, int esz);
 
 cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
                                const double* dvec, int is_d2, uint64_t seed, long long k,

@@ -57,6 +57,9 @@ struct lp_handle {
   int lwork_potrf = 0;
   long long qr_fallbacks = 0;
   long long cheb_fallbacks = 0;
+  bool use_df = false;   // double-float kernel for the FP64-accurate products
+  bool qinv_ok = false;  // explicit Q^{-1} formed for the current factor
+  double* qinv = nullptr;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -220,14 +223,23 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
     ev = ev_next(h);
     if (ev) cudaEventRecord(ev->a, h->st);
   }
-  cudaError_t e = use64 ? launch_stream(h->dtype, true, M_ADAT, a, h->plan, h->st)
-                        : launch_adat_fused(h->dtype, a, h->plan, h->st);
+  cudaError_t e;
+  if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st);
+  else if (h->use_df) e = launch_adat_df(h->dtype, a, h->plan, h->st);
+  else e = launch_stream(h->dtype, true, M_ADAT, a, h->plan, h->st);
   if (ev) cudaEventRecord(ev->b, h->st);
   if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "adat launch: %s", cudaGetErrorString(e));
   return LP_OK;
 }
 
 int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_level) {
+  if (h->qinv_ok) {  // one full GEMV with the explicit Q^{-1} = R^{-1} R^{-T}
+    cudaError_t e = launch_gemv_tri(h->qinv, h->m, 2, r, z, epi, skip_level, h->r, h->pdir, h->dy,
+                                    h->sc, h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef,
+                                    h->num_sms, h->st);
+    if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
+    return LP_OK;
+  }
   cudaError_t e = launch_gemv_tri(h->rinv_cm, h->m, 1, r, h->wv, GH_NONE, skip_level, nullptr,
                                   nullptr, nullptr, h->sc, h->tickets + 1, &h->sc->err, 0, nullptr,
                                   h->num_sms, h->st);
@@ -235,6 +247,21 @@ int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_le
   e = launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, z, epi, skip_level, h->r, h->pdir, h->dy, h->sc,
                       h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st);
   if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
+  return LP_OK;
+}
+
+// Q^{-1} = R^{-1} R^{-T} (cuBLAS DSYRK on the explicit R^{-1}, then mirrored),
+// so each CG step applies the preconditioner with one GEMV.
+int form_qinv(lp_handle* h) {
+  h->qinv_ok = false;
+  if (!h->blas) return LP_OK;
+  const int m = h->m;
+  const double one = 1.0, zero = 0.0;
+  if (cublasDsyrk(h->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, m, m, &one, h->rinv_cm, m, &zero,
+                  h->qinv, m) != CUBLAS_STATUS_SUCCESS)
+    return LP_OK;  // keep the two triangular GEMVs
+  CK(launch_factor_utils(3, h->qinv, m, m, h->qinv, h->sc, 0.0, h->num_sms, h->st));
+  h->qinv_ok = true;
   return LP_OK;
 }
 
@@ -264,7 +291,7 @@ int factor(lp_handle* h) {
       CK(launch_factor_utils(2, h->rinv_cm, w, m, h->rinv_rm, h->sc, 0.0, h->num_sms, h->st));
       CK(cudaMemcpyAsync(h->hinfo + 1, h->dinfo + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
       RET(sync_read(h));
-      if (h->hinfo[1] == 0) return LP_OK;
+      if (h->hinfo[1] == 0) return form_qinv(h);
     }
     h->qr_fallbacks += 1;
   }
@@ -288,7 +315,7 @@ int factor_qr(lp_handle* h) {
   if (h->hsc->rank_bad || h->hinfo[0] != 0 || h->hinfo[1] != 0)
     return h->fail(LP_ERR_SKETCH_RANK, "A D W is numerically rank deficient (|R_ii| range %.3e..%.3e)",
                    h->hsc->diag_min, h->hsc->diag_max);
-  return LP_OK;
+  return form_qinv(h);
 }
 
 // sketch for (k, retry) + factor, redrawing on a rank failure (Lemma 4.1)
@@ -617,6 +644,9 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   h->w = (int)w;
   // kernel shape limits
   h->plan = make_stream_plan(h->m, h->n, h->lda, h->esz, h->num_sms, 4);
+  h->use_df = h->dtype != LP_F64 && adat_df_supported(h->lda, h->esz) &&
+              (long long)(fused_vpl(h->lda, h->esz) >= 8 ? 8 : 16) * h->lda * 8 <=
+                  (long long)h->plan.stages * make_layout(h->lda, h->esz, h->plan.nb, h->plan.stages, 8).stage_bytes;
   if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
   if (h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0)
     return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the fused product kernel", h->m);
@@ -646,6 +676,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->tau, (size_t)h->m));
   RET(h->alloc(&h->rinv_cm, (size_t)h->m * h->m));
   RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
+  RET(h->alloc(&h->qinv, (size_t)h->m * h->m));
   RET(h->alloc(&h->uw, (size_t)h->w));
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));

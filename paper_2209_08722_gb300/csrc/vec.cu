@@ -55,12 +55,20 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = gridDim.x * warps_per_block;
   for (int i = gw; i < a.m; i += nw) {
+    // lower == 1: columns [0, i]; 0: [i, m); 2: the full row
     const int lo = a.lower ? 0 : i;
-    const int hi = a.lower ? i + 1 : a.m;
+    const int hi = a.lower == 1 ? i + 1 : a.m;
     const double* row = a.M + (size_t)i * a.m;
-    double acc = 0.0;
-    for (int j = lo + lane; j < hi; j += 32) acc = fma(row[j], a.x[j], acc);
-    acc = warp_sum(acc);
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    int j = lo + lane;
+    for (; j + 96 < hi; j += 128) {
+      acc0 = fma(row[j], a.x[j], acc0);
+      acc1 = fma(row[j + 32], a.x[j + 32], acc1);
+      acc2 = fma(row[j + 64], a.x[j + 64], acc2);
+      acc3 = fma(row[j + 96], a.x[j + 96], acc3);
+    }
+    for (; j < hi; j += 32) acc0 = fma(row[j], a.x[j], acc0);
+    double acc = warp_sum((acc0 + acc1) + (acc2 + acc3));
     if (lane == 0) a.y[i] = a.y_add ? a.y_add[i] + acc : acc;
   }
   if (a.epi == G_NONE) return;
@@ -483,6 +491,16 @@ __global__ void k_diag_range(const double* __restrict__ r, int m, DevScalars* sc
   }
 }
 
+// mirror the upper triangle of a column-major m x m matrix into its lower one
+__global__ void k_symmetrize(double* __restrict__ a, int m) {
+  const long long total = (long long)m * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / m), i = (int)(e % m);  // column j, row i
+    if (i > j) a[e] = a[(size_t)i * m + j];
+  }
+}
+
 __global__ void k_transpose(const double* __restrict__ src, int m, double* __restrict__ dst) {
   __shared__ double tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -507,6 +525,11 @@ cudaError_t launch_factor_utils(int which, const double* a, int w, int m, double
   } else if (which == 1) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k_diag_range<<<1, 256, 0, st>>>(a, m, sc, rank_tol);
+  } else if (which == 3) {
+    const long long total = (long long)m * m;
+    const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, num_sms * 4));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    k_symmetrize<<<grid, 256, 0, st>>>(b, m);
   } else {
     dim3 grid((m + 31) / 32, (m + 31) / 32);
     g_launches.fetch_add(1, std::memory_order_relaxed);
