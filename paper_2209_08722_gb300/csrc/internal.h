@@ -27,6 +27,13 @@ cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& 
 cudaError_t launch_adat_df(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
 bool adat_df_supported(int lda, int esz);
 
+int sparse_grid(int num_sms);
+cudaError_t launch_sparse(int dtype, bool fp64, int mode, const StreamArgs& a, int grid,
+                          cudaStream_t st);
+cudaError_t launch_sparse_sketch(int dtype, const long long* cp, const int* ri, const void* val,
+                                 long long n, const double* dvec, int is_d2, uint64_t seed,
+                                 long long k, int retry, int s_blocks, int w, double* adw, int m,
+                                 int num_sms, cudaStream_t st);
 cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
                                const double* dvec, int is_d2, uint64_t seed, long long k,
                                int retry, int s_blocks, int w, double* adw, int num_sms,

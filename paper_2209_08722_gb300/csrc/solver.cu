@@ -58,6 +58,12 @@ struct lp_handle {
   long long qr_fallbacks = 0;
   long long cheb_fallbacks = 0;
   bool use_df = false;   // double-float kernel for the FP64-accurate products
+  bool sparse = false;   // CSC storage
+  long long* colptr = nullptr;
+  int* rowidx = nullptr;
+  void* spval = nullptr;
+  long long nnz = 0;
+  int sp_grid = 0;
   bool qinv_ok = false;  // explicit Q^{-1} formed for the current factor
   double* qinv = nullptr;
   // n-vectors (padded)
@@ -174,6 +180,9 @@ StreamArgs base_args(lp_handle* h) {
   a.partials = h->partials;
   a.gpart = h->gpart;
   a.gtickets = h->gtickets;
+  a.colptr = h->colptr;
+  a.rowidx = h->rowidx;
+  a.spval = h->spval;
   a.ticket = h->tickets + 0;
   a.sc = h->sc;
   a.err = &h->sc->err;
@@ -224,7 +233,8 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
     if (ev) cudaEventRecord(ev->a, h->st);
   }
   cudaError_t e;
-  if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st);
+  if (h->sparse) e = launch_sparse(h->dtype, use64, M_ADAT, a, h->sp_grid, h->st);
+  else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st);
   else if (h->use_df) e = launch_adat_df(h->dtype, a, h->plan, h->st);
   else e = launch_stream(h->dtype, true, M_ADAT, a, h->plan, h->st);
   if (ev) cudaEventRecord(ev->b, h->st);
@@ -318,12 +328,21 @@ int factor_qr(lp_handle* h) {
   return form_qinv(h);
 }
 
+// A D W for the CountSketch of (seed, k, retry): dense or CSC kernel
+cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t seed, long long k,
+                          int retry) {
+  if (h->sparse)
+    return launch_sparse_sketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
+                                retry, h->s_blocks, h->w, h->adw, h->m, h->num_sms, h->st);
+  return launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, seed, k, retry,
+                            h->s_blocks, h->w, h->adw, h->num_sms, h->st);
+}
+
 // sketch for (k, retry) + factor, redrawing on a rank failure (Lemma 4.1)
 int sketch_and_factor(lp_handle* h, const double* dvec, int is_d2, long long k, int* retries) {
   int rc = LP_ERR_SKETCH_RANK;
   for (int retry = 0; retry < kMaxRetry; ++retry) {
-    CK(launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, h->opt.seed, k, retry,
-                          h->s_blocks, h->w, h->adw, h->num_sms, h->st));
+    CK(launch_sketch(h, dvec, is_d2, h->opt.seed, k, retry));
     rc = factor(h);
     if (rc != LP_ERR_SKETCH_RANK) {
       if (retries) *retries = retry;
@@ -518,7 +537,8 @@ int residual_pass(lp_handle* h, bool feasible) {
   a.out_m0 = h->rp;
   a.out_m1 = h->p;
   a.bvec = h->b;
-  CK(launch_stream(h->dtype, true, M_RESID, a, h->plan, h->st));
+  if (h->sparse) CK(launch_sparse(h->dtype, true, M_RESID, a, h->sp_grid, h->st));
+  else CK(launch_stream(h->dtype, true, M_RESID, a, h->plan, h->st));
   return LP_OK;
 }
 
@@ -536,7 +556,8 @@ int direction_pass(lp_handle* h, bool feasible) {
   a.out_col[1] = h->ds;
   a.red_partials = h->red_partials;
   a.epilogue = E_DIR;
-  CK(launch_stream(h->dtype, true, M_DIR, a, h->plan, h->st));
+  if (h->sparse) CK(launch_sparse(h->dtype, true, M_DIR, a, h->sp_grid, h->st));
+  else CK(launch_stream(h->dtype, true, M_DIR, a, h->plan, h->st));
   return LP_OK;
 }
 
@@ -611,10 +632,22 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
                        int bc_on_device, const lp_options* opt) {
   if (!A || !b || !c) return h->fail(LP_ERR_ARG, "A, b and c are required");
   if (A->m < 1 || A->n < A->m) return h->fail(LP_ERR_ARG, "need 1 <= m <= n (m=%d n=%lld)", A->m, (long long)A->n);
-  if (A->fmt != LP_DENSE_COLMAJOR)
-    return h->fail(LP_ERR_UNSUPPORTED, "sparse (CSC) storage is not built in this version");
+  if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC) return h->fail(LP_ERR_ARG, "bad format");
   if (A->dtype < LP_F64 || A->dtype > LP_BF16) return h->fail(LP_ERR_ARG, "bad dtype");
-  if (!A->val || A->ld < A->m) return h->fail(LP_ERR_ARG, "dense A needs val and ld >= m");
+  if (A->fmt == LP_DENSE_COLMAJOR && (!A->val || A->ld < A->m))
+    return h->fail(LP_ERR_ARG, "dense A needs val and ld >= m");
+  if (A->fmt == LP_CSC) {
+    if (!A->val || !A->ptr || !A->idx || A->nnz < 0) return h->fail(LP_ERR_ARG, "CSC A needs ptr, idx, val");
+    if (A->dtype == LP_BF16) return h->fail(LP_ERR_UNSUPPORTED, "CSC values must be FP32 or FP64");
+    if (A->nnz >= (1LL << 40)) return h->fail(LP_ERR_ARG, "nnz too large");
+    if (!A->on_device) {  // structural check of a host CSC
+      if (A->ptr[0] != 0 || A->ptr[A->n] != A->nnz) return h->fail(LP_ERR_ARG, "CSC ptr[0] != 0 or ptr[n] != nnz");
+      for (long long j = 0; j < A->n; ++j)
+        if (A->ptr[j + 1] < A->ptr[j]) return h->fail(LP_ERR_ARG, "CSC ptr not monotone");
+      for (long long q = 0; q < A->nnz; ++q)
+        if (A->idx[q] < 0 || A->idx[q] >= A->m) return h->fail(LP_ERR_ARG, "CSC row index out of range");
+    }
+  }
   lp_options_default(&h->opt);
   if (opt) h->opt = *opt;
   std::string why;
@@ -642,22 +675,43 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   if (w < h->m) return h->fail(LP_ERR_ARG, "sketch width w=%lld < m=%d: A D W cannot have rank m", w, h->m);
   if (w > (1 << 30)) return h->fail(LP_ERR_ARG, "sketch width too large");
   h->w = (int)w;
+  h->sparse = A->fmt == LP_CSC;
+  if (h->sparse) {
+    h->lda = (int)round_up_ll(h->m, 4);
+    if (h->lda * 3 * 8 > 200 * 1024)
+      return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the CSC kernels' shared-memory vectors", h->m);
+    h->sp_grid = sparse_grid(h->num_sms);
+    h->plan.grid = h->sp_grid;
+    h->plan.ok = true;
+  }
   // kernel shape limits
-  h->plan = make_stream_plan(h->m, h->n, h->lda, h->esz, h->num_sms, 4);
-  h->use_df = h->dtype != LP_F64 && adat_df_supported(h->lda, h->esz) &&
+  if (!h->sparse) h->plan = make_stream_plan(h->m, h->n, h->lda, h->esz, h->num_sms, 4);
+  h->use_df = !h->sparse && h->dtype != LP_F64 && adat_df_supported(h->lda, h->esz) &&
               (long long)(fused_vpl(h->lda, h->esz) >= 8 ? 8 : 16) * h->lda * 8 <=
                   (long long)h->plan.stages * make_layout(h->lda, h->esz, h->plan.nb, h->plan.stages, 8).stage_bytes;
   if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
-  if (h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0)
+  if (!h->sparse && h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0)
     return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the fused product kernel", h->m);
-  if (h->lda / vec > 4 * kThreads)
+  if (!h->sparse && h->lda / vec > 4 * kThreads)
     return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the FP64 streaming kernel", h->m);
   // device memory
   const size_t n = (size_t)h->npad, m = (size_t)h->lda;
-  RET(h->alloc(reinterpret_cast<char**>(&h->A), (size_t)h->lda * h->n * h->esz));
-  CK(cudaMemcpy2DAsync(h->A, (size_t)h->lda * h->esz, A->val, (size_t)A->ld * h->esz,
-                       (size_t)h->m * h->esz, (size_t)h->n,
-                       A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (h->sparse) {
+    h->nnz = A->nnz;
+    RET(h->alloc(&h->colptr, (size_t)h->n + 1));
+    RET(h->alloc(&h->rowidx, (size_t)std::max<long long>(h->nnz, 1)));
+    RET(h->alloc(reinterpret_cast<char**>(&h->spval), (size_t)std::max<long long>(h->nnz, 1) * h->esz));
+    CK(cudaMemcpyAsync(h->colptr, A->ptr, sizeof(long long) * ((size_t)h->n + 1), kind, h->st));
+    if (h->nnz > 0) {
+      CK(cudaMemcpyAsync(h->rowidx, A->idx, sizeof(int) * (size_t)h->nnz, kind, h->st));
+      CK(cudaMemcpyAsync(h->spval, A->val, (size_t)h->esz * h->nnz, kind, h->st));
+    }
+  } else {
+    RET(h->alloc(reinterpret_cast<char**>(&h->A), (size_t)h->lda * h->n * h->esz));
+    CK(cudaMemcpy2DAsync(h->A, (size_t)h->lda * h->esz, A->val, (size_t)A->ld * h->esz,
+                         (size_t)h->m * h->esz, (size_t)h->n, kind, h->st));
+  }
   double** nvecs[] = {&h->c, &h->x, &h->y, &h->s, &h->rd, &h->d2d, &h->dx, &h->ds, &h->v,
                       &h->nb0, &h->nb1, &h->nb2};
   for (double** p : nvecs) RET(h->alloc(p, n));
@@ -778,8 +832,7 @@ int lp_sketch(lp_handle* h, const double* D, uint64_t seed, int64_t k, int32_t r
   if (!h || !D || !adw || retry < 0 || retry >= kMaxRetry || k < 0) return LP_ERR_ARG;
   h->err.clear();
   RET(copy_in(h, h->nb0, D, h->n, 1));
-  CK(launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, h->nb0, 0, seed, k, retry, h->s_blocks,
-                        h->w, h->adw, h->num_sms, h->st));
+  CK(launch_sketch(h, h->nb0, 0, seed, k, retry));
   CK(cudaMemcpyAsync(adw, h->adw, sizeof(double) * (size_t)h->m * h->w, cudaMemcpyDeviceToDevice, h->st));
   RET(sync_read(h));
   if (w_out) *w_out = h->w;
@@ -853,7 +906,8 @@ int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st) {
   ev_flush(h);
   st->launches = h->k1_launches;
   st->ms = h->k1_ms;
-  st->bytes_per_launch = (int64_t)h->m * h->n * h->esz + 4 * h->n + 2 * 8 * (int64_t)h->m;
+  st->bytes_per_launch = h->sparse ? (int64_t)h->nnz * (h->esz + 4) + 8 * (h->n + 1) + 4 * h->n + 16 * (int64_t)h->m
+                                    : (int64_t)h->m * h->n * h->esz + 4 * h->n + 2 * 8 * (int64_t)h->m;
   st->all_launches = g_launches.load() - h->launch_base;
   return LP_OK;
 }

@@ -75,6 +75,9 @@ struct StreamArgs {
   int* err;
   int skip_level;      // return at once if sc->inner_done >= skip_level (0: never)
   double* coef;        // E_PCG_A: alpha of CG step j stored at coef[2j] (Lanczos interval)
+  const long long* colptr;  // CSC: n+1 column pointers
+  const int* rowidx;        // CSC: row indices
+  const void* spval;        // CSC: values (FP32 or FP64)
   double* gpart;       // [ceil(grid/kGroup)][2][lda] FP64 group sums of the partials
   unsigned* gtickets;  // [kMaxGroups + 1] self-resetting tickets of the two-level reduction
 };

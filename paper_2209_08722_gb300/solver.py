@@ -69,7 +69,8 @@ class LPSolver:
     torch.bfloat16 tensor).
     """
 
-    def __init__(self, A, b, c, m: int, n: int, dtype: str = "f32", stream=None, **options):
+    def __init__(self, A, b, c, m: int, n: int, dtype: str = "f32", stream=None, csc=None,
+                 **options):
         self._lib = nat.load()
         self._h = ctypes.c_void_p()
         self.m, self.n, self.dtype = int(m), int(n), dtype
@@ -82,16 +83,29 @@ class LPSolver:
         if stream is not None:
             opt.stream = stream
         self.options = opt
-        if _is_torch(A):
+        if csc is not None:
+            # sparse A in CSC form: (col_ptr int64 [n+1], row_idx int32 [nnz], values [nnz])
+            cp, ri, vals = csc
+            if not _is_torch(cp):
+                cp = np.ascontiguousarray(cp, dtype=np.int64)
+                ri = np.ascontiguousarray(ri, dtype=np.int32)
+                vals = np.ascontiguousarray(vals, dtype=_NP_DT[dtype])
+            nnz = int(vals.shape[0])
+            mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_CSC, dtype=_DTYPES[dtype],
+                               val=_ptr(vals), ld=0, ptr=_ptr(cp), idx=_ptr(ri), nnz=nnz,
+                               on_device=1 if _on_device(vals) else 0)
+            A = (cp, ri, vals)
+        elif _is_torch(A):
             if tuple(A.shape) != (self.n, self.m):
                 raise ValueError("A must have shape (n, m) (column-major)")
         else:
             A = np.ascontiguousarray(A, dtype=_NP_DT[dtype])
             if A.shape != (self.n, self.m):
                 raise ValueError("A must have shape (n, m) (column-major)")
-        mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype],
-                           val=_ptr(A), ld=self.m, ptr=None, idx=None, nnz=0,
-                           on_device=1 if _on_device(A) else 0)
+        if csc is None:
+            mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype],
+                               val=_ptr(A), ld=self.m, ptr=None, idx=None, nnz=0,
+                               on_device=1 if _on_device(A) else 0)
         bc_dev = _on_device(b)
         if not bc_dev:
             b = np.ascontiguousarray(b, dtype=np.float64)
@@ -261,7 +275,11 @@ class LPSolver:
 
 
 def from_planted(lp, device: bool = False, **options) -> LPSolver:
-    """An LPSolver for an ``lpgen.PlantedLP`` (dense)."""
+    """An LPSolver for an ``lpgen.PlantedLP`` (dense or CSC)."""
+    if lp.sparse:
+        vals = lp.val.astype(np.float32 if lp.storage == "f32" else np.float64)
+        return LPSolver(None, lp.b, lp.c, lp.m, lp.n, dtype=lp.storage,
+                        csc=(lp.col_ptr, lp.row_idx, vals), **options)
     A = lp.storage_array()
     b, c = lp.b, lp.c
     if device:

@@ -23,8 +23,8 @@ def host(t):
 
 
 def solver_for(lp, **opts):
-    from paper_2209_08722_gb300 import LPSolver
-    return LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype=lp.storage, **opts)
+    from paper_2209_08722_gb300 import from_planted
+    return from_planted(lp, **opts)
 
 
 def adat_bound(A, d2, v):
