@@ -96,16 +96,22 @@ def gaussian_matrix(seed: int, k: int, retry: int, n: int, w: int) -> np.ndarray
 
     The draw for (k, retry) uses its own stream, seeded with
     S_kr = draw(draw(seed, 0), k*MAX_RETRY + retry); entry (i, j) is the draw
-    at counter i*w + j of that stream.  Its 64 bits give two 24-bit uniforms
-    u1 = (bits 40..63 + 1/2)/2^24, u2 = (bits 16..39 + 1/2)/2^24 and
-    z = sqrt(-2 ln u1) cos(2 pi u2).
+    at counter i*w + j of that stream.  Its 64 bits give two uniforms that are
+    exact in FP32: u1 = (bits 41..63 + 1) / 2^23 in (0, 1] and
+    u2 = (bits 18..40) / 2^23 in [0, 1); z = sqrt(-2 ln u1) cos(2 pi u2).
     """
+    u1, u2 = gaussian_uniforms(seed, k, retry, n, w)
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return (z / np.sqrt(w)).reshape(n, w)
+
+
+def gaussian_uniforms(seed: int, k: int, retry: int, n: int, w: int):
+    """The two uniforms of every entry of W_G (flattened row-major)."""
     s_g = int(draw(seed, np.array([0], dtype=np.uint64))[0])
     s_kr = int(draw(s_g, np.array([k * MAX_RETRY + retry], dtype=np.uint64))[0])
     idx = np.arange(n * w, dtype=np.uint64)
     with np.errstate(over="ignore"):
         val = draw(s_kr, idx)
-    u1 = ((val >> _U64(40)).astype(np.float64) + 0.5) / 16777216.0
-    u2 = (((val >> _U64(16)) & _U64(0xFFFFFF)).astype(np.float64) + 0.5) / 16777216.0
-    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
-    return (z / np.sqrt(w)).reshape(n, w)
+    u1 = ((val >> _U64(41)).astype(np.float64) + 1.0) / 8388608.0
+    u2 = ((val >> _U64(18)) & _U64(0x7FFFFF)).astype(np.float64) / 8388608.0
+    return u1, u2

@@ -106,3 +106,20 @@ def test_gaussian_sketch_moments():
     assert abs((G ** 4).mean() - 3.0) < 0.15
     G2 = sketch.gaussian_matrix(9, 2, 0, n, w)
     assert not np.allclose(G / np.sqrt(w), G2)
+
+
+def test_gaussian_uniforms_are_exact_fp32_and_in_range():
+    u1, u2 = sketch.gaussian_uniforms(3, 1, 0, 50, 40)
+    assert np.array_equal(u1.astype(np.float32).astype(np.float64), u1)
+    assert np.array_equal(u2.astype(np.float32).astype(np.float64), u2)
+    assert (u1 > 0).all() and (u1 <= 1).all() and (u2 >= 0).all() and (u2 < 1).all()
+
+
+def test_gaussian_sketch_subspace_embedding():
+    # Section 6: a Gaussian W with w >> m is a subspace embedding (eq. pdprec)
+    rng = np.random.default_rng(4)
+    m, n, w = 4, 3000, 2000
+    V, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    W = sketch.gaussian_matrix(8, 0, 0, n, w)
+    G = (V.T @ W) @ (W.T @ V)
+    assert np.linalg.norm(G - np.eye(m), 2) < 0.25
