@@ -59,6 +59,8 @@ struct lp_handle {
   long long cheb_fallbacks = 0;
   bool use_df = false;   // double-float kernel for the FP64-accurate products
   bool sparse = false;   // CSC storage
+  const double* sk_dvec = nullptr;  // D (or D^2) used by the current sketch
+  int sk_is_d2 = 0;
   long long* colptr = nullptr;
   int* rowidx = nullptr;
   void* spval = nullptr;
@@ -328,9 +330,15 @@ int factor_qr(lp_handle* h) {
   return form_qinv(h);
 }
 
-// A D W for the CountSketch of (seed, k, retry): dense or CSC kernel
+// A D W for the sketch of (seed, k, retry): Gaussian (dense A) or CountSketch
+// (dense or CSC).  Remembers which D it used, for the correction vector.
 cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t seed, long long k,
                           int retry) {
+  h->sk_dvec = dvec;
+  h->sk_is_d2 = is_d2;
+  if (h->opt.sketch == LP_SKETCH_GAUSS)
+    return launch_gauss_sketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, seed, k, retry, h->w,
+                               h->adw, h->num_sms, h->st);
   if (h->sparse)
     return launch_sparse_sketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
                                 retry, h->s_blocks, h->w, h->adw, h->m, h->num_sms, h->st);
@@ -503,8 +511,12 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
   CK(launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, h->z, GH_NONE, 0, nullptr, nullptr, nullptr,
                      h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z));
   CK(launch_adwt(h->adw, h->m, h->w, h->z, h->adwt_part, h->adwt_parts, h->uw, h->num_sms, h->st));
-  CK(launch_v_gather(h->n, xs_x, xs_s, h->uw, h->opt.seed, k, retry, h->s_blocks, h->w, -1.0, h->v,
-                     h->num_sms, h->st));
+  if (h->opt.sketch == LP_SKETCH_GAUSS)
+    CK(launch_gauss_v(h->n, xs_x, xs_s, h->sk_dvec, h->sk_is_d2, h->uw, h->opt.seed, k, retry, h->w,
+                      -1.0, h->v, h->num_sms, h->st));
+  else
+    CK(launch_v_gather(h->n, xs_x, xs_s, h->uw, h->opt.seed, k, retry, h->s_blocks, h->w, -1.0, h->v,
+                       h->num_sms, h->st));
   return LP_OK;
 }
 
@@ -571,7 +583,7 @@ void options_check(const lp_options* o, std::string* why) {
   if (!(o->sigma > 0 && o->sigma < 1)) *why = "sigma must be in (0, 1)";
   else if (!(o->gamma > 0 && o->gamma < 1)) *why = "gamma must be in (0, 1)";
   else if (o->s < 1 || o->s > kMaxBlocks) *why = "s must be in [1, 16]";
-  else if (o->sketch != LP_SKETCH_COUNT) *why = "only the CountSketch sketch is built";
+  else if (o->sketch != LP_SKETCH_COUNT && o->sketch != LP_SKETCH_GAUSS) *why = "unknown sketch";
   else if (o->inner != LP_INNER_CG && o->inner != LP_INNER_CHEBYSHEV) *why = "inner must be CG or Chebyshev";
   else if (o->t_max < 1 || o->k_max < 0) *why = "t_max >= 1 and k_max >= 0 required";
 }
@@ -676,6 +688,8 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   if (w > (1 << 30)) return h->fail(LP_ERR_ARG, "sketch width too large");
   h->w = (int)w;
   h->sparse = A->fmt == LP_CSC;
+  if (h->sparse && h->opt.sketch == LP_SKETCH_GAUSS)
+    return h->fail(LP_ERR_UNSUPPORTED, "the Gaussian sketch is built for dense A only");
   if (h->sparse) {
     h->lda = (int)round_up_ll(h->m, 4);
     if (h->lda * 3 * 8 > 200 * 1024)
