@@ -95,6 +95,8 @@ typedef struct {
     int64_t w;             /* explicit sketch width (multiple of s), or 0 */
     uint64_t seed;         /* seed of the sketch generator; 0 */
     void* stream;          /* cudaStream_t to run on, or NULL for a private stream */
+    int32_t tensor_sketch; /* Gaussian sketch with FP32/BF16 A: 1 = tcgen05 tensor-core GEMM,
+                              0 = FP32 SIMT kernel; 1 */
 } lp_options;
 
 /* ---- results -------------------------------------------------------------- */

@@ -12,27 +12,11 @@
 // k_gauss_sketch: FP32 SIMT tiled product with split-K: each CTA owns a
 // 128 x 64 output tile and a slice of the n columns of A, regenerates its W'
 // tile in shared memory and adds its FP32 tile into the FP64 result with
-// atomics.  Used as the reference for the tensor-core version.
-#include "internal.h"
+// atomics.  It serves FP64 storage and is the cross-check of the tensor-core
+// version in gauss_tc.cu, which computes the same product.
+#include "gauss.cuh"
 
 namespace lpk {
-
-__host__ __device__ inline uint64_t gauss_stream(uint64_t seed, long long k, int retry) {
-  const uint64_t s_g = sm64_draw(seed, 0ull);
-  return sm64_draw(s_g, (uint64_t)(k * kMaxRetry + retry));
-}
-
-__device__ __forceinline__ float gauss_entry(uint64_t s_kr, uint64_t idx, float inv_sqrt_w) {
-  const uint64_t v = sm64_draw(s_kr, idx);
-  const float u1 = (float)((v >> 41) + 1ull) * 0x1p-23f;
-  const float u2 = (float)((v >> 18) & 0x7FFFFFull) * 0x1p-23f;
-  return __fmul_rn(__fmul_rn(sqrtf(-2.0f * logf(u1)), cospif(2.0f * u2)), inv_sqrt_w);
-}
-
-__device__ __forceinline__ float dval(const double* dvec, long long j, int is_d2) {
-  const double d = dvec[j];
-  return (float)(is_d2 ? sqrt(d) : d);
-}
 
 constexpr int GBM = 128, GBN = 64, GBK = 16;
 
@@ -71,7 +55,7 @@ __global__ void __launch_bounds__(256) k_gauss_sketch(const TA* __restrict__ A, 
       const long long j = jb + jj;
       float wv = 0.0f;
       if (j < j1 && k0 + kk < w)
-        wv = __fmul_rn(dval(dvec, j, is_d2), gauss_entry(s_kr, (uint64_t)j * w + k0 + kk, inv_sqrt_w));
+        wv = gauss_wprime(dvec, j, is_d2, s_kr, (uint64_t)j * w + k0 + kk, inv_sqrt_w);
       Ws[jj][kk] = wv;
     }
     __syncthreads();
@@ -113,7 +97,7 @@ __global__ void __launch_bounds__(256) k_gauss_v(long long n, const double* __re
   const int lane = threadIdx.x & 31;
   const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long j = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
-    const float dj = dval(dvec, j, is_d2);
+    const float dj = gauss_dval(dvec, j, is_d2);
     double acc = 0.0;
     for (int k = lane; k < w; k += 32)
       acc = fma((double)__fmul_rn(dj, gauss_entry(s_kr, (uint64_t)j * w + k, inv_sqrt_w)), u_s[k], acc);
@@ -127,11 +111,14 @@ __global__ void __launch_bounds__(256) k_gauss_v(long long n, const double* __re
 
 cudaError_t launch_gauss_sketch(int dtype, const void* A, int lda, int m, long long n,
                                 const double* dvec, int is_d2, uint64_t seed, long long k, int retry,
-                                int w, double* adw, int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(adw, 0, sizeof(double) * (size_t)m * w, st);
-  if (e != cudaSuccess) return e;
+                                int w, double* adw, int tensor, int* err, int num_sms,
+                                cudaStream_t st) {
   const uint64_t s_kr = gauss_stream(seed, k, retry);
   const float inv_sqrt_w = (float)(1.0 / sqrt((double)w));
+  if (tensor && (dtype == 1 || dtype == 2))
+    return launch_gauss_tc(dtype, A, lda, m, n, dvec, is_d2, s_kr, w, inv_sqrt_w, adw, err, num_sms, st);
+  cudaError_t e = cudaMemsetAsync(adw, 0, sizeof(double) * (size_t)m * w, st);
+  if (e != cudaSuccess) return e;
   const int gx = (m + GBM - 1) / GBM, gy = (w + GBN - 1) / GBN;
   long long ks = std::max<long long>(1, std::min<long long>((n + 4095) / 4096, 64));
   const long long kper = ((n + ks - 1) / ks + GBK - 1) / GBK * GBK;

@@ -36,7 +36,11 @@ cudaError_t launch_sparse_sketch(int dtype, const long long* cp, const int* ri, 
                                  int num_sms, cudaStream_t st);
 cudaError_t launch_gauss_sketch(int dtype, const void* A, int lda, int m, long long n,
                                 const double* dvec, int is_d2, uint64_t seed, long long k, int retry,
-                                int w, double* adw, int num_sms, cudaStream_t st);
+                                int w, double* adw, int tensor, int* err, int num_sms,
+                                cudaStream_t st);
+cudaError_t launch_gauss_tc(int dtype, const void* A, int lda, int m, long long n, const double* dvec,
+                            int is_d2, uint64_t s_kr, int w, float inv_sqrt_w, double* adw, int* err,
+                            int num_sms, cudaStream_t st);
 cudaError_t launch_gauss_v(long long n, const double* x, const double* s, const double* dvec,
                            int is_d2, const double* u, uint64_t seed, long long k, int retry, int w,
                            double scale, double* v, int num_sms, cudaStream_t st);

@@ -338,7 +338,7 @@ cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t 
   h->sk_is_d2 = is_d2;
   if (h->opt.sketch == LP_SKETCH_GAUSS)
     return launch_gauss_sketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, seed, k, retry, h->w,
-                               h->adw, h->num_sms, h->st);
+                               h->adw, h->opt.tensor_sketch, &h->sc->err, h->num_sms, h->st);
   if (h->sparse)
     return launch_sparse_sketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
                                 retry, h->s_blocks, h->w, h->adw, h->m, h->num_sms, h->st);
@@ -615,6 +615,7 @@ void lp_options_default(lp_options* o) {
   o->w = 0;
   o->seed = 0;
   o->stream = nullptr;
+  o->tensor_sketch = 1;
 }
 
 const char* lp_create_error(void) { return g_create_error.c_str(); }
