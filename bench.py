@@ -196,6 +196,49 @@ def run_kernel(args):
     return 0
 
 
+def run_gauss_kernel(args):
+    """Microbenchmark of the Gaussian sketch A D W_G (Section 6) on the bench's A,
+    w = 2048: the tcgen05 split-TF32 product ("gauss") or the FP32 SIMT product
+    ("gauss-simt").  Each timed call is lp_sketch: zero-fill, the product, and a
+    device copy of the m x w FP64 result.  Algorithmic FLOPs = 2 m n w."""
+    import torch
+    from paper_2209_08722_gb300 import LPSolver
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lp = make_lp(0)
+    stream = torch.cuda.current_stream()
+    tensor = 1 if args.kernel == "gauss" else 0
+    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", sketch=1,
+                      w_factor=W_FACTOR, tensor_sketch=tensor, stream=stream.cuda_stream)
+    rng = np.random.default_rng(0)
+    D = torch.from_numpy(np.exp(rng.uniform(-3, 3, lp.n))).cuda()
+    for i in range(args.warmup):
+        solver.sketch(D, 1, i, 0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        solver.sketch(D, 1, i, 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    w = solver.sketch_width
+    flops = 2.0 * lp.m * lp.n * w
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    # TF32 dense peak: the measured BF16 peak x the nominal TF32/BF16 ratio (1.1 / 2.25)
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    tf32 = bf16 * 1.1 / 2.25
+    tfs = flops / (ms * 1e-3) / 1e12
+    print(json.dumps({"kernel": "k_gauss_tc" if tensor else "k_gauss_sketch", "m": lp.m, "n": lp.n,
+                      "w": w, "mean_ms_per_call": ms, "algorithmic_tflops": tfs,
+                      "tf32_peak_tflops": tf32, "frac_of_tf32": tfs / tf32,
+                      "peak_kind": "measured bf16 x nominal ratio" if peaks else "fallback"}),
+          flush=True)
+    solver.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,11 +246,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", choices=["adat"], default=None,
-                    help="time only the hot product kernel (lp_adat, FP32) on the same A")
+    ap.add_argument("--kernel", choices=["adat", "gauss", "gauss-simt"], default=None,
+                    help="time one kernel on the same A: the hot product (lp_adat, FP32), or the "
+                         "Gaussian sketch on the tensor cores / FP32 SIMT")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel in ("gauss", "gauss-simt"):
+        return run_gauss_kernel(args)
     if args.kernel:
         return run_kernel(args)
 

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) k_gauss_sketch(const TA* __restrict__ A, 
                                                       long long kper, double* __restrict__ adw) {
   __shared__ float As[GBK][GBM];
   __shared__ float Ws[GBK][GBN];
+  __shared__ float ds[GBK];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int i0 = blockIdx.x * GBM, k0 = blockIdx.y * GBN;
   const long long j0 = blockIdx.z * kper;
@@ -49,13 +50,15 @@ __global__ void __launch_bounds__(256) k_gauss_sketch(const TA* __restrict__ A, 
       }
       As[jj][ii] = av;
     }
+    if (tid < GBK) ds[tid] = jb + tid < j1 ? gauss_dval(dvec, jb + tid, is_d2) : 0.0f;
+    __syncthreads();
     // W' tile: GBK rows x GBN sketch columns
     for (int e = tid; e < GBK * GBN; e += 256) {
       const int jj = e / GBN, kk = e % GBN;
       const long long j = jb + jj;
       float wv = 0.0f;
       if (j < j1 && k0 + kk < w)
-        wv = gauss_wprime(dvec, j, is_d2, s_kr, (uint64_t)j * w + k0 + kk, inv_sqrt_w);
+        wv = gauss_wprime(ds[jj], s_kr, (uint64_t)j * w + k0 + kk, inv_sqrt_w);
       Ws[jj][kk] = wv;
     }
     __syncthreads();

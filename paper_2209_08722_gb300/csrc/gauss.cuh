@@ -19,8 +19,9 @@ __host__ __device__ inline uint64_t gauss_stream(uint64_t seed, long long k, int
 
 __device__ __forceinline__ float gauss_entry(uint64_t s_kr, uint64_t idx, float inv_sqrt_w) {
   const uint64_t v = sm64_draw(s_kr, idx);
-  const float u1 = (float)((v >> 41) + 1ull) * 0x1p-23f;
-  const float u2 = (float)((v >> 18) & 0x7FFFFFull) * 0x1p-23f;
+  // both integers are below 2^24, so the 32-bit conversions are exact
+  const float u1 = (float)(uint32_t)((v >> 41) + 1ull) * 0x1p-23f;
+  const float u2 = (float)(uint32_t)((v >> 18) & 0x7FFFFFull) * 0x1p-23f;
   return __fmul_rn(__fmul_rn(sqrtf(-2.0f * logf(u1)), cospif(2.0f * u2)), inv_sqrt_w);
 }
 
@@ -29,9 +30,9 @@ __device__ __forceinline__ float gauss_dval(const double* dvec, long long j, int
   return (float)(is_d2 ? sqrt(d) : d);
 }
 
-__device__ __forceinline__ float gauss_wprime(const double* dvec, long long j, int is_d2, uint64_t s_kr,
-                                              uint64_t idx, float inv_sqrt_w) {
-  return __fmul_rn(gauss_dval(dvec, j, is_d2), gauss_entry(s_kr, idx, inv_sqrt_w));
+// dj = gauss_dval(dvec, j, is_d2), computed once per column j by the caller
+__device__ __forceinline__ float gauss_wprime(float dj, uint64_t s_kr, uint64_t idx, float inv_sqrt_w) {
+  return __fmul_rn(dj, gauss_entry(s_kr, idx, inv_sqrt_w));
 }
 
 }  // namespace lpk

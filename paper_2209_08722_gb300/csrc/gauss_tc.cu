@@ -9,7 +9,7 @@
 //                                                   FP32 rounding and dropped)
 // BF16 A is exact in TF32 (A_lo = 0), so it takes two products.
 //
-// Work split: a CTA (8 warps) owns up to MB = 4 row blocks of 128 rows, one
+// Work split: a CTA (16 warps) owns up to MB = 4 row blocks of 128 rows, one
 // 128-column block of W' and a slice of the n columns of A (split-K), so for
 // m <= 512 every W' entry is drawn exactly once.  Per chunk of 16 columns of A
 // the threads stage A_hi, A_lo, W_hi and W_lo in shared memory in the K-major
@@ -28,7 +28,7 @@ namespace {
 constexpr int TC_M = 128;       // MMA M: rows of A in one row block
 constexpr int TC_N = 128;       // MMA N: columns of W' per CTA
 constexpr int TC_BK = 16;       // columns of A per chunk (two MMA k-steps of 8)
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;
 constexpr int TC_MAXMB = 4;     // row blocks per CTA: MB * 128 TMEM columns <= 512
 // K-major, no-swizzle core-matrix layout of a rows x 16 FP32 tile: element
 // (r, k) at (r/8)*SBO + (k/4)*LBO + (r%8)*16 + (k%4)*4 bytes.
@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) char smem[];
   __shared__ uint64_t bars[2];
   __shared__ uint32_t tmem_base_s;
+  __shared__ float d_s[2][TC_BK];  // fl32(d_j) of the chunk's columns, double-buffered
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.x * mb * TC_M, k0 = blockIdx.y * TC_N;
   const long long j0 = blockIdx.z * kper;
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(&bars[1], 1);
     fence_mbar_init();
   }
+  if (tid < TC_BK) d_s[0][tid] = j0 + tid < j1 ? gauss_dval(dvec, j0 + tid, is_d2) : 0.0f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -140,10 +142,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   bool ok = true;
   long long issued = 0;  // chunks whose MMAs were committed
 
-  // staging roles: thread t owns operand row r = t % 128 and the k4 groups
-  // {2h, 2h+1} of the chunk, h = t / 128
+  // staging roles: thread t owns operand row r = t % 128 and the k4 group
+  // g = t / 128 (columns 4g .. 4g+3 of the chunk)
   const int r = tid & (TC_M - 1);
-  const int h = tid >> 7;
+  const int g = tid >> 7;
+
+  // A of the next chunk is loaded into registers while the current chunk's W'
+  // is drawn, so the global-load latency hides behind the generator
+  float an[TC_MAXMB][4];
+  auto load_chunk = [&](long long jb) {
+#pragma unroll
+    for (int rb = 0; rb < TC_MAXMB; ++rb) {
+      const int i = i0 + rb * TC_M + r;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long j = jb + g * 4 + q;
+        an[rb][q] = (rb < mb && i < m && j < j1) ? load_a<TA>(A, (size_t)j * lda + i) : 0.0f;
+      }
+    }
+  };
+  if (nchunks > 0) load_chunk(j0);
 
   for (long long c = 0; c < nchunks; ++c) {
     const int b = (int)(c & 1);
@@ -155,51 +173,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
     }
     const long long jb = j0 + c * TC_BK;
+    // d of the next chunk into the other buffer; its last readers (chunk c - 1)
+    // finished before the barrier that ended chunk c - 1's staging
+    if (tid < TC_BK) {
+      const long long jn = jb + TC_BK + tid;
+      d_s[(c + 1) & 1][tid] = jn < j1 ? gauss_dval(dvec, jn, is_d2) : 0.0f;
+    }
     // ---- A: MB row blocks, split into TF32 hi / lo ----
-    for (int rb = 0; rb < mb; ++rb) {
-      const int i = i0 + rb * TC_M + r;
-      float a[2][4];
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long j = jb + (2 * h + kk) * 4 + q;
-          a[kk][q] = (i < m && j < j1) ? load_a<TA>(A, (size_t)j * lda + i) : 0.0f;
-        }
-#pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
+    for (int rb = 0; rb < TC_MAXMB; ++rb) {
+      if (rb < mb) {
         uint32_t hi[4], lo[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          hi[q] = to_tf32(a[kk][q]);
-          lo[q] = SPLIT_A ? to_tf32(a[kk][q] - __uint_as_float(hi[q])) : 0u;
+          hi[q] = to_tf32(an[rb][q]);
+          lo[q] = SPLIT_A ? to_tf32(an[rb][q] - __uint_as_float(hi[q])) : 0u;
         }
-        const int off = rb * TC_BLK + core_off(r, 2 * h + kk);
+        const int off = rb * TC_BLK + core_off(r, g);
         *reinterpret_cast<uint4*>(stage + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
         if (SPLIT_A)
           *reinterpret_cast<uint4*>(stage + mb * TC_BLK + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
     }
+    if (c + 1 < nchunks) load_chunk(jb + TC_BK);
     // ---- W': operand rows are the columns k of W', K runs over j ----
     {
       char* whi = stage + (SPLIT_A ? 2 : 1) * mb * TC_BLK;
       char* wlo = whi + TC_BLK;
       const int k = k0 + r;
+      uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long j = jb + (2 * h + kk) * 4 + q;
-          const float wv = (j < j1 && k < w) ? gauss_wprime(dvec, j, is_d2, s_kr, (uint64_t)j * w + k, inv_sqrt_w)
-                                             : 0.0f;
-          hi[q] = to_tf32(wv);
-          lo[q] = to_tf32(wv - __uint_as_float(hi[q]));
-        }
-        const int off = core_off(r, 2 * h + kk);
-        *reinterpret_cast<uint4*>(whi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(wlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      for (int q = 0; q < 4; ++q) {
+        const long long j = jb + g * 4 + q;
+        const float wv = (j < j1 && k < w)
+                             ? gauss_wprime(d_s[c & 1][g * 4 + q], s_kr, (uint64_t)j * w + k, inv_sqrt_w)
+                             : 0.0f;
+        hi[q] = to_tf32(wv);
+        lo[q] = to_tf32(wv - __uint_as_float(hi[q]));
       }
+      const int off = core_off(r, g);
+      *reinterpret_cast<uint4*>(whi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(wlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     // make the generic-proxy stores visible to the tensor core, then issue
     fence_proxy_async_smem();
@@ -234,13 +248,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   all_ok = __syncthreads_and(all_ok) != 0;
   tc_fence_after();
   if (all_ok && issued > 0) {
-    // warp q reads TMEM lanes [32 (q % 4), +32) and half (q / 4) of the columns
-    const int lg = warp & 3, half = warp >> 2;
+    // warp q reads TMEM lanes [32 (q % 4), +32) and quarter q / 4 of the columns
+    const int lg = warp & 3, quarter = warp >> 2;
     for (int rb = 0; rb < mb; ++rb) {
       const int i = i0 + rb * TC_M + lg * 32 + lane;
 #pragma unroll 1
-      for (int cc = 0; cc < TC_N / 2; cc += 8) {
-        const int col = half * (TC_N / 2) + cc;
+      for (int cc = 0; cc < TC_N / 4; cc += 8) {
+        const int col = quarter * (TC_N / 4) + cc;
         uint32_t v[8];
         const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(rb * TC_N + col);
         asm volatile(
