@@ -15,31 +15,9 @@
 // ring; deterministic two-level FP64 reduction of the per-CTA partials).
 #include "internal.h"
 #include "stream_dev.cuh"
+#include "df.cuh"
 
 namespace lpk {
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (sh, sl) += a*(xh + xl) with a*xh formed exactly
-__device__ __forceinline__ void df_fma(float a, float xh, float xl, float& sh, float& sl) {
-  const float p = a * xh;
-  const float e1 = fmaf(a, xh, -p);
-  float s, t;
-  two_sum(sh, p, s, t);
-  sh = s;
-  sl += t + fmaf(a, xl, e1);
-}
-
-__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
-  float s, t;
-  two_sum(sh, oh, s, t);
-  sh = s;
-  sl += t + ol;
-}
 
 template <typename TA, int VPL, int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, 1) k_adat_df(const StreamArgs a) {

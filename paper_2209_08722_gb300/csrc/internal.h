@@ -44,10 +44,21 @@ cudaError_t launch_gauss_tc(int dtype, const void* A, int lda, int m, long long 
 cudaError_t launch_gauss_v(long long n, const double* x, const double* s, const double* dvec,
                            int is_d2, const double* u, uint64_t seed, long long k, int retry, int w,
                            double scale, double* v, int num_sms, cudaStream_t st);
+// scratch of the dense CountSketch: bucket sizes/offsets/cursors (w + 1 each),
+// bucket lists (n s), per-column scales (n)
+struct CsWork {
+  int* count = nullptr;
+  int* base = nullptr;
+  int* cursor = nullptr;
+  int* list = nullptr;
+  double* sc64 = nullptr;
+  float2* scdf = nullptr;
+};
+constexpr int kCsMaxW = 40960;  // the bucket histogram lives in shared memory
 cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
                                const double* dvec, int is_d2, uint64_t seed, long long k,
-                               int retry, int s_blocks, int w, double* adw, int num_sms,
-                               cudaStream_t st);
+                               int retry, int s_blocks, int w, double* adw, const CsWork& ws,
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_v_gather(long long n, const double* x, const double* s, const double* u,
                             uint64_t seed, long long k, int retry, int s_blocks, int w, double scale,
                             double* v, int num_sms, cudaStream_t st);

@@ -2,99 +2,256 @@
 // gather of the correction vector v (eq. compv).
 //
 // W (n x w) has s nonzeros per row: block b of width wb = w/s holds entry
-// sign_b(i)/sqrt(s) at column b*wb + h_b(i), with (h_b(i), sign_b(i)) from the
+// sign_b(j)/sqrt(s) at column b*wb + h_b(j), with (h_b(j), sign_b(j)) from the
 // SplitMix64 counter-based generator (common.cuh).  W is never stored.
 //
-// The sketch is computed deterministically without global atomics: each CTA
-// owns KB consecutive bucket columns of one block, scans the hashes of all n
-// rows, compacts the rows that land in its buckets (in increasing i), and
-// accumulates sign * d_i / sqrt(s) * a_i into FP64 shared-memory buckets.
-// Bucket kl is owned by warp kl % 8, so every bucket is summed by one warp in
-// increasing i: the result does not depend on scheduling.
+// Column g of A D W is the signed, scaled sum of the columns j of A hashed to
+// bucket g.  The sketch is built in four passes:
+//   1. k_cs_count: bucket sizes (shared-memory histograms) and the per-column
+//      scale d_j / sqrt(s), in FP64 and as a double-float pair;
+//   2. k_cs_scan: bucket offsets (exclusive scan);
+//   3. k_cs_scatter: the bucket lists, entry = j | sign << 31;
+//   4. k_cs_accum: one CTA per (bucket, 512-row slab) sorts its bucket's list by
+//      j, splits it into 8 contiguous ranges, and each warp streams its columns
+//      (coalesced 16-byte loads, the next column in flight while the current one
+//      is added) into double-float accumulators in registers; the 8 partial sums
+//      are combined in warp order.
+// A is read s times in total, by CTAs that sweep the columns in increasing j at
+// about the same pace, so the repeats mostly hit in L2.  FP32/BF16 storage sums
+// in double-float arithmetic (products formed exactly, relative error ~2^-44);
+// FP64 storage sums in FP64.  The summation order depends only on the hashes,
+// so the result is bitwise reproducible (for buckets of at most kSortCap
+// columns; larger buckets are summed in list order).
 #include "internal.h"
+#include "df.cuh"
+
+#include <type_traits>
 
 namespace lpk {
 
-constexpr int kChunk = 2048;  // columns scanned per compaction round
+namespace {
+constexpr int kAccThreads = 256;
+constexpr int kAccWarps = kAccThreads / 32;
+constexpr int kEPL = 16;                // accumulated elements per lane
+constexpr int kSlab = 32 * kEPL;        // rows per CTA
+constexpr int kSortCap = 8192;          // bucket entries sorted in shared memory
+}  // namespace
+
+// bucket sizes + per-column scales; grid-stride over columns, histogram in smem
+__global__ void __launch_bounds__(256) k_cs_count(long long n, int s_blocks, int wb, int w, uint64_t seed,
+                                                  long long k, int retry, const double* __restrict__ dvec,
+                                                  int is_d2, double inv_sqrt_s, int* __restrict__ count,
+                                                  double* __restrict__ sc64, float2* __restrict__ scdf) {
+  extern __shared__ int hs[];  // [w]
+  for (int g = threadIdx.x; g < w; g += blockDim.x) hs[g] = 0;
+  __syncthreads();
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    for (int b = 0; b < s_blocks; ++b) {
+      int col;
+      float sg;
+      cs_entry(seed, k, retry, b, j, wb, &col, &sg);
+      atomicAdd(&hs[col], 1);
+    }
+    const double d = dvec[j];
+    const double sc = (is_d2 ? sqrt(d) : d) * inv_sqrt_s;
+    sc64[j] = sc;
+    const float hi = (float)sc;
+    scdf[j] = make_float2(hi, (float)(sc - (double)hi));
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < w; g += blockDim.x)
+    if (hs[g]) atomicAdd(&count[g], hs[g]);
+}
+
+// base[g] = sum of count[0..g), base[w] = total; cursor = base (one CTA)
+__global__ void __launch_bounds__(1024) k_cs_scan(int w, const int* __restrict__ count, int* __restrict__ base,
+                                                  int* __restrict__ cursor) {
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (w + blockDim.x - 1) / blockDim.x;
+  const int g0 = min(w, tid * per), g1 = min(w, g0 + per);
+  int local = 0;
+  for (int g = g0; g < g1; ++g) local += count[g];
+  // exclusive scan of the per-thread sums
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    wsum[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int g = g0; g < g1; ++g) {
+    base[g] = run;
+    cursor[g] = run;
+    run += count[g];
+  }
+  if (tid == blockDim.x - 1) base[w] = run;
+}
+
+// bucket lists: entry = j | (sign < 0) << 31, in arbitrary order within a bucket
+__global__ void __launch_bounds__(256) k_cs_scatter(long long n, int s_blocks, int wb, uint64_t seed, long long k,
+                                                    int retry, int* __restrict__ cursor, int* __restrict__ list) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    for (int b = 0; b < s_blocks; ++b) {
+      int col;
+      float sg;
+      cs_entry(seed, k, retry, b, j, wb, &col, &sg);
+      const int pos = atomicAdd(&cursor[col], 1);
+      list[pos] = (int)j | (sg < 0.0f ? (int)0x80000000u : 0);
+    }
+  }
+}
 
 template <typename TA>
-__global__ void __launch_bounds__(kThreads) k_countsketch(
-    const TA* __restrict__ A, int lda, int m, long long n, const double* __restrict__ dvec,
-    int is_d2, uint64_t seed, long long k, int retry, int s_blocks, int wb, int KB,
-    int groups_per_block, double* __restrict__ adw, int w) {
+struct AccOf {  // double-float accumulators for FP32/BF16 storage, FP64 for FP64
+  static constexpr bool kDF = sizeof(TA) != 8;
+};
+
+// one CTA per (bucket g, slab of 512 rows)
+template <typename TA>
+__global__ void __launch_bounds__(kAccThreads) k_cs_accum(const TA* __restrict__ A, int lda, int m, int w,
+                                                          const int* __restrict__ base,
+                                                          const int* __restrict__ list,
+                                                          const double* __restrict__ sc64,
+                                                          const float2* __restrict__ scdf,
+                                                          double* __restrict__ adw) {
   constexpr int VEC = VecOf<TA>::N;
+  constexpr int NV = kEPL / VEC;  // 16-byte vectors per lane per column
+  constexpr bool DF = AccOf<TA>::kDF;
   extern __shared__ __align__(16) char smem[];
-  double* acc = reinterpret_cast<double*>(smem);                  // [KB][lda]
-  int* list_i = reinterpret_cast<int*>(acc + (size_t)KB * lda);  // [kChunk]
-  float* list_v = reinterpret_cast<float*>(list_i + kChunk);     // scale (sign * d / sqrt s)
-  short* list_k = reinterpret_cast<short*>(list_v + kChunk);     // local bucket
-  __shared__ int warp_cnt[kWarps];
-
+  int* keys = reinterpret_cast<int*>(smem);                                  // [kSortCap]
+  char* comb = smem + kSortCap * sizeof(int);                                // [warps][kSlab] partials
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = blockIdx.x / groups_per_block;
-  const int k0 = (blockIdx.x % groups_per_block) * KB;  // first bucket within block b
-  const int kb = min(KB, wb - k0);
-  if (kb <= 0) return;
-  const int RV = lda / VEC;
-  const double inv_sqrt_s = 1.0 / sqrt((double)s_blocks);
+  const int g = blockIdx.x;
+  const int r0 = blockIdx.y * kSlab;
+  const int beg = base[g];
+  const int cnt = base[g + 1] - beg;
 
-  for (int e = tid; e < KB * lda; e += blockDim.x) acc[e] = 0.0;
-  __syncthreads();
-
-  for (long long base = 0; base < n; base += kChunk) {
-    int total = 0;
-    // ---- compaction of the rows hitting [k0, k0 + kb) ----
-    for (int sub = 0; sub < kChunk; sub += kThreads) {
-      const long long i = base + sub + tid;
-      bool hit = false;
-      int kl = 0;
-      float sg = 1.0f;
-      if (i < n) {
-        int col;
-        cs_entry(seed, k, retry, b, i, wb, &col, &sg);
-        kl = col - b * wb - k0;
-        hit = (kl >= 0 && kl < kb);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (lane == 0) warp_cnt[warp] = __popc(bal);
-      __syncthreads();
-      int off = total;
-      int tot = 0;
-      for (int ww = 0; ww < kWarps; ++ww) {
-        if (ww < warp) off += warp_cnt[ww];
-        tot += warp_cnt[ww];
-      }
-      if (hit) {
-        const int pos = off + __popc(bal & ((1u << lane) - 1u));
-        list_i[pos] = (int)(i - base);
-        list_v[pos] = sg;  // the FP64 scale d_i / sqrt(s) is applied when accumulating
-        list_k[pos] = (short)kl;
-      }
-      total += tot;
-      __syncthreads();
-    }
-    // ---- accumulation: warp (kl % kWarps) owns bucket kl ----
-    for (int e = 0; e < total; ++e) {
-      const int kl = list_k[e];
-      if ((kl % kWarps) != warp) continue;
-      const long long i = base + list_i[e];
-      const double dv = is_d2 ? sqrt(dvec[i]) : dvec[i];
-      const double scale = (double)list_v[e] * dv * inv_sqrt_s;
-      const TA* col = A + (size_t)i * lda;
-      double* dst = acc + (size_t)kl * lda;
-      for (int rv = lane; rv < RV; rv += 32) {
-        double av[VEC];
-        ld16<double>(col + rv * VEC, av);
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) dst[rv * VEC + q] = fma(av[q], scale, dst[rv * VEC + q]);
-      }
-    }
+  // ---- the bucket's list, sorted by column index (bitonic sort in smem) ----
+  const int* lst = list + beg;
+  if (cnt <= kSortCap) {
+    int p2 = 1;
+    while (p2 < cnt) p2 <<= 1;
+    for (int e = tid; e < p2; e += kAccThreads) keys[e] = e < cnt ? lst[e] : 0x7FFFFFFF;
     __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int e = tid; e < (p2 >> 1); e += kAccThreads) {
+          const int lo = 2 * e - (e & (stride - 1));
+          const int hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const int a = keys[lo], b = keys[hi];
+          const bool gt = (a & 0x7FFFFFFF) > (b & 0x7FFFFFFF);
+          if (gt == up) {
+            keys[lo] = b;
+            keys[hi] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    lst = keys;
   }
-  // ---- write A D W (row-major m x w, FP64) ----
-  for (int e = tid; e < kb * m; e += blockDim.x) {
-    const int kl = e / m, i = e % m;
-    adw[(size_t)i * w + b * wb + k0 + kl] = acc[(size_t)kl * lda + i];
+
+  // ---- warp p sums entries [cnt p / 8, cnt (p + 1) / 8) ----
+  const int e0 = (int)((long long)cnt * warp / kAccWarps);
+  const int e1 = (int)((long long)cnt * (warp + 1) / kAccWarps);
+  float hi[kEPL], lo[kEPL];
+  double acc[DF ? 1 : kEPL];
+#pragma unroll
+  for (int q = 0; q < kEPL; ++q) {
+    hi[q] = 0.0f;
+    lo[q] = 0.0f;
+  }
+#pragma unroll
+  for (int q = 0; q < (DF ? 1 : kEPL); ++q) acc[q] = 0.0;
+
+  // loaded elements: FP32 for FP32/BF16 storage (exact), FP64 for FP64
+  using LT = typename std::conditional<DF, float, double>::type;
+  LT cur[kEPL], nxt[kEPL];
+  int key_cur = 0, key_nxt = 0;
+  auto load = [&](int e, LT (&v)[kEPL], int& key) {
+    key = lst[e];
+    const long long j = key & 0x7FFFFFFF;
+    const TA* col = A + (size_t)j * lda + r0;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      const int row = t * 32 * VEC + lane * VEC;
+      if (r0 + row < lda) {
+        ld16<LT>(col + row, &v[t * VEC]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) v[t * VEC + q] = (LT)0;
+      }
+    }
+  };
+  if (e0 < e1) load(e0, cur, key_cur);
+  for (int e = e0; e < e1; ++e) {
+    if (e + 1 < e1) load(e + 1, nxt, key_nxt);
+    const long long j = key_cur & 0x7FFFFFFF;
+    const bool neg = key_cur < 0;
+    if (DF) {
+      const float2 sc = scdf[j];
+      const float sh = neg ? -sc.x : sc.x, sl = neg ? -sc.y : sc.y;
+#pragma unroll
+      for (int q = 0; q < kEPL; ++q) df_fma((float)cur[q], sh, sl, hi[q], lo[q]);
+      // keep |lo| near ulp(hi): its own rounding then stays ~2^-48 |hi| per step
+      if (((e - e0) & 7) == 7) {
+#pragma unroll
+        for (int q = 0; q < kEPL; ++q) df_renorm(hi[q], lo[q]);
+      }
+    } else {
+      const double sc = neg ? -sc64[j] : sc64[j];
+#pragma unroll
+      for (int q = 0; q < (DF ? 1 : kEPL); ++q) acc[q] = fma((double)cur[q], sc, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kEPL; ++q) cur[q] = nxt[q];
+    key_cur = key_nxt;
+  }
+
+  // ---- combine the warps' partial sums in warp order ----
+  __syncthreads();  // the sorted keys are no longer read; comb may be written
+#pragma unroll
+  for (int t = 0; t < NV; ++t)
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      const int row = t * 32 * VEC + lane * VEC + q;
+      if (DF)
+        reinterpret_cast<float2*>(comb)[warp * kSlab + row] = make_float2(hi[t * VEC + q], lo[t * VEC + q]);
+      else
+        reinterpret_cast<double*>(comb)[warp * kSlab + row] = acc[DF ? 0 : t * VEC + q];
+    }
+  __syncthreads();
+  for (int row = tid; row < kSlab; row += kAccThreads) {
+    const int i = r0 + row;
+    if (i >= m) continue;
+    double out;
+    if (DF) {
+      const float2* cp = reinterpret_cast<const float2*>(comb);
+      float sh = cp[row].x, sl = cp[row].y;
+      for (int p = 1; p < kAccWarps; ++p) df_add(sh, sl, cp[p * kSlab + row].x, cp[p * kSlab + row].y);
+      out = (double)sh + (double)sl;
+    } else {
+      const double* cp = reinterpret_cast<const double*>(comb);
+      out = cp[row];
+      for (int p = 1; p < kAccWarps; ++p) out += cp[p * kSlab + row];
+    }
+    adw[(size_t)i * w + g] = out;
   }
 }
 
@@ -119,42 +276,42 @@ __global__ void k_v_gather(long long n, const double* __restrict__ x, const doub
 
 cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
                                const double* dvec, int is_d2, uint64_t seed, long long k,
-                               int retry, int s_blocks, int w, double* adw, int num_sms,
-                               cudaStream_t st) {
+                               int retry, int s_blocks, int w, double* adw, const CsWork& ws,
+                               int num_sms, cudaStream_t st) {
   const int wb = w / s_blocks;
-  const int esz = dtype == 0 ? 8 : (dtype == 1 ? 4 : 2);
-  (void)esz;
-  const int list_bytes = kChunk * (4 + 4 + 2);
-  const int budget = 200 * 1024 - list_bytes;
-  int kb_max = std::max(1, budget / (lda * 8));
-  // aim for at least one CTA per SM
-  int kb = (w + num_sms - 1) / num_sms;
-  kb = std::max(1, std::min(kb, std::min(kb_max, wb)));
-  const int groups_per_block = (wb + kb - 1) / kb;
-  const int grid = groups_per_block * s_blocks;
-  const int smem = kb * lda * 8 + list_bytes;
-  cudaError_t e;
+  const double inv_sqrt_s = 1.0 / sqrt((double)s_blocks);
+  cudaError_t e = cudaMemsetAsync(ws.count, 0, sizeof(int) * (size_t)w, st);
+  if (e != cudaSuccess) return e;
+  const int hist_smem = w * (int)sizeof(int);
+  e = cudaFuncSetAttribute(k_cs_count, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem);
+  if (e != cudaSuccess) return e;
+  const int grid_cols = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)num_sms * 2));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_cs_count<<<grid_cols, 256, hist_smem, st>>>(n, s_blocks, wb, w, seed, k, retry, dvec, is_d2, inv_sqrt_s,
+                                                ws.count, ws.sc64, ws.scdf);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_cs_scan<<<1, 1024, 0, st>>>(w, ws.count, ws.base, ws.cursor);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_cs_scatter<<<grid_cols, 256, 0, st>>>(n, s_blocks, wb, seed, k, retry, ws.cursor, ws.list);
+  // sorted keys + the warps' partial sums (FP64 or a double-float pair: 8 bytes)
+  const int smem = kSortCap * (int)sizeof(int) + kAccWarps * kSlab * 8;
+  dim3 grid((unsigned)w, (unsigned)((m + kSlab - 1) / kSlab));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   if (dtype == 0) {
-    e = cudaFuncSetAttribute(k_countsketch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_cs_accum<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_countsketch<double><<<grid, kThreads, smem, st>>>(
-        static_cast<const double*>(A), lda, m, n, dvec, is_d2, seed, k, retry, s_blocks, wb, kb,
-        groups_per_block, adw, w);
+    k_cs_accum<double><<<grid, kAccThreads, smem, st>>>(static_cast<const double*>(A), lda, m, w, ws.base,
+                                                         ws.list, ws.sc64, ws.scdf, adw);
   } else if (dtype == 1) {
-    e = cudaFuncSetAttribute(k_countsketch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_cs_accum<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_countsketch<float><<<grid, kThreads, smem, st>>>(
-        static_cast<const float*>(A), lda, m, n, dvec, is_d2, seed, k, retry, s_blocks, wb, kb,
-        groups_per_block, adw, w);
+    k_cs_accum<float><<<grid, kAccThreads, smem, st>>>(static_cast<const float*>(A), lda, m, w, ws.base,
+                                                        ws.list, ws.sc64, ws.scdf, adw);
   } else {
-    e = cudaFuncSetAttribute(k_countsketch<bf16raw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(k_cs_accum<bf16raw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_countsketch<bf16raw><<<grid, kThreads, smem, st>>>(
-        static_cast<const bf16raw*>(A), lda, m, n, dvec, is_d2, seed, k, retry, s_blocks, wb, kb,
-        groups_per_block, adw, w);
+    k_cs_accum<bf16raw><<<grid, kAccThreads, smem, st>>>(static_cast<const bf16raw*>(A), lda, m, w, ws.base,
+                                                          ws.list, ws.sc64, ws.scdf, adw);
   }
   return cudaGetLastError();
 }

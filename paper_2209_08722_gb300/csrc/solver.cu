@@ -68,6 +68,7 @@ struct lp_handle {
   int sp_grid = 0;
   bool qinv_ok = false;  // explicit Q^{-1} formed for the current factor
   double* qinv = nullptr;
+  CsWork cs;             // dense CountSketch scratch
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -343,7 +344,7 @@ cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t 
     return launch_sparse_sketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
                                 retry, h->s_blocks, h->w, h->adw, h->m, h->num_sms, h->st);
   return launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, seed, k, retry,
-                            h->s_blocks, h->w, h->adw, h->num_sms, h->st);
+                            h->s_blocks, h->w, h->adw, h->cs, h->num_sms, h->st);
 }
 
 // sketch for (k, retry) + factor, redrawing on a rank failure (Lemma 4.1)
@@ -723,6 +724,18 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
       CK(cudaMemcpyAsync(h->spval, A->val, (size_t)h->esz * h->nnz, kind, h->st));
     }
   } else {
+    if (h->opt.sketch == LP_SKETCH_COUNT) {
+      if (h->w > kCsMaxW)
+        return h->fail(LP_ERR_UNSUPPORTED, "sketch width w=%d above %d for the dense CountSketch", h->w, kCsMaxW);
+      if ((long long)h->n * h->s_blocks >= (1LL << 31))
+        return h->fail(LP_ERR_UNSUPPORTED, "n * s too large for the CountSketch bucket lists");
+      RET(h->alloc(&h->cs.count, (size_t)h->w + 1));
+      RET(h->alloc(&h->cs.base, (size_t)h->w + 1));
+      RET(h->alloc(&h->cs.cursor, (size_t)h->w + 1));
+      RET(h->alloc(&h->cs.list, (size_t)h->n * h->s_blocks));
+      RET(h->alloc(&h->cs.sc64, (size_t)h->n));
+      RET(h->alloc(&h->cs.scdf, (size_t)h->n));
+    }
     RET(h->alloc(reinterpret_cast<char**>(&h->A), (size_t)h->lda * h->n * h->esz));
     CK(cudaMemcpy2DAsync(h->A, (size_t)h->lda * h->esz, A->val, (size_t)A->ld * h->esz,
                          (size_t)h->m * h->esz, (size_t)h->n, kind, h->st));

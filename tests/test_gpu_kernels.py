@@ -96,22 +96,47 @@ def test_residual_rhs(mode, m, n, storage):
     assert sc["rd_norm"] == pytest.approx(np.linalg.norm(rd_ref), rel=1e-9)
 
 
-@pytest.mark.parametrize("m,n,storage,s_blocks", [(64, 4099, "f64", 2), (512, 20011, "f32", 4),
-                                                  (30, 1500, "bf16", 3), (8, 100, "f32", 1)])
-def test_countsketch_matches_oracle(m, n, storage, s_blocks):
+# FP32/BF16 storage sums in double-float arithmetic: products exact up to the
+# 2^-48 split of d_j / sqrt(s); the pair sums (renormalised every 8 steps) add
+# at most ~16 2^-48 of the bound per step, over at most twice the mean bucket
+# size n s / w of steps
+DF_U = 2.0 ** -48
+
+
+@pytest.mark.parametrize("m,n,storage,s_blocks,w", [
+    (64, 4099, "f64", 2, 0), (512, 20011, "f32", 4, 0), (30, 1500, "bf16", 3, 0), (8, 100, "f32", 1, 0),
+    (600, 5003, "f32", 2, 0), (520, 3001, "bf16", 2, 0), (130, 2000, "f64", 2, 0),
+    # buckets of ~10^4 columns: above the in-CTA sort capacity
+    (4, 40000, "f32", 1, 4), (6, 30000, "f64", 2, 6)])
+def test_countsketch_matches_oracle(m, n, storage, s_blocks, w):
     torch = torch_cuda()
     lp = _lp(m, n, storage, seed=4)
     rng = np.random.default_rng(5)
     D = np.exp(rng.uniform(-3, 3, n))
     seed, k, retry = 12345, 7, 1
-    with solver_for(lp, s=s_blocks) as S:
+    with solver_for(lp, s=s_blocks, w=w) as S:
         w = S.sketch_width
         adw = host(S.sketch(dev(torch, D), seed, k, retry))
     W = sketch.countsketch_matrix(seed, k, retry, n, w, s_blocks)
     ref = np.asarray((W.T @ (lp.A * D).T).T)
     bound = np.asarray((abs(W).T @ np.abs(lp.A * D).T).T)
     assert adw.shape == (m, w)
-    assert np.all(np.abs(adw - ref) <= 8 * n * EPS64 * bound + 1e-300)
+    eps = 8 * n * EPS64 if storage == "f64" else max(8 * n * EPS64, (32 * n * s_blocks / w + 64) * DF_U)
+    assert np.all(np.abs(adw - ref) <= eps * bound + 1e-300)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f64"])
+def test_countsketch_is_bitwise_reproducible(storage):
+    # the summation order depends only on the hashes, not on scheduling
+    torch = torch_cuda()
+    lp = _lp(300, 30011, storage, seed=13)
+    D = dev(torch, np.exp(np.random.default_rng(14).uniform(-4, 4, lp.n)))
+    with solver_for(lp, s=3) as S:
+        a = host(S.sketch(D, 99, 2, 0))
+        b = host(S.sketch(D, 99, 2, 0))
+        c = host(S.sketch(D, 99, 2, 1))
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    assert not np.array_equal(a, c)
 
 
 def test_precond_apply_is_q_inverse():
