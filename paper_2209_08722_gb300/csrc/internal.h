@@ -44,6 +44,13 @@ cudaError_t launch_gauss_tc(int dtype, const void* A, int lda, int m, long long 
 cudaError_t launch_gauss_v(long long n, const double* x, const double* s, const double* dvec,
                            int is_d2, const double* u, uint64_t seed, long long k, int retry, int w,
                            double scale, double* v, int num_sms, cudaStream_t st);
+// Gram (ADW)(ADW)^T in double-float: upper triangle of the column-major m x m
+// g; scratch holds gram_df_scratch_floats() floats
+void gram_df_split(int m, int w, int num_sms, int* ks, int* kper);
+size_t gram_df_scratch_floats(int m, int w, int num_sms);
+cudaError_t launch_gram_df(const double* x, int m, int w, float* scratch, double* g, int num_sms,
+                           cudaStream_t st);
+
 // scratch of the dense CountSketch: bucket sizes/offsets/cursors (w + 1 each),
 // bucket lists (n s), per-column scales (n)
 struct CsWork {

@@ -69,6 +69,7 @@ struct lp_handle {
   bool qinv_ok = false;  // explicit Q^{-1} formed for the current factor
   double* qinv = nullptr;
   CsWork cs;             // dense CountSketch scratch
+  float* gram_scratch = nullptr;  // double-float Gram: split ADW + split-K partials
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -281,16 +282,14 @@ int form_qinv(lp_handle* h) {
 // QR of (ADW)^T and R^{-1}; LP_ERR_SKETCH_RANK on a rank failure.
 int factor_qr(lp_handle* h);
 
-// Q = (ADW)(ADW)^T = R^T R by an FP64 Gram (cuBLAS DSYRK) and Cholesky; the
-// Gram squares kappa(ADW), which stays far below 1/eps_64 on the IPM path; if
-// the Cholesky breaks down the QR of (ADW)^T is used instead.
+// Q = (ADW)(ADW)^T = R^T R by a Gram in double-float arithmetic (FP64-class
+// accuracy on the FP32 pipe, gram.cu) and an FP64 Cholesky; the Gram squares
+// kappa(ADW), which stays far below the inverse unit roundoff on the IPM path;
+// if the Cholesky breaks down the QR of (ADW)^T is used instead.
 int factor(lp_handle* h) {
   const int m = h->m, w = h->w;
   if (h->blas) {
-    const double one = 1.0, zero = 0.0;
-    if (cublasDsyrk(h->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, m, w, &one, h->adw, w, &zero,
-                    h->rinv_cm, m) != CUBLAS_STATUS_SUCCESS)
-      return h->fail(LP_ERR_CUDA, "cublasDsyrk failed");
+    CK(launch_gram_df(h->adw, m, w, h->gram_scratch, h->rinv_cm, h->num_sms, h->st));
     CS(cusolverDnDpotrf(h->sol, CUBLAS_FILL_MODE_UPPER, m, h->rinv_cm, m,
                         static_cast<double*>(h->dwork), h->lwork_potrf, h->dinfo));
     CK(launch_factor_utils(0, h->rinv_cm, m, m, h->rinv_cm, h->sc, 0.0, h->num_sms, h->st));
@@ -759,6 +758,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->rinv_cm, (size_t)h->m * h->m));
   RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv, (size_t)h->m * h->m));
+  RET(h->alloc(&h->gram_scratch, gram_df_scratch_floats(h->m, h->w, h->num_sms)));
   RET(h->alloc(&h->uw, (size_t)h->w));
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));
