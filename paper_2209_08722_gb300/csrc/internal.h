@@ -51,6 +51,12 @@ size_t gram_df_scratch_floats(int m, int w, int num_sms);
 cudaError_t launch_gram_df(const double* x, int m, int w, float* scratch, double* g, int num_sms,
                            cudaStream_t st);
 
+// Q^{-1} from the upper triangle of the column-major Gram g by the blocked
+// symmetric sweep in double-float; rank check into sc (|R_ii| range)
+size_t sweep_scratch_floats(int m);
+cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, DevScalars* sc,
+                                 double rank_tol, int num_sms, cudaStream_t st);
+
 // scratch of the dense CountSketch: bucket sizes/offsets/cursors (w + 1 each),
 // bucket lists (n s), per-column scales (n)
 struct CsWork {

@@ -70,6 +70,8 @@ struct lp_handle {
   double* qinv = nullptr;
   CsWork cs;             // dense CountSketch scratch
   float* gram_scratch = nullptr;  // double-float Gram: split ADW + split-K partials
+  float* sweep_scratch = nullptr; // double-float sweep: two m x m iterates + pivots
+  long long sweep_fallbacks = 0;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -282,31 +284,47 @@ int form_qinv(lp_handle* h) {
 // QR of (ADW)^T and R^{-1}; LP_ERR_SKETCH_RANK on a rank failure.
 int factor_qr(lp_handle* h);
 
-// Q = (ADW)(ADW)^T = R^T R by a Gram in double-float arithmetic (FP64-class
-// accuracy on the FP32 pipe, gram.cu) and an FP64 Cholesky; the Gram squares
+// Cholesky of the Gram left in rinv_cm (upper triangle) by cuSOLVER potrf,
+// R^{-1} by trtri and Q^{-1} = R^{-1} R^{-T}; the fallback of the sweep.
+int factor_chol(lp_handle* h) {
+  const int m = h->m, w = h->w;
+  CS(cusolverDnDpotrf(h->sol, CUBLAS_FILL_MODE_UPPER, m, h->rinv_cm, m,
+                      static_cast<double*>(h->dwork), h->lwork_potrf, h->dinfo));
+  CK(launch_factor_utils(0, h->rinv_cm, m, m, h->rinv_cm, h->sc, 0.0, h->num_sms, h->st));
+  CK(launch_factor_utils(1, h->rinv_cm, m, m, nullptr, h->sc, 1e-13, h->num_sms, h->st));
+  CK(cudaMemcpyAsync(h->hinfo, h->dinfo, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  RET(sync_read(h));
+  if (h->hinfo[0] == 0 && !h->hsc->rank_bad) {
+    CS(cusolverDnXtrtri(h->sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, m, CUDA_R_64F,
+                        h->rinv_cm, m, h->dwork, h->dwork_bytes, h->hwork, h->hwork_bytes,
+                        h->dinfo + 1));
+    CK(launch_factor_utils(2, h->rinv_cm, w, m, h->rinv_rm, h->sc, 0.0, h->num_sms, h->st));
+    CK(cudaMemcpyAsync(h->hinfo + 1, h->dinfo + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    RET(sync_read(h));
+    if (h->hinfo[1] == 0) return form_qinv(h);
+  }
+  h->qr_fallbacks += 1;
+  return factor_qr(h);
+}
+
+// Q = (ADW)(ADW)^T by a Gram in double-float arithmetic (FP64-class accuracy
+// on the FP32 pipe, gram.cu) and Q^{-1} directly by the blocked symmetric
+// sweep (sweep.cu), whose pivots give the rank check.  The Gram squares
 // kappa(ADW), which stays far below the inverse unit roundoff on the IPM path;
-// if the Cholesky breaks down the QR of (ADW)^T is used instead.
+// if a pivot is not safely positive, the FP64 Cholesky of the same Gram and
+// then the QR of (ADW)^T are tried.
 int factor(lp_handle* h) {
   const int m = h->m, w = h->w;
-  if (h->blas) {
-    CK(launch_gram_df(h->adw, m, w, h->gram_scratch, h->rinv_cm, h->num_sms, h->st));
-    CS(cusolverDnDpotrf(h->sol, CUBLAS_FILL_MODE_UPPER, m, h->rinv_cm, m,
-                        static_cast<double*>(h->dwork), h->lwork_potrf, h->dinfo));
-    CK(launch_factor_utils(0, h->rinv_cm, m, m, h->rinv_cm, h->sc, 0.0, h->num_sms, h->st));
-    CK(launch_factor_utils(1, h->rinv_cm, m, m, nullptr, h->sc, 1e-13, h->num_sms, h->st));
-    CK(cudaMemcpyAsync(h->hinfo, h->dinfo, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-    RET(sync_read(h));
-    if (h->hinfo[0] == 0 && !h->hsc->rank_bad) {
-      CS(cusolverDnXtrtri(h->sol, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, m, CUDA_R_64F,
-                          h->rinv_cm, m, h->dwork, h->dwork_bytes, h->hwork, h->hwork_bytes,
-                          h->dinfo + 1));
-      CK(launch_factor_utils(2, h->rinv_cm, w, m, h->rinv_rm, h->sc, 0.0, h->num_sms, h->st));
-      CK(cudaMemcpyAsync(h->hinfo + 1, h->dinfo + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-      RET(sync_read(h));
-      if (h->hinfo[1] == 0) return form_qinv(h);
-    }
-    h->qr_fallbacks += 1;
+  h->qinv_ok = false;
+  CK(launch_gram_df(h->adw, m, w, h->gram_scratch, h->rinv_cm, h->num_sms, h->st));
+  CK(launch_sweep_inverse(h->rinv_cm, m, h->sweep_scratch, h->qinv, h->sc, 1e-13, h->num_sms, h->st));
+  RET(sync_read(h));
+  if (!h->hsc->rank_bad) {
+    h->qinv_ok = true;
+    return LP_OK;
   }
+  h->sweep_fallbacks += 1;
+  if (h->blas) return factor_chol(h);
   return factor_qr(h);
 }
 
@@ -506,10 +524,15 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
   // the precision of the factor: e = r - Q z, z += R^{-1} R^{-T} e.
   CK(launch_adwt(h->adw, h->m, h->w, h->z, h->adwt_part, h->adwt_parts, h->uw, h->num_sms, h->st));
   CK(launch_gemv_rows(h->adw, h->m, h->w, h->uw, h->r, 1.0, -1.0, h->mb0, h->num_sms, h->st));
-  CK(launch_gemv_tri(h->rinv_cm, h->m, 1, h->mb0, h->wv, GH_NONE, 0, nullptr, nullptr, nullptr,
-                     h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st));
-  CK(launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, h->z, GH_NONE, 0, nullptr, nullptr, nullptr,
-                     h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z));
+  if (h->qinv_ok) {
+    CK(launch_gemv_tri(h->qinv, h->m, 2, h->mb0, h->z, GH_NONE, 0, nullptr, nullptr, nullptr, h->sc,
+                       h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z));
+  } else {
+    CK(launch_gemv_tri(h->rinv_cm, h->m, 1, h->mb0, h->wv, GH_NONE, 0, nullptr, nullptr, nullptr,
+                       h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st));
+    CK(launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, h->z, GH_NONE, 0, nullptr, nullptr, nullptr,
+                       h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z));
+  }
   CK(launch_adwt(h->adw, h->m, h->w, h->z, h->adwt_part, h->adwt_parts, h->uw, h->num_sms, h->st));
   if (h->opt.sketch == LP_SKETCH_GAUSS)
     CK(launch_gauss_v(h->n, xs_x, xs_s, h->sk_dvec, h->sk_is_d2, h->uw, h->opt.seed, k, retry, h->w,
@@ -759,6 +782,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv, (size_t)h->m * h->m));
   RET(h->alloc(&h->gram_scratch, gram_df_scratch_floats(h->m, h->w, h->num_sms)));
+  RET(h->alloc(&h->sweep_scratch, sweep_scratch_floats(h->m)));
   RET(h->alloc(&h->uw, (size_t)h->w));
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));
