@@ -24,8 +24,10 @@ int fused_vpl(int lda, int esz);
 cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
                           const StreamPlan& p, cudaStream_t st);
 cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
-cudaError_t launch_adat_df(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
-bool adat_df_supported(int lda, int esz);
+// double-float streaming passes (M_ADAT, M_RESID, M_DIR) for FP32/BF16 storage
+cudaError_t launch_stream_df(int dtype, int mode, const StreamArgs& a, const StreamPlan& p,
+                             cudaStream_t st);
+bool stream_df_supported(int mode, int lda, int esz, const StreamPlan& p);
 
 int sparse_grid(int num_sms);
 cudaError_t launch_sparse(int dtype, bool fp64, int mode, const StreamArgs& a, int grid,

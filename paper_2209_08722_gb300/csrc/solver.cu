@@ -58,6 +58,7 @@ struct lp_handle {
   long long qr_fallbacks = 0;
   long long cheb_fallbacks = 0;
   bool use_df = false;   // double-float kernel for the FP64-accurate products
+  bool use_df_resid = false, use_df_dir = false;  // ... and for the residual / direction passes
   bool sparse = false;   // CSC storage
   const double* sk_dvec = nullptr;  // D (or D^2) used by the current sketch
   int sk_is_d2 = 0;
@@ -241,7 +242,7 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
   cudaError_t e;
   if (h->sparse) e = launch_sparse(h->dtype, use64, M_ADAT, a, h->sp_grid, h->st);
   else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st);
-  else if (h->use_df) e = launch_adat_df(h->dtype, a, h->plan, h->st);
+  else if (h->use_df) e = launch_stream_df(h->dtype, M_ADAT, a, h->plan, h->st);
   else e = launch_stream(h->dtype, true, M_ADAT, a, h->plan, h->st);
   if (ev) cudaEventRecord(ev->b, h->st);
   if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "adat launch: %s", cudaGetErrorString(e));
@@ -573,6 +574,7 @@ int residual_pass(lp_handle* h, bool feasible) {
   a.out_m1 = h->p;
   a.bvec = h->b;
   if (h->sparse) CK(launch_sparse(h->dtype, true, M_RESID, a, h->sp_grid, h->st));
+  else if (h->use_df_resid) CK(launch_stream_df(h->dtype, M_RESID, a, h->plan, h->st));
   else CK(launch_stream(h->dtype, true, M_RESID, a, h->plan, h->st));
   return LP_OK;
 }
@@ -592,6 +594,7 @@ int direction_pass(lp_handle* h, bool feasible) {
   a.red_partials = h->red_partials;
   a.epilogue = E_DIR;
   if (h->sparse) CK(launch_sparse(h->dtype, true, M_DIR, a, h->sp_grid, h->st));
+  else if (h->use_df_dir) CK(launch_stream_df(h->dtype, M_DIR, a, h->plan, h->st));
   else CK(launch_stream(h->dtype, true, M_DIR, a, h->plan, h->st));
   return LP_OK;
 }
@@ -724,9 +727,9 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   }
   // kernel shape limits
   if (!h->sparse) h->plan = make_stream_plan(h->m, h->n, h->lda, h->esz, h->num_sms, 4);
-  h->use_df = !h->sparse && h->dtype != LP_F64 && adat_df_supported(h->lda, h->esz) &&
-              (long long)(fused_vpl(h->lda, h->esz) >= 8 ? 8 : 16) * h->lda * 8 <=
-                  (long long)h->plan.stages * make_layout(h->lda, h->esz, h->plan.nb, h->plan.stages, 8).stage_bytes;
+  h->use_df = !h->sparse && h->dtype != LP_F64 && stream_df_supported(M_ADAT, h->lda, h->esz, h->plan);
+  h->use_df_resid = !h->sparse && h->dtype != LP_F64 && stream_df_supported(M_RESID, h->lda, h->esz, h->plan);
+  h->use_df_dir = !h->sparse && h->dtype != LP_F64 && stream_df_supported(M_DIR, h->lda, h->esz, h->plan);
   if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
   if (!h->sparse && h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0)
     return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the fused product kernel", h->m);
