@@ -41,3 +41,45 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol)
 }
 
 }  // namespace lpk
+
+namespace lpk {
+
+// ---- double-float values for scalar formulas (normalised results) ----
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl dfl_make(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+
+__device__ __forceinline__ dfl dfl_neg(dfl a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return dfl_make(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ dfl dfl_sub(dfl a, dfl b) { return dfl_add(a, dfl_neg(b)); }
+
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return dfl_make(p, e);
+}
+
+// a / b: FP32 quotient, then one correction from the exact remainder
+__device__ __forceinline__ dfl dfl_div(dfl a, dfl b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const float p = __fmul_rn(q1, b.h);
+  const float pe = fmaf(q1, b.h, -p);
+  // r = a - q1 b, its leading part a.h - p is exact (Sterbenz)
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.h, p), pe), __fsub_rn(a.l, __fmul_rn(q1, b.l)));
+  return dfl_make(q1, __fdiv_rn(r, b.h));
+}
+
+}  // namespace lpk

@@ -24,6 +24,31 @@ int fused_vpl(int lda, int esz);
 cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
                           const StreamPlan& p, cudaStream_t st);
 cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
+// FP64 n-vectors <-> FP32 pairs for the double-float streaming passes
+struct DfPackArgs {
+  const double* src[4];
+  float2* dst[4];
+  int k;
+  long long n;
+};
+struct DfUnpackArgs {
+  int mode;  // 0: residual pass (r_d, d2, fl32(d2)); 1: direction pass (dx, ds)
+  long long n;
+  const float2* df0;
+  const float2* df1;
+  double* out0;
+  double* out1;
+  float* outf;
+  const double* x;
+  const double* s;
+  const double* c;
+  DevScalars* sc;
+  double* part;     // [2 x grid] partial column sums
+  unsigned* ticket;
+};
+cudaError_t launch_df_pack(const DfPackArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_df_unpack(const DfUnpackArgs& a, int num_sms, cudaStream_t st);
+
 // double-float streaming passes (M_ADAT, M_RESID, M_DIR) for FP32/BF16 storage
 cudaError_t launch_stream_df(int dtype, int mode, const StreamArgs& a, const StreamPlan& p,
                              cudaStream_t st);

@@ -59,6 +59,11 @@ struct lp_handle {
   long long cheb_fallbacks = 0;
   bool use_df = false;   // double-float kernel for the FP64-accurate products
   bool use_df_resid = false, use_df_dir = false;  // ... and for the residual / direction passes
+  float2* dfin[4] = {nullptr, nullptr, nullptr, nullptr};  // packed per-column inputs
+  float2* dfout[2] = {nullptr, nullptr};                   // per-column outputs as pairs
+  float2* d2df = nullptr;  // d2 as pairs for the double-float refresh
+  float2* cdf = nullptr;   // c as pairs (constant)
+  bool d2df_valid = false;
   bool sparse = false;   // CSC storage
   const double* sk_dvec = nullptr;  // D (or D^2) used by the current sketch
   int sk_is_d2 = 0;
@@ -222,7 +227,13 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
                 double* out_m0) {
   StreamArgs a = base_args(h);
   const bool use64 = fp64 || h->dtype == LP_F64;
-  a.cv[0] = use64 ? (const void*)h->d2d : (const void*)h->d2f;
+  const bool dfk = use64 && !h->sparse && h->use_df;
+  if (dfk && !h->d2df_valid) {
+    DfPackArgs pk{{h->d2d}, {h->d2df}, 1, h->n};
+    CK(launch_df_pack(pk, h->num_sms, h->st));
+    h->d2df_valid = true;
+  }
+  a.cv[0] = dfk ? (const void*)h->d2df : (use64 ? (const void*)h->d2d : (const void*)h->d2f);
   a.cv_esz[0] = use64 ? 8 : 4;
   a.ncv = 1;
   a.vin = vin;
@@ -573,8 +584,25 @@ int residual_pass(lp_handle* h, bool feasible) {
   a.out_m0 = h->rp;
   a.out_m1 = h->p;
   a.bvec = h->b;
+  if (!h->sparse && h->use_df_resid) {
+    // double-float pass: x, s (and the constant c) as pairs in, r_d and d2 as pairs out
+    DfPackArgs pk{{h->x, h->s}, {h->dfin[0], h->dfin[1]}, 2, h->n};
+    CK(launch_df_pack(pk, h->num_sms, h->st));
+    a.cv[0] = h->dfin[0];
+    a.cv[1] = h->dfin[1];
+    a.cv[2] = h->cdf;
+    a.out_df[0] = h->dfout[0];
+    a.out_df[1] = h->d2df;
+    a.red_partials = nullptr;
+    CK(launch_stream_df(h->dtype, M_RESID, a, h->plan, h->st));
+    DfUnpackArgs up{0, h->n, h->dfout[0], h->d2df, h->rd, h->d2d, h->d2f, h->x, h->s, h->c, h->sc,
+                    h->vpart, h->tickets + 7};
+    CK(launch_df_unpack(up, h->num_sms, h->st));
+    h->d2df_valid = true;
+    return LP_OK;
+  }
+  h->d2df_valid = false;
   if (h->sparse) CK(launch_sparse(h->dtype, true, M_RESID, a, h->sp_grid, h->st));
-  else if (h->use_df_resid) CK(launch_stream_df(h->dtype, M_RESID, a, h->plan, h->st));
   else CK(launch_stream(h->dtype, true, M_RESID, a, h->plan, h->st));
   return LP_OK;
 }
@@ -594,7 +622,24 @@ int direction_pass(lp_handle* h, bool feasible) {
   a.red_partials = h->red_partials;
   a.epilogue = E_DIR;
   if (h->sparse) CK(launch_sparse(h->dtype, true, M_DIR, a, h->sp_grid, h->st));
-  else if (h->use_df_dir) CK(launch_stream_df(h->dtype, M_DIR, a, h->plan, h->st));
+  else if (h->use_df_dir) {
+    // double-float pass: x, s, v, r_d as pairs in, dx and ds as pairs out
+    DfPackArgs pk{{h->x, h->s, h->v, h->rd}, {h->dfin[0], h->dfin[1], h->dfin[2], h->dfin[3]},
+                  feasible ? 3 : 4, h->n};
+    CK(launch_df_pack(pk, h->num_sms, h->st));
+    for (int q = 0; q < 4; ++q) {
+      a.cv[q] = h->dfin[q];
+      a.cv_esz[q] = 8;
+    }
+    a.ncv = feasible ? 3 : 4;
+    a.out_df[0] = h->dfout[0];
+    a.out_df[1] = h->dfout[1];
+    a.red_partials = nullptr;
+    CK(launch_stream_df(h->dtype, M_DIR, a, h->plan, h->st));
+    DfUnpackArgs up{1, h->n, h->dfout[0], h->dfout[1], h->dx, h->ds, nullptr, h->x, h->s, nullptr, h->sc,
+                    h->vpart, h->tickets + 7};
+    CK(launch_df_unpack(up, h->num_sms, h->st));
+  }
   else CK(launch_stream(h->dtype, true, M_DIR, a, h->plan, h->st));
   return LP_OK;
 }
@@ -769,6 +814,12 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
                       &h->nb0, &h->nb1, &h->nb2};
   for (double** p : nvecs) RET(h->alloc(p, n));
   RET(h->alloc(&h->d2f, n));
+  if (!h->sparse && h->dtype != LP_F64) {
+    for (int q = 0; q < 4; ++q) RET(h->alloc(&h->dfin[q], n));
+    for (int q = 0; q < 2; ++q) RET(h->alloc(&h->dfout[q], n));
+    RET(h->alloc(&h->d2df, n));
+    RET(h->alloc(&h->cdf, n));
+  }
   double** mvecs[] = {&h->b, &h->rp, &h->p, &h->dy, &h->r, &h->z, &h->pdir, &h->q, &h->wv,
                       &h->mb0, &h->mb1};
   for (double** p : mvecs) RET(h->alloc(p, m + 64));
@@ -777,6 +828,10 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
                      bc_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(h->c, c, sizeof(double) * h->n,
                      bc_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+  if (h->cdf) {
+    DfPackArgs pk{{h->c}, {h->cdf}, 1, h->n};
+    CK(launch_df_pack(pk, h->num_sms, h->st));
+  }
   const size_t mw = (size_t)h->m * h->w;
   RET(h->alloc(&h->adw, mw));
   RET(h->alloc(&h->qr, mw));
@@ -849,6 +904,7 @@ int lp_adat(lp_handle* h, const double* d2, const double* v, double* u, int32_t 
   if (!h || !d2 || !v || !u) return LP_ERR_ARG;
   h->err.clear();
   CK(cudaMemcpyAsync(h->d2d, d2, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
+  h->d2df_valid = false;
   CK(launch_to_f32(h->n, h->d2d, h->d2f, 0, h->num_sms, h->st));
   CK(cudaMemcpyAsync(h->mb0, v, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, h->st));
   CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
@@ -987,6 +1043,7 @@ int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double
   RET(copy_in(h, h->nb0, D, h->n, io_on_device));
   RET(copy_in(h, h->p, p, h->m, io_on_device));
   CK(launch_square(h->n, h->nb0, h->d2d, h->num_sms, h->st));
+  h->d2df_valid = false;
   CK(launch_to_f32(h->n, h->nb0, h->d2f, 1, h->num_sms, h->st));
   int retry = 0;
   RET(sketch_and_factor(h, h->nb0, 0, k, &retry));

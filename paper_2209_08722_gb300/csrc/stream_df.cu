@@ -14,10 +14,12 @@
 //   * the m-vector v (FP64) is split once into vh + vl in shared memory;
 //     a * vh is formed exactly as p + e with an FMA, a * vl in FP32;
 //   * sums use the error-free TwoSum, keeping the compensation in lo;
-//   * per column, lane 0 forms the column scalars (d2_j (a_j^T v), or the
-//     residual/direction formulas) in FP64, splits them into FP32 pairs and
-//     broadcasts them; the rank-1 updates acc += a_j t_j use the same exact
-//     products.
+//   * the per-column inputs (d2, or x, s, c / x, s, v, r_d) arrive as FP32
+//     pairs (packed from the FP64 vectors by k_df_pack) and lane 0 forms the
+//     column scalars (d2_j (a_j^T v), or the residual/direction formulas) in
+//     double-float and broadcasts them; the rank-1 updates acc += a_j t_j use
+//     the same exact products.  Per-column outputs are written as pairs and
+//     unpacked to FP64 (with the column sums the epilogues need) afterwards.
 // The relative error of each sum is about 2^-46 of the sum of |terms|.
 // Pipeline: one producer warp issues bulk copies of column tiles into a ring
 // of stages; CW consumer warps take whole columns (warp-per-column), keep the
@@ -35,6 +37,12 @@ namespace {
 __device__ __forceinline__ void split_df(double v, float& h, float& l) {
   h = (float)v;
   l = (float)(v - (double)h);
+}
+
+// per-column input q of the current tile, stored as FP32 pairs
+__device__ __forceinline__ dfl cv_df(const char* stage, const SmemLayout& L, int q, int jj) {
+  const float2 v = reinterpret_cast<const float2*>(stage + L.cv_off[q])[jj];
+  return {v.x, v.y};
 }
 }  // namespace
 
@@ -56,7 +64,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
   const int RV = a.lda / VEC;
   const int S = a.stages;
   const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const double sigma_mu = (MODE == M_RESID || MODE == M_DIR) ? a.sigma * a.sc->mu : 0.0;
+  dfl smu = {0.0f, 0.0f};  // sigma mu as a pair (one FP64 product per CTA)
+  if (MODE == M_RESID || MODE == M_DIR) {
+    const double v = a.sigma * a.sc->mu;
+    smu.h = (float)v;
+    smu.l = (float)(v - (double)smu.h);
+  }
 
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
@@ -78,7 +91,6 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
   for (int c = 0; c < (NACC > 1 ? VPL : 1); ++c)
 #pragma unroll
     for (int e = 0; e < VEC; ++e) bh[c][e] = bl[c][e] = 0.0f;
-  double cred0 = 0.0, cred1 = 0.0;  // column reductions (lane 0)
   bool aborted = false;
 
   if (warp == CW) {
@@ -133,41 +145,43 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
           const float ol = __shfl_xor_sync(0xffffffffu, sl[0], o);
           df_add(sh[0], sl[0], oh, ol);
         }
-        // ---- per-column scalars, in FP64 on lane 0 ----
+        // ---- per-column scalars, in double-float on lane 0 (the FP64 pipe
+        // would serialise them: a one-lane FP64 instruction costs the pipe as
+        // much as a full warp's) ----
         float t0h = 0.0f, t0l = 0.0f, t1h = 0.0f, t1l = 0.0f;
         if (lane == 0) {
-          const double dot = (double)sh[0] + (double)sl[0];
+          const dfl dot = dfl_make(sh[0], sl[0]);
           const long long j = j0 + jj;
-          double t0 = 0.0, t1 = 0.0;
+          dfl t0 = {0.0f, 0.0f}, t1 = {0.0f, 0.0f};
           if (MODE == M_ADAT) {
-            t0 = cv_at(stage, L, a, 0, jj) * dot;
+            t0 = dfl_mul(cv_df(stage, L, 0, jj), dot);
           } else if (MODE == M_RESID) {
-            const double x = cv_at(stage, L, a, 0, jj);
-            const double s = cv_at(stage, L, a, 1, jj);
-            const double c = cv_at(stage, L, a, 2, jj);
-            const double rd = dot + s - c;
-            const double d2 = x / s;
-            a.out_col[0][j] = rd;
-            a.out_col[1][j] = d2;
-            a.out_colf[j] = (float)d2;
+            const dfl x = cv_df(stage, L, 0, jj);
+            const dfl s = cv_df(stage, L, 1, jj);
+            const dfl c = cv_df(stage, L, 2, jj);
+            const dfl rd = dfl_sub(dfl_add(dot, s), c);
+            const dfl d2 = dfl_div(x, s);
+            a.out_df[0][j] = make_float2(rd.h, rd.l);
+            a.out_df[1][j] = make_float2(d2.h, d2.l);
             t0 = x;
-            t1 = a.feasible ? (x - sigma_mu / s) : (x - sigma_mu / s - d2 * rd);
-            cred0 += rd * rd;
-            cred1 += c * x;
+            const dfl xc = dfl_sub(x, dfl_div(smu, s));
+            t1 = a.feasible ? xc : dfl_sub(xc, dfl_mul(d2, rd));
           } else if (MODE == M_DIR) {
-            const double x = cv_at(stage, L, a, 0, jj);
-            const double s = cv_at(stage, L, a, 1, jj);
-            const double v = cv_at(stage, L, a, 2, jj);
-            const double rd = a.feasible ? 0.0 : cv_at(stage, L, a, 3, jj);
-            const double ds = -rd - dot;
-            const double dx = -x + sigma_mu / s - (x / s) * ds - v / s;
-            a.out_col[0][j] = dx;
-            a.out_col[1][j] = ds;
-            cred0 += x * ds + s * dx;
-            cred1 += dx * ds;
+            const dfl x = cv_df(stage, L, 0, jj);
+            const dfl s = cv_df(stage, L, 1, jj);
+            const dfl v = cv_df(stage, L, 2, jj);
+            const dfl rd = a.feasible ? dfl{0.0f, 0.0f} : cv_df(stage, L, 3, jj);
+            const dfl ds = dfl_neg(dfl_add(rd, dot));
+            // dx = -x + (sigma mu - x ds - v) / s
+            const dfl num = dfl_sub(dfl_sub(smu, dfl_mul(x, ds)), v);
+            const dfl dx = dfl_sub(dfl_div(num, s), x);
+            a.out_df[0][j] = make_float2(dx.h, dx.l);
+            a.out_df[1][j] = make_float2(ds.h, ds.l);
           }
-          if (NACC > 0) split_df(t0, t0h, t0l);
-          if (NACC > 1) split_df(t1, t1h, t1l);
+          t0h = t0.h;
+          t0l = t0.l;
+          t1h = t1.h;
+          t1l = t1.l;
         }
         if (NACC > 0) {
           t0h = __shfl_sync(0xffffffffu, t0h, 0);
@@ -216,14 +230,6 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
       part[r] = aborted ? 0.0 : (double)h + (double)l;
     }
     __syncthreads();
-  }
-  if (a.red_partials) {
-    const double r0 = block_sum(lane == 0 && warp < CW ? cred0 : 0.0, red);
-    const double r1 = block_sum(lane == 0 && warp < CW ? cred1 : 0.0, red);
-    if (tid == 0) {
-      a.red_partials[2 * blockIdx.x] = r0;
-      a.red_partials[2 * blockIdx.x + 1] = r1;
-    }
   }
   if (a.epilogue == E_NONE) return;
   if (tree_reduce<double>(a, NACC, &s_flag)) stream_epilogue<double>(a, NACC, red);

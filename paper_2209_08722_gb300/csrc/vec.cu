@@ -375,9 +375,11 @@ __global__ void k_update(long long n, int m, double* x, double* s, double* y, co
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
   if (!last_block_ticket(ticket, &s_flag)) return;
+  // fixed-order block-parallel sum of the partials
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+  t = block_sum(t, red);
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(part + b);
     sc->xs_next = t;
     sc->mu = t / (double)n;
   }
