@@ -81,8 +81,8 @@ cudaError_t launch_gram_df(const double* x, int m, int w, float* scratch, double
 // Q^{-1} from the upper triangle of the column-major Gram g by the blocked
 // symmetric sweep in double-float; rank check into sc (|R_ii| range)
 size_t sweep_scratch_floats(int m);
-cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, DevScalars* sc,
-                                 double rank_tol, int num_sms, cudaStream_t st);
+cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, float2* qinv_df,
+                                 DevScalars* sc, double rank_tol, int num_sms, cudaStream_t st);
 
 // scratch of the dense CountSketch: bucket sizes/offsets/cursors (w + 1 each),
 // bucket lists (n s), per-column scales (n)
@@ -110,7 +110,8 @@ enum GemvEpiHost : int {
 cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
-                            cudaStream_t st, const double* y_add = nullptr);
+                            cudaStream_t st, const double* y_add = nullptr,
+                            const float2* Mdf = nullptr);
 cudaError_t launch_gemv_rows(const double* M, int rows, int cols, const double* x, const double* y0,
                              double alpha, double beta, double* y, int num_sms, cudaStream_t st);
 cudaError_t launch_cheb_pre(int m, double* dy, const double* dir, DevScalars* sc, cudaStream_t st);

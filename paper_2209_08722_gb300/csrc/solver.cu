@@ -74,6 +74,8 @@ struct lp_handle {
   int sp_grid = 0;
   bool qinv_ok = false;  // explicit Q^{-1} formed for the current factor
   double* qinv = nullptr;
+  bool qinv_df_ok = false;  // ... and as FP32 pairs (the sweep's output), for the double-float GEMV
+  float2* qinv_df = nullptr;
   CsWork cs;             // dense CountSketch scratch
   float* gram_scratch = nullptr;  // double-float Gram: split ADW + split-K partials
   float* sweep_scratch = nullptr; // double-float sweep: two m x m iterates + pivots
@@ -261,10 +263,10 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
 }
 
 int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_level) {
-  if (h->qinv_ok) {  // one full GEMV with the explicit Q^{-1} = R^{-1} R^{-T}
+  if (h->qinv_ok) {  // one full GEMV with the explicit Q^{-1} (as pairs when the sweep formed it)
     cudaError_t e = launch_gemv_tri(h->qinv, h->m, 2, r, z, epi, skip_level, h->r, h->pdir, h->dy,
                                     h->sc, h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef,
-                                    h->num_sms, h->st);
+                                    h->num_sms, h->st, nullptr, h->qinv_df_ok ? h->qinv_df : nullptr);
     if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
     return LP_OK;
   }
@@ -329,10 +331,14 @@ int factor(lp_handle* h) {
   const int m = h->m, w = h->w;
   h->qinv_ok = false;
   CK(launch_gram_df(h->adw, m, w, h->gram_scratch, h->rinv_cm, h->num_sms, h->st));
-  CK(launch_sweep_inverse(h->rinv_cm, m, h->sweep_scratch, h->qinv, h->sc, 1e-13, h->num_sms, h->st));
+  h->qinv_df_ok = false;
+  // Q^{-1} is kept as pairs only: the double-float GEMV applies it
+  CK(launch_sweep_inverse(h->rinv_cm, m, h->sweep_scratch, nullptr, h->qinv_df, h->sc, 1e-13, h->num_sms,
+                          h->st));
   RET(sync_read(h));
   if (!h->hsc->rank_bad) {
     h->qinv_ok = true;
+    h->qinv_df_ok = true;
     return LP_OK;
   }
   h->sweep_fallbacks += 1;
@@ -538,7 +544,8 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
   CK(launch_gemv_rows(h->adw, h->m, h->w, h->uw, h->r, 1.0, -1.0, h->mb0, h->num_sms, h->st));
   if (h->qinv_ok) {
     CK(launch_gemv_tri(h->qinv, h->m, 2, h->mb0, h->z, GH_NONE, 0, nullptr, nullptr, nullptr, h->sc,
-                       h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z));
+                       h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st, h->z,
+                       h->qinv_df_ok ? h->qinv_df : nullptr));
   } else {
     CK(launch_gemv_tri(h->rinv_cm, h->m, 1, h->mb0, h->wv, GH_NONE, 0, nullptr, nullptr, nullptr,
                        h->sc, h->tickets + 1, &h->sc->err, 0, nullptr, h->num_sms, h->st));
@@ -839,6 +846,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->rinv_cm, (size_t)h->m * h->m));
   RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv, (size_t)h->m * h->m));
+  RET(h->alloc(&h->qinv_df, (size_t)h->m * h->m));
   RET(h->alloc(&h->gram_scratch, gram_df_scratch_floats(h->m, h->w, h->num_sms)));
   RET(h->alloc(&h->sweep_scratch, sweep_scratch_floats(h->m)));
   RET(h->alloc(&h->uw, (size_t)h->w));

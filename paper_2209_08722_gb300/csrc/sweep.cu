@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restri
 __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ ah, const float* __restrict__ al,
                                                       int m, int mp, const double* __restrict__ scale,
                                                       const float* __restrict__ piv, double* __restrict__ qinv,
-                                                      DevScalars* sc, double rank_tol) {
+                                                      float2* __restrict__ qinv_df, DevScalars* sc,
+                                                      double rank_tol) {
   __shared__ double red[32];
   const double s = *scale;
   if (blockIdx.x == 0) {
@@ -265,12 +266,15 @@ __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ 
       sc->rank_bad = (any_bad || !(mn > rank_tol * mx) || !isfinite(mx)) ? 1 : 0;
     }
   }
+  // -2^-e A as pairs: scaling by a power of two is exact in FP32 as well
+  const int e = ilogb(s);
   const long long total = (long long)m * m;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / m), j = (int)(t % m);
     const size_t src = (size_t)i * mp + j;
-    qinv[t] = -((double)ah[src] + (double)al[src]) / s;
+    if (qinv) qinv[t] = -ldexp((double)ah[src] + (double)al[src], -e);
+    if (qinv_df) qinv_df[t] = make_float2(-ldexpf(ah[src], -e), -ldexpf(al[src], -e));
   }
 }
 
@@ -280,8 +284,8 @@ size_t sweep_scratch_floats(int m) {
 }
 
 // G: upper triangle of the column-major m x m Gram; qinv: m x m output
-cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, DevScalars* sc,
-                                 double rank_tol, int num_sms, cudaStream_t st) {
+cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, float2* qinv_df,
+                                 DevScalars* sc, double rank_tol, int num_sms, cudaStream_t st) {
   const int mp = (m + SB - 1) / SB * SB;
   const size_t mm = (size_t)mp * mp;
   float* a0h = scratch;
@@ -304,7 +308,8 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   const bool in0 = (nt & 1) == 0;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   const int g2 = (int)std::max<long long>(1, std::min<long long>(((long long)m * m + 255) / 256, (long long)num_sms * 4));
-  k_sweep_finish<<<g2, 256, 0, st>>>(in0 ? a0h : a1h, in0 ? a0l : a1l, m, mp, scale_buf, piv, qinv, sc, rank_tol);
+  k_sweep_finish<<<g2, 256, 0, st>>>(in0 ? a0h : a1h, in0 ? a0l : a1l, m, mp, scale_buf, piv, qinv, qinv_df, sc,
+                                     rank_tol);
   return cudaGetLastError();
 }
 

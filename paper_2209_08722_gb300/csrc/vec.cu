@@ -9,6 +9,7 @@
 //   - small utilities (dot products, FP32 copies, R extraction, rank check).
 // All arithmetic here is FP64.
 #include "internal.h"
+#include "df.cuh"
 
 namespace lpk {
 
@@ -44,6 +45,7 @@ struct GemvArgs {
   int t_max;
   double* coef;      // G_PCG_B: beta of CG step j stored at coef[2j+1]
   const double* y_add;  // G_NONE: y = y_add + M x when non-null
+  const float2* Mdf;    // full M as FP32 pairs (used instead of M when non-null)
 };
 
 __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
@@ -54,6 +56,64 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   const int warps_per_block = blockDim.x >> 5;
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = gridDim.x * warps_per_block;
+  if (a.Mdf) {
+    // full rows in double-float on the FP32 pipe: x split into pairs in shared
+    // memory once per CTA, each warp one row, FP64 only for the row result
+    extern __shared__ float2 xs[];
+    for (int j0 = 0; j0 < a.m; j0 += 4 * (int)blockDim.x) {
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = j0 + k * (int)blockDim.x + (int)threadIdx.x;
+        v[k] = j < a.m ? a.x[j] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = j0 + k * (int)blockDim.x + (int)threadIdx.x;
+        const float h = (float)v[k];
+        if (j < a.m) xs[j] = make_float2(h, (float)(v[k] - (double)h));
+      }
+    }
+    __syncthreads();
+    for (int i = gw; i < a.m; i += nw) {
+      const float2* row = a.Mdf + (size_t)i * a.m;
+      float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
+      // 8 row entries per lane in flight at once: the row loads are the latency
+      for (int j0 = 0; j0 < a.m; j0 += 8 * 32) {
+        float2 q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int j = j0 + k * 32 + lane;
+          q[k] = j < a.m ? __ldg(row + j) : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int j = j0 + k * 32 + lane;
+          const float2 v = j < a.m ? xs[j] : make_float2(0.0f, 0.0f);
+          // (qh + ql)(vh + vl): exact product of the high parts plus the cross terms
+          const float pr = __fmul_rn(q[k].x, v.x);
+          float e = fmaf(q[k].x, v.x, -pr);
+          e = fmaf(q[k].x, v.y, e);
+          e = fmaf(q[k].y, v.x, e);
+          float t, c;
+          two_sum(sh[k & 1], pr, t, c);
+          sh[k & 1] = t;
+          sl[k & 1] = __fadd_rn(sl[k & 1], __fadd_rn(c, e));
+        }
+      }
+      df_add(sh[0], sl[0], sh[1], sl[1]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh[0], o);
+        const float ol = __shfl_xor_sync(0xffffffffu, sl[0], o);
+        df_add(sh[0], sl[0], oh, ol);
+      }
+      if (lane == 0) {
+        const double acc = (double)sh[0] + (double)sl[0];
+        a.y[i] = a.y_add ? a.y_add[i] + acc : acc;
+      }
+    }
+  } else
   for (int i = gw; i < a.m; i += nw) {
     // lower == 1: columns [0, i]; 0: [i, m); 2: the full row
     const int lo = a.lower ? 0 : i;
@@ -156,13 +216,19 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
 cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
-                            cudaStream_t st, const double* y_add) {
-  GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef, y_add};
-  const int warps = 8;
+                            cudaStream_t st, const double* y_add, const float2* Mdf) {
+  if (Mdf && lower != 2) return cudaErrorInvalidValue;
+  GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef, y_add, Mdf};
+  const int warps = Mdf ? 4 : 8;
   int grid = (m + warps - 1) / warps;
   grid = std::max(1, std::min(grid, num_sms * 4));
+  const size_t smem = Mdf ? (size_t)m * sizeof(float2) : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemv_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  k_gemv_tri<<<grid, warps * 32, 0, st>>>(a);
+  k_gemv_tri<<<grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
