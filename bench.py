@@ -114,6 +114,21 @@ def make_lp(seed: int):
     return lpgen.planted_dense(M, N_COLS, seed=seed, storage="f32", col_scale_log10=(-2.0, 2.0))
 
 
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own LP of the same family (replicas, weak scaling)."""
+    return rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time: the whole job is done only when every replica is."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample(lp, budget_s: float = 20.0):
     """Times the CPU oracle (exact-Cholesky IPM) on the full LP for a bounded
     number of outer iterations, and counts the outer iterations it needs on the
@@ -274,7 +289,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    lp = make_lp(rank)
+    lp = make_lp(replica_seed(rank))
     stream = torch.cuda.current_stream()
     solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=S_BLOCKS,
                       w_factor=W_FACTOR, profile=1, stream=stream.cuda_stream)
@@ -297,10 +312,7 @@ def main():
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     stats = solver.kernel_stats()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     obj_err = abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective))
     assert all(i["status"] == 0 for i in infos), infos
@@ -329,11 +341,7 @@ def main():
         assert inf2["status"] == 0
         if it >= args.warmup:
             e2e_ms.append(dt)
-    e2e = float(np.mean(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(float(np.mean(e2e_ms)), dist, "cuda")
 
     if rank != 0:
         if dist is not None:
