@@ -97,6 +97,9 @@ typedef struct {
     void* stream;          /* cudaStream_t to run on, or NULL for a private stream */
     int32_t tensor_sketch; /* Gaussian sketch with FP32/BF16 A: 1 = tcgen05 tensor-core GEMM,
                               0 = FP32 SIMT kernel; 1 */
+    int32_t precondition;  /* 1 = the paper's method (sketch, Q^{-1}, correction v);
+                              0 = the standard IPM of Section 7's comparison: unpreconditioned
+                              CG on eq. normal (Q = I), no sketch, v = 0; 1 */
 } lp_options;
 
 /* ---- results -------------------------------------------------------------- */

@@ -42,7 +42,7 @@ class Options:
     tol: float = 1e-8
     k_max: int = 200
     mode: str = "infeasible"    # "feasible" (Alg. 2) or "infeasible" (Alg. 3)
-    solver: str = "exact"       # "exact" (Cholesky, v = 0) or "sketch"
+    solver: str = "exact"       # "exact" (Cholesky, v = 0), "sketch", or "cg" (unpreconditioned)
     sketch: str = "countsketch"  # or "gaussian"
     w: Optional[int] = None     # sketch width (default 4m)
     s: int = 2                  # nonzeros per row of a CountSketch
@@ -307,6 +307,25 @@ def normal_solve(A, x, s, p, opt: Options, k: int, inner_tol: float,
                        precond=pre, ADW=ADW, retry=retry, lam=lam)
 
 
+def normal_solve_unpreconditioned(A, x, s, p, opt: Options, inner_tol: float) -> NormalSolve:
+    """The standard IPM's inner solve (the comparison system of Section 7):
+    CG on eq. (normal) itself, i.e. Q = I in eq. (precond), and no correction
+    (v = 0, there is no sketch).  ||f|| = ||p - A D^2 A^T dy||."""
+    m, n = A.shape
+    d2 = x / s
+
+    def Mmv(z):
+        return A @ (d2 * (A.T @ z))
+
+    f0 = float(np.linalg.norm(p))
+    tol = inner_tol if opt.inner_rule == "theory" else opt.tol_cg * f0
+    tr = pcg.cg(Mmv, p, opt.t_max, tol)
+    dy = tr.z
+    f_norm = float(np.linalg.norm(Mmv(dy) - p))
+    return NormalSolve(dy=dy, v=np.zeros(n), z=dy, trace=tr, f_norm=f_norm, f0_norm=f0,
+                       precond=None, ADW=None, retry=0, lam=(0.0, 0.0))
+
+
 def _cg_coeffs(Bmv, rhs_, steps):
     r = rhs_.copy()
     d = r.copy()
@@ -382,6 +401,13 @@ def solve(A, b, c, opt: Options, x0=None, y0=None, s0=None) -> Result:
             cf = sla.cho_factor(M)
             dy = sla.cho_solve(cf, p)
             v = np.zeros(n)
+        elif opt.solver == "cg":
+            tol_f = pcg.theory_inner_tol(mu, n, opt.gamma, opt.sigma)
+            ns = normal_solve_unpreconditioned(A, x, s, p, opt, tol_f)
+            dy, v = ns.dy, ns.v
+            rec.inner_its = ns.trace.iterations
+            rec.f_norm = ns.f_norm
+            rec.f0_norm = ns.f0_norm
         else:
             tol_f = pcg.theory_inner_tol(mu, n, opt.gamma, opt.sigma)
             ns = normal_solve(A, x, s, p, opt, k, tol_f)

@@ -52,7 +52,8 @@ class LpOptions(ctypes.Structure):
                 ("inner", c_int32), ("refine_every", c_int32), ("k_max", c_int32),
                 ("t_max", c_int32), ("v_correction", c_int32), ("cheb_lanczos", c_int32),
                 ("profile", c_int32), ("w_factor", c_double), ("w", c_int64),
-                ("seed", c_uint64), ("stream", c_void_p), ("tensor_sketch", c_int32)]
+                ("seed", c_uint64), ("stream", c_void_p), ("tensor_sketch", c_int32),
+                ("precondition", c_int32)]
 
 
 class LpResult(ctypes.Structure):

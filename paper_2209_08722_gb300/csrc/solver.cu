@@ -263,6 +263,12 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
 }
 
 int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_level) {
+  if (!h->opt.precondition) {  // Q = I: z = r, then the same CG / Chebyshev epilogue
+    cudaError_t e = launch_gemv_tri(nullptr, h->m, 2, r, z, epi, skip_level, h->r, h->pdir, h->dy, h->sc,
+                                    h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st);
+    if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
+    return LP_OK;
+  }
   if (h->qinv_ok) {  // one full GEMV with the explicit Q^{-1} (as pairs when the sweep formed it)
     cudaError_t e = launch_gemv_tri(h->qinv, h->m, 2, r, z, epi, skip_level, h->r, h->pdir, h->dy,
                                     h->sc, h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef,
@@ -384,6 +390,10 @@ cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t 
 
 // sketch for (k, retry) + factor, redrawing on a rank failure (Lemma 4.1)
 int sketch_and_factor(lp_handle* h, const double* dvec, int is_d2, long long k, int* retries) {
+  if (!h->opt.precondition) {  // the unpreconditioned comparison: no sketch, no factor
+    *retries = 0;
+    return LP_OK;
+  }
   int rc = LP_ERR_SKETCH_RANK;
   for (int retry = 0; retry < kMaxRetry; ++retry) {
     CK(launch_sketch(h, dvec, is_d2, h->opt.seed, k, retry));
@@ -533,7 +543,7 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
 // v = (XS)^{1/2} W (ADW)^T Q^{-1} (M dy - p); the last refresh left r = p - M dy
 // and z = Q^{-1} r, so (ADW)^+ (M dy - p) = -(ADW)^T z.
 int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k, int retry) {
-  if (!h->opt.v_correction) {
+  if (!h->opt.v_correction || !h->opt.precondition) {
     CK(cudaMemsetAsync(h->v, 0, sizeof(double) * h->npad, h->st));
     return LP_OK;
   }
@@ -662,6 +672,7 @@ void options_check(const lp_options* o, std::string* why) {
   else if (!(o->gamma > 0 && o->gamma < 1)) *why = "gamma must be in (0, 1)";
   else if (o->s < 1 || o->s > kMaxBlocks) *why = "s must be in [1, 16]";
   else if (o->sketch != LP_SKETCH_COUNT && o->sketch != LP_SKETCH_GAUSS) *why = "unknown sketch";
+  else if (o->precondition != 0 && o->precondition != 1) *why = "precondition must be 0 or 1";
   else if (o->inner != LP_INNER_CG && o->inner != LP_INNER_CHEBYSHEV) *why = "inner must be CG or Chebyshev";
   else if (o->t_max < 1 || o->k_max < 0) *why = "t_max >= 1 and k_max >= 0 required";
 }
@@ -694,6 +705,7 @@ void lp_options_default(lp_options* o) {
   o->seed = 0;
   o->stream = nullptr;
   o->tensor_sketch = 1;
+  o->precondition = 1;
 }
 
 const char* lp_create_error(void) { return g_create_error.c_str(); }

@@ -56,7 +56,11 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   const int warps_per_block = blockDim.x >> 5;
   const int gw = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int nw = gridDim.x * warps_per_block;
-  if (a.Mdf) {
+  if (!a.M && !a.Mdf) {
+    // identity (no preconditioner): y = x
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.m; i += gridDim.x * blockDim.x)
+      a.y[i] = a.y_add ? a.y_add[i] + a.x[i] : a.x[i];
+  } else if (a.Mdf) {
     // full rows in double-float on the FP32 pipe: x split into pairs in shared
     // memory once per CTA, each warp one row, FP64 only for the row result
     extern __shared__ float2 xs[];
@@ -217,7 +221,7 @@ cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, 
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
                             cudaStream_t st, const double* y_add, const float2* Mdf) {
-  if (Mdf && lower != 2) return cudaErrorInvalidValue;
+  if ((Mdf || !M) && lower != 2) return cudaErrorInvalidValue;
   GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef, y_add, Mdf};
   const int warps = Mdf ? 4 : 8;
   int grid = (m + warps - 1) / warps;

@@ -114,3 +114,31 @@ def test_tiny_lp_matches_vertex_enumeration():
         x, y, s, info = S.solve(tol=1e-9)
     assert info["status"] == 0
     assert abs(lp.c @ x - best) <= 1e-7 * (1 + abs(best))
+
+
+def test_standard_ipm_plain_cg_needs_10x_more_inner_steps():
+    # Section 7 / Tables 1-2: precondition = 0 is the standard IPM with
+    # unpreconditioned CG (Q = I, v = 0); with the experiments' relative inner
+    # rule, over the outer iterations the sketched method needs, plain CG
+    # takes >= 10x the inner steps on a column-scaled LP
+    lp = lpgen.planted_dense(64, 8000, seed=37, storage="f32", col_scale_log10=(-2, 2))
+    common = dict(s=2, inner_rule=1, tol_cg=1e-5, t_max=20000)
+    with solver_for(lp, k_max=60, **common) as S:
+        _, _, _, sk = S.solve(tol=1e-8)
+    assert sk["status"] == 0, sk
+    with solver_for(lp, precondition=0, k_max=sk["outer_iterations"], **common) as S:
+        _, _, _, plain = S.solve(tol=1e-8)
+    assert plain["inner_total"] >= 10 * sk["inner_total"], (plain["inner_total"], sk["inner_total"])
+
+
+def test_w_sweep_inner_iterations_fall_with_w():
+    # Figures 2-3 qualitatively: a wider sketch is a better embedding, so the
+    # mean inner iteration count falls as w grows (same LP, same outer path)
+    lp = lpgen.planted_dense(64, 8000, seed=38, storage="f32", col_scale_log10=(-2, 2))
+    means = []
+    for wf in (2.0, 4.0, 16.0):
+        with solver_for(lp, s=2, w_factor=wf) as S:
+            _, _, _, info = S.solve(tol=1e-8)
+        assert info["status"] == 0, info
+        means.append(info["inner_total"] / info["outer_iterations"])
+    assert means[0] > means[1] > means[2], means

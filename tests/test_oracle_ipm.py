@@ -226,6 +226,53 @@ def test_sketched_cg_needs_far_fewer_inner_iterations_than_plain_cg():
     assert plain.iterations >= 10 * ns.trace.iterations
 
 
+def test_unpreconditioned_normal_solve_is_cg_on_eq_normal():
+    # the comparison system: Q = I, so at a tight tolerance dy is the Cholesky
+    # solution, and there is no correction vector
+    rng = np.random.default_rng(31)
+    m, n = 20, 400
+    A = rng.standard_normal((m, n))
+    x, s = np.exp(rng.uniform(-1, 1, n)), np.exp(rng.uniform(-1, 1, n))
+    p = rng.standard_normal(m)
+    M = (A * (x / s)) @ A.T
+    exact = np.linalg.solve(M, p)
+    opt = ipm.Options(solver="cg", inner_rule="relative", tol_cg=1e-13, t_max=500)
+    ns = ipm.normal_solve_unpreconditioned(A, x, s, p, opt, inner_tol=0.0)
+    assert np.linalg.norm(ns.dy - exact) <= 1e-9 * np.linalg.norm(exact)
+    assert not ns.v.any()
+    assert ns.f_norm <= 1e-12 * np.linalg.norm(p)
+
+
+def test_standard_ipm_with_plain_cg_vs_sketched_inner_counts():
+    # Section 7 / Tables 1-2 qualitatively, at the IPM level: with the
+    # experiments' relative inner rule the sketched method converges, and over
+    # the same outer iterations the standard IPM's plain CG needs >= 10x more
+    # inner steps on a column-scaled LP
+    m, n = 64, 3000
+    lp = lpgen.planted_dense(m, n, seed=32, storage="f64", col_scale_log10=(-2, 2))
+    common = dict(mode="infeasible", inner_rule="relative", tol_cg=1e-5, t_max=20000)
+    sk = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(solver="sketch", w=4 * m, s=2, k_max=60, **common))
+    assert sk.status == "optimal"
+    plain = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(solver="cg", k_max=sk.iterations, **common))
+    n_plain = sum(r.inner_its for r in plain.history)
+    n_sk = sum(r.inner_its for r in sk.history)
+    assert n_plain >= 10 * n_sk, (n_plain, n_sk)
+
+
+def test_w_sweep_inner_iterations_fall_with_w():
+    # Figures 2-3 qualitatively: a wider sketch embeds better (Lemma 3.1), so
+    # the mean inner iteration count falls as w grows
+    m, n = 64, 3000
+    lp = lpgen.planted_dense(m, n, seed=33, storage="f64", col_scale_log10=(-2, 2))
+    means = []
+    for wf in (2, 4, 16):
+        r = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(solver="sketch", w=wf * m, s=2))
+        assert r.status == "optimal"
+        its = [h.inner_its for h in r.history if h.inner_its]
+        means.append(sum(its) / len(its))
+    assert means[0] > means[1] > means[2], means
+
+
 # ---------------------------------------------------------------------------
 # step lengths
 # ---------------------------------------------------------------------------
