@@ -51,7 +51,8 @@ typedef struct lp_handle lp_handle;
 #define LP_ERR_UNSUPPORTED     -8  /* valid request this build does not implement */
 #define LP_STATUS_MAX_ITER      1  /* lp_solve: k_max outer iterations reached */
 #define LP_WARN_INNER_MAXIT     2  /* an inner solve stopped at t_max */
-#define LP_STATUS_STALLED       3  /* lp_solve: step length reached zero */
+#define LP_STATUS_STALLED       3  /* lp_solve: step length reached zero, or mu fell far below the gap
+                                      tolerance while a residual test still fails */
 
 /* ---- matrix description -------------------------------------------------- */
 typedef enum { LP_DENSE_COLMAJOR = 0, LP_CSC = 1 } lp_format;
@@ -262,6 +263,32 @@ int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
  * LP_ERR_DEVICE_TIMEOUT. */
 int lp_adat_noalloc(const void* A, int32_t dtype, int32_t m, int64_t n, int64_t ld,
                     const double* d2, const double* v, double* u, void* stream);
+
+/* Phase-1 primal start (Appendix "Feasible starting point").
+ * Rows with b_i < 0 are negated; then the LP
+ *     min 1^T z  s.t.  A x + I z = b,  x, z >= 0          (m x (n+m) constraint matrix)
+ * is solved by this library's infeasible-start IPM (Algorithm 3, same options)
+ * to relative tolerance tol (1e-7 is ample: the start only needs z small next
+ * to x, and the phase-1 optimal face is usually unbounded, which makes tight
+ * tolerances slow).  A x = b, x >= 0 is feasible exactly when its
+ * optimum has z = 0; the interior x > 0 it returns is then moved onto A x = b by
+ * the minimum-norm correction x0 = x + A^T (A A^T)^{-1} (b - A x), computed with
+ * the sketched normal-equation solver (D = I).
+ * A: host matrix (dense column-major or CSC, any storage dtype); b: host m-vector;
+ * opt: NULL for defaults; x0: caller-owned host n-vector, written when the LP is
+ * found feasible.  Returns LP_OK with x0 > 0 and A x0 = b to rounding,
+ * LP_ERR_NOT_FEASIBLE when the phase-1 optimum 1^T z exceeds
+ * 1e-6 (1 + ||b||) (info->z_sum holds it), LP_ERR_NUMERICAL when the
+ * correction leaves some x0_j <= 0, or the error of the inner calls. */
+typedef struct {
+    double z_sum;               /* 1^T z at the phase-1 solution */
+    double residual;            /* ||A x0 - b|| after the correction */
+    double x0_min;              /* min_j x0_j */
+    int32_t outer_iterations;   /* of the phase-1 IPM */
+    int64_t inner_total;
+} lp_phase1_info;
+int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt, double tol,
+                    double* x0, lp_phase1_info* info);
 
 /* Statistics of the hot product kernel (requires opt.profile = 1). */
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);

@@ -27,3 +27,4 @@ from .planted import (  # noqa: F401
     config_small,
     CONFIGS,
 )
+from .random_lp import RandomLP, random_lp  # noqa: F401

@@ -88,6 +88,14 @@ class LpIterRecord(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class LpPhase1Info(ctypes.Structure):
+    _fields_ = [("z_sum", c_double), ("residual", c_double), ("x0_min", c_double),
+                ("outer_iterations", c_int32), ("inner_total", c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LpKernelStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("ms", c_double), ("bytes_per_launch", c_int64),
                 ("all_launches", c_int64)]
@@ -112,6 +120,8 @@ SIGNATURES = {
     "lp_step_lengths": (c_int32, [P, P, P, P, P, c_int32, c_double, c_double, P]),
     "lp_get_history": (c_int32, [P, POINTER(LpIterRecord), c_int32]),
     "lp_adat_noalloc": (c_int32, [P, c_int32, c_int32, c_int64, c_int64, P, P, P, P]),
+    "lp_phase1_start": (c_int32, [POINTER(LpMatrix), P, POINTER(LpOptions), c_double, P,
+                                  POINTER(LpPhase1Info)]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }

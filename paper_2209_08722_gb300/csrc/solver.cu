@@ -80,6 +80,8 @@ struct lp_handle {
   float* gram_scratch = nullptr;  // double-float Gram: split ADW + split-K partials
   float* sweep_scratch = nullptr; // double-float sweep: two m x m iterates + pivots
   long long sweep_fallbacks = 0;
+  long long breakdown_recoveries = 0;  // inner solves that switched product after a CG breakdown
+  long long qr_refactors = 0;          // inner solves rerun after refactoring by QR
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -355,6 +357,8 @@ int factor(lp_handle* h) {
 // Q = R^T R from the QR of (ADW)^T (cuSOLVER geqrf), R^{-1} by trtri.
 int factor_qr(lp_handle* h) {
   const int m = h->m, w = h->w;
+  h->qinv_ok = false;
+  h->qinv_df_ok = false;
   CK(cudaMemcpyAsync(h->qr, h->adw, sizeof(double) * (size_t)m * w, cudaMemcpyDeviceToDevice, h->st));
   CS(cusolverDnDgeqrf(h->sol, w, m, h->qr, w, h->tau, static_cast<double*>(h->dwork),
                       h->lwork_geqrf, h->dinfo));
@@ -516,6 +520,26 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
     // FP64 true residual r = p - M dy, ||f|| = sqrt(r^T Q^{-1} r)
     RET(launch_adat(h, h->dy, E_TRUE_RES, true, 2, nullptr));
     RET(precond_gemvs(h, h->r, h->z, inner == LP_INNER_CHEBYSHEV ? GH_CHEB_REFRESH : GH_REFRESH, 2));
+    CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (h->hsc->err == ERR_NUMERICAL && !use64) {
+      // A CG breakdown (p^T M p <= 0 or a non-finite value) with the FP32
+      // product, on a matrix too ill-conditioned for it: the step that broke
+      // was not applied, so continue from the current iterate with the
+      // FP64-class product, restarting the recurrence from the true residual.
+      use64 = true;
+      h->breakdown_recoveries += 1;
+      CK(cudaMemsetAsync(&h->sc->err, 0, sizeof(int), h->st));
+      CK(cudaMemsetAsync(&h->sc->inner_done, 0, sizeof(int), h->st));
+      RET(set_scalar(h, &h->sc->f_rec, 0.0));  // forces beta = 0 at the refresh
+      if (inner == LP_INNER_CHEBYSHEV) inner = LP_INNER_CG;
+      RET(launch_adat(h, h->dy, E_TRUE_RES, true, 0, nullptr));
+      RET(precond_gemvs(h, h->r, h->z, GH_REFRESH, 0));
+      RET(sync_read(h));
+      f_prev = h->hsc->f_true;
+      if (h->hsc->inner_done == 2) break;
+      continue;
+    }
     RET(sync_read(h));
     if (h->opt.profile) ev_flush(h);
     if (h->hsc->inner_done == 2) break;
@@ -538,6 +562,31 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
   }
   *iters_out = total_iters + h->hsc->inner_iters;
   return status;
+}
+
+// inner_solve, and once more after refactoring by the QR of (ADW)^T when the
+// iteration limit was hit with the sweep's Q^{-1}: the sweep works on the Gram,
+// which squares kappa(ADW), and near degenerate vertices (or with s = 1) its
+// double-float accuracy can stop being enough for a useful preconditioner.
+int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out) {
+  int st = inner_solve(h, tol_f, iters_out);
+  // a small t_max is the caller's choice, not a sign of a failed preconditioner
+  if (st != LP_WARN_INNER_MAXIT || h->opt.t_max < 50 || !h->opt.precondition || !h->qinv_df_ok)
+    return st;
+  h->qr_refactors += 1;
+  const int rc = factor_qr(h);
+  if (rc == LP_ERR_SKETCH_RANK) {
+    // the QR judges this sketch rank deficient: keep the first solve and restore
+    // its factor (deterministic, so z = Q^{-1} r from the last refresh still holds)
+    h->err.clear();
+    RET(factor(h));
+    return st;
+  }
+  if (rc != LP_OK) return rc;
+  int more = 0;
+  st = inner_solve(h, tol_f, &more);
+  *iters_out += more;
+  return st;
 }
 
 // v = (XS)^{1/2} W (ADW)^T Q^{-1} (M dy - p); the last refresh left r = p - M dy
@@ -1068,7 +1117,7 @@ int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double
   int retry = 0;
   RET(sketch_and_factor(h, h->nb0, 0, k, &retry));
   int iters = 0;
-  const int status = inner_solve(h, tol_f, &iters);
+  const int status = inner_solve_robust(h, tol_f, &iters);
   if (status < 0) return status;
   const double f_true = h->hsc->f_true, f0 = sqrt(std::max(h->hsc->rho0, 0.0));
   double vnorm = 0.0;
@@ -1177,6 +1226,13 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
       status = LP_OK;
       break;
     }
+    // mu has fallen far below what the gap test needs while a residual test
+    // still fails: the residuals have stopped following (1 - alpha) r (the
+    // inexact solves' floor); further iterations only drive mu to underflow
+    if (S.mu <= 1e-3 * tol * mu0 && gap <= tol) {
+      status = LP_STATUS_STALLED;
+      break;
+    }
     if (k == h->opt.k_max) break;
     const double mu = S.mu;
     const double res_ratio = feasible ? 0.0 : sqrt(S.rp2 + S.rd2) / r0;
@@ -1192,7 +1248,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
                              ? h->opt.gamma * h->opt.sigma * sqrt(mu) / (4.0 * sqrt(3.0 * (double)n))
                              : 0.0;
     int iters = 0;
-    const int ist = inner_solve(h, tol_f, &iters);
+    const int ist = inner_solve_robust(h, tol_f, &iters);
     if (ist < 0) return ist;
     {
       lp_iter_record& hr = h->history.back();
@@ -1235,6 +1291,147 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   res.ms_step = ms_step;
   if (info) *info = res;
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// phase-1 primal start (Appendix "Feasible starting point")
+// ---------------------------------------------------------------------------
+namespace {
+// element (row i, column j) of a host matrix of any storage dtype, sign-flipped
+void put_neg(int dtype, void* dst, size_t idx, const void* src, size_t sidx, bool neg) {
+  if (dtype == LP_F64) {
+    const double v = static_cast<const double*>(src)[sidx];
+    static_cast<double*>(dst)[idx] = neg ? -v : v;
+  } else if (dtype == LP_F32) {
+    const float v = static_cast<const float*>(src)[sidx];
+    static_cast<float*>(dst)[idx] = neg ? -v : v;
+  } else {
+    const uint16_t v = static_cast<const uint16_t*>(src)[sidx];
+    static_cast<uint16_t*>(dst)[idx] = neg ? (uint16_t)(v ^ 0x8000u) : v;  // bf16 sign bit
+  }
+}
+
+void put_one(int dtype, void* dst, size_t idx) {
+  if (dtype == LP_F64) static_cast<double*>(dst)[idx] = 1.0;
+  else if (dtype == LP_F32) static_cast<float*>(dst)[idx] = 1.0f;
+  else static_cast<uint16_t*>(dst)[idx] = 0x3F80u;  // bf16 1.0
+}
+}  // namespace
+
+int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt_in, double tol,
+                    double* x0, lp_phase1_info* info) {
+  if (!A || !b || !x0 || !(tol > 0) || A->on_device || A->m <= 0 || A->n <= 0) return LP_ERR_ARG;
+  if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC) return LP_ERR_ARG;
+  if (A->dtype != LP_F64 && A->dtype != LP_F32 && A->dtype != LP_BF16) return LP_ERR_ARG;
+  if (A->fmt == LP_DENSE_COLMAJOR && A->ld < A->m) return LP_ERR_ARG;
+  const int m = A->m;
+  const long long n = A->n, n1 = n + m;
+  const int esz = A->dtype == LP_F64 ? 8 : (A->dtype == LP_F32 ? 4 : 2);
+  lp_options opt;
+  if (opt_in) opt = *opt_in;
+  else lp_options_default(&opt);
+  std::vector<char> neg(m);
+  std::vector<double> b1(m), c1(n1, 0.0), zero_c(n, 0.0);
+  double bnorm = 0.0;
+  for (int i = 0; i < m; ++i) {
+    neg[i] = b[i] < 0;
+    b1[i] = std::fabs(b[i]);
+    bnorm += b[i] * b[i];
+  }
+  bnorm = std::sqrt(bnorm);
+  for (long long j = n; j < n1; ++j) c1[j] = 1.0;
+  // [A | I] with the rows of negative b negated, same storage dtype and format
+  lp_matrix A1 = *A;
+  A1.n = n1;
+  std::vector<char> val1;
+  std::vector<int64_t> ptr1;
+  std::vector<int32_t> idx1;
+  if (A->fmt == LP_DENSE_COLMAJOR) {
+    A1.ld = m;
+    val1.assign((size_t)m * n1 * esz, 0);
+    for (long long j = 0; j < n; ++j)
+      for (int i = 0; i < m; ++i)
+        put_neg(A->dtype, val1.data(), (size_t)j * m + i, A->val, (size_t)j * A->ld + i, neg[i] != 0);
+    for (int i = 0; i < m; ++i) put_one(A->dtype, val1.data(), (size_t)(n + i) * m + i);
+    A1.val = val1.data();
+  } else {
+    const int64_t nnz = A->ptr[n] - A->ptr[0];
+    ptr1.resize(n1 + 1);
+    idx1.resize(nnz + m);
+    val1.assign((size_t)(nnz + m) * esz, 0);
+    for (long long j = 0; j <= n; ++j) ptr1[j] = A->ptr[j] - A->ptr[0];
+    for (int64_t e = 0; e < nnz; ++e) {
+      const int32_t i = A->idx[A->ptr[0] + e];
+      if (i < 0 || i >= m) return LP_ERR_ARG;
+      idx1[e] = i;
+      put_neg(A->dtype, val1.data(), (size_t)e, A->val, (size_t)(A->ptr[0] + e), neg[i] != 0);
+    }
+    for (int i = 0; i < m; ++i) {
+      idx1[nnz + i] = i;
+      put_one(A->dtype, val1.data(), (size_t)(nnz + i));
+      ptr1[n + i + 1] = nnz + i + 1;
+    }
+    A1.val = val1.data();
+    A1.ptr = ptr1.data();
+    A1.idx = idx1.data();
+    A1.nnz = nnz + m;
+  }
+  // phase-1 IPM from the usual infeasible start
+  lp_handle* h1 = nullptr;
+  int rc = lp_create(&h1, &A1, b1.data(), c1.data(), 0, &opt);
+  if (rc != LP_OK) return rc;
+  std::vector<double> x1(n1), y1(m), s1(n1);
+  lp_result r1;
+  rc = lp_solve(h1, tol, LP_INFEASIBLE, nullptr, nullptr, nullptr, 0, x1.data(), y1.data(), s1.data(), &r1);
+  lp_destroy(h1);
+  if (rc < 0) return rc;
+  double z_sum = 0.0;
+  for (int i = 0; i < m; ++i) z_sum += x1[n + i];
+  lp_phase1_info inf{};
+  inf.z_sum = z_sum;
+  inf.outer_iterations = r1.outer_iterations;
+  inf.inner_total = r1.inner_total;
+  if (info) *info = inf;
+  if (!(z_sum <= 1e-6 * (1.0 + bnorm))) return LP_ERR_NOT_FEASIBLE;
+  // minimum-norm correction onto A x = b: x0 = x + A^T (A A^T)^{-1} (b - A x)
+  lp_handle* h = nullptr;
+  lp_options o0 = opt;
+  o0.inner_rule = LP_RULE_RELATIVE;
+  o0.tol_cg = 1e-13;
+  rc = lp_create(&h, A, b, zero_c.data(), 0, &o0);
+  if (rc != LP_OK) return rc;
+  auto run = [&]() -> int {
+    RET(copy_in(h, h->x, x1.data(), (size_t)n, 0));
+    CK(launch_fill(n, h->s, 1.0, h->num_sms, h->st));
+    CK(cudaMemsetAsync(h->y, 0, sizeof(double) * m, h->st));
+    CK(cudaMemsetAsync(h->v, 0, sizeof(double) * h->npad, h->st));
+    RET(set_scalar(h, &h->sc->mu, 0.0));
+    RET(residual_pass(h, true));                                  // rp = A x - b
+    CK(launch_axpby(m, -1.0, h->rp, 0.0, h->rp, h->p, h->num_sms, h->st));  // p = b - A x
+    CK(launch_fill(n, h->d2d, 1.0, h->num_sms, h->st));               // D = I
+    CK(launch_to_f32(n, h->d2d, h->d2f, 0, h->num_sms, h->st));
+    h->d2df_valid = false;
+    int retry = 0;
+    RET(sketch_and_factor(h, h->d2d, 1, 0, &retry));
+    int iters = 0;
+    const int st = inner_solve_robust(h, 0.0, &iters);              // dy = (A A^T)^{-1} p
+    if (st < 0) return st;
+    RET(direction_pass(h, true));                                   // ds = -A^T dy
+    CK(launch_axpby(n, 1.0, h->x, -1.0, h->ds, h->x, h->num_sms, h->st));  // x0 = x - ds
+    RET(residual_pass(h, true));                                    // ||A x0 - b||
+    RET(copy_out(h, x0, h->x, (size_t)n, 0));
+    RET(sync_read(h));
+    inf.residual = std::sqrt(h->hsc->rp2);
+    return LP_OK;
+  };
+  rc = run();
+  lp_destroy(h);
+  if (rc < 0) return rc;
+  double xmin = INFINITY;
+  for (long long j = 0; j < n; ++j) xmin = std::min(xmin, x0[j]);
+  inf.x0_min = xmin;
+  if (info) *info = inf;
+  return xmin > 0.0 ? LP_OK : LP_ERR_NUMERICAL;
 }
 
 }  // extern "C"

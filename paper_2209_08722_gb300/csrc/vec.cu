@@ -467,6 +467,22 @@ cudaError_t launch_update(long long n, int m, double* x, double* s, double* y, c
 // ---------------------------------------------------------------------------
 // utilities
 // ---------------------------------------------------------------------------
+// out = alpha x + beta y
+__global__ void k_axpby(long long n, double alpha, const double* __restrict__ x, double beta,
+                        const double* __restrict__ y, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = alpha * x[i] + beta * y[i];
+}
+
+cudaError_t launch_axpby(long long n, double alpha, const double* x, double beta, const double* y,
+                         double* out, int num_sms, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)num_sms * 4));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_axpby<<<grid, 256, 0, st>>>(n, alpha, x, beta, y, out);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill(long long n, double* x, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)

@@ -288,3 +288,45 @@ def from_planted(lp, device: bool = False, **options) -> LPSolver:
         b = torch.from_numpy(np.ascontiguousarray(b)).cuda()
         c = torch.from_numpy(np.ascontiguousarray(c)).cuda()
     return LPSolver(A, b, c, lp.m, lp.n, dtype=lp.storage, **options)
+
+
+def phase1_start(A, b, m: int, n: int, dtype: str = "f64", csc=None, tol: float = 1e-7, **options):
+    """lp_phase1_start: a strictly positive x0 with A x0 = b (Appendix
+    "Feasible starting point"), from host arrays.  tol is the phase-1 IPM's
+    tolerance: the start only needs z small next to x before the exact
+    correction, and the phase-1 optimal face is usually unbounded.  A is the (n, m) C-contiguous
+    column-major buffer (or csc=(col_ptr, row_idx, values)).  Returns
+    (x0, info); raises LPError with code LP_ERR_NOT_FEASIBLE when the phase-1
+    optimum shows A x = b, x >= 0 infeasible."""
+    lib = nat.load()
+    opt = nat.LpOptions()
+    lib.lp_options_default(ctypes.byref(opt))
+    for k, v in options.items():
+        if not hasattr(opt, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(opt, k, v)
+    if csc is not None:
+        cp = np.ascontiguousarray(csc[0], dtype=np.int64)
+        ri = np.ascontiguousarray(csc[1], dtype=np.int32)
+        vals = np.ascontiguousarray(csc[2], dtype=_NP_DT[dtype])
+        keep = (cp, ri, vals)
+        mat = nat.LpMatrix(m=m, n=n, fmt=nat.LP_CSC, dtype=_DTYPES[dtype], val=_ptr(vals), ld=0,
+                           ptr=_ptr(cp), idx=_ptr(ri), nnz=int(vals.shape[0]), on_device=0)
+    else:
+        A = np.ascontiguousarray(A, dtype=_NP_DT[dtype])
+        if A.shape != (n, m):
+            raise ValueError("A must have shape (n, m) (column-major)")
+        keep = (A,)
+        mat = nat.LpMatrix(m=m, n=n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype], val=_ptr(A),
+                           ld=m, ptr=None, idx=None, nnz=0, on_device=0)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x0 = np.empty(n, dtype=np.float64)
+    info = nat.LpPhase1Info()
+    rc = lib.lp_phase1_start(ctypes.byref(mat), _ptr(b), ctypes.byref(opt), float(tol), _ptr(x0),
+                             ctypes.byref(info))
+    del keep
+    if rc < 0:
+        err = LPError(rc, "phase-1 start failed")
+        err.info = info.as_dict()
+        raise err
+    return x0, info.as_dict()
