@@ -254,6 +254,39 @@ def run_gauss_kernel(args):
     return 0
 
 
+def run_batch(args):
+    """Batched-LP family (m ~ U{32..512}, n = m U{64..256}, FP32, CountSketch
+    w = 4m, s = 2): the same LPs solved one at a time and with lp_solve_batch
+    (concurrent handles, one stream each); wall time of each, LPs per second."""
+    import torch
+    from paper_2209_08722_gb300 import LPSolver, solve_batch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lps = lpgen.batch_family(args.batch, seed=0)
+    solvers = [LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=2) for lp in lps]
+    for S in solvers:                       # warm-up: every kernel shape once
+        S.solve(tol=TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [S.solve(tol=TOL) for S in solvers]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    bat = solve_batch(solvers, tol=TOL)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    optimal = sum(1 for lp, b in zip(lps, bat) if b[3]["status"] == 0
+                  and abs(float(lp.c @ b[0]) - lp.objective) <= 1e-7 * (1 + abs(lp.objective)))
+    same = all(np.array_equal(a[0], b[0]) for a, b in zip(seq, bat))
+    print(json.dumps({"mode": "batch", "lps": len(lps), "total_bytes_A": int(sum(lp.m * lp.n * 4 for lp in lps)),
+                      "sequential_s": t_seq, "batched_s": t_bat, "lps_per_s": len(lps) / t_bat,
+                      "speedup": t_seq / t_bat, "optimal": optimal,
+                      "statuses": [b[3]["status"] for b in bat], "identical_to_sequential": same}),
+          flush=True)
+    for S in solvers:
+        S.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -261,12 +294,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time N LPs of the batched family one at a time and batched")
     ap.add_argument("--kernel", choices=["adat", "gauss", "gauss-simt"], default=None,
                     help="time one kernel on the same A: the hot product (lp_adat, FP32), or the "
                          "Gaussian sketch on the tensor cores / FP32 SIMT")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     if args.kernel in ("gauss", "gauss-simt"):
         return run_gauss_kernel(args)
     if args.kernel:

@@ -186,6 +186,20 @@ int lp_solve(lp_handle* h, double tol, int32_t mode,
              const double* x0, const double* y0, const double* s0, int32_t io_on_device,
              double* x, double* y, double* s, lp_result* info);
 
+/* Batched solve of independent LPs (one handle each, created with its own
+ * stream: opt.stream = NULL): lp_solve(hs[i], tol, mode, default start, ...)
+ * for i < count, run concurrently by up to max_threads host workers (0: one per
+ * LP, at most 64), so the kernels of different LPs overlap on the GPU.
+ * x, y, s: arrays of count output pointers (entries may be NULL), all host or
+ * all device (io_on_device); results: count entries (nullable).  The LPs may
+ * have different sizes.  Returns LP_OK when every solve returned a
+ * non-negative status (per-LP statuses are in results[i].status), else the
+ * first error in index order.  Handles must not be shared between batches
+ * running at the same time. */
+int lp_solve_batch(lp_handle* const* hs, int32_t count, double tol, int32_t mode,
+                   int32_t io_on_device, double* const* x, double* const* y, double* const* s,
+                   int32_t max_threads, lp_result* results);
+
 /* One inexact normal-equation solve A D^2 A^T dy = p (Algorithm 1 + eq. compv)
  * with the sketch drawn for outer-iteration index k.  D (n) is the diagonal of
  * D; p (m) the right-hand side.  tol_f > 0: stop when ||f^(t)|| <= tol_f;

@@ -26,5 +26,6 @@ from .planted import (  # noqa: F401
     feasible_start,
     config_small,
     CONFIGS,
+    batch_family,
 )
 from .random_lp import RandomLP, random_lp  # noqa: F401

@@ -278,3 +278,16 @@ def config_small(name: str, div: int = 8, seed: Optional[int] = None) -> Planted
     """The named workload with m and n divided by ``div`` (CI-sized)."""
     cfg = CONFIGS[name]
     return make(cfg, m=max(4, cfg["m"] // div), n=max(16, cfg["n"] // div), seed=seed)
+
+
+def batch_family(count: int, seed: int = 0, m_range=(32, 512), k_range=(64, 256),
+                 storage: str = "f32"):
+    """The batched-LP family: LP i has m_i ~ U{m_range}, n_i = m_i k_i with
+    k_i ~ U{k_range}, N(0,1) entries, planted optimum, seed (seed, i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        out.append(planted_dense(m, m * k, seed=int(seed * 100003 + i), storage=storage))
+    return out

@@ -122,6 +122,8 @@ SIGNATURES = {
     "lp_adat_noalloc": (c_int32, [P, c_int32, c_int32, c_int64, c_int64, P, P, P, P]),
     "lp_phase1_start": (c_int32, [POINTER(LpMatrix), P, POINTER(LpOptions), c_double, P,
                                   POINTER(LpPhase1Info)]),
+    "lp_solve_batch": (c_int32, [POINTER(P), c_int32, c_double, c_int32, c_int32, POINTER(P),
+                                 POINTER(P), POINTER(P), c_int32, POINTER(LpResult)]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }

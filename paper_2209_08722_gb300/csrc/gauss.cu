@@ -146,7 +146,7 @@ cudaError_t launch_gauss_v(long long n, const double* x, const double* s, const 
   const uint64_t s_kr = gauss_stream(seed, k, retry);
   const float inv_sqrt_w = (float)(1.0 / sqrt((double)w));
   const int smem = w * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_gauss_v, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem((const void*)k_gauss_v, smem);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::max<long long>(1, std::min<long long>((n + 7) / 8, num_sms * 4));
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -301,14 +301,13 @@ cudaError_t launch_gauss_tc(int dtype, const void* A, int lda, int m, long long 
   const int smem = std::max(2 * stage_bytes(mb, split), TC_SMEM_PER_SM / (max_ctas + 1) + 1024);
   dim3 grid((unsigned)gxb, (unsigned)gy, (unsigned)ks);
   if (split) {
-    e = cudaFuncSetAttribute(k_gauss_tc<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = ensure_smem((const void*)k_gauss_tc<float, true>, smem);
     if (e != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k_gauss_tc<float, true><<<grid, TC_THREADS, smem, st>>>(static_cast<const float*>(A), lda, m, n, dvec,
                                                            is_d2, s_kr, w, inv_sqrt_w, mb, kper, adw, err);
   } else {
-    e = cudaFuncSetAttribute(k_gauss_tc<bf16raw, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
+    e = ensure_smem((const void*)k_gauss_tc<bf16raw, false>, smem);
     if (e != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k_gauss_tc<bf16raw, false><<<grid, TC_THREADS, smem, st>>>(static_cast<const bf16raw*>(A), lda, m, n,

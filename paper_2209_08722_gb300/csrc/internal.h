@@ -49,6 +49,9 @@ struct DfUnpackArgs {
 cudaError_t launch_df_pack(const DfPackArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_df_unpack(const DfUnpackArgs& a, int num_sms, cudaStream_t st);
 
+// raise (never lower) a kernel's dynamic shared-memory limit; thread-safe
+cudaError_t ensure_smem(const void* func, int bytes);
+
 // double-float streaming passes (M_ADAT, M_RESID, M_DIR) for FP32/BF16 storage
 cudaError_t launch_stream_df(int dtype, int mode, const StreamArgs& a, const StreamPlan& p,
                              cudaStream_t st);

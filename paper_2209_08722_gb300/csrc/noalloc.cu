@@ -213,7 +213,7 @@ void* g_na_ptr[64] = {nullptr};
 template <typename TA, int VPL>
 cudaError_t na_launch(const NaArgs& a, int grid, int smem, cudaStream_t st) {
   auto k = k_adat_noalloc<TA, VPL>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k<<<grid, kFusedThreads, smem, st>>>(a);

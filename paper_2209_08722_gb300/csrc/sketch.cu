@@ -283,7 +283,7 @@ cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long lo
   cudaError_t e = cudaMemsetAsync(ws.count, 0, sizeof(int) * (size_t)w, st);
   if (e != cudaSuccess) return e;
   const int hist_smem = w * (int)sizeof(int);
-  e = cudaFuncSetAttribute(k_cs_count, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem);
+  e = ensure_smem((const void*)k_cs_count, hist_smem);
   if (e != cudaSuccess) return e;
   const int grid_cols = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)num_sms * 2));
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -298,17 +298,17 @@ cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long lo
   dim3 grid((unsigned)w, (unsigned)((m + kSlab - 1) / kSlab));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (dtype == 0) {
-    e = cudaFuncSetAttribute(k_cs_accum<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = ensure_smem((const void*)k_cs_accum<double>, smem);
     if (e != cudaSuccess) return e;
     k_cs_accum<double><<<grid, kAccThreads, smem, st>>>(static_cast<const double*>(A), lda, m, w, ws.base,
                                                          ws.list, ws.sc64, ws.scdf, adw);
   } else if (dtype == 1) {
-    e = cudaFuncSetAttribute(k_cs_accum<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = ensure_smem((const void*)k_cs_accum<float>, smem);
     if (e != cudaSuccess) return e;
     k_cs_accum<float><<<grid, kAccThreads, smem, st>>>(static_cast<const float*>(A), lda, m, w, ws.base,
                                                         ws.list, ws.sc64, ws.scdf, adw);
   } else {
-    e = cudaFuncSetAttribute(k_cs_accum<bf16raw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = ensure_smem((const void*)k_cs_accum<bf16raw>, smem);
     if (e != cudaSuccess) return e;
     k_cs_accum<bf16raw><<<grid, kAccThreads, smem, st>>>(static_cast<const bf16raw*>(A), lda, m, w, ws.base,
                                                           ws.list, ws.sc64, ws.scdf, adw);

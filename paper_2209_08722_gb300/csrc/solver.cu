@@ -29,6 +29,9 @@
 #include "../../include/lp_sketch_ipm.h"
 #include "internal.h"
 
+#include <atomic>
+#include <thread>
+
 using namespace lpk;
 
 namespace {
@@ -1291,6 +1294,41 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   res.ms_step = ms_step;
   if (info) *info = res;
   return status;
+}
+
+int lp_solve_batch(lp_handle* const* hs, int32_t count, double tol, int32_t mode,
+                   int32_t io_on_device, double* const* x, double* const* y, double* const* s,
+                   int32_t max_threads, lp_result* results) {
+  if (!hs || count < 0 || !(tol > 0)) return LP_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!hs[i]) return LP_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    for (int j = i + 1; j < count; ++j)
+      if (hs[i] == hs[j]) return LP_ERR_ARG;  // one worker per handle
+  std::vector<int> rc(count, LP_OK);
+  std::vector<lp_result> res(count);
+  std::atomic<int> next{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LP_ERR_CUDA;
+  auto worker = [&]() {
+    cudaSetDevice(dev);  // the current device is per host thread
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+      std::memset(&res[i], 0, sizeof(lp_result));
+      rc[i] = lp_solve(hs[i], tol, mode, nullptr, nullptr, nullptr, io_on_device, x ? x[i] : nullptr,
+                       y ? y[i] : nullptr, s ? s[i] : nullptr, &res[i]);
+    }
+  };
+  int nt = max_threads > 0 ? max_threads : count;
+  nt = std::max(1, std::min(std::min(nt, count), 64));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  if (results)
+    for (int i = 0; i < count; ++i) results[i] = res[i];
+  for (int i = 0; i < count; ++i)
+    if (rc[i] < 0) return rc[i];
+  return LP_OK;
 }
 
 // ---------------------------------------------------------------------------

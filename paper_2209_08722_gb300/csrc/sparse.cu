@@ -138,7 +138,7 @@ cudaError_t sp_launch(const StreamArgs& a, int grid, cudaStream_t st) {
   const int nvec = (MODE == M_RESID) ? 3 : 2;
   const int smem = nvec * a.lda * (int)sizeof(TC);
   auto k = k_sparse<TV, TC, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k<<<grid, 256, smem, st>>>(a);

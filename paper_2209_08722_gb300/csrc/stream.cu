@@ -360,7 +360,7 @@ namespace {
 template <typename TA, typename TC, int MODE>
 cudaError_t launch_stream_t(const StreamArgs& a, int grid, int smem, cudaStream_t st) {
   auto k = k_stream<TA, TC, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k<<<grid, kThreads, smem, st>>>(a);
@@ -370,7 +370,7 @@ cudaError_t launch_stream_t(const StreamArgs& a, int grid, int smem, cudaStream_
 template <typename TA, int VPL>
 cudaError_t launch_fused_t(const StreamArgs& a, int grid, int smem, cudaStream_t st) {
   auto k = k_adat_fused<TA, VPL>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = ensure_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k<<<grid, kFusedThreads, smem, st>>>(a);

@@ -264,7 +264,7 @@ cudaError_t df_launch(const StreamArgs& a, int grid, int smem, cudaStream_t st) 
   } else {
     constexpr int CW = df_cw<MODE>(VPL * VEC);
     auto k = k_stream_df<TA, VPL, CW, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     k<<<grid, (CW + 1) * 32, smem, st>>>(a);

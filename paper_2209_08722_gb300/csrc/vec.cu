@@ -9,11 +9,29 @@
 //   - small utilities (dot products, FP32 copies, R extraction, rank check).
 // All arithmetic here is FP64.
 #include "internal.h"
+
+#include <mutex>
+#include <unordered_map>
 #include "df.cuh"
 
 namespace lpk {
 
 std::atomic<long long> g_launches{0};
+
+// The dynamic shared-memory limit is a process-wide attribute of a kernel.
+// Handles solving different LPs from different host threads launch the same
+// kernel with different sizes, so the attribute only ever grows (under a
+// lock): lowering it could invalidate another thread's launch in flight.
+cudaError_t ensure_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> set;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = set[func];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // triangular GEMV with a fused epilogue
@@ -228,7 +246,7 @@ cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, 
   grid = std::max(1, std::min(grid, num_sms * 4));
   const size_t smem = Mdf ? (size_t)m * sizeof(float2) : 0;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemv_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem((const void*)k_gemv_tri, (int)smem);
     if (e != cudaSuccess) return e;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);

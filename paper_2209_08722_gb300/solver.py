@@ -330,3 +330,21 @@ def phase1_start(A, b, m: int, n: int, dtype: str = "f64", csc=None, tol: float 
         err.info = info.as_dict()
         raise err
     return x0, info.as_dict()
+
+
+def solve_batch(solvers, tol: float = 1e-8, mode: str = "infeasible", max_threads: int = 0):
+    """lp_solve_batch: solve independent LPs (one LPSolver each) concurrently
+    from the default start; returns [(x, y, s, info), ...] with host arrays."""
+    lib = nat.load()
+    count = len(solvers)
+    hs = (ctypes.c_void_p * count)(*[S._h.value for S in solvers])
+    outs = [(np.empty(S.n), np.empty(S.m), np.empty(S.n)) for S in solvers]
+    xs = (ctypes.c_void_p * count)(*[o[0].ctypes.data for o in outs])
+    ys = (ctypes.c_void_p * count)(*[o[1].ctypes.data for o in outs])
+    ss = (ctypes.c_void_p * count)(*[o[2].ctypes.data for o in outs])
+    res = (nat.LpResult * count)()
+    m = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+    rc = lib.lp_solve_batch(hs, count, float(tol), m, 0, xs, ys, ss, int(max_threads), res)
+    if rc < 0:
+        raise LPError(rc, "batched solve failed")
+    return [(o[0], o[1], o[2], res[i].as_dict()) for i, o in enumerate(outs)]

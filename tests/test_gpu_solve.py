@@ -142,3 +142,23 @@ def test_w_sweep_inner_iterations_fall_with_w():
         assert info["status"] == 0, info
         means.append(info["inner_total"] / info["outer_iterations"])
     assert means[0] > means[1] > means[2], means
+
+
+def test_batched_solve_matches_sequential_solves():
+    # the batched-LP family (uneven m, n): lp_solve_batch runs the LPs
+    # concurrently on their own streams; every LP reaches its planted optimum
+    # and the results equal the one-at-a-time solves bit for bit
+    from paper_2209_08722_gb300 import solve_batch
+    lps = lpgen.batch_family(6, seed=3, m_range=(32, 160), k_range=(64, 128))
+    solvers = [solver_for(lp, s=2) for lp in lps]
+    try:
+        seq = [S.solve(tol=1e-8) for S in solvers]
+        bat = solve_batch(solvers, tol=1e-8, max_threads=0)
+    finally:
+        for S in solvers:
+            S.close()
+    for lp, (x1, y1, _, i1), (x2, y2, _, i2) in zip(lps, seq, bat):
+        assert i2["status"] == 0, i2
+        assert abs(lp.c @ x2 - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+        assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+        assert i1["inner_total"] == i2["inner_total"]
