@@ -101,6 +101,11 @@ typedef struct {
     int32_t precondition;  /* 1 = the paper's method (sketch, Q^{-1}, correction v);
                               0 = the standard IPM of Section 7's comparison: unpreconditioned
                               CG on eq. normal (Q = I), no sketch, v = 0; 1 */
+    int32_t sigma_rule;    /* 0 = fixed sigma (Algorithms 2-3); 1 = two right-hand sides per
+                              outer iteration on one sketch and Q: p(sigma) = p(0) + sigma
+                              (p(1) - p(0)) is affine in sigma, so are dy, v and the
+                              directions; sigma = clip((mu_aff/mu)^3, 0.1, 0.75) from the
+                              affine direction's largest positivity-keeping step; 0 */
 } lp_options;
 
 /* ---- results -------------------------------------------------------------- */
@@ -148,6 +153,7 @@ typedef struct {
     double f0_norm;             /* ||Q^{-1/2} p|| */
     double tol_f;               /* the inner target used */
     double alpha_max, alpha_bar;
+    double sigma;               /* centering parameter used */
 } lp_iter_record;
 
 /* ---- lifecycle -------------------------------------------------------------- */

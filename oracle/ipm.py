@@ -54,6 +54,8 @@ class Options:
     v_correction: bool = True
     cheb_lanczos: int = 10      # CG steps used to estimate the Chebyshev interval
     keep_vectors: bool = False
+    sigma_rule: str = "fixed"   # "fixed" (the paper) or "adaptive" (two right-hand sides)
+    sigma_range: tuple = (0.1, 0.75)
 
 
 @dataclasses.dataclass
@@ -70,6 +72,8 @@ class IterRecord:
     alpha_max: float = 0.0
     alpha_bar: float = 0.0
     vectors: Optional[dict] = None
+    sigma_used: float = 0.0
+
 
 
 @dataclasses.dataclass
@@ -307,6 +311,42 @@ def normal_solve(A, x, s, p, opt: Options, k: int, inner_tol: float,
                        precond=pre, ADW=ADW, retry=retry, lam=lam)
 
 
+def _adaptive_sigma_solve(A, x, s, r_p, r_d, mu, feasible, opt: Options, k: int, rec):
+    """Two right-hand sides on one normal matrix (and, for the sketched solver,
+    one sketch and Q): the RHS is affine in sigma, p(sigma) = p_aff + sigma p_c
+    with p_aff = p(0) and p_c = -mu A S^{-1} 1, so dy and v are affine in sigma
+    too.  sigma comes from the affine direction's largest positivity-keeping
+    step: sigma = clip((mu_aff / mu)^3, sigma_range) (Mehrotra's centering
+    heuristic), inside the paper's sigma range (0, 4/5).  Returns (dy, v, sigma)."""
+    m, n = A.shape
+    p_aff = rhs(A, x, s, r_p, r_d, 0.0, mu, feasible)
+    p_c = rhs(A, x, s, r_p, r_d, 1.0, mu, feasible) - p_aff
+    lo, hi = opt.sigma_range
+    if opt.solver == "exact":
+        cf = sla.cho_factor(normal_matrix(A, x / s))
+        dy_a, dy_c = sla.cho_solve(cf, p_aff), sla.cho_solve(cf, p_c)
+        v_a = v_c = np.zeros(n)
+    else:
+        tol_f = pcg.theory_inner_tol(mu, n, opt.gamma, lo)
+        solve = normal_solve if opt.solver == "sketch" else (
+            lambda A_, x_, s_, p_, o_, k_, t_: normal_solve_unpreconditioned(A_, x_, s_, p_, o_, t_))
+        na = solve(A, x, s, p_aff, opt, k, tol_f)
+        nc = solve(A, x, s, p_c, opt, k, tol_f)
+        dy_a, dy_c, v_a, v_c = na.dy, nc.dy, na.v, nc.v
+        rec.inner_its = na.trace.iterations + nc.trace.iterations
+    dx_a, ds_a = directions(A, x, s, r_d, dy_a, v_a, 0.0, mu, feasible)
+    a_aff = 1.0
+    neg = dx_a < 0
+    if neg.any():
+        a_aff = min(a_aff, float(np.min(-x[neg] / dx_a[neg])))
+    neg = ds_a < 0
+    if neg.any():
+        a_aff = min(a_aff, float(np.min(-s[neg] / ds_a[neg])))
+    mu_aff = float((x + a_aff * dx_a) @ (s + a_aff * ds_a)) / n
+    sigma = float(np.clip((mu_aff / mu) ** 3, lo, hi))
+    return dy_a + sigma * dy_c, v_a + sigma * v_c, sigma
+
+
 def normal_solve_unpreconditioned(A, x, s, p, opt: Options, inner_tol: float) -> NormalSolve:
     """The standard IPM's inner solve (the comparison system of Section 7):
     CG on eq. (normal) itself, i.e. Q = I in eq. (precond), and no correction
@@ -396,7 +436,11 @@ def solve(A, b, c, opt: Options, x0=None, y0=None, s0=None) -> Result:
             r_d_used = r_d
             p = rhs(A, x, s, r_p, r_d, opt.sigma, mu, False)
         d2 = x / s
-        if opt.solver == "exact":
+        if opt.sigma_rule == "adaptive":
+            dy, v, sigma_k = _adaptive_sigma_solve(A, x, s, r_p, r_d_used, mu, feasible, opt, k, rec)
+            dx, ds = directions(A, x, s, r_d_used, dy, v, sigma_k, mu, feasible)
+            rec.sigma_used = sigma_k
+        elif opt.solver == "exact":
             M = normal_matrix(A, d2)
             cf = sla.cho_factor(M)
             dy = sla.cho_solve(cf, p)
@@ -416,7 +460,9 @@ def solve(A, b, c, opt: Options, x0=None, y0=None, s0=None) -> Result:
             rec.f_norm = ns.f_norm
             rec.f0_norm = ns.f0_norm
             rec.v_norm = float(np.linalg.norm(v))
-        dx, ds = directions(A, x, s, r_d_used, dy, v, opt.sigma, mu, feasible)
+        if opt.sigma_rule != "adaptive":
+            dx, ds = directions(A, x, s, r_d_used, dy, v, opt.sigma, mu, feasible)
+            rec.sigma_used = opt.sigma
         res_ratio = 0.0 if feasible else np.sqrt(r_p @ r_p + r_d @ r_d) / r0_norm
         a_max, a_bar = step_lengths(x, s, dx, ds, opt.gamma, feasible, res_ratio, mu0)
         rec.alpha_max, rec.alpha_bar = a_max, a_bar

@@ -53,7 +53,7 @@ class LpOptions(ctypes.Structure):
                 ("t_max", c_int32), ("v_correction", c_int32), ("cheb_lanczos", c_int32),
                 ("profile", c_int32), ("w_factor", c_double), ("w", c_int64),
                 ("seed", c_uint64), ("stream", c_void_p), ("tensor_sketch", c_int32),
-                ("precondition", c_int32)]
+                ("precondition", c_int32), ("sigma_rule", c_int32)]
 
 
 class LpResult(ctypes.Structure):
@@ -82,7 +82,7 @@ class LpIterRecord(ctypes.Structure):
                 ("inner_status", c_int32), ("mu", c_double), ("rel_gap", c_double),
                 ("rp_rel", c_double), ("rd_rel", c_double), ("f_norm", c_double),
                 ("f0_norm", c_double), ("tol_f", c_double), ("alpha_max", c_double),
-                ("alpha_bar", c_double)]
+                ("alpha_bar", c_double), ("sigma", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -52,6 +52,7 @@ struct DevScalars {
   int rank_bad;       // sketch factor rank check failed
   int err;            // ERR_* (sticky)
   double diag_min, diag_max;
+  double alpha_aff;   // largest positivity-keeping step of the affine direction (<= 1)
   double pad[4];
 };
 

@@ -131,6 +131,9 @@ cudaError_t launch_update(long long n, int m, double* x, double* s, double* y, c
 cudaError_t launch_fill(long long n, double* x, double v, int num_sms, cudaStream_t st);
 cudaError_t launch_axpby(long long n, double alpha, const double* x, double beta, const double* y,
                          double* out, int num_sms, cudaStream_t st);
+cudaError_t launch_pos_step(long long n, const double* x, const double* s, const double* dx,
+                            const double* ds, double* part, unsigned* ticket, DevScalars* sc, int num_sms,
+                            cudaStream_t st);
 cudaError_t launch_min_prod(long long n, const double* x, const double* y, double* part,
                             unsigned* ticket, double* out, int num_sms, cudaStream_t st);
 cudaError_t launch_to_f32(long long n, const double* x, float* y, int square, int num_sms,

@@ -85,6 +85,8 @@ struct lp_handle {
   long long sweep_fallbacks = 0;
   long long breakdown_recoveries = 0;  // inner solves that switched product after a CG breakdown
   long long qr_refactors = 0;          // inner solves rerun after refactoring by QR
+  double *dy_aff = nullptr, *dy_c = nullptr, *p_aff = nullptr, *p_c = nullptr;  // two-RHS variant (m)
+  double *v_aff = nullptr, *v_c = nullptr;                                        // ... (n)
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -636,9 +638,10 @@ int copy_out(lp_handle* h, double* dst, const double* src, size_t count, int on_
   return LP_OK;
 }
 
-int residual_pass(lp_handle* h, bool feasible) {
+int residual_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
   StreamArgs a = base_args(h);
   a.feasible = feasible ? 1 : 0;
+  if (sigma >= 0.0) a.sigma = sigma;
   a.cv[0] = h->x;
   a.cv[1] = h->s;
   a.cv[2] = h->c;
@@ -676,9 +679,10 @@ int residual_pass(lp_handle* h, bool feasible) {
   return LP_OK;
 }
 
-int direction_pass(lp_handle* h, bool feasible) {
+int direction_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
   StreamArgs a = base_args(h);
   a.feasible = feasible ? 1 : 0;
+  if (sigma >= 0.0) a.sigma = sigma;
   a.cv[0] = h->x;
   a.cv[1] = h->s;
   a.cv[2] = h->v;
@@ -725,6 +729,7 @@ void options_check(const lp_options* o, std::string* why) {
   else if (o->s < 1 || o->s > kMaxBlocks) *why = "s must be in [1, 16]";
   else if (o->sketch != LP_SKETCH_COUNT && o->sketch != LP_SKETCH_GAUSS) *why = "unknown sketch";
   else if (o->precondition != 0 && o->precondition != 1) *why = "precondition must be 0 or 1";
+  else if (o->sigma_rule != 0 && o->sigma_rule != 1) *why = "sigma_rule must be 0 or 1";
   else if (o->inner != LP_INNER_CG && o->inner != LP_INNER_CHEBYSHEV) *why = "inner must be CG or Chebyshev";
   else if (o->t_max < 1 || o->k_max < 0) *why = "t_max >= 1 and k_max >= 0 required";
 }
@@ -758,6 +763,7 @@ void lp_options_default(lp_options* o) {
   o->stream = nullptr;
   o->tensor_sketch = 1;
   o->precondition = 1;
+  o->sigma_rule = 0;
 }
 
 const char* lp_create_error(void) { return g_create_error.c_str(); }
@@ -911,6 +917,10 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv_df, (size_t)h->m * h->m));
+  if (h->opt.sigma_rule == 1) {
+    for (double** q : {&h->dy_aff, &h->dy_c, &h->p_aff, &h->p_c}) RET(h->alloc(q, (size_t)h->lda + 64));
+    for (double** q : {&h->v_aff, &h->v_c}) RET(h->alloc(q, (size_t)h->npad));
+  }
   RET(h->alloc(&h->gram_scratch, gram_df_scratch_floats(h->m, h->w, h->num_sms)));
   RET(h->alloc(&h->sweep_scratch, sweep_scratch_floats(h->m)));
   RET(h->alloc(&h->uw, (size_t)h->w));
@@ -1188,7 +1198,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   for (int k = 0; k <= h->opt.k_max; ++k) {
     auto t0 = now();
     // ---- step 3: residuals, mu, right-hand side, d^2 ----
-    RET(residual_pass(h, feasible));
+    RET(residual_pass(h, feasible, h->opt.sigma_rule == 1 ? 0.0 : -1.0));
     RET(sync_read(h));
     ms_res += ms_since(t0);
     const DevScalars& S = *h->hsc;
@@ -1247,12 +1257,59 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
     ms_fac += ms_since(t0);
     // ---- Algorithm 1 step 3: inner solve to the Lemma 4.4 level ----
     t0 = now();
+    const bool adaptive = h->opt.sigma_rule == 1;
+    const double sig_lo = 0.1, sig_hi = 0.75;  // inside the analysis range (0, 4/5)
     const double tol_f = h->opt.inner_rule == LP_RULE_THEORY
-                             ? h->opt.gamma * h->opt.sigma * sqrt(mu) / (4.0 * sqrt(3.0 * (double)n))
+                             ? h->opt.gamma * (adaptive ? sig_lo : h->opt.sigma) * sqrt(mu) /
+                                   (4.0 * sqrt(3.0 * (double)n))
                              : 0.0;
-    int iters = 0;
-    const int ist = inner_solve_robust(h, tol_f, &iters);
-    if (ist < 0) return ist;
+    double sigma_k = h->opt.sigma;
+    int iters = 0, ist = 0;
+    const size_t mb = sizeof(double) * (size_t)m, nbytes = sizeof(double) * (size_t)n;
+    if (!adaptive) {
+      ist = inner_solve_robust(h, tol_f, &iters);
+      if (ist < 0) return ist;
+      ms_in += ms_since(t0);
+      // ---- step 5: correction v, directions ----
+      t0 = now();
+      RET(correction(h, h->x, h->s, k, retry));
+      RET(direction_pass(h, feasible));
+    } else {
+      // two right-hand sides on this sketch and Q: p(sigma) = p_aff + sigma p_c
+      CK(cudaMemcpyAsync(h->p_aff, h->p, mb, cudaMemcpyDeviceToDevice, h->st));  // p(0)
+      RET(residual_pass(h, feasible, 1.0));                                       // p(1)
+      CK(launch_axpby(m, 1.0, h->p, -1.0, h->p_aff, h->p_c, h->num_sms, h->st));
+      int it2 = 0;
+      CK(cudaMemcpyAsync(h->p, h->p_aff, mb, cudaMemcpyDeviceToDevice, h->st));
+      ist = inner_solve_robust(h, tol_f, &iters);
+      if (ist < 0) return ist;
+      RET(correction(h, h->x, h->s, k, retry));
+      CK(cudaMemcpyAsync(h->dy_aff, h->dy, mb, cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpyAsync(h->v_aff, h->v, nbytes, cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpyAsync(h->p, h->p_c, mb, cudaMemcpyDeviceToDevice, h->st));
+      const int ist2 = inner_solve_robust(h, tol_f, &it2);
+      if (ist2 < 0) return ist2;
+      RET(correction(h, h->x, h->s, k, retry));
+      CK(cudaMemcpyAsync(h->dy_c, h->dy, mb, cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpyAsync(h->v_c, h->v, nbytes, cudaMemcpyDeviceToDevice, h->st));
+      iters += it2;
+      ist = std::max(ist, ist2);
+      ms_in += ms_since(t0);
+      t0 = now();
+      // affine direction (sigma = 0) and its largest positivity-keeping step
+      CK(cudaMemcpyAsync(h->dy, h->dy_aff, mb, cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpyAsync(h->v, h->v_aff, nbytes, cudaMemcpyDeviceToDevice, h->st));
+      RET(direction_pass(h, feasible, 0.0));
+      CK(launch_pos_step(n, h->x, h->s, h->dx, h->ds, h->vpart, h->tickets + 8, h->sc, h->num_sms, h->st));
+      RET(sync_read(h));
+      const double aa = h->hsc->alpha_aff;
+      const double mu_aff = mu + h->hsc->c1 * aa + h->hsc->c2 * aa * aa;
+      sigma_k = std::min(sig_hi, std::max(sig_lo, std::pow(std::max(mu_aff, 0.0) / mu, 3.0)));
+      // the direction for sigma_k: dy, v (and dx, ds) are affine in sigma
+      CK(launch_axpby(m, 1.0, h->dy_aff, sigma_k, h->dy_c, h->dy, h->num_sms, h->st));
+      CK(launch_axpby(n, 1.0, h->v_aff, sigma_k, h->v_c, h->v, h->num_sms, h->st));
+      RET(direction_pass(h, feasible, sigma_k));
+    }
     {
       lp_iter_record& hr = h->history.back();
       hr.inner_iterations = iters;
@@ -1261,14 +1318,10 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
       hr.f_norm = h->hsc->f_true;
       hr.f0_norm = sqrt(std::max(h->hsc->rho0, 0.0));
       hr.tol_f = tol_f > 0 ? tol_f : h->opt.tol_cg * hr.f0_norm;
+      hr.sigma = sigma_k;
     }
     res.inner_total += iters;
     res.inner_max = std::max(res.inner_max, iters);
-    ms_in += ms_since(t0);
-    // ---- step 5: correction v, directions ----
-    t0 = now();
-    RET(correction(h, h->x, h->s, k, retry));
-    RET(direction_pass(h, feasible));
     CK(cudaStreamSynchronize(h->st));
     ms_cor += ms_since(t0);
     // ---- steps 6-8: step lengths and update ----

@@ -442,6 +442,37 @@ cudaError_t launch_step(long long n, const double* x, const double* s, const dou
   return cudaGetLastError();
 }
 
+// sc->alpha_aff = min(1, min_i {-x_i/dx_i : dx_i < 0}, min_i {-s_i/ds_i : ds_i < 0})
+__global__ void __launch_bounds__(256) k_pos_step(long long n, const double* __restrict__ x,
+                                                  const double* __restrict__ s, const double* __restrict__ dx,
+                                                  const double* __restrict__ ds, double* part, unsigned* ticket,
+                                                  DevScalars* sc) {
+  __shared__ double red[32];
+  __shared__ int s_flag;
+  double pos = 1.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (dx[i] < 0.0) pos = fmin(pos, -x[i] / dx[i]);
+    if (ds[i] < 0.0) pos = fmin(pos, -s[i] / ds[i]);
+  }
+  pos = block_min(pos, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = pos;
+  if (!last_block_ticket(ticket, &s_flag)) return;
+  double p = 1.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) p = fmin(p, __ldcg(part + b));
+  p = block_min(p, red);
+  if (threadIdx.x == 0) sc->alpha_aff = p;
+}
+
+cudaError_t launch_pos_step(long long n, const double* x, const double* s, const double* dx,
+                            const double* ds, double* part, unsigned* ticket, DevScalars* sc, int num_sms,
+                            cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)num_sms * 2));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_pos_step<<<grid, 256, 0, st>>>(n, x, s, dx, ds, part, ticket, sc);
+  return cudaGetLastError();
+}
+
 // x += a dx, s += a ds (n), y += a dy (m); sc->mu = x^T s / n afterwards
 __global__ void k_update(long long n, int m, double* x, double* s, double* y, const double* dx,
                          const double* ds, const double* dy, DevScalars* sc, double* part,

@@ -162,3 +162,27 @@ def test_batched_solve_matches_sequential_solves():
         assert abs(lp.c @ x2 - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
         assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
         assert i1["inner_total"] == i2["inner_total"]
+
+
+@pytest.mark.parametrize("col_scale", [None, (-2, 2)])
+def test_two_rhs_adaptive_sigma_matches_oracle_and_cuts_iterations(col_scale):
+    # sigma_rule = 1: two right-hand sides on one sketch and Q per outer
+    # iteration; the oracle implements the same variant
+    from oracle import ipm
+    m, n = 48, 3000
+    lp = lpgen.planted_dense(m, n, seed=42, storage="f64", col_scale_log10=col_scale)
+    ref = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(solver="sketch", sigma_rule="adaptive", w=4 * m, s=2))
+    with solver_for(lp, s=2) as S:
+        _, _, _, fixed = S.solve(tol=1e-8)
+    with solver_for(lp, s=2, sigma_rule=1) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+        hist = S.history()
+    assert info["status"] == 0, info
+    assert abs(lp.c @ x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert info["outer_iterations"] <= 0.7 * fixed["outer_iterations"]
+    assert abs(info["outer_iterations"] - ref.iterations) <= 2
+    sig = [h["sigma"] for h in hist[:-1]]
+    assert min(sig) >= 0.1 - 1e-12 and max(sig) <= 0.75 + 1e-12
+    ref_sig = [h.sigma_used for h in ref.history[:-1]]
+    k = min(5, len(sig), len(ref_sig))
+    assert np.allclose(sig[:k], ref_sig[:k], rtol=1e-3, atol=1e-6)

@@ -352,3 +352,39 @@ def test_sketch_redraw_on_rank_failure():
     opt = ipm.Options(solver="sketch", w=4, s=1)
     with pytest.raises(np.linalg.LinAlgError):
         ipm.normal_solve(A, x, s, rng.standard_normal(m), opt, k=0, inner_tol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# two right-hand sides per outer iteration (adaptive sigma)
+# ---------------------------------------------------------------------------
+def test_two_rhs_combination_is_the_solve_with_p_sigma():
+    # p is affine in sigma, so dy_aff + sigma dy_c must equal the direct solve
+    # with p(sigma) (exact solver: v = 0)
+    lp = lpgen.planted_dense(24, 600, seed=40)
+    rng = np.random.default_rng(41)
+    x, s = np.exp(rng.uniform(-1, 1, lp.n)), np.exp(rng.uniform(-1, 1, lp.n))
+    y = rng.standard_normal(lp.m)
+    r_p, r_d = ipm.residuals(lp.A, lp.b, lp.c, x, y, s)
+    mu = x @ s / lp.n
+    opt = ipm.Options(solver="exact", sigma_rule="adaptive")
+    rec = ipm.IterRecord(k=0, mu=mu, gap=0.0, rp_norm=0.0, rd_norm=0.0)
+    dy, v, sigma = ipm._adaptive_sigma_solve(lp.A, x, s, r_p, r_d, mu, False, opt, 0, rec)
+    assert 0.1 <= sigma <= 0.75
+    M = ipm.normal_matrix(lp.A, x / s)
+    direct = np.linalg.solve(M, ipm.rhs(lp.A, x, s, r_p, r_d, sigma, mu, False))
+    assert np.linalg.norm(dy - direct) <= 1e-9 * np.linalg.norm(direct)
+    assert not v.any()
+
+
+@pytest.mark.parametrize("col_scale", [None, (-2, 2)])
+def test_two_rhs_adaptive_sigma_needs_fewer_outer_iterations(col_scale):
+    lp = lpgen.planted_dense(48, 3000, seed=42, storage="f64", col_scale_log10=col_scale)
+    out = {}
+    for rule in ("fixed", "adaptive"):
+        r = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(solver="sketch", sigma_rule=rule, w=4 * 48, s=2))
+        assert r.status == "optimal"
+        assert abs(lp.c @ r.x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+        out[rule] = r
+    assert out["adaptive"].iterations <= 0.7 * out["fixed"].iterations
+    sig = [h.sigma_used for h in out["adaptive"].history if h.sigma_used > 0]
+    assert min(sig) >= 0.1 and max(sig) <= 0.75
