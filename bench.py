@@ -287,6 +287,66 @@ def run_batch(args):
     return 0
 
 
+def run_warm_start(args):
+    """Learned warm start on the BF16 dense family at 1/8 scale (m = 256,
+    n = 65536): record (features, dy) from the solves of training LPs (seeds
+    1..24), train the 3m -> 1024 -> 1024 -> m model, then solve held-out LPs
+    (seeds 1000..1007) cold and warm-started; inner iterations and the
+    objective error of each."""
+    import torch
+    from paper_2209_08722_gb300 import LPSolver, Mlp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    m, n = 256, 65536
+
+    def make(seed):
+        return lpgen.planted_dense(m, n, seed=seed, storage="bf16")
+
+    def solver(lp):
+        return LPSolver(lp.storage_array(), lp.b, lp.c, m, n, dtype="bf16", s=2)
+    cap = 4000
+    recX = torch.zeros(cap, 3 * m, device="cuda")
+    recT = torch.zeros(cap, m, device="cuda")
+    total = 0
+    for seed in range(1, 25):
+        S = solver(make(seed))
+        S.set_warm_start("none", None, recX[total:], recT[total:])
+        S.solve(tol=TOL)
+        total += S.warm_start_stats()["recorded"]
+        S.close()
+    net = Mlp(3 * m, 1024, m, seed=7)
+    X, T = recX[:total].contiguous(), recT[:total].contiguous()
+    t0 = time.perf_counter()
+    for it in range(2000):
+        loss = net.train_step(X, T, 1e-3 if it < 1400 else 3e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {}
+    for mode in ("none", "model"):
+        inner, outer, err, acc, props, secs = 0, 0, 0.0, 0, 0, 0.0
+        for seed in range(1000, 1008):
+            lp = make(seed)
+            S = solver(lp)
+            S.set_warm_start(mode, net if mode == "model" else None)
+            t0 = time.perf_counter()
+            x, _, _, info = S.solve(tol=TOL)
+            secs += time.perf_counter() - t0
+            st = S.warm_start_stats()
+            S.close()
+            inner += info["inner_total"]
+            outer += info["outer_iterations"]
+            err = max(err, abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective)))
+            acc += st["accepted"]
+            props += st["proposals"]
+        out[mode] = {"inner_total": inner, "outer_total": outer, "max_objective_rel_err": err,
+                     "accepted": acc, "proposals": props, "solve_s": secs}
+    print(json.dumps({"mode": "warm_start", "workload": f"planted dense BF16 m={m} n={n}, 24 training / 8 test LPs",
+                      "samples": total, "params": net.num_params, "train_s": t_train, "final_loss": loss,
+                      "cold": out["none"], "learned": out["model"],
+                      "inner_saved_frac": 1.0 - out["model"]["inner_total"] / out["none"]["inner_total"]}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,6 +354,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="train the learned warm start on the BF16 family at 1/8 scale and compare")
     ap.add_argument("--batch", type=int, default=0,
                     help="time N LPs of the batched family one at a time and batched")
     ap.add_argument("--kernel", choices=["adat", "gauss", "gauss-simt"], default=None,
@@ -304,6 +366,8 @@ def main():
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.warm_start:
+        return run_warm_start(args)
     if args.kernel in ("gauss", "gauss-simt"):
         return run_gauss_kernel(args)
     if args.kernel:

@@ -114,7 +114,7 @@ typedef struct {
     int32_t outer_iterations;
     int64_t inner_total;        /* sum of inner iterations */
     int32_t inner_max;          /* max inner iterations of one outer iteration */
-    int32_t sketch_retries;     /* total redraws after a rank failure */
+    int32_t sketch_retries;     /* total redraws of W: rank failures and failed Ritz checks */
     double primal_obj;          /* c^T x */
     double dual_obj;            /* b^T y */
     double rel_gap;             /* |c^T x - b^T y| / (1 + |c^T x|) */
@@ -212,6 +212,10 @@ int lp_solve_batch(lp_handle* const* hs, int32_t count, double tol, int32_t mode
  * tol_f <= 0: stop when ||f^(t)|| <= tol_cg * ||f^(0)||.  If xs (n, x o s) and
  * v (n) are both non-NULL, v = (XS)^{1/2} W (ADW)^+ (A D^2 A^T dy - p) is
  * returned too (requires D^2 = x/s for the invariant of eq. addl to hold).
+ * A draw of W is an embedding only with probability 1 - delta (eq. pdprec):
+ * when the Ritz values of the first CG steps spread by more than 1e3 and the
+ * solve is still running after 32 steps, W is redrawn (retry + 1, at most
+ * twice) and CG continues from the current dy; v uses the final draw.
  * Returns LP_OK, LP_WARN_INNER_MAXIT or an error. */
 int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double* xs,
                     int64_t k, double tol_f, int32_t io_on_device,
@@ -309,6 +313,43 @@ typedef struct {
 } lp_phase1_info;
 int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt, double tol,
                     double* x0, lp_phase1_info* info);
+
+/* ---- learned warm start of the inner solve ---------------------------------
+ * A multilayer perceptron in -> H -> H -> out with GELU after both hidden layers
+ * (trained by mean-squared error with Adam), used to propose the inner solve's
+ * starting point.  The paper does not define this; the features are
+ *   X = [dy_{k-1} / |u|, u / |u|, log10(mu_k) / 10 * 1_m],  u = Q^{-1} p_k
+ * (3m values, dy_{k-1} = 0 at the first outer iteration) and the target is
+ * dy_k / |u|, so in = 3m and out = m.  Batches are column-major (features x
+ * batch) device FP32 arrays; parameters W1 (H x in), b1, W2 (H x H), b2,
+ * W3 (out x H), b3 are column-major in one FP32 vector. */
+typedef struct lp_mlp lp_mlp;
+int lp_mlp_create(lp_mlp** model, int32_t in, int32_t hidden, int32_t out, uint64_t seed, void* stream);
+int lp_mlp_destroy(lp_mlp* model);
+int64_t lp_mlp_num_params(const lp_mlp* model);
+int lp_mlp_get_params(lp_mlp* model, float* host);       /* host: num_params floats */
+int lp_mlp_set_params(lp_mlp* model, const float* host);
+int lp_mlp_get_grads(lp_mlp* model, float* host);        /* gradients of the last loss_grad / train_step */
+/* Y (out x batch) = model(X (in x batch)), device arrays */
+int lp_mlp_forward(lp_mlp* model, const float* X, int32_t batch, float* Y);
+/* loss = 1/(2 batch) sum ||model(X) - T||^2 and its gradients (no update) */
+int lp_mlp_loss_grad(lp_mlp* model, const float* X, const float* T, int32_t batch, double* loss);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) at learning rate lr on the batch */
+int lp_mlp_train_step(lp_mlp* model, const float* X, const float* T, int32_t batch, float lr, double* loss);
+
+/* Warm start of lp_solve's inner solves (fixed-sigma rule).  mode 0: none (the
+ * paper: dy^0 = 0); 1: dy^0 = dy_{k-1}; 2: dy^0 = |u| model(X).  A proposal is
+ * used only while mu >= 1e-6 mu_0 and only if its true residual is smaller,
+ * sqrt(r^T Q^{-1} r) < sqrt(p^T Q^{-1} p) with r = p - A D^2 A^T dy^0, and
+ * |dy^0| <= 4 |Q^{-1} p|; the stopping rule (relative to the cold residual
+ * sqrt(p^T Q^{-1} p)) is unchanged, so the iterate returned satisfies the same bound.  rec_X (3m x capacity) and rec_T
+ * (m x capacity), device FP32, nullable: every outer iteration's features and
+ * target are appended until capacity (for training).  The model is borrowed,
+ * not owned. */
+int lp_set_warm_start(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, float* rec_T,
+                      int32_t rec_capacity);
+/* counters since lp_set_warm_start: recorded samples, proposals, accepted proposals */
+int lp_get_warm_start_stats(lp_handle* h, int64_t* recorded, int64_t* proposals, int64_t* accepted);
 
 /* Statistics of the hot product kernel (requires opt.profile = 1). */
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);

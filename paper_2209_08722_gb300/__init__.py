@@ -10,7 +10,7 @@ from .build_native import build, lib_path  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("LPSolver", "LPError", "from_planted", "phase1_start", "solve_batch"):
+    if name in ("LPSolver", "LPError", "from_planted", "phase1_start", "solve_batch", "Mlp"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_uint64, c_void_p
+from ctypes import c_float, POINTER, c_char_p, c_double, c_int32, c_int64, c_uint64, c_void_p
 
 from .build_native import lib_path
 
@@ -124,6 +124,17 @@ SIGNATURES = {
                                   POINTER(LpPhase1Info)]),
     "lp_solve_batch": (c_int32, [POINTER(P), c_int32, c_double, c_int32, c_int32, POINTER(P),
                                  POINTER(P), POINTER(P), c_int32, POINTER(LpResult)]),
+    "lp_mlp_create": (c_int32, [POINTER(P), c_int32, c_int32, c_int32, c_uint64, P]),
+    "lp_mlp_destroy": (c_int32, [P]),
+    "lp_mlp_num_params": (c_int64, [P]),
+    "lp_mlp_get_params": (c_int32, [P, P]),
+    "lp_mlp_set_params": (c_int32, [P, P]),
+    "lp_mlp_get_grads": (c_int32, [P, P]),
+    "lp_mlp_forward": (c_int32, [P, P, c_int32, P]),
+    "lp_mlp_loss_grad": (c_int32, [P, P, P, c_int32, POINTER(c_double)]),
+    "lp_mlp_train_step": (c_int32, [P, P, P, c_int32, c_float, POINTER(c_double)]),
+    "lp_set_warm_start": (c_int32, [P, c_int32, P, P, P, c_int32]),
+    "lp_get_warm_start_stats": (c_int32, [P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }

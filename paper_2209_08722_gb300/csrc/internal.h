@@ -9,6 +9,8 @@
 #include "common.cuh"
 #include "stream.cuh"
 
+struct lp_mlp;  // the warm-start model (mlp.cu; opaque in the C ABI)
+
 namespace lpk {
 
 // kernels launched by this library since load (cuSOLVER's own kernels excluded)
@@ -48,6 +50,10 @@ struct DfUnpackArgs {
 };
 cudaError_t launch_df_pack(const DfPackArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_df_unpack(const DfUnpackArgs& a, int num_sms, cudaStream_t st);
+
+// the warm-start model's forward pass for one sample on stream st (mlp.cu)
+int mlp_predict(::lp_mlp* M, const float* X, float* Y, cudaStream_t st);
+void mlp_dims(const ::lp_mlp* M, int* in, int* out);
 
 // raise (never lower) a kernel's dynamic shared-memory limit; thread-safe
 cudaError_t ensure_smem(const void* func, int bytes);
@@ -131,6 +137,10 @@ cudaError_t launch_update(long long n, int m, double* x, double* s, double* y, c
 cudaError_t launch_fill(long long n, double* x, double v, int num_sms, cudaStream_t st);
 cudaError_t launch_axpby(long long n, double alpha, const double* x, double beta, const double* y,
                          double* out, int num_sms, cudaStream_t st);
+cudaError_t launch_ws_features(int m, const double* dy_prev, int have_prev, const double* u,
+                               const DevScalars* sc, float* X, cudaStream_t st);
+cudaError_t launch_ws_scale(int m, int dir, const float* yf, const double* in, const DevScalars* sc,
+                            double* out, float* of, cudaStream_t st);
 cudaError_t launch_pos_step(long long n, const double* x, const double* s, const double* dx,
                             const double* ds, double* part, unsigned* ticket, DevScalars* sc, int num_sms,
                             cudaStream_t st);

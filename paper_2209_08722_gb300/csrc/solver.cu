@@ -85,8 +85,17 @@ struct lp_handle {
   long long sweep_fallbacks = 0;
   long long breakdown_recoveries = 0;  // inner solves that switched product after a CG breakdown
   long long qr_refactors = 0;          // inner solves rerun after refactoring by QR
+  long long poor_redraws = 0;          // draws of W replaced after failing the Ritz check
   double *dy_aff = nullptr, *dy_c = nullptr, *p_aff = nullptr, *p_c = nullptr;  // two-RHS variant (m)
   double *v_aff = nullptr, *v_c = nullptr;                                        // ... (n)
+  // learned / previous-direction warm start of the inner solve
+  int ws_mode = 0;
+  lp_mlp* ws_model = nullptr;
+  float *ws_rec_X = nullptr, *ws_rec_T = nullptr;
+  long long ws_cap = 0, ws_count = 0, ws_props = 0, ws_acc = 0;
+  bool ws_have_prev = false;
+  double *dy_prev = nullptr, *ws_u = nullptr;
+  float *ws_X = nullptr, *ws_Y = nullptr;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -449,15 +458,52 @@ void tridiag_extremes(const std::vector<double>& dg, const std::vector<double>& 
   *hi = kth(k - 1);
 }
 
+// Extreme Ritz values of Q^{-1} M from the first kk CG steps: the Lanczos
+// tridiagonal has diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal
+// sqrt(beta_j)/alpha_j (alpha_j at coef[2j], beta_j at coef[2j+1]).
+int ritz_extremes(lp_handle* h, int kk, double* lo, double* hi) {
+  *lo = 0.5;
+  *hi = 2.0;
+  if (kk <= 0) return LP_OK;
+  std::vector<double> coef(2 * (size_t)kk);
+  CK(cudaMemcpyAsync(coef.data(), h->coef, sizeof(double) * 2 * kk, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  std::vector<double> dg(kk), off(std::max(0, kk - 1));
+  for (int j = 0; j < kk; ++j) {
+    const double al = coef[2 * j], be_prev = j > 0 ? coef[2 * (j - 1) + 1] : 0.0;
+    const double al_prev = j > 0 ? coef[2 * (j - 1)] : 1.0;
+    if (!(al > 0.0) || !(al_prev > 0.0) || !(be_prev >= 0.0)) return LP_OK;  // broken recurrence
+    dg[j] = 1.0 / al + (j > 0 ? be_prev / al_prev : 0.0);
+    if (j + 1 < kk) off[j] = sqrt(std::max(coef[2 * j + 1], 0.0)) / al;
+  }
+  tridiag_extremes(dg, off, lo, hi);
+  return LP_OK;
+}
+
+// Inner-solve status (never returned to the caller of the library): the first
+// CG steps show Q^{-1} M with a spread far beyond what an embedding of eq.
+// pdprec allows, i.e. this draw of W is one of the probability-delta failures
+// of Lemma 4.1, and the solve has not converged.
+constexpr int kInnerSketchPoor = 100;
+constexpr double kRitzSpread = 1e3;  // ((1 + e)/(1 - e))^2 = 1e3 at e ~ 0.94
+constexpr int kPoorCheckIters = 32;  // act only on solves still running here
+
 // The inner solve on the current factor: dy ~ M^{-1} p.  Returns LP_OK or
-// LP_WARN_INNER_MAXIT.  tol_f > 0: absolute ||f|| target; else relative tol_cg.
-int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
+// LP_WARN_INNER_MAXIT (or kInnerSketchPoor when check_sketch is set).
+// tol_f > 0: absolute ||f|| target; else relative tol_cg.
+// warm: h->dy holds the starting point (CG only); otherwise dy^0 = 0 (Alg. 1)
+int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
+                bool check_sketch = false) {
   const int m = h->m;
   int inner = h->opt.inner;
-  CK(cudaMemsetAsync(h->dy, 0, sizeof(double) * m, h->st));
-  CK(cudaMemcpyAsync(h->r, h->p, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  if (warm && inner != LP_INNER_CG) warm = false;
+  if (!warm) {
+    CK(cudaMemsetAsync(h->dy, 0, sizeof(double) * m, h->st));
+    CK(cudaMemcpyAsync(h->r, h->p, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+  }
   CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
   RET(set_scalar(h, &h->sc->tol_f, tol_f > 0 ? tol_f : 0.0));
+  if (warm) RET(launch_adat(h, h->dy, E_TRUE_RES, true, 0, nullptr));  // r = p - M dy^0
   const int refine = std::max(1, h->opt.refine_every);
   int total_iters = 0;
   if (inner == LP_INNER_CHEBYSHEV) {
@@ -470,18 +516,9 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
       RET(precond_gemvs(h, h->r, h->z, GH_PCG_B, 0));
     }
     RET(sync_read(h));
-    std::vector<double> coef(2 * kl);
-    CK(cudaMemcpy(coef.data(), h->coef, sizeof(double) * 2 * kl, cudaMemcpyDeviceToHost));
     const int kk = std::min(kl, h->hsc->inner_iters);
-    std::vector<double> dg(kk), off(std::max(0, kk - 1));
-    for (int j = 0; j < kk; ++j) {
-      const double al = coef[2 * j], be_prev = j > 0 ? coef[2 * (j - 1) + 1] : 0.0;
-      const double al_prev = j > 0 ? coef[2 * (j - 1)] : 1.0;
-      dg[j] = 1.0 / al + (j > 0 ? be_prev / al_prev : 0.0);
-      if (j + 1 < kk) off[j] = sqrt(coef[2 * j + 1]) / al;
-    }
     double tmin = 0.5, tmax = 2.0;
-    if (kk > 0) tridiag_extremes(dg, off, &tmin, &tmax);
+    RET(ritz_extremes(h, kk, &tmin, &tmax));
     total_iters += kk;
     // restart from dy = 0 with the Chebyshev recurrence
     CK(cudaMemsetAsync(h->dy, 0, sizeof(double) * m, h->st));
@@ -511,6 +548,10 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
   // product's precision floor); then FP64 products for the rest of this solve.
   bool use64 = false;
   double f_prev = h->hsc->f_true;
+  // sketch check: Ritz values of the first refine-block of CG steps (one
+  // unbroken Lanczos run from dy^0)
+  check_sketch = check_sketch && inner == LP_INNER_CG && h->opt.precondition;
+  bool poor = false, ritz_done = false;
   while (true) {
     for (int j = 0; j < refine; ++j) {
       if (inner == LP_INNER_CHEBYSHEV) {
@@ -552,6 +593,16 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
       status = LP_WARN_INNER_MAXIT;
       break;
     }
+    if (check_sketch && !ritz_done) {
+      ritz_done = true;
+      double lo = 0.0, hi = 0.0;
+      RET(ritz_extremes(h, std::min(refine, h->hsc->inner_iters), &lo, &hi));
+      poor = lo > 0.0 && hi > kRitzSpread * lo;
+    }
+    if (poor && h->hsc->inner_iters >= kPoorCheckIters) {
+      status = kInnerSketchPoor;
+      break;
+    }
     if (inner == LP_INNER_CHEBYSHEV && h->hsc->f_true > f_prev) {
       // The residual grew: the interval from the Lanczos estimate misses part
       // of the spectrum.  Continue with CG from the current iterate and the
@@ -569,12 +620,56 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out) {
   return status;
 }
 
-// inner_solve, and once more after refactoring by the QR of (ADW)^T when the
-// iteration limit was hit with the sweep's Q^{-1}: the sweep works on the Gram,
-// which squares kappa(ADW), and near degenerate vertices (or with s = 1) its
-// double-float accuracy can stop being enough for a useful preconditioner.
-int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out) {
-  int st = inner_solve(h, tol_f, iters_out);
+// The sketch an inner solve runs on: D (or D^2), the outer index k and the
+// retry index of the draw in use (updated when the draw is replaced).
+struct SketchRef {
+  const double* dvec;
+  int is_d2;
+  long long k;
+  int* retry;
+};
+
+constexpr int kPoorRedraws = 2;
+
+// inner_solve with two safeguards.
+// (1) A draw of W that fails the embedding (kInnerSketchPoor) is replaced by the
+//     next draw (retry + 1) and the solve continues from the current dy on the
+//     new factor, at most kPoorRedraws times; the stopping rule keeps its
+//     target (relative targets are re-based on the new factor's ||f(0)||).
+// (2) Once more after refactoring by the QR of (ADW)^T when the iteration limit
+//     was hit with the sweep's Q^{-1}: the sweep works on the Gram, which
+//     squares kappa(ADW), and near degenerate vertices its double-float
+//     accuracy can stop being enough for a useful preconditioner.
+int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
+                       const SketchRef* sk = nullptr) {
+  int st = inner_solve(h, tol_f, iters_out, warm, sk != nullptr);
+  for (int redraw = 0; st == kInnerSketchPoor; ++redraw) {
+    if (redraw >= kPoorRedraws || *sk->retry + 1 >= kMaxRetry) {
+      int more = 0;  // keep this draw: finish the solve without the check
+      st = inner_solve(h, tol_f, &more, true, false);
+      *iters_out += more;
+      break;
+    }
+    h->poor_redraws += 1;
+    int rc = LP_ERR_SKETCH_RANK;
+    while (rc == LP_ERR_SKETCH_RANK && *sk->retry + 1 < kMaxRetry) {
+      *sk->retry += 1;
+      CK(launch_sketch(h, sk->dvec, sk->is_d2, h->opt.seed, sk->k, *sk->retry));
+      rc = factor(h);
+    }
+    if (rc != LP_OK) return rc;
+    double tf = tol_f;
+    if (tf <= 0) {  // relative rule: tol_cg ||f(0)|| in the new factor's norm
+      RET(precond_gemvs(h, h->p, h->z, GH_NONE, 0));
+      CK(launch_dot(h->m, h->p, h->z, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[1], h->num_sms, h->st));
+      RET(sync_read(h));
+      tf = h->opt.tol_cg * sqrt(std::max(h->hsc->pad[1], 0.0));
+    }
+    int more = 0;
+    st = inner_solve(h, tf, &more, true, true);
+    *iters_out += more;
+    tol_f = tf;
+  }
   // a small t_max is the caller's choice, not a sign of a failed preconditioner
   if (st != LP_WARN_INNER_MAXIT || h->opt.t_max < 50 || !h->opt.precondition || !h->qinv_df_ok)
     return st;
@@ -623,6 +718,64 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
   else
     CK(launch_v_gather(h->n, xs_x, xs_s, h->uw, h->opt.seed, k, retry, h->s_blocks, h->w, -1.0, h->v,
                        h->num_sms, h->st));
+  return LP_OK;
+}
+
+// Warm start of the inner solve (fixed-sigma rule): features, recording, and a
+// proposal dy^0 accepted only when its true residual beats dy^0 = 0.  Leaves
+// |u|^2 in sc->pad[0] for recording the target after the solve.
+int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
+  *warm = false;
+  if (h->ws_mode == 0 && !h->ws_rec_X) return LP_OK;
+  const int m = h->m;
+  RET(precond_gemvs(h, h->p, h->ws_u, GH_NONE, 0));  // u = Q^{-1} p
+  CK(launch_dot(m, h->ws_u, h->ws_u, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[0], h->num_sms, h->st));
+  CK(launch_dot(m, h->p, h->ws_u, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[1], h->num_sms, h->st));
+  CK(launch_ws_features(m, h->dy_prev, h->ws_have_prev ? 1 : 0, h->ws_u, h->sc, h->ws_X, h->st));
+  if (h->ws_rec_X && h->ws_count < h->ws_cap)
+    CK(cudaMemcpyAsync(h->ws_rec_X + (size_t)h->ws_count * 3 * m, h->ws_X, sizeof(float) * 3 * m,
+                       cudaMemcpyDeviceToDevice, h->st));
+  bool propose = false;
+  if (h->ws_mode == 1 && h->ws_have_prev) {
+    CK(cudaMemcpyAsync(h->dy, h->dy_prev, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    propose = true;
+  } else if (h->ws_mode == 2 && h->ws_model) {
+    if (mlp_predict(h->ws_model, h->ws_X, h->ws_Y, h->st) != LP_OK)
+      return h->fail(LP_ERR_CUDA, "warm-start model forward failed");
+    CK(launch_ws_scale(m, 0, h->ws_Y, nullptr, h->sc, h->dy, nullptr, h->st));
+    propose = true;
+  }
+  // no proposals in the end game (mu < 1e-6 mu_0), where the iterates and the
+  // preconditioner are most delicate and the inner solves are short anyway
+  if (!propose || h->opt.inner != LP_INNER_CG || mu_ratio < 1e-6) return LP_OK;
+  h->ws_props += 1;
+  RET(launch_adat(h, h->dy, E_TRUE_RES, true, 0, nullptr));  // r = p - M dy^0
+  RET(precond_gemvs(h, h->r, h->z, GH_NONE, 0));
+  CK(launch_dot(m, h->r, h->z, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[2], h->num_sms, h->st));
+  CK(launch_dot(m, h->dy, h->dy, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[3], h->num_sms, h->st));
+  RET(sync_read(h));
+  // ||f(dy^0)|| < ||f(0)|| (Q^{-1}-norms), and no large component along nearly
+  // null directions of M, which the residual does not see but which would raise
+  // the rounding floor of the refreshed residual: |dy^0| <= 4 |Q^{-1} p|
+  // (Q^{-1} p approximates dy = M^{-1} p within the preconditioner's spread)
+  if (h->hsc->pad[2] < h->hsc->pad[1] && h->hsc->pad[3] <= 16.0 * h->hsc->pad[0]) {
+    *warm = true;
+    h->ws_acc += 1;
+  }
+  return LP_OK;
+}
+
+// after the inner solve: record the target, keep dy for the next proposal
+int warm_start_finish(lp_handle* h) {
+  const int m = h->m;
+  if (h->ws_rec_X && h->ws_count < h->ws_cap) {
+    CK(launch_ws_scale(m, 1, nullptr, h->dy, h->sc, nullptr, h->ws_rec_T + (size_t)h->ws_count * m, h->st));
+    h->ws_count += 1;
+  }
+  if (h->ws_mode != 0 || h->ws_rec_X) {
+    CK(cudaMemcpyAsync(h->dy_prev, h->dy, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
+    h->ws_have_prev = true;
+  }
   return LP_OK;
 }
 
@@ -917,6 +1070,10 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->rinv_rm, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv, (size_t)h->m * h->m));
   RET(h->alloc(&h->qinv_df, (size_t)h->m * h->m));
+  RET(h->alloc(&h->dy_prev, (size_t)h->lda + 64));
+  RET(h->alloc(&h->ws_u, (size_t)h->lda + 64));
+  RET(h->alloc(&h->ws_X, (size_t)3 * h->m + 64));
+  RET(h->alloc(&h->ws_Y, (size_t)h->m + 64));
   if (h->opt.sigma_rule == 1) {
     for (double** q : {&h->dy_aff, &h->dy_c, &h->p_aff, &h->p_c}) RET(h->alloc(q, (size_t)h->lda + 64));
     for (double** q : {&h->v_aff, &h->v_c}) RET(h->alloc(q, (size_t)h->npad));
@@ -1130,7 +1287,8 @@ int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double
   int retry = 0;
   RET(sketch_and_factor(h, h->nb0, 0, k, &retry));
   int iters = 0;
-  const int status = inner_solve_robust(h, tol_f, &iters);
+  const SketchRef skr{h->nb0, 0, (long long)k, &retry};
+  const int status = inner_solve_robust(h, tol_f, &iters, false, &skr);
   if (status < 0) return status;
   const double f_true = h->hsc->f_true, f0 = sqrt(std::max(h->hsc->rho0, 0.0));
   double vnorm = 0.0;
@@ -1167,6 +1325,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   const auto t_start = std::chrono::steady_clock::now();
   const bool feasible = mode == LP_FEASIBLE;
   h->history.clear();
+  h->ws_have_prev = false;
   lp_result res;
   std::memset(&res, 0, sizeof res);
   const long long n = h->n;
@@ -1254,6 +1413,8 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
     int retry = 0;
     RET(sketch_and_factor(h, h->d2d, 1, k, &retry));
     res.sketch_retries += retry;
+    const int retry0 = retry;
+    const SketchRef skr{h->d2d, 1, (long long)k, &retry};
     ms_fac += ms_since(t0);
     // ---- Algorithm 1 step 3: inner solve to the Lemma 4.4 level ----
     t0 = now();
@@ -1267,8 +1428,13 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
     int iters = 0, ist = 0;
     const size_t mb = sizeof(double) * (size_t)m, nbytes = sizeof(double) * (size_t)n;
     if (!adaptive) {
-      ist = inner_solve_robust(h, tol_f, &iters);
+      bool warm = false;
+      RET(warm_start_prepare(h, mu / mu0, &warm));
+      double tf = tol_f;
+      if (warm && tf <= 0) tf = h->opt.tol_cg * sqrt(std::max(h->hsc->pad[1], 0.0));  // cold ||f^0||
+      ist = inner_solve_robust(h, tf, &iters, warm, &skr);
       if (ist < 0) return ist;
+      RET(warm_start_finish(h));
       ms_in += ms_since(t0);
       // ---- step 5: correction v, directions ----
       t0 = now();
@@ -1281,13 +1447,13 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
       CK(launch_axpby(m, 1.0, h->p, -1.0, h->p_aff, h->p_c, h->num_sms, h->st));
       int it2 = 0;
       CK(cudaMemcpyAsync(h->p, h->p_aff, mb, cudaMemcpyDeviceToDevice, h->st));
-      ist = inner_solve_robust(h, tol_f, &iters);
+      ist = inner_solve_robust(h, tol_f, &iters, false, &skr);
       if (ist < 0) return ist;
       RET(correction(h, h->x, h->s, k, retry));
       CK(cudaMemcpyAsync(h->dy_aff, h->dy, mb, cudaMemcpyDeviceToDevice, h->st));
       CK(cudaMemcpyAsync(h->v_aff, h->v, nbytes, cudaMemcpyDeviceToDevice, h->st));
       CK(cudaMemcpyAsync(h->p, h->p_c, mb, cudaMemcpyDeviceToDevice, h->st));
-      const int ist2 = inner_solve_robust(h, tol_f, &it2);
+      const int ist2 = inner_solve_robust(h, tol_f, &it2, false, &skr);
       if (ist2 < 0) return ist2;
       RET(correction(h, h->x, h->s, k, retry));
       CK(cudaMemcpyAsync(h->dy_c, h->dy, mb, cudaMemcpyDeviceToDevice, h->st));
@@ -1315,6 +1481,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
       hr.inner_iterations = iters;
       hr.retries = retry;
       hr.inner_status = ist;
+      res.sketch_retries += retry - retry0;  // draws replaced by the inner solve's check
       hr.f_norm = h->hsc->f_true;
       hr.f0_norm = sqrt(std::max(h->hsc->rho0, 0.0));
       hr.tol_f = tol_f > 0 ? tol_f : h->opt.tol_cg * hr.f0_norm;
@@ -1347,6 +1514,33 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   res.ms_step = ms_step;
   if (info) *info = res;
   return status;
+}
+
+int lp_set_warm_start(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, float* rec_T,
+                      int32_t rec_capacity) {
+  if (!h || mode < 0 || mode > 2 || (mode == 2 && !model) || rec_capacity < 0) return LP_ERR_ARG;
+  if ((rec_X == nullptr) != (rec_T == nullptr)) return LP_ERR_ARG;
+  if (model) {
+    int in = 0, out = 0;
+    mlp_dims(model, &in, &out);
+    if (in != 3 * h->m || out != h->m) return LP_ERR_ARG;  // features 3m -> dy (m)
+  }
+  h->ws_mode = mode;
+  h->ws_model = model;
+  h->ws_rec_X = rec_X;
+  h->ws_rec_T = rec_T;
+  h->ws_cap = rec_X ? rec_capacity : 0;
+  h->ws_count = h->ws_props = h->ws_acc = 0;
+  h->ws_have_prev = false;
+  return LP_OK;
+}
+
+int lp_get_warm_start_stats(lp_handle* h, int64_t* recorded, int64_t* proposals, int64_t* accepted) {
+  if (!h) return LP_ERR_ARG;
+  if (recorded) *recorded = h->ws_count;
+  if (proposals) *proposals = h->ws_props;
+  if (accepted) *accepted = h->ws_acc;
+  return LP_OK;
 }
 
 int lp_solve_batch(lp_handle* const* hs, int32_t count, double tol, int32_t mode,
@@ -1505,7 +1699,8 @@ int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt_i
     int retry = 0;
     RET(sketch_and_factor(h, h->d2d, 1, 0, &retry));
     int iters = 0;
-    const int st = inner_solve_robust(h, 0.0, &iters);              // dy = (A A^T)^{-1} p
+    const SketchRef skr{h->d2d, 1, 0, &retry};
+    const int st = inner_solve_robust(h, 0.0, &iters, false, &skr);  // dy = (A A^T)^{-1} p
     if (st < 0) return st;
     RET(direction_pass(h, true));                                   // ds = -A^T dy
     CK(launch_axpby(n, 1.0, h->x, -1.0, h->ds, h->x, h->num_sms, h->st));  // x0 = x - ds

@@ -473,6 +473,42 @@ cudaError_t launch_pos_step(long long n, const double* x, const double* s, const
   return cudaGetLastError();
 }
 
+// warm-start features X = [dy_prev / |u|, u / |u|, log10(mu) / 10 * 1] (3m, FP32)
+__global__ void k_ws_features(int m, const double* __restrict__ dy_prev, int have_prev,
+                              const double* __restrict__ u, const DevScalars* sc, float* __restrict__ X) {
+  const double inv = sc->pad[0] > 0.0 ? 1.0 / sqrt(sc->pad[0]) : 0.0;  // 1 / |u|
+  const float lm = (float)(log10(fmax(sc->mu, 1e-300)) / 10.0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    X[i] = have_prev ? (float)(dy_prev[i] * inv) : 0.0f;
+    X[m + i] = (float)(u[i] * inv);
+    X[2 * m + i] = lm;
+  }
+}
+
+// dir 0: out = |u| * Y (FP32 -> FP64);  dir 1: Yf = in / |u| (FP64 -> FP32)
+__global__ void k_ws_scale(int m, int dir, const float* __restrict__ yf, const double* __restrict__ in,
+                           const DevScalars* sc, double* __restrict__ out, float* __restrict__ of) {
+  const double su = sqrt(fmax(sc->pad[0], 0.0));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    if (dir == 0) out[i] = su * (double)yf[i];
+    else of[i] = su > 0.0 ? (float)(in[i] / su) : 0.0f;
+  }
+}
+
+cudaError_t launch_ws_features(int m, const double* dy_prev, int have_prev, const double* u,
+                               const DevScalars* sc, float* X, cudaStream_t st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_ws_features<<<(m + 255) / 256, 256, 0, st>>>(m, dy_prev, have_prev, u, sc, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_scale(int m, int dir, const float* yf, const double* in, const DevScalars* sc,
+                            double* out, float* of, cudaStream_t st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_ws_scale<<<(m + 255) / 256, 256, 0, st>>>(m, dir, yf, in, sc, out, of);
+  return cudaGetLastError();
+}
+
 // x += a dx, s += a ds (n), y += a dy (m); sc->mu = x^T s / n afterwards
 __global__ void k_update(long long n, int m, double* x, double* s, double* y, const double* dx,
                          const double* ds, const double* dy, DevScalars* sc, double* part,

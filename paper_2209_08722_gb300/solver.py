@@ -348,3 +348,88 @@ def solve_batch(solvers, tol: float = 1e-8, mode: str = "infeasible", max_thread
     if rc < 0:
         raise LPError(rc, "batched solve failed")
     return [(o[0], o[1], o[2], res[i].as_dict()) for i, o in enumerate(outs)]
+
+
+class Mlp:
+    """lp_mlp: the warm-start model (features 3m -> hidden -> hidden -> m, GELU).
+    Batches are torch CUDA float32 tensors of shape (batch, features)."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, seed: int = 0, stream=None):
+        self._lib = nat.load()
+        self._h = ctypes.c_void_p()
+        rc = self._lib.lp_mlp_create(ctypes.byref(self._h), int(in_dim), int(hidden), int(out_dim),
+                                     int(seed), stream)
+        if rc != nat.LP_OK:
+            raise LPError(rc, "lp_mlp_create failed")
+        self.in_dim, self.hidden, self.out_dim = int(in_dim), int(hidden), int(out_dim)
+
+    def close(self):
+        if self._h:
+            self._lib.lp_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self) -> int:
+        return int(self._lib.lp_mlp_num_params(self._h))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._check(self._lib.lp_mlp_get_params(self._h, out.ctypes.data))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self._lib.lp_mlp_set_params(self._h, flat.ctypes.data))
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        self._check(self._lib.lp_mlp_get_grads(self._h, out.ctypes.data))
+        return out
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty(X.shape[0], self.out_dim, dtype=torch.float32, device="cuda")
+        self._check(self._lib.lp_mlp_forward(self._h, _ptr(X), int(X.shape[0]), _ptr(Y)))
+        return Y
+
+    def loss_grad(self, X, T) -> float:
+        loss = ctypes.c_double()
+        self._check(self._lib.lp_mlp_loss_grad(self._h, _ptr(X), _ptr(T), int(X.shape[0]), ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, X, T, lr: float) -> float:
+        loss = ctypes.c_double()
+        self._check(self._lib.lp_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
+                                                ctypes.byref(loss)))
+        return loss.value
+
+    def _check(self, rc):
+        if rc != nat.LP_OK:
+            raise LPError(rc, "lp_mlp call failed")
+
+
+def _set_warm_start(self, mode: str = "none", model: Mlp = None, rec_X=None, rec_T=None):
+    """lp_set_warm_start: mode "none" | "previous" | "model"; rec_X (cap, 3m) and
+    rec_T (cap, m) float32 CUDA tensors receive (features, target) per outer
+    iteration when given."""
+    modes = {"none": 0, "previous": 1, "model": 2}
+    cap = 0 if rec_X is None else int(rec_X.shape[0])
+    self._warm_keep = (model, rec_X, rec_T)
+    self._check(self._lib.lp_set_warm_start(self._h, modes[mode], model._h if model else None, _ptr(rec_X),
+                                            _ptr(rec_T), cap))
+
+
+def _warm_start_stats(self) -> dict:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    self._check(self._lib.lp_get_warm_start_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"recorded": a.value, "proposals": b.value, "accepted": c.value}
+
+
+LPSolver.set_warm_start = _set_warm_start
+LPSolver.warm_start_stats = _warm_start_stats
