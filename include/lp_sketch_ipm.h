@@ -154,6 +154,12 @@ typedef struct {
     double tol_f;               /* the inner target used */
     double alpha_max, alpha_bar;
     double sigma;               /* centering parameter used */
+    double r_ratio;             /* max |R_ii| / min |R_ii| of the factor in use (a lower
+                                   bound on kappa(A D W)) */
+    int32_t factor_kind;        /* factor in use at the end of the inner solve: 0 the
+                                   double-float sweep of the Gram, 1 FP64 Cholesky of
+                                   the Gram, 2 FP64 QR of (A D W)^T */
+    int32_t reserved;           /* 0 */
 } lp_iter_record;
 
 /* ---- lifecycle -------------------------------------------------------------- */

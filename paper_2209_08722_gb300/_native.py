@@ -82,7 +82,8 @@ class LpIterRecord(ctypes.Structure):
                 ("inner_status", c_int32), ("mu", c_double), ("rel_gap", c_double),
                 ("rp_rel", c_double), ("rd_rel", c_double), ("f_norm", c_double),
                 ("f0_norm", c_double), ("tol_f", c_double), ("alpha_max", c_double),
-                ("alpha_bar", c_double), ("sigma", c_double)]
+                ("alpha_bar", c_double), ("sigma", c_double), ("r_ratio", c_double),
+                ("factor_kind", c_int32), ("reserved", c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

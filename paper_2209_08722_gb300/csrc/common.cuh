@@ -47,7 +47,8 @@ struct DevScalars {
   double dot_tmp;
   double cheb_rho;    // Chebyshev recurrence scalar
   double lam_min, lam_max;
-  int inner_done;     // 1: recursive residual small, 2: true residual converged
+  int inner_done;     // 1: recursive residual small, 2: true residual converged,
+                      // 3: r^T Q^{-1} r <= 0 (indefinite stored Q^{-1})
   int inner_iters;    // iterations taken by the inner solver
   int rank_bad;       // sketch factor rank check failed
   int err;            // ERR_* (sticky)

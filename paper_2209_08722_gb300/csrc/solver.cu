@@ -86,6 +86,10 @@ struct lp_handle {
   long long breakdown_recoveries = 0;  // inner solves that switched product after a CG breakdown
   long long qr_refactors = 0;          // inner solves rerun after refactoring by QR
   long long poor_redraws = 0;          // draws of W replaced after failing the Ritz check
+  long long indefinite_refactors = 0;  // FP64 refactors after r^T Q^{-1} r <= 0
+  int factor_kind = 0;  // factor in use: 0 double-float sweep, 1 FP64 Cholesky, 2 FP64 QR
+  double ratio_ref = 0.0;  // largest accepted max/min |R_ii| of this solve (0: none yet)
+  long long jump_redraws = 0;  // draws of W replaced after a jump of max/min |R_ii|
   double *dy_aff = nullptr, *dy_c = nullptr, *p_aff = nullptr, *p_c = nullptr;  // two-RHS variant (m)
   double *v_aff = nullptr, *v_c = nullptr;                                        // ... (n)
   // learned / previous-direction warm start of the inner solve
@@ -337,7 +341,10 @@ int factor_chol(lp_handle* h) {
     CK(launch_factor_utils(2, h->rinv_cm, w, m, h->rinv_rm, h->sc, 0.0, h->num_sms, h->st));
     CK(cudaMemcpyAsync(h->hinfo + 1, h->dinfo + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     RET(sync_read(h));
-    if (h->hinfo[1] == 0) return form_qinv(h);
+    if (h->hinfo[1] == 0) {
+      h->factor_kind = 1;
+      return form_qinv(h);
+    }
   }
   h->qr_fallbacks += 1;
   return factor_qr(h);
@@ -361,6 +368,7 @@ int factor(lp_handle* h) {
   if (!h->hsc->rank_bad) {
     h->qinv_ok = true;
     h->qinv_df_ok = true;
+    h->factor_kind = 0;
     return LP_OK;
   }
   h->sweep_fallbacks += 1;
@@ -387,6 +395,7 @@ int factor_qr(lp_handle* h) {
   if (h->hsc->rank_bad || h->hinfo[0] != 0 || h->hinfo[1] != 0)
     return h->fail(LP_ERR_SKETCH_RANK, "A D W is numerically rank deficient (|R_ii| range %.3e..%.3e)",
                    h->hsc->diag_min, h->hsc->diag_max);
+  h->factor_kind = 2;
   return form_qinv(h);
 }
 
@@ -406,20 +415,45 @@ cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t 
                             h->s_blocks, h->w, h->adw, h->cs, h->num_sms, h->st);
 }
 
-// sketch for (k, retry) + factor, redrawing on a rank failure (Lemma 4.1)
+// Largest jump of max/min |R_ii| (a lower bound on kappa(A D W)) over the
+// largest accepted value of the solve that a draw may show.  On the central path
+// kappa(A D) grows smoothly (about 2.5x per outer iteration at most on the
+// planted families); near the optimum range((AD)^T) is close to the span of the
+// m basic coordinates, and a draw whose rows for those columns are linearly
+// dependent (with s = 2: two columns sharing both buckets, or a cycle of
+// shared buckets with the wrong sign parity) leaves only the nonbasic columns,
+// about (mu / x_B)^{1/2} times smaller, to fill the lost direction: the ratio
+// jumps by 1e4 or more in one iteration (the double-float Gram's rounding
+// floor can hide part of the jump from the sweep's pivots).
+constexpr double kRatioJump = 1e2;
+constexpr int kJumpRedraws = 6;
+
+// sketch for (k, retry) + factor, redrawing (retry + 1) on a rank failure
+// (Lemma 4.1) and, within a solve, on a jump of max/min |R_ii| (above).
+// *retries holds the first retry index to try and receives the one in use.
 int sketch_and_factor(lp_handle* h, const double* dvec, int is_d2, long long k, int* retries) {
   if (!h->opt.precondition) {  // the unpreconditioned comparison: no sketch, no factor
     *retries = 0;
     return LP_OK;
   }
   int rc = LP_ERR_SKETCH_RANK;
-  for (int retry = 0; retry < kMaxRetry; ++retry) {
+  int jumps = 0;
+  for (int retry = *retries; retry < kMaxRetry; ++retry) {
     CK(launch_sketch(h, dvec, is_d2, h->opt.seed, k, retry));
     rc = factor(h);
-    if (rc != LP_ERR_SKETCH_RANK) {
-      if (retries) *retries = retry;
-      return rc;
+    *retries = retry;
+    if (rc == LP_ERR_SKETCH_RANK) continue;
+    if (rc != LP_OK) return rc;
+    const double ratio = h->hsc->diag_min > 0 ? h->hsc->diag_max / h->hsc->diag_min : INFINITY;
+    if (h->ratio_ref > 0.0 && ratio > kRatioJump * h->ratio_ref && jumps < kJumpRedraws &&
+        retry + 1 < kMaxRetry) {
+      jumps += 1;
+      h->jump_redraws += 1;
+      continue;
     }
+    if (ratio <= kRatioJump * h->ratio_ref || h->ratio_ref == 0.0)
+      h->ratio_ref = std::max(h->ratio_ref, ratio);
+    return LP_OK;
   }
   return rc;
 }
@@ -485,8 +519,16 @@ int ritz_extremes(lp_handle* h, int kk, double* lo, double* hi) {
 // pdprec allows, i.e. this draw of W is one of the probability-delta failures
 // of Lemma 4.1, and the solve has not converged.
 constexpr int kInnerSketchPoor = 100;
+// Inner-solve status: r^T Q^{-1} r <= 0 for r != 0 (inner_done = 3), i.e. the
+// stored Q^{-1} is not positive definite at this residual.  The double-float
+// sweep inverts the Gram by Gauss-Jordan, whose error relative to ||Q^{-1}|| is
+// about kappa(Q) u; once that exceeds 1 / kappa(Q) the stored inverse can be
+// indefinite.  Q^{-1} = R^{-1} R^{-T} from an FP64 Cholesky or QR is the Gram
+// of R^{-1} and keeps its definiteness up to kappa(Q) ~ 1 / u_64.
+constexpr int kInnerIndefinite = 101;
 constexpr double kRitzSpread = 1e3;  // ((1 + e)/(1 - e))^2 = 1e3 at e ~ 0.94
-constexpr int kPoorCheckIters = 32;  // act only on solves still running here
+constexpr int kPoorCheckIters = 32;  // act only on solves still running here ...
+constexpr double kRitzSevere = 1e6;  // ... or at once beyond this spread
 
 // The inner solve on the current factor: dy ~ M^{-1} p.  Returns LP_OK or
 // LP_WARN_INNER_MAXIT (or kInnerSketchPoor when check_sketch is set).
@@ -516,6 +558,10 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
       RET(precond_gemvs(h, h->r, h->z, GH_PCG_B, 0));
     }
     RET(sync_read(h));
+    if (h->hsc->inner_done == 3) {
+      *iters_out = total_iters + h->hsc->inner_iters;
+      return kInnerIndefinite;
+    }
     const int kk = std::min(kl, h->hsc->inner_iters);
     double tmin = 0.5, tmax = 2.0;
     RET(ritz_extremes(h, kk, &tmin, &tmax));
@@ -532,6 +578,10 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
     RET(precond_gemvs(h, h->r, h->z, GH_PCG_INIT, 0));
   }
   RET(sync_read(h));
+  if (h->hsc->inner_done == 3) {
+    *iters_out = total_iters;
+    return kInnerIndefinite;
+  }
   if (tol_f <= 0) {
     const double f0 = sqrt(std::max(h->hsc->rho0, 0.0));
     RET(set_scalar(h, &h->sc->tol_f, h->opt.tol_cg * f0));
@@ -551,7 +601,7 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
   // sketch check: Ritz values of the first refine-block of CG steps (one
   // unbroken Lanczos run from dy^0)
   check_sketch = check_sketch && inner == LP_INNER_CG && h->opt.precondition;
-  bool poor = false, ritz_done = false;
+  bool poor = false, severe = false, ritz_done = false;
   while (true) {
     for (int j = 0; j < refine; ++j) {
       if (inner == LP_INNER_CHEBYSHEV) {
@@ -583,11 +633,19 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
       RET(precond_gemvs(h, h->r, h->z, GH_REFRESH, 0));
       RET(sync_read(h));
       f_prev = h->hsc->f_true;
+      if (h->hsc->inner_done == 3) {
+        status = kInnerIndefinite;
+        break;
+      }
       if (h->hsc->inner_done == 2) break;
       continue;
     }
     RET(sync_read(h));
     if (h->opt.profile) ev_flush(h);
+    if (h->hsc->inner_done == 3) {
+      status = kInnerIndefinite;
+      break;
+    }
     if (h->hsc->inner_done == 2) break;
     if (h->hsc->inner_iters >= h->opt.t_max) {
       status = LP_WARN_INNER_MAXIT;
@@ -598,8 +656,9 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
       double lo = 0.0, hi = 0.0;
       RET(ritz_extremes(h, std::min(refine, h->hsc->inner_iters), &lo, &hi));
       poor = lo > 0.0 && hi > kRitzSpread * lo;
+      severe = lo > 0.0 && hi > kRitzSevere * lo;
     }
-    if (poor && h->hsc->inner_iters >= kPoorCheckIters) {
+    if (poor && (severe || h->hsc->inner_iters >= kPoorCheckIters)) {
       status = kInnerSketchPoor;
       break;
     }
@@ -629,35 +688,67 @@ struct SketchRef {
   int* retry;
 };
 
-constexpr int kPoorRedraws = 2;
+constexpr int kPoorRedraws = 4;
+constexpr int kIndefRefactors = 2;
 
-// inner_solve with two safeguards.
+// inner_solve with three safeguards.
 // (1) A draw of W that fails the embedding (kInnerSketchPoor) is replaced by the
 //     next draw (retry + 1) and the solve continues from the current dy on the
-//     new factor, at most kPoorRedraws times; the stopping rule keeps its
-//     target (relative targets are re-based on the new factor's ||f(0)||).
-// (2) Once more after refactoring by the QR of (ADW)^T when the iteration limit
+//     new factor, at most kPoorRedraws times.
+// (2) An indefinite stored Q^{-1} (kInnerIndefinite) is replaced by the FP64
+//     Cholesky of the same Gram (sweep -> Cholesky) or the FP64 QR of (ADW)^T
+//     (Cholesky -> QR), and the solve continues from the current dy.
+//     In both cases the stopping rule keeps its target (relative targets are
+//     re-based on the new factor's ||f(0)||).
+// (3) Once more after refactoring by the QR of (ADW)^T when the iteration limit
 //     was hit with the sweep's Q^{-1}: the sweep works on the Gram, which
 //     squares kappa(ADW), and near degenerate vertices its double-float
 //     accuracy can stop being enough for a useful preconditioner.
 int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
                        const SketchRef* sk = nullptr) {
   int st = inner_solve(h, tol_f, iters_out, warm, sk != nullptr);
-  for (int redraw = 0; st == kInnerSketchPoor; ++redraw) {
-    if (redraw >= kPoorRedraws || *sk->retry + 1 >= kMaxRetry) {
+  int redraws = 0, refactors = 0;
+  while (st == kInnerSketchPoor || st == kInnerIndefinite) {
+    if (st == kInnerSketchPoor && (redraws >= kPoorRedraws || *sk->retry + 1 >= kMaxRetry)) {
       int more = 0;  // keep this draw: finish the solve without the check
       st = inner_solve(h, tol_f, &more, true, false);
       *iters_out += more;
-      break;
+      redraws = kPoorRedraws;
+      continue;
     }
-    h->poor_redraws += 1;
-    int rc = LP_ERR_SKETCH_RANK;
-    while (rc == LP_ERR_SKETCH_RANK && *sk->retry + 1 < kMaxRetry) {
+    if (st == kInnerSketchPoor) {
+      redraws += 1;
+      h->poor_redraws += 1;
       *sk->retry += 1;
-      CK(launch_sketch(h, sk->dvec, sk->is_d2, h->opt.seed, sk->k, *sk->retry));
-      rc = factor(h);
+      RET(sketch_and_factor(h, sk->dvec, sk->is_d2, sk->k, sk->retry));
+    } else {
+      if (h->factor_kind == 2 || refactors >= kIndefRefactors) {
+        st = LP_WARN_INNER_MAXIT;  // no better factor to turn to
+        break;
+      }
+      refactors += 1;
+      h->indefinite_refactors += 1;
+      const int rc = (h->factor_kind == 0 && h->blas) ? factor_chol(h) : factor_qr(h);
+      const bool can_redraw = sk && redraws < kPoorRedraws && *sk->retry + 1 < kMaxRetry;
+      const double ratio = h->hsc->diag_min > 0 ? h->hsc->diag_max / h->hsc->diag_min : INFINITY;
+      if ((rc == LP_ERR_SKETCH_RANK || (rc == LP_OK && h->ratio_ref > 0.0 &&
+                                         ratio > kRatioJump * h->ratio_ref)) && can_redraw) {
+        // the FP64 factor shows the draw itself collapsed: replace it
+        h->err.clear();
+        redraws += 1;
+        h->poor_redraws += 1;
+        *sk->retry += 1;
+        RET(sketch_and_factor(h, sk->dvec, sk->is_d2, sk->k, sk->retry));
+      } else if (rc == LP_ERR_SKETCH_RANK) {
+        // judged rank deficient in FP64: keep the solve so far on the sweep
+        h->err.clear();
+        RET(factor(h));
+        st = LP_WARN_INNER_MAXIT;
+        break;
+      } else if (rc != LP_OK) {
+        return rc;
+      }
     }
-    if (rc != LP_OK) return rc;
     double tf = tol_f;
     if (tf <= 0) {  // relative rule: tol_cg ||f(0)|| in the new factor's norm
       RET(precond_gemvs(h, h->p, h->z, GH_NONE, 0));
@@ -666,7 +757,7 @@ int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out, bool warm = f
       tf = h->opt.tol_cg * sqrt(std::max(h->hsc->pad[1], 0.0));
     }
     int more = 0;
-    st = inner_solve(h, tf, &more, true, true);
+    st = inner_solve(h, tf, &more, true, sk != nullptr && redraws < kPoorRedraws);
     *iters_out += more;
     tol_f = tf;
   }
@@ -686,7 +777,7 @@ int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out, bool warm = f
   int more = 0;
   st = inner_solve(h, tol_f, &more);
   *iters_out += more;
-  return st;
+  return st == kInnerIndefinite ? LP_WARN_INNER_MAXIT : st;
 }
 
 // v = (XS)^{1/2} W (ADW)^T Q^{-1} (M dy - p); the last refresh left r = p - M dy
@@ -1285,6 +1376,7 @@ int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double
   h->d2df_valid = false;
   CK(launch_to_f32(h->n, h->nb0, h->d2f, 1, h->num_sms, h->st));
   int retry = 0;
+  h->ratio_ref = 0.0;  // a single solve: no earlier factor to compare with
   RET(sketch_and_factor(h, h->nb0, 0, k, &retry));
   int iters = 0;
   const SketchRef skr{h->nb0, 0, (long long)k, &retry};
@@ -1325,6 +1417,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   const auto t_start = std::chrono::steady_clock::now();
   const bool feasible = mode == LP_FEASIBLE;
   h->history.clear();
+  h->ratio_ref = 0.0;
   h->ws_have_prev = false;
   lp_result res;
   std::memset(&res, 0, sizeof res);
@@ -1481,6 +1574,8 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
       hr.inner_iterations = iters;
       hr.retries = retry;
       hr.inner_status = ist;
+      hr.factor_kind = h->factor_kind;
+      hr.r_ratio = h->hsc->diag_min > 0 ? h->hsc->diag_max / h->hsc->diag_min : INFINITY;
       res.sketch_retries += retry - retry0;  // draws replaced by the inner solve's check
       hr.f_norm = h->hsc->f_true;
       hr.f0_norm = sqrt(std::max(h->hsc->rho0, 0.0));

@@ -41,6 +41,7 @@ enum GemvEpi : int {
   G_PCG_INIT = 1,   // rho = r.z, p = z, f_rec = sqrt(rho)
   G_PCG_B = 2,      // rho' = r.z; beta = rho'/rho; p = z + beta p; done if sqrt(rho') <= 0.5 tol
   G_REFRESH = 3,    // true residual: rho' = r.z; converged if sqrt(rho') <= tol; else residual replacement
+                    // (INIT and REFRESH kinds: r.z <= 0 with r != 0 sets inner_done = 3)
   G_CHEB_INIT = 4,  // rho = r.z; dir = z / theta; cheb_rho = 1/s1
   G_CHEB_B = 5,     // cheb recurrence on dir; f_rec = sqrt(r.z)
   G_CHEB_REFRESH = 6,  // true residual: converged if sqrt(r.z) <= tol; direction untouched
@@ -158,14 +159,30 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   // ---- epilogue (one CTA): m-vector CG / Chebyshev updates ----
   DevScalars* sc = a.sc;
   const double* z = a.y;
-  double rz = 0.0;
-  for (int i = threadIdx.x; i < a.m; i += blockDim.x) rz += a.r[i] * __ldcg(z + i);
+  double rz = 0.0, rr = 0.0;
+  for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
+    const double ri = a.r[i];
+    rz += ri * __ldcg(z + i);
+    rr += ri * ri;
+  }
   rz = block_sum(rz, red);
+  rr = block_sum(rr, red);
   if (!isfinite(rz)) {
     if (threadIdx.x == 0) atomicExch(a.err, ERR_NUMERICAL);
     return;
   }
   const double f = sqrt(fmax(rz, 0.0));
+  // r^T Q^{-1} r <= 0 with r != 0: the stored Q^{-1} has lost definiteness
+  // (rounding), so ||f|| means nothing; the host refactors (inner_done = 3)
+  const bool indefinite = rz <= 0.0 && rr > 0.0;
+  if (indefinite && (a.epi == G_PCG_INIT || a.epi == G_REFRESH || a.epi == G_CHEB_INIT ||
+                     a.epi == G_CHEB_REFRESH)) {
+    if (threadIdx.x == 0) {
+      sc->f_true = 0.0;
+      sc->inner_done = 3;
+    }
+    return;
+  }
   if (a.epi == G_PCG_INIT) {
     for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i);
     if (threadIdx.x == 0) {
