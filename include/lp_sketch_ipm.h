@@ -344,11 +344,17 @@ int lp_mlp_loss_grad(lp_mlp* model, const float* X, const float* T, int32_t batc
 int lp_mlp_train_step(lp_mlp* model, const float* X, const float* T, int32_t batch, float lr, double* loss);
 
 /* Warm start of lp_solve's inner solves (fixed-sigma rule).  mode 0: none (the
- * paper: dy^0 = 0); 1: dy^0 = dy_{k-1}; 2: dy^0 = |u| model(X).  A proposal is
- * used only while mu >= 1e-6 mu_0 and only if its true residual is smaller,
- * sqrt(r^T Q^{-1} r) < sqrt(p^T Q^{-1} p) with r = p - A D^2 A^T dy^0, and
- * |dy^0| <= 4 |Q^{-1} p|; the stopping rule (relative to the cold residual
- * sqrt(p^T Q^{-1} p)) is unchanged, so the iterate returned satisfies the same bound.  rec_X (3m x capacity) and rec_T
+ * paper: dy^0 = 0); 1: the previous outer iteration's dy; 2: the model's
+ * proposal |u| model(X) and the previous dy.  The candidates v_i are combined
+ * by one Galerkin step on M = A D^2 A^T, dy^0 = sum c_i v_i with
+ * (v_i^T M v_j) c = (v_i^T p) (one FP64-class product per candidate), the
+ * start of least ||M^{-1} p - dy^0||_M in their span.  dy^0 is used only while
+ * mu >= 1e-6 mu_0, only if its true residual is smaller, sqrt(r^T Q^{-1} r) <
+ * sqrt(p^T Q^{-1} p) with r = p - M dy^0, and only if |dy^0| <= 4 |Q^{-1} p|;
+ * the stopping rule (relative to the cold residual sqrt(p^T Q^{-1} p)) is
+ * unchanged, so the iterate returned satisfies the same bound.  Features X
+ * (3m, FP32): [dy_{k-1} / |u|, u / |u|, (log10(mu) / 10) 1_m] with
+ * u = Q^{-1} p; target dy_k / |u|.  rec_X (3m x capacity) and rec_T
  * (m x capacity), device FP32, nullable: every outer iteration's features and
  * target are appended until capacity (for training).  The model is borrowed,
  * not owned. */

@@ -99,6 +99,8 @@ struct lp_handle {
   long long ws_cap = 0, ws_count = 0, ws_props = 0, ws_acc = 0;
   bool ws_have_prev = false;
   double *dy_prev = nullptr, *ws_u = nullptr;
+  double *ws_v = nullptr, *ws_w = nullptr, *ws_dots = nullptr;  // proposal, M v_i (2 m), dots
+  bool warm_r_ready = false;  // h->r already holds p - M dy^0 for the warm start
   float *ws_X = nullptr, *ws_Y = nullptr;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
@@ -545,7 +547,9 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
   }
   CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
   RET(set_scalar(h, &h->sc->tol_f, tol_f > 0 ? tol_f : 0.0));
-  if (warm) RET(launch_adat(h, h->dy, E_TRUE_RES, true, 0, nullptr));  // r = p - M dy^0
+  // r = p - M dy^0, unless the warm start just formed it from the same products
+  if (warm && !h->warm_r_ready) RET(launch_adat(h, h->dy, E_TRUE_RES, true, 0, nullptr));
+  h->warm_r_ready = false;
   const int refine = std::max(1, h->opt.refine_every);
   int total_iters = 0;
   if (inner == LP_INNER_CHEBYSHEV) {
@@ -813,10 +817,16 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
 }
 
 // Warm start of the inner solve (fixed-sigma rule): features, recording, and a
-// proposal dy^0 accepted only when its true residual beats dy^0 = 0.  Leaves
-// |u|^2 in sc->pad[0] for recording the target after the solve.
+// proposal.  The candidates v_1 = |u| model(X) (mode 2) and v_2 = dy_{k-1}
+// (modes 1 and 2) are combined by one Galerkin step on M: dy^0 = sum c_i v_i
+// with (v_i^T M v_j) c = (v_i^T p), the start of least energy-norm error
+// ||M^{-1} p - dy^0||_M in their span, never worse than dy^0 = 0 in that norm.
+// Its residual r^0 = p - sum c_i M v_i comes from the same products (one
+// FP64-class product per candidate), and dy^0 is used only when its true
+// residual beats dy^0 = 0.  Leaves |u|^2 in sc->pad[0] for recording the target.
 int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   *warm = false;
+  h->warm_r_ready = false;
   if (h->ws_mode == 0 && !h->ws_rec_X) return LP_OK;
   const int m = h->m;
   RET(precond_gemvs(h, h->p, h->ws_u, GH_NONE, 0));  // u = Q^{-1} p
@@ -826,21 +836,46 @@ int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   if (h->ws_rec_X && h->ws_count < h->ws_cap)
     CK(cudaMemcpyAsync(h->ws_rec_X + (size_t)h->ws_count * 3 * m, h->ws_X, sizeof(float) * 3 * m,
                        cudaMemcpyDeviceToDevice, h->st));
-  bool propose = false;
-  if (h->ws_mode == 1 && h->ws_have_prev) {
-    CK(cudaMemcpyAsync(h->dy, h->dy_prev, sizeof(double) * m, cudaMemcpyDeviceToDevice, h->st));
-    propose = true;
-  } else if (h->ws_mode == 2 && h->ws_model) {
+  const double* v[2];
+  int nv = 0;
+  if (h->ws_mode == 2 && h->ws_model) {
     if (mlp_predict(h->ws_model, h->ws_X, h->ws_Y, h->st) != LP_OK)
       return h->fail(LP_ERR_CUDA, "warm-start model forward failed");
-    CK(launch_ws_scale(m, 0, h->ws_Y, nullptr, h->sc, h->dy, nullptr, h->st));
-    propose = true;
+    CK(launch_ws_scale(m, 0, h->ws_Y, nullptr, h->sc, h->ws_v, nullptr, h->st));
+    v[nv++] = h->ws_v;
   }
+  if (h->ws_mode != 0 && h->ws_have_prev) v[nv++] = h->dy_prev;
   // no proposals in the end game (mu < 1e-6 mu_0), where the iterates and the
   // preconditioner are most delicate and the inner solves are short anyway
-  if (!propose || h->opt.inner != LP_INNER_CG || mu_ratio < 1e-6) return LP_OK;
+  if (nv == 0 || h->opt.inner != LP_INNER_CG || mu_ratio < 1e-6) return LP_OK;
   h->ws_props += 1;
-  RET(launch_adat(h, h->dy, E_TRUE_RES, true, 0, nullptr));  // r = p - M dy^0
+  const size_t wst = (size_t)h->lda + 64;
+  double* wv[2] = {h->ws_w, h->ws_w + wst};
+  for (int i = 0; i < nv; ++i) RET(launch_adat(h, v[i], E_PLAIN, true, 0, wv[i]));  // M v_i
+  // dots: [0] v0.Mv0 [1] v0.Mv1 [2] v1.Mv0 [3] v1.Mv1 [4] v0.p [5] v1.p
+  for (int i = 0; i < nv; ++i) {
+    for (int j = 0; j < nv; ++j)
+      CK(launch_dot(m, v[i], wv[j], 1.0, h->vpart, h->tickets + 3, h->ws_dots + 2 * i + j, h->num_sms, h->st));
+    CK(launch_dot(m, v[i], h->p, 1.0, h->vpart, h->tickets + 3, h->ws_dots + 4 + i, h->num_sms, h->st));
+  }
+  double g[6] = {0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(g, h->ws_dots, sizeof g, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  double c0 = 0.0, c1 = 0.0;
+  const double g01 = 0.5 * (g[1] + g[2]);
+  const double det = g[0] * g[3] - g01 * g01;
+  if (nv == 2 && g[0] > 0.0 && g[3] > 0.0 && det > 1e-10 * g[0] * g[3]) {
+    c0 = (g[4] * g[3] - g01 * g[5]) / det;
+    c1 = (g[0] * g[5] - g01 * g[4]) / det;
+  } else if (g[0] > 0.0) {
+    c0 = g[4] / g[0];  // the first candidate alone
+    nv = 1;
+  } else {
+    return LP_OK;
+  }
+  CK(launch_axpby(m, c0, v[0], nv == 2 ? c1 : 0.0, nv == 2 ? v[1] : v[0], h->dy, h->num_sms, h->st));
+  CK(launch_axpby(m, 1.0, h->p, -c0, wv[0], h->r, h->num_sms, h->st));  // r^0 = p - sum c_i M v_i
+  if (nv == 2) CK(launch_axpby(m, 1.0, h->r, -c1, wv[1], h->r, h->num_sms, h->st));
   RET(precond_gemvs(h, h->r, h->z, GH_NONE, 0));
   CK(launch_dot(m, h->r, h->z, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[2], h->num_sms, h->st));
   CK(launch_dot(m, h->dy, h->dy, 1.0, h->vpart, h->tickets + 3, &h->sc->pad[3], h->num_sms, h->st));
@@ -851,6 +886,7 @@ int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   // (Q^{-1} p approximates dy = M^{-1} p within the preconditioner's spread)
   if (h->hsc->pad[2] < h->hsc->pad[1] && h->hsc->pad[3] <= 16.0 * h->hsc->pad[0]) {
     *warm = true;
+    h->warm_r_ready = true;
     h->ws_acc += 1;
   }
   return LP_OK;
@@ -1163,6 +1199,9 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->qinv_df, (size_t)h->m * h->m));
   RET(h->alloc(&h->dy_prev, (size_t)h->lda + 64));
   RET(h->alloc(&h->ws_u, (size_t)h->lda + 64));
+  RET(h->alloc(&h->ws_v, (size_t)h->lda + 64));
+  RET(h->alloc(&h->ws_w, 2 * ((size_t)h->lda + 64)));
+  RET(h->alloc(&h->ws_dots, 16));
   RET(h->alloc(&h->ws_X, (size_t)3 * h->m + 64));
   RET(h->alloc(&h->ws_Y, (size_t)h->m + 64));
   if (h->opt.sigma_rule == 1) {

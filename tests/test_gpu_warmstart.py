@@ -70,5 +70,8 @@ def test_learned_warm_start_keeps_the_solution_and_saves_inner_iterations():
                 inner += info["inner_total"]
                 accepted += S.warm_start_stats()["accepted"]
         counts[mode] = (inner, accepted)
-    assert counts["model"][1] > 0
-    assert counts["model"][0] <= counts["none"][0], counts
+    # the Galerkin-combined proposals are used on most outer iterations and
+    # save a clear share of the inner iterations (about a quarter here)
+    assert counts["model"][1] > 0.5 * 4 * 30, counts
+    assert counts["previous"][0] <= 0.9 * counts["none"][0], counts
+    assert counts["model"][0] <= 0.9 * counts["none"][0], counts
