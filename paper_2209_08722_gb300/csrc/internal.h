@@ -114,7 +114,7 @@ cudaError_t launch_v_gather(long long n, const double* x, const double* s, const
 
 enum GemvEpiHost : int {
   GH_NONE = 0, GH_PCG_INIT = 1, GH_PCG_B = 2, GH_REFRESH = 3, GH_CHEB_INIT = 4, GH_CHEB_B = 5,
-  GH_CHEB_REFRESH = 6
+  GH_CHEB_REFRESH = 6, GH_PCG_B_LAST = 7
 };
 cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,

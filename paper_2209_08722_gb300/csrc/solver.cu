@@ -614,7 +614,7 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
         RET(precond_gemvs(h, h->r, h->z, GH_CHEB_B, 1));
       } else {
         RET(launch_adat(h, h->pdir, E_PCG_A, use64, 1, h->q));
-        RET(precond_gemvs(h, h->r, h->z, GH_PCG_B, 1));
+        RET(precond_gemvs(h, h->r, h->z, j + 1 == refine ? GH_PCG_B_LAST : GH_PCG_B, 1));
       }
     }
     // FP64 true residual r = p - M dy, ||f|| = sqrt(r^T Q^{-1} r)

@@ -45,6 +45,7 @@ enum GemvEpi : int {
   G_CHEB_INIT = 4,  // rho = r.z; dir = z / theta; cheb_rho = 1/s1
   G_CHEB_B = 5,     // cheb recurrence on dir; f_rec = sqrt(r.z)
   G_CHEB_REFRESH = 6,  // true residual: converged if sqrt(r.z) <= tol; direction untouched
+  G_PCG_B_LAST = 7,    // G_PCG_B on the last step before a refresh: p and rho are left for it
 };
 
 struct GemvArgs {
@@ -192,32 +193,40 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
       sc->f_true = f;
       sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
     }
-  } else if (a.epi == G_PCG_B || a.epi == G_REFRESH) {
-    double beta = rz / sc->rho;
-    bool stop;
-    if (a.epi == G_PCG_B) {
-      stop = f <= 0.5 * sc->tol_f;
-    } else {
-      stop = f <= sc->tol_f;
-      // The recursion drifted far from the FP64 residual (FP32 products):
-      // restart CG from the current iterate (iterative refinement) instead of
-      // residual replacement.
-      if (f > 4.0 * sc->f_rec) beta = 0.0;
+  } else if (a.epi == G_PCG_B || a.epi == G_PCG_B_LAST) {
+    // CG step k: beta_k = rho_{k+1} / rho_k, p_{k+1} = z + beta_k p_k.  The last
+    // step before a refresh (and a step that stops) leaves p_k and rho_k in
+    // place: the refresh replaces r and z by their true values and makes this
+    // direction update itself, once (residual replacement).
+    const double beta = rz / sc->rho;
+    const bool stop = f <= 0.5 * sc->tol_f;
+    const bool defer = stop || a.epi == G_PCG_B_LAST || sc->inner_iters + 1 >= a.t_max;
+    if (!defer)
+      for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) + beta * a.p[i];
+    if (threadIdx.x == 0) {
+      if (!defer) {
+        sc->rho = rz;
+        if (a.coef && sc->inner_iters < 1024) a.coef[2 * sc->inner_iters + 1] = beta;
+      }
+      sc->f_rec = f;
+      sc->inner_iters += 1;
+      if (stop || sc->inner_iters >= a.t_max) sc->inner_done = 1;
     }
+  } else if (a.epi == G_REFRESH) {
+    // true residual r = p - M dy, z = Q^{-1} r: converged if sqrt(r.z) <= tol;
+    // else p = z + (r.z / rho_k) p_k, or p = z (restart) when the recursion
+    // drifted far from the FP64 residual (FP32 products).
+    double beta = rz / sc->rho;
+    const bool stop = f <= sc->tol_f;
+    if (f > 4.0 * sc->f_rec) beta = 0.0;
     if (!stop)
       for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) + beta * a.p[i];
     if (threadIdx.x == 0) {
       sc->rho = rz;
-      if (a.epi == G_PCG_B) {
-        if (a.coef && sc->inner_iters < 1024) a.coef[2 * sc->inner_iters + 1] = beta;
-        sc->f_rec = f;
-        sc->inner_iters += 1;
-        if (stop) sc->inner_done = 1;
-        else if (sc->inner_iters >= a.t_max) sc->inner_done = 1;
-      } else {
-        sc->f_true = f;
-        sc->inner_done = stop ? 2 : 0;
-      }
+      const int j = sc->inner_iters - 1;  // the deferred step's coefficient
+      if (a.coef && j >= 0 && j < 1024) a.coef[2 * j + 1] = beta;
+      sc->f_true = f;
+      sc->inner_done = stop ? 2 : 0;
     }
   } else if (a.epi == G_CHEB_INIT) {
     const double theta = 0.5 * (sc->lam_max + sc->lam_min);
