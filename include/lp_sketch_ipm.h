@@ -347,7 +347,7 @@ int lp_mlp_train_step(lp_mlp* model, const float* X, const float* T, int32_t bat
  * paper: dy^0 = 0); 1: the previous outer iteration's dy; 2: the model's
  * proposal |u| model(X) and the previous dy.  The candidates v_i are combined
  * by one Galerkin step on M = A D^2 A^T, dy^0 = sum c_i v_i with
- * (v_i^T M v_j) c = (v_i^T p) (one FP64-class product per candidate), the
+ * (v_i^T M v_j) c = (v_i^T p) (one FP32 product per candidate), the
  * start of least ||M^{-1} p - dy^0||_M in their span.  dy^0 is used only while
  * mu >= 1e-6 mu_0, only if its true residual is smaller, sqrt(r^T Q^{-1} r) <
  * sqrt(p^T Q^{-1} p) with r = p - M dy^0, and only if |dy^0| <= 4 |Q^{-1} p|;

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -52,8 +53,9 @@ cudaError_t launch_df_pack(const DfPackArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_df_unpack(const DfUnpackArgs& a, int num_sms, cudaStream_t st);
 
 // the warm-start model's forward pass for one sample on stream st (mlp.cu)
-int mlp_predict(::lp_mlp* M, const float* X, float* Y, cudaStream_t st);
-void mlp_dims(const ::lp_mlp* M, int* in, int* out);
+int mlp_predict(::lp_mlp* M, cublasHandle_t blas, const float* X, float* scratch, float* Y,
+                cudaStream_t st);
+void mlp_dims(const ::lp_mlp* M, int* in, int* out, int* hid);
 
 // raise (never lower) a kernel's dynamic shared-memory limit; thread-safe
 cudaError_t ensure_smem(const void* func, int bytes);

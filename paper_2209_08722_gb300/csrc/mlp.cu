@@ -301,21 +301,34 @@ int lp_mlp_train_step(lp_mlp* M, const float* X, const float* T, int32_t batch, 
 
 }  // extern "C"
 
-// used by the solver's warm start: Y (out x 1) from X (in x 1), on the solver's stream
+// used by the solver's warm start: Y (out x 1) from X (in x 1) on the caller's
+// cuBLAS handle (bound to the caller's stream) and scratch (2 hid floats), so
+// the model is only read: handles solving concurrently may share it, and no
+// cuBLAS stream switch (which resets its workspace) happens per call.
 namespace lpk {
-void mlp_dims(const lp_mlp* M, int* in, int* out) {
+void mlp_dims(const lp_mlp* M, int* in, int* out, int* hid) {
   *in = M->in;
   *out = M->out;
+  if (hid) *hid = M->hid;
 }
 
-int mlp_predict(lp_mlp* M, const float* X, float* Y, cudaStream_t st) {
-  cudaStream_t keep = M->st;
-  M->st = st;
-  cublasSetStream(M->blas, st);
-  const int rc = M->forward(X, 1);
-  if (rc == LP_OK) cudaMemcpyAsync(Y, M->y, sizeof(float) * M->out, cudaMemcpyDeviceToDevice, st);
-  M->st = keep;
-  cublasSetStream(M->blas, keep);
-  return rc;
+int mlp_predict(lp_mlp* M, cublasHandle_t blas, const float* X, float* scratch, float* Y,
+                cudaStream_t st) {
+  const float one = 1.0f, zero = 0.0f;
+  float* h1 = scratch;
+  float* h2 = scratch + M->hid;
+  const int hid = M->hid, in = M->in, out = M->out;
+  auto gemv = [&](int rows, int cols, const float* W, const float* x, float* y) {
+    return cublasSgemv(blas, CUBLAS_OP_N, rows, cols, &one, W, rows, x, 1, &zero, y, 1) ==
+           CUBLAS_STATUS_SUCCESS;
+  };
+  if (!gemv(hid, in, M->W1(), X, h1)) return LP_ERR_CUDA;
+  k_bias_act<<<grid_for(hid, M->num_sms), 256, 0, st>>>(hid, 1, M->b1(), h1, h1, 1);
+  if (!gemv(hid, hid, M->W2(), h1, h2)) return LP_ERR_CUDA;
+  k_bias_act<<<grid_for(hid, M->num_sms), 256, 0, st>>>(hid, 1, M->b2(), h2, h2, 1);
+  if (!gemv(out, hid, M->W3(), h2, Y)) return LP_ERR_CUDA;
+  k_bias_act<<<grid_for(out, M->num_sms), 256, 0, st>>>(out, 1, M->b3(), Y, nullptr, 0);
+  g_launches.fetch_add(3, std::memory_order_relaxed);
+  return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
 }
 }  // namespace lpk

@@ -102,6 +102,8 @@ struct lp_handle {
   double *ws_v = nullptr, *ws_w = nullptr, *ws_dots = nullptr;  // proposal, M v_i (2 m), dots
   bool warm_r_ready = false;  // h->r already holds p - M dy^0 for the warm start
   float *ws_X = nullptr, *ws_Y = nullptr;
+  float* ws_hid = nullptr;  // 2 x hidden floats: the model's activations (per handle)
+  long long ws_hid_cap = 0;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
          *dx = nullptr, *ds = nullptr, *v = nullptr, *nb0 = nullptr, *nb1 = nullptr, *nb2 = nullptr;
@@ -821,9 +823,10 @@ int correction(lp_handle* h, const double* xs_x, const double* xs_s, long long k
 // (modes 1 and 2) are combined by one Galerkin step on M: dy^0 = sum c_i v_i
 // with (v_i^T M v_j) c = (v_i^T p), the start of least energy-norm error
 // ||M^{-1} p - dy^0||_M in their span, never worse than dy^0 = 0 in that norm.
-// Its residual r^0 = p - sum c_i M v_i comes from the same products (one
-// FP64-class product per candidate), and dy^0 is used only when its true
-// residual beats dy^0 = 0.  Leaves |u|^2 in sc->pad[0] for recording the target.
+// Its residual r^0 = p - sum c_i M v_i comes from the same products (one FP32
+// product per candidate; the inner solve's first refresh replaces it by the
+// FP64 residual), and dy^0 is used only when that residual beats dy^0 = 0.
+// Leaves |u|^2 in sc->pad[0] for recording the target.
 int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   *warm = false;
   h->warm_r_ready = false;
@@ -839,7 +842,7 @@ int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   const double* v[2];
   int nv = 0;
   if (h->ws_mode == 2 && h->ws_model) {
-    if (mlp_predict(h->ws_model, h->ws_X, h->ws_Y, h->st) != LP_OK)
+    if (mlp_predict(h->ws_model, h->blas, h->ws_X, h->ws_hid, h->ws_Y, h->st) != LP_OK)
       return h->fail(LP_ERR_CUDA, "warm-start model forward failed");
     CK(launch_ws_scale(m, 0, h->ws_Y, nullptr, h->sc, h->ws_v, nullptr, h->st));
     v[nv++] = h->ws_v;
@@ -851,7 +854,9 @@ int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   h->ws_props += 1;
   const size_t wst = (size_t)h->lda + 64;
   double* wv[2] = {h->ws_w, h->ws_w + wst};
-  for (int i = 0; i < nv; ++i) RET(launch_adat(h, v[i], E_PLAIN, true, 0, wv[i]));  // M v_i
+  // M v_i with the FP32 product: the coefficients need no more, and the first
+  // refresh of the inner solve replaces r^0 by the FP64 residual
+  for (int i = 0; i < nv; ++i) RET(launch_adat(h, v[i], E_PLAIN, false, 0, wv[i]));
   // dots: [0] v0.Mv0 [1] v0.Mv1 [2] v1.Mv0 [3] v1.Mv1 [4] v0.p [5] v1.p
   for (int i = 0; i < nv; ++i) {
     for (int j = 0; j < nv; ++j)
@@ -1655,9 +1660,16 @@ int lp_set_warm_start(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, f
   if (!h || mode < 0 || mode > 2 || (mode == 2 && !model) || rec_capacity < 0) return LP_ERR_ARG;
   if ((rec_X == nullptr) != (rec_T == nullptr)) return LP_ERR_ARG;
   if (model) {
-    int in = 0, out = 0;
-    mlp_dims(model, &in, &out);
+    int in = 0, out = 0, hid = 0;
+    mlp_dims(model, &in, &out, &hid);
     if (in != 3 * h->m || out != h->m) return LP_ERR_ARG;  // features 3m -> dy (m)
+    if (!h->blas) return LP_ERR_UNSUPPORTED;
+    if (2LL * hid > h->ws_hid_cap) {
+      if (cudaStreamSynchronize(h->st) != cudaSuccess) return LP_ERR_CUDA;
+      h->err.clear();
+      if (h->alloc(&h->ws_hid, 2 * (size_t)hid) != LP_OK) return LP_ERR_OOM;
+      h->ws_hid_cap = 2LL * hid;
+    }
   }
   h->ws_mode = mode;
   h->ws_model = model;
