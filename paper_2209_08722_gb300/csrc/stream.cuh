@@ -79,7 +79,8 @@ struct StreamArgs {
   const long long* colptr;  // CSC: n+1 column pointers
   const int* rowidx;        // CSC: row indices
   const void* spval;        // CSC: values (FP32 or FP64)
-  double* gpart;       // [ceil(grid/kGroup)][2][lda] FP64 group sums of the partials
+  double* gpart;       // [ceil(grid/kGroup)][2][lda] group sums of the partials (FP64, or FP32
+                       // pairs in the same 8 bytes when the partials are FP32)
   unsigned* gtickets;  // [kMaxGroups + 1] self-resetting tickets of the two-level reduction
 };
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df.cuh"
 #include "stream.cuh"
 
 namespace lpk {
@@ -84,10 +85,20 @@ __device__ bool tree_reduce(const StreamArgs& a, int nacc, int* s_flag) {
 #pragma unroll
       for (int q = 0; q < kGroup; ++q)
         v[q] = (q < gsize) ? __ldcg(part + (size_t)(b0 + q) * pstride + (size_t)k * a.lda + i) : (TC)0;
-      double s = 0.0;
+      if constexpr (sizeof(TC) == 4) {
+        // FP32 partials: the group sum as an FP32 pair (FP32 pipe; an FP64
+        // warp instruction costs GB300's FP64 unit about 16 cycles)
+        float sh = 0.0f, sl = 0.0f;
 #pragma unroll
-      for (int q = 0; q < kGroup; ++q) s += (double)v[q];
-      a.gpart[((size_t)grp * 2 + k) * a.lda + i] = s;
+        for (int q = 0; q < kGroup; ++q) df_add(sh, sl, (float)v[q], 0.0f);
+        df_renorm(sh, sl);
+        reinterpret_cast<float2*>(a.gpart)[((size_t)grp * 2 + k) * a.lda + i] = make_float2(sh, sl);
+      } else {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) s += (double)v[q];
+        a.gpart[((size_t)grp * 2 + k) * a.lda + i] = s;
+      }
     }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -109,10 +120,36 @@ __device__ void stream_epilogue(const StreamArgs& a, int nacc, double* red) {
   const int G = gridDim.x;
   const int ngroups = (G + kGroup - 1) / kGroup;
   if (*a.err != ERR_NONE) return;
+  // sum of row i over the group sums, in group order; the loads are issued
+  // eight at a time so that their L2 latencies overlap
   auto acc_row = [&](int k, int i) -> double {
-    double s = 0.0;
-    for (int g = 0; g < ngroups; ++g) s += __ldcg(a.gpart + ((size_t)g * 2 + k) * a.lda + i);
-    return s;
+    const size_t gs = (size_t)2 * a.lda;
+    if constexpr (sizeof(TC) == 4) {
+      // group sums held as FP32 pairs: summed as pairs, one conversion at the end
+      const float2* base = reinterpret_cast<const float2*>(a.gpart) + (size_t)k * a.lda + i;
+      float sh = 0.0f, sl = 0.0f;
+      for (int g0 = 0; g0 < ngroups; g0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          v[q] = (g0 + q < ngroups) ? __ldcg(base + (size_t)(g0 + q) * gs) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) df_add(sh, sl, v[q].x, v[q].y);
+      }
+      return (double)sh + (double)sl;
+    } else {
+      const double* base = a.gpart + (size_t)k * a.lda + i;
+      double s = 0.0;
+      for (int g0 = 0; g0 < ngroups; g0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (g0 + q < ngroups) ? __ldcg(base + (size_t)(g0 + q) * gs) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (g0 + q < ngroups) s += v[q];
+      }
+      return s;
+    }
   };
   // column reductions (two FP64 sums over columns), block-parallel in a fixed order
   double cr0 = 0.0, cr1 = 0.0;
@@ -136,19 +173,69 @@ __device__ void stream_epilogue(const StreamArgs& a, int nacc, double* red) {
       for (int i = tid; i < a.m; i += blockDim.x) a.pcg_r[i] = a.bvec[i] - acc_row(0, i);
       break;
     case E_PCG_A: {
+      // the first kRows rows of each thread stay in registers (q, p, dy, r all
+      // loaded before the reduction of p^T q); rows beyond are re-read
+      constexpr int kRows = 4;
+      double qv[kRows], pv[kRows], dv[kRows], rv[kRows];
       double pq = 0.0;
-      for (int i = tid; i < a.m; i += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < kRows; ++c) {
+        const int i = tid + c * (int)blockDim.x;
+        if (i < a.m) {
+          pv[c] = a.pcg_p[i];
+          dv[c] = a.pcg_dy[i];
+          rv[c] = a.pcg_r[i];
+          qv[c] = acc_row(0, i);
+          a.out_m0[i] = qv[c];
+          pq += pv[c] * qv[c];
+        }
+      }
+      for (int i = tid + kRows * (int)blockDim.x; i < a.m; i += blockDim.x) {
         const double q = acc_row(0, i);
         a.out_m0[i] = q;
         pq += a.pcg_p[i] * q;
       }
-      pq = block_sum(pq, red);
-      const double alpha = a.sc->rho / pq;
-      if (!(pq > 0.0) || !isfinite(alpha)) {
-        if (tid == 0) atomicExch(a.err, ERR_NUMERICAL);
-        return;
+      // p^T q: each thread's FP64 partial as an FP32 pair, reduced on the FP32
+      // pipe; alpha = rho / p^T q once, in thread 0, and broadcast
+      {
+        float ph = (float)pq;
+        float pl = (float)(pq - (double)ph);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          const float oh = __shfl_xor_sync(0xffffffffu, ph, off);
+          const float ol = __shfl_xor_sync(0xffffffffu, pl, off);
+          df_add(ph, pl, oh, ol);
+        }
+        float2* redf = reinterpret_cast<float2*>(red);
+        const int nw = (int)(blockDim.x + 31) / 32;
+        __syncthreads();
+        if ((tid & 31) == 0) redf[tid >> 5] = make_float2(ph, pl);
+        __syncthreads();
+        if (tid == 0) {
+          float sh = 0.0f, sl = 0.0f;
+          for (int w = 0; w < nw; ++w) df_add(sh, sl, redf[w].x, redf[w].y);
+          const double pqs = (double)sh + (double)sl;
+          const double al = a.sc->rho / pqs;
+          const bool bad = !(pqs > 0.0) || !isfinite(al);
+          if (bad) atomicExch(a.err, ERR_NUMERICAL);
+          red[32] = al;
+          red[33] = pqs;
+          red[34] = bad ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        pq = red[33];
       }
-      for (int i = tid; i < a.m; i += blockDim.x) {
+      const double alpha = red[32];
+      if (red[34] != 0.0) return;  // breakdown (p^T q <= 0 or non-finite), flagged above
+#pragma unroll
+      for (int c = 0; c < kRows; ++c) {
+        const int i = tid + c * (int)blockDim.x;
+        if (i < a.m) {
+          a.pcg_dy[i] = dv[c] + alpha * pv[c];
+          a.pcg_r[i] = rv[c] - alpha * qv[c];
+        }
+      }
+      for (int i = tid + kRows * (int)blockDim.x; i < a.m; i += blockDim.x) {
         a.pcg_dy[i] += alpha * a.pcg_p[i];
         a.pcg_r[i] -= alpha * a.out_m0[i];
       }

@@ -70,7 +70,7 @@ struct GemvArgs {
 
 __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   __shared__ int s_flag;
-  __shared__ double red[32];
+  __shared__ __align__(16) double red[32];  // also read as float4 in the epilogue
   if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
@@ -158,106 +158,132 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   if (a.epi == G_NONE) return;
   if (!last_block_ticket(a.ticket, &s_flag)) return;
   // ---- epilogue (one CTA): m-vector CG / Chebyshev updates ----
+  // r^T z and r^T r: FP64 per thread, then reduced as FP32 pairs on the FP32
+  // pipe (an FP64 warp instruction costs GB300's FP64 unit about 16 cycles);
+  // the scalar logic runs in thread 0, which broadcasts the coefficients of the
+  // one vector update p = c_z z + c_p p.
   DevScalars* sc = a.sc;
   const double* z = a.y;
+  __shared__ double s_coef[3];  // c_z, c_p, update flag
   double rz = 0.0, rr = 0.0;
   for (int i = threadIdx.x; i < a.m; i += blockDim.x) {
     const double ri = a.r[i];
-    rz += ri * __ldcg(z + i);
-    rr += ri * ri;
+    rz = fma(ri, __ldcg(z + i), rz);
+    rr = fma(ri, ri, rr);
   }
-  rz = block_sum(rz, red);
-  rr = block_sum(rr, red);
-  if (!isfinite(rz)) {
-    if (threadIdx.x == 0) atomicExch(a.err, ERR_NUMERICAL);
-    return;
-  }
-  const double f = sqrt(fmax(rz, 0.0));
-  // r^T Q^{-1} r <= 0 with r != 0: the stored Q^{-1} has lost definiteness
-  // (rounding), so ||f|| means nothing; the host refactors (inner_done = 3)
-  const bool indefinite = rz <= 0.0 && rr > 0.0;
-  if (indefinite && (a.epi == G_PCG_INIT || a.epi == G_REFRESH || a.epi == G_CHEB_INIT ||
-                     a.epi == G_CHEB_REFRESH)) {
-    if (threadIdx.x == 0) {
-      sc->f_true = 0.0;
-      sc->inner_done = 3;
+  {
+    float zh = (float)rz, zl = (float)(rz - (double)(float)rz);
+    float qh = (float)rr, ql = (float)(rr - (double)(float)rr);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float a0 = __shfl_xor_sync(0xffffffffu, zh, off), a1 = __shfl_xor_sync(0xffffffffu, zl, off);
+      const float b0 = __shfl_xor_sync(0xffffffffu, qh, off), b1 = __shfl_xor_sync(0xffffffffu, ql, off);
+      df_add(zh, zl, a0, a1);
+      df_add(qh, ql, b0, b1);
     }
-    return;
-  }
-  if (a.epi == G_PCG_INIT) {
-    for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i);
+    float4* redf = reinterpret_cast<float4*>(red);  // 32 doubles = 16 float4
+    const int nwb = (int)(blockDim.x + 31) / 32;    // <= 8 (256 threads)
+    if (lane == 0) redf[threadIdx.x >> 5] = make_float4(zh, zl, qh, ql);
+    __syncthreads();
     if (threadIdx.x == 0) {
-      sc->rho = rz;
-      sc->rho0 = rz;
-      sc->f_rec = f;
-      sc->f_true = f;
-      sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
-    }
-  } else if (a.epi == G_PCG_B || a.epi == G_PCG_B_LAST) {
-    // CG step k: beta_k = rho_{k+1} / rho_k, p_{k+1} = z + beta_k p_k.  The last
-    // step before a refresh (and a step that stops) leaves p_k and rho_k in
-    // place: the refresh replaces r and z by their true values and makes this
-    // direction update itself, once (residual replacement).
-    const double beta = rz / sc->rho;
-    const bool stop = f <= 0.5 * sc->tol_f;
-    const bool defer = stop || a.epi == G_PCG_B_LAST || sc->inner_iters + 1 >= a.t_max;
-    if (!defer)
-      for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) + beta * a.p[i];
-    if (threadIdx.x == 0) {
-      if (!defer) {
-        sc->rho = rz;
-        if (a.coef && sc->inner_iters < 1024) a.coef[2 * sc->inner_iters + 1] = beta;
+      float sh = 0.0f, sl = 0.0f, th = 0.0f, tl = 0.0f;
+      for (int w = 0; w < nwb; ++w) {
+        df_add(sh, sl, redf[w].x, redf[w].y);
+        df_add(th, tl, redf[w].z, redf[w].w);
       }
-      sc->f_rec = f;
-      sc->inner_iters += 1;
-      if (stop || sc->inner_iters >= a.t_max) sc->inner_done = 1;
+      rz = (double)sh + (double)sl;
+      rr = (double)th + (double)tl;
+      double cz = 0.0, cp = 0.0;
+      bool upd = false;
+      const double f = sqrt(fmax(rz, 0.0));
+      // r^T Q^{-1} r <= 0 with r != 0: the stored Q^{-1} has lost definiteness
+      // (rounding), so ||f|| means nothing; the host refactors (inner_done = 3)
+      const bool indefinite = rz <= 0.0 && rr > 0.0;
+      if (!isfinite(rz)) {
+        atomicExch(a.err, ERR_NUMERICAL);
+      } else if (indefinite && (a.epi == G_PCG_INIT || a.epi == G_REFRESH || a.epi == G_CHEB_INIT ||
+                                a.epi == G_CHEB_REFRESH)) {
+        sc->f_true = 0.0;
+        sc->inner_done = 3;
+      } else if (a.epi == G_PCG_INIT) {
+        cz = 1.0;
+        upd = true;
+        sc->rho = rz;
+        sc->rho0 = rz;
+        sc->f_rec = f;
+        sc->f_true = f;
+        sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
+      } else if (a.epi == G_PCG_B || a.epi == G_PCG_B_LAST) {
+        // CG step k: beta_k = rho_{k+1} / rho_k, p_{k+1} = z + beta_k p_k.  The
+        // last step before a refresh (and a step that stops) leaves p_k and
+        // rho_k in place: the refresh replaces r and z by their true values and
+        // makes this direction update itself, once (residual replacement).
+        const double beta = rz / sc->rho;
+        const bool stop = f <= 0.5 * sc->tol_f;
+        const bool defer = stop || a.epi == G_PCG_B_LAST || sc->inner_iters + 1 >= a.t_max;
+        if (!defer) {
+          cz = 1.0;
+          cp = beta;
+          upd = true;
+          sc->rho = rz;
+          if (a.coef && sc->inner_iters < 1024) a.coef[2 * sc->inner_iters + 1] = beta;
+        }
+        sc->f_rec = f;
+        sc->inner_iters += 1;
+        if (stop || sc->inner_iters >= a.t_max) sc->inner_done = 1;
+      } else if (a.epi == G_REFRESH) {
+        // true residual r = p - M dy, z = Q^{-1} r: converged if sqrt(r.z) <= tol;
+        // else p = z + (r.z / rho_k) p_k, or p = z (restart) when the recursion
+        // drifted far from the FP64 residual (FP32 products).
+        double beta = rz / sc->rho;
+        const bool stop = f <= sc->tol_f;
+        if (f > 4.0 * sc->f_rec) beta = 0.0;
+        if (!stop) {
+          cz = 1.0;
+          cp = beta;
+          upd = true;
+        }
+        sc->rho = rz;
+        const int j = sc->inner_iters - 1;  // the deferred step's coefficient
+        if (a.coef && j >= 0 && j < 1024) a.coef[2 * j + 1] = beta;
+        sc->f_true = f;
+        sc->inner_done = stop ? 2 : 0;
+      } else if (a.epi == G_CHEB_INIT) {
+        const double theta = 0.5 * (sc->lam_max + sc->lam_min);
+        const double delta = 0.5 * (sc->lam_max - sc->lam_min);
+        cz = 1.0 / theta;
+        upd = true;
+        sc->cheb_rho = delta / theta;
+        sc->rho0 = rz;
+        sc->f_rec = f;
+        sc->f_true = f;
+        sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
+      } else if (a.epi == G_CHEB_REFRESH) {
+        sc->f_true = f;
+        sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
+      } else if (a.epi == G_CHEB_B) {
+        const double theta = 0.5 * (sc->lam_max + sc->lam_min);
+        const double delta = 0.5 * (sc->lam_max - sc->lam_min);
+        const double s1 = theta / delta;
+        const double rho = sc->cheb_rho;
+        const double rho_new = 1.0 / (2.0 * s1 - rho);
+        cz = 2.0 * rho_new / delta;
+        cp = rho_new * rho;
+        upd = true;
+        sc->cheb_rho = rho_new;
+        sc->f_rec = f;
+        sc->inner_iters += 1;
+        if (f <= 0.5 * sc->tol_f || sc->inner_iters >= a.t_max) sc->inner_done = 1;
+      }
+      s_coef[0] = cz;
+      s_coef[1] = cp;
+      s_coef[2] = upd ? 1.0 : 0.0;
     }
-  } else if (a.epi == G_REFRESH) {
-    // true residual r = p - M dy, z = Q^{-1} r: converged if sqrt(r.z) <= tol;
-    // else p = z + (r.z / rho_k) p_k, or p = z (restart) when the recursion
-    // drifted far from the FP64 residual (FP32 products).
-    double beta = rz / sc->rho;
-    const bool stop = f <= sc->tol_f;
-    if (f > 4.0 * sc->f_rec) beta = 0.0;
-    if (!stop)
-      for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) + beta * a.p[i];
-    if (threadIdx.x == 0) {
-      sc->rho = rz;
-      const int j = sc->inner_iters - 1;  // the deferred step's coefficient
-      if (a.coef && j >= 0 && j < 1024) a.coef[2 * j + 1] = beta;
-      sc->f_true = f;
-      sc->inner_done = stop ? 2 : 0;
-    }
-  } else if (a.epi == G_CHEB_INIT) {
-    const double theta = 0.5 * (sc->lam_max + sc->lam_min);
-    const double delta = 0.5 * (sc->lam_max - sc->lam_min);
-    for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = __ldcg(z + i) / theta;
-    if (threadIdx.x == 0) {
-      sc->cheb_rho = delta / theta;
-      sc->rho0 = rz;
-      sc->f_rec = f;
-      sc->f_true = f;
-      sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
-    }
-  } else if (a.epi == G_CHEB_REFRESH) {
-    if (threadIdx.x == 0) {
-      sc->f_true = f;
-      sc->inner_done = (f <= sc->tol_f) ? 2 : 0;
-    }
-  } else if (a.epi == G_CHEB_B) {
-    const double theta = 0.5 * (sc->lam_max + sc->lam_min);
-    const double delta = 0.5 * (sc->lam_max - sc->lam_min);
-    const double s1 = theta / delta;
-    const double rho = sc->cheb_rho;
-    const double rho_new = 1.0 / (2.0 * s1 - rho);
-    for (int i = threadIdx.x; i < a.m; i += blockDim.x)
-      a.p[i] = rho_new * rho * a.p[i] + (2.0 * rho_new / delta) * __ldcg(z + i);
-    if (threadIdx.x == 0) {
-      sc->cheb_rho = rho_new;
-      sc->f_rec = f;
-      sc->inner_iters += 1;
-      if (f <= 0.5 * sc->tol_f || sc->inner_iters >= a.t_max) sc->inner_done = 1;
-    }
+  }
+  __syncthreads();  // every thread of the CTA reaches this one barrier
+  if (s_coef[2] != 0.0) {
+    const double cz = s_coef[0], cp = s_coef[1];
+    for (int i = threadIdx.x; i < a.m; i += blockDim.x) a.p[i] = fma(cp, a.p[i], cz * __ldcg(z + i));
   }
 }
 
