@@ -54,16 +54,26 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+# the translation unit of the hot kernel and the headers it is built from
+HOT_KERNEL_SOURCES = ("stream.cu", "stream_dev.cuh", "stream.cuh", "common.cuh", "df.cuh")
+
+
+def hot_kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in HOT_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2209_08722_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record():
     """Per-launch DRAM bytes of the hot kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged."""
+    valid only while the kernel's sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic_k_adat_fused_m512_n131072.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    import hashlib
-    src = open(os.path.join(ROOT, "paper_2209_08722_gb300", "csrc", "stream.cu"), "rb").read()
-    if hashlib.sha256(src).hexdigest() != rec.get("stream_cu_sha256"):
+    if hot_kernel_source_hash() != rec.get("kernel_sources_sha256"):
         return None
     return float(rec["dram_bytes_per_launch"])
 
@@ -315,14 +325,18 @@ def run_warm_start(args):
         S.close()
     net = Mlp(3 * m, 1024, m, seed=7)
     X, T = recX[:total].contiguous(), recT[:total].contiguous()
+    loss = net.train_step(X, T, 1e-3)       # first step: library and kernel loading, untimed
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for it in range(2000):
+    for it in range(1, 2000):
         loss = net.train_step(X, T, 1e-3 if it < 1400 else 3e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     tests = [make(seed) for seed in range(1000, 1008)]
     solvers = [solver(lp) for lp in tests]
-    solvers[0].solve(tol=TOL)               # warm-up: every kernel shape once
+    for mode in ("none", "model"):          # warm-up: every kernel shape and library path once
+        solvers[0].set_warm_start(mode, net if mode == "model" else None)
+        solvers[0].solve(tol=TOL)
     torch.cuda.synchronize()
     out = {}
     for mode in ("none", "previous", "model"):
