@@ -14,10 +14,11 @@
 // m x m matrix with m in the hundreds is latency-bound in library code, so:
 //   * the matrix is prescaled by a power of two (max diagonal -> [1, 2)) and
 //     held as FP32 pairs (relative accuracy ~2^-46 per operation);
-//   * each of the m/32 pivot steps is ONE launch over all 32 x 32 tiles: every
-//     CTA sweeps the 32 x 32 pivot block itself in shared memory (redundant
-//     but short), then writes its tile of the next iterate; two buffers
-//     alternate, so no tile is read after it is overwritten.
+//   * each of the m/32 pivot steps is two launches: one CTA of 32 x 32 threads
+//     sweeps the 32 x 32 pivot block (the step's serial chain of 32 pivots,
+//     one element per thread), then one launch over all 32 x 32 tiles writes
+//     the next iterate from it; two buffers alternate, so no tile is read after
+//     it is overwritten.
 #include "internal.h"
 #include "df.cuh"
 
@@ -87,26 +88,76 @@ __global__ void __launch_bounds__(256) k_sweep_init(const double* __restrict__ g
   }
 }
 
-// one pivot step K: src -> dst for every 32 x 32 tile (I, J)
+// The pivot block of step K swept on its 32 pivots, once: P -> -P^{-1} into
+// (qh, ql), and the pivots (the squares of the Cholesky diagonal) into piv.
+// One CTA of SB x SB threads, thread (a, b) owning entry (a, b); per pivot t
+// every thread reads d = P_tt, P_at and P_bt, then writes its new entry
+// (a == t or b == t: the scaled column or -1/d; otherwise P_ab - (P_at/d) P_bt).
+__global__ void __launch_bounds__(SB* SB) k_sweep_pivot(const float* __restrict__ sh_, const float* __restrict__ sl_,
+                                                       int mp, int K, float* __restrict__ qh,
+                                                       float* __restrict__ ql, float* __restrict__ piv) {
+  __shared__ float Ph[SB][SB + 1], Pl[SB][SB + 1];
+  const int a = threadIdx.x / SB, b = threadIdx.x % SB;
+  const int k0 = K * SB;
+  {
+    const size_t src = (size_t)(k0 + a) * mp + k0 + b;
+    Ph[a][b] = sh_[src];
+    Pl[a][b] = sl_[src];
+  }
+  __syncthreads();
+  for (int t = 0; t < SB; ++t) {
+    const float dh = Ph[t][t], dl = Pl[t][t];
+    const float ah = Ph[a][t], al = Pl[a][t];
+    const float bh = Ph[b][t], bl = Pl[b][t];
+    float h = Ph[a][b], l = Pl[a][b];
+    __syncthreads();  // every read of this pivot's iterate is done
+    float rh, rl;
+    df_recip(dh, dl, rh, rl);
+    if (threadIdx.x == 0 && piv) piv[k0 + t] = dh;
+    if (a == t && b == t) {
+      h = -rh;
+      l = -rl;
+    } else if (a == t) {
+      df_mul(bh, bl, rh, rl, h, l);  // P_bt / d
+    } else {
+      float wh, wl;
+      df_mul(ah, al, rh, rl, wh, wl);  // P_at / d
+      if (b == t) {
+        h = wh;
+        l = wl;
+      } else {
+        df_mac(-wh, -wl, bh, bl, h, l);
+        df_renorm(h, l);
+      }
+    }
+    Ph[a][b] = h;
+    Pl[a][b] = l;
+    __syncthreads();
+  }
+  qh[a * SB + b] = Ph[a][b];
+  ql[a * SB + b] = Pl[a][b];
+}
+
+// one pivot step K: src -> dst for every 32 x 32 tile (I, J); the swept pivot
+// block -P^{-1} comes from k_sweep_pivot
 __global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restrict__ sh_, const float* __restrict__ sl_,
                                                            float* __restrict__ dh_, float* __restrict__ dl_,
-                                                           int mp, int K, float* __restrict__ piv) {
+                                                           int mp, int K, const float* __restrict__ qh,
+                                                           const float* __restrict__ ql) {
   __shared__ float Ph[SB][SB + 1], Pl[SB][SB + 1];  // pivot block, swept in place -> -P^{-1}
   __shared__ float Ch[SB][SB + 1], Cl[SB][SB + 1];  // panel rows of the other block: A_{J,K}
   __shared__ float Th[SB][SB + 1], Tl[SB][SB + 1];  // A_{X,K} (-P^{-1})... see below
-  __shared__ float uh[SB], ul[SB], wh[SB], wl[SB];
   const int nt = mp / SB;
   const int I = blockIdx.x % nt, J = blockIdx.x / nt;
   const int k0 = K * SB;
   const int tid = threadIdx.x;
   const int r = tid >> 3, c4 = (tid & 7) * 4;  // this thread's outputs: row r, columns c4..c4+3
 
-  // ---- load the pivot block P = A_KK ----
+  // ---- load the swept pivot block -P^{-1} ----
   for (int e = tid; e < SB * SB; e += SW_THREADS) {
     const int a = e / SB, b = e % SB;
-    const size_t src = (size_t)(k0 + a) * mp + k0 + b;
-    Ph[a][b] = sh_[src];
-    Pl[a][b] = sl_[src];
+    Ph[a][b] = qh[e];
+    Pl[a][b] = ql[e];
   }
   // ---- load the panels needed by this tile ----
   // case 1 (I != K, J != K): T <- A_{I,K}, C <- A_{J,K}; case 2 (J == K): T <- A_{I,K};
@@ -129,45 +180,6 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restri
     }
   }
   __syncthreads();
-
-  // ---- sweep the pivot block on each of its 32 pivots: P -> -P^{-1} ----
-  for (int t = 0; t < SB; ++t) {
-    if (tid < SB) {
-      float rh, rl;
-      df_recip(Ph[t][t], Pl[t][t], rh, rl);
-      const float xh = Ph[tid][t], xl = Pl[tid][t];
-      uh[tid] = xh;
-      ul[tid] = xl;
-      float fh, fl;
-      df_mul(xh, xl, rh, rl, fh, fl);
-      wh[tid] = fh;  // A_it / d
-      wl[tid] = fl;
-      if (tid == t) {
-        wh[tid] = -rh;  // the new pivot entry, -1/d
-        wl[tid] = -rl;
-      }
-      if (tid == 0 && blockIdx.x == 0 && piv) piv[k0 + t] = Ph[t][t];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int a = r, b = c4 + q;
-      if (a == t) {
-        Ph[a][b] = wh[b];
-        Pl[a][b] = wl[b];
-      } else if (b == t) {
-        Ph[a][b] = wh[a];
-        Pl[a][b] = wl[a];
-      } else {
-        float h = Ph[a][b], l = Pl[a][b];
-        df_mac(-wh[a], -wl[a], uh[b], ul[b], h, l);  // A_ab - (A_at / d) A_tb
-        df_renorm(h, l);
-        Ph[a][b] = h;
-        Pl[a][b] = l;
-      }
-    }
-    __syncthreads();
-  }
 
   // ---- this thread's four outputs ----
   float oh[4], ol[4];
@@ -280,7 +292,7 @@ __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ 
 
 size_t sweep_scratch_floats(int m) {
   const size_t mp = (size_t)(m + SB - 1) / SB * SB;
-  return 4 * mp * mp + mp + 8;
+  return 4 * mp * mp + mp + 8 + 2 * SB * SB;
 }
 
 // G: upper triangle of the column-major m x m Gram; qinv: m x m output
@@ -295,6 +307,8 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   float* piv = scratch + 4 * mm;
   // the prescale 2^e, 8-byte aligned after the mp pivots (mp is a multiple of 32)
   double* scale_buf = reinterpret_cast<double*>(scratch + 4 * mm + mp);
+  float* qh = scratch + 4 * mm + mp + 8;  // the swept pivot block of the current step
+  float* ql = qh + SB * SB;
   const int g1 = (int)std::max<long long>(1, std::min<long long>(((long long)mm + 255) / 256, (long long)num_sms * 4));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sweep_init<<<g1, 256, 0, st>>>(g, m, mp, a0h, a0l, scale_buf);
@@ -302,8 +316,10 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   for (int K = 0; K < nt; ++K) {
     const bool even = (K & 1) == 0;
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    k_sweep_pivot<<<1, SB * SB, 0, st>>>(even ? a0h : a1h, even ? a0l : a1l, mp, K, qh, ql, piv);
     k_sweep_step<<<nt * nt, SW_THREADS, 0, st>>>(even ? a0h : a1h, even ? a0l : a1l, even ? a1h : a0h,
-                                                 even ? a1l : a0l, mp, K, piv);
+                                                 even ? a1l : a0l, mp, K, qh, ql);
   }
   const bool in0 = (nt & 1) == 0;
   g_launches.fetch_add(1, std::memory_order_relaxed);
