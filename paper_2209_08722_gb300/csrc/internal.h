@@ -92,8 +92,12 @@ cudaError_t launch_gram_df(const double* x, int m, int w, float* scratch, double
 // Q^{-1} from the upper triangle of the column-major Gram g by the blocked
 // symmetric sweep in double-float; rank check into sc (|R_ii| range)
 size_t sweep_scratch_floats(int m);
+// st_aux, ev_x, ev_p (nullable): second stream and events on which the pivot
+// kernels overlap the tile kernels; without them everything runs on st
 cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, float2* qinv_df,
-                                 DevScalars* sc, double rank_tol, int num_sms, cudaStream_t st);
+                                 DevScalars* sc, double rank_tol, int num_sms, cudaStream_t st,
+                                 cudaStream_t st_aux = nullptr, cudaEvent_t ev_x = nullptr,
+                                 cudaEvent_t ev_p = nullptr);
 
 // scratch of the dense CountSketch: bucket sizes/offsets/cursors (w + 1 each),
 // bucket lists (n s), per-column scales (n)

@@ -55,6 +55,9 @@ struct lp_handle {
   double bnorm = 0.0, cnorm = 0.0;
   cudaStream_t st = nullptr;
   bool own_stream = false;
+  // second stream and events for the factor's overlapped pivot kernels (sweep.cu)
+  cudaStream_t st_aux = nullptr;
+  cudaEvent_t ev_x = nullptr, ev_p = nullptr;
   cusolverDnHandle_t sol = nullptr;
   cublasHandle_t blas = nullptr;
   int lwork_potrf = 0;
@@ -367,7 +370,7 @@ int factor(lp_handle* h) {
   h->qinv_df_ok = false;
   // Q^{-1} is kept as pairs only: the double-float GEMV applies it
   CK(launch_sweep_inverse(h->rinv_cm, m, h->sweep_scratch, nullptr, h->qinv_df, h->sc, 1e-13, h->num_sms,
-                          h->st));
+                          h->st, h->st_aux, h->ev_x, h->ev_p));
   RET(sync_read(h));
   if (!h->hsc->rank_bad) {
     h->qinv_ok = true;
@@ -1069,6 +1072,12 @@ int lp_destroy(lp_handle* h) {
   if (h->hwork) free(h->hwork);
   if (h->sol) cusolverDnDestroy(h->sol);
   if (h->blas) cublasDestroy(h->blas);
+  if (h->st_aux) {
+    cudaStreamSynchronize(h->st_aux);
+    cudaStreamDestroy(h->st_aux);
+  }
+  if (h->ev_x) cudaEventDestroy(h->ev_x);
+  if (h->ev_p) cudaEventDestroy(h->ev_p);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
   return LP_OK;
@@ -1107,6 +1116,9 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
     CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
     h->own_stream = true;
   }
+  CK(cudaStreamCreateWithFlags(&h->st_aux, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_x, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_p, cudaEventDisableTiming));
   h->m = A->m;
   h->n = A->n;
   h->dtype = A->dtype;

@@ -26,7 +26,23 @@ namespace lpk {
 
 namespace {
 constexpr int SB = 32;          // pivot block = tile
-constexpr int SW_THREADS = 256; // 8 x 32 threads, 4 outputs each
+constexpr int SW_THREADS = 256; // 8 x 32 threads per tile, 4 outputs each
+// Tiles per CTA of the tile kernel: two halves of 256 threads, each with its own
+// shared memory and named barrier, so the kernel occupies half as many SMs as
+// it has tiles and leaves SMs free for the pivot kernel running beside it.
+constexpr int kTilesPerCta = 2;
+
+struct TileSmem {
+  float Ph[SB][SB + 1], Pl[SB][SB + 1];  // -P^{-1}
+  float Ch[SB][SB + 1], Cl[SB][SB + 1];  // panel rows of the other block: A_{J,K}
+  float Th[SB][SB + 1], Tl[SB][SB + 1];  // A_{X,K}, then U = A_{X,K} (-P^{-1})
+};
+
+// barrier over the 256 threads of one half of the CTA (ids 1 and 2; 0 is
+// __syncthreads')
+__device__ __forceinline__ void half_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(SW_THREADS) : "memory");
+}
 
 // (ah + al)(bh + bl) as a normalised pair
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
@@ -88,29 +104,65 @@ __global__ void __launch_bounds__(256) k_sweep_init(const double* __restrict__ g
   }
 }
 
-// The pivot block of step K swept on its 32 pivots, once: P -> -P^{-1} into
-// (qh, ql), and the pivots (the squares of the Cholesky diagonal) into piv.
-// One CTA of SB x SB threads, thread (a, b) owning entry (a, b); per pivot t
-// every thread reads d = P_tt, P_at and P_bt, then writes its new entry
-// (a == t or b == t: the scaled column or -1/d; otherwise P_ab - (P_at/d) P_bt).
-__global__ void __launch_bounds__(SB* SB) k_sweep_pivot(const float* __restrict__ sh_, const float* __restrict__ sl_,
-                                                       int mp, int K, float* __restrict__ qh,
+// The pivot block of step K swept on its 32 pivots: -P_K^{-1} into (qh, ql)
+// and the pivots (the squares of the Cholesky diagonal) into piv.  For K = 0,
+// P_0 is tile (0, 0) of the iterate x.  For K >= 1, x is the iterate that step
+// K-1 reads, and P_K = A_KK + U A_{K,K-1}^T with U = A_{K,K-1} (-P_{K-1}^{-1})
+// ((qph, qpl)): the operations, in the order, by which k_sweep_step forms tile
+// (K, K) of the next iterate, so both hold the same values and this kernel can
+// run beside step K-1's tile kernel.  One CTA of SB x SB threads, thread (a, b)
+// owning entry (a, b); per pivot t every thread reads d = P_tt, P_at and P_bt
+// from one copy of the block and writes its new entry to the other (a == t or
+// b == t: the scaled column or -1/d; otherwise P_ab - (P_at/d) P_bt).
+__global__ void __launch_bounds__(SB* SB) k_sweep_pivot(const float* __restrict__ xh, const float* __restrict__ xl,
+                                                       int mp, int K, const float* __restrict__ qph,
+                                                       const float* __restrict__ qpl, float* __restrict__ qh,
                                                        float* __restrict__ ql, float* __restrict__ piv) {
   __shared__ float Ph[SB][SB + 1], Pl[SB][SB + 1];
+  __shared__ float Th[SB][SB + 1], Tl[SB][SB + 1];  // A_{K,K-1}, then U
+  __shared__ float Ch[SB][SB + 1], Cl[SB][SB + 1];  // A_{K,K-1}
+  __shared__ float Qh[SB][SB + 1], Ql[SB][SB + 1];  // -P_{K-1}^{-1}
   const int a = threadIdx.x / SB, b = threadIdx.x % SB;
   const int k0 = K * SB;
-  {
-    const size_t src = (size_t)(k0 + a) * mp + k0 + b;
-    Ph[a][b] = sh_[src];
-    Pl[a][b] = sl_[src];
+  const size_t akk = (size_t)(k0 + a) * mp + k0 + b;
+  if (K == 0 || !qph) {
+    Ph[a][b] = xh[akk];
+    Pl[a][b] = xl[akk];
+    __syncthreads();
+  } else {
+    const size_t akp = (size_t)(k0 + a) * mp + (k0 - SB) + b;
+    Th[a][b] = xh[akp];
+    Tl[a][b] = xl[akp];
+    Ch[a][b] = xh[akp];
+    Cl[a][b] = xl[akp];
+    Qh[a][b] = qph[a * SB + b];
+    Ql[a][b] = qpl[a * SB + b];
+    float oh = xh[akk], ol = xl[akk];
+    __syncthreads();
+    float uh = 0.0f, ul = 0.0f;
+    for (int c = 0; c < SB; ++c) df_mac(Th[a][c], Tl[a][c], Qh[c][b], Ql[c][b], uh, ul);
+    df_renorm(uh, ul);
+    __syncthreads();  // every read of T is done
+    Th[a][b] = uh;
+    Tl[a][b] = ul;
+    __syncthreads();
+    for (int c = 0; c < SB; ++c) df_mac(Th[a][c], Tl[a][c], Ch[b][c], Cl[b][c], oh, ol);
+    df_renorm(oh, ol);
+    Ph[a][b] = oh;
+    Pl[a][b] = ol;
+    __syncthreads();
   }
-  __syncthreads();
+  // the 32 pivots, reading one copy of the block and writing the other (the
+  // Q buffers are free by now), so one barrier per pivot suffices
+  float(*ch)[SB + 1] = Ph;
+  float(*cl)[SB + 1] = Pl;
+  float(*nh)[SB + 1] = Qh;
+  float(*nl)[SB + 1] = Ql;
   for (int t = 0; t < SB; ++t) {
-    const float dh = Ph[t][t], dl = Pl[t][t];
-    const float ah = Ph[a][t], al = Pl[a][t];
-    const float bh = Ph[b][t], bl = Pl[b][t];
-    float h = Ph[a][b], l = Pl[a][b];
-    __syncthreads();  // every read of this pivot's iterate is done
+    const float dh = ch[t][t], dl = cl[t][t];
+    const float ah = ch[a][t], al = cl[a][t];
+    const float bh = ch[b][t], bl = cl[b][t];
+    float h = ch[a][b], l = cl[a][b];
     float rh, rl;
     df_recip(dh, dl, rh, rl);
     if (threadIdx.x == 0 && piv) piv[k0 + t] = dh;
@@ -130,34 +182,43 @@ __global__ void __launch_bounds__(SB* SB) k_sweep_pivot(const float* __restrict_
         df_renorm(h, l);
       }
     }
-    Ph[a][b] = h;
-    Pl[a][b] = l;
+    nh[a][b] = h;
+    nl[a][b] = l;
     __syncthreads();
+    float(*th)[SB + 1] = ch;
+    float(*tl)[SB + 1] = cl;
+    ch = nh;
+    cl = nl;
+    nh = th;
+    nl = tl;
   }
-  qh[a * SB + b] = Ph[a][b];
-  ql[a * SB + b] = Pl[a][b];
+  qh[a * SB + b] = ch[a][b];
+  ql[a * SB + b] = cl[a][b];
 }
 
 // one pivot step K: src -> dst for every 32 x 32 tile (I, J); the swept pivot
 // block -P^{-1} comes from k_sweep_pivot
-__global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restrict__ sh_, const float* __restrict__ sl_,
-                                                           float* __restrict__ dh_, float* __restrict__ dl_,
-                                                           int mp, int K, const float* __restrict__ qh,
-                                                           const float* __restrict__ ql) {
-  __shared__ float Ph[SB][SB + 1], Pl[SB][SB + 1];  // pivot block, swept in place -> -P^{-1}
-  __shared__ float Ch[SB][SB + 1], Cl[SB][SB + 1];  // panel rows of the other block: A_{J,K}
-  __shared__ float Th[SB][SB + 1], Tl[SB][SB + 1];  // A_{X,K} (-P^{-1})... see below
+__global__ void __launch_bounds__(SW_THREADS* kTilesPerCta) k_sweep_step(const float* __restrict__ sh_, const float* __restrict__ sl_,
+                                                                         float* __restrict__ dh_, float* __restrict__ dl_,
+                                                                         int mp, int K, const float* __restrict__ qh,
+                                                                         const float* __restrict__ ql) {
+  extern __shared__ __align__(16) char sw_smem[];
+  const int half = threadIdx.x / SW_THREADS;
+  TileSmem& S = reinterpret_cast<TileSmem*>(sw_smem)[half];
   const int nt = mp / SB;
-  const int I = blockIdx.x % nt, J = blockIdx.x / nt;
+  const int tile = blockIdx.x * kTilesPerCta + half;
+  if (tile >= nt * nt) return;  // no tile for this half; the other half's barrier counts its own threads
+  const int I = tile % nt, J = tile / nt;
   const int k0 = K * SB;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x % SW_THREADS;
+  const int bar = 1 + half;
   const int r = tid >> 3, c4 = (tid & 7) * 4;  // this thread's outputs: row r, columns c4..c4+3
 
   // ---- load the swept pivot block -P^{-1} ----
   for (int e = tid; e < SB * SB; e += SW_THREADS) {
     const int a = e / SB, b = e % SB;
-    Ph[a][b] = qh[e];
-    Pl[a][b] = ql[e];
+    S.Ph[a][b] = qh[e];
+    S.Pl[a][b] = ql[e];
   }
   // ---- load the panels needed by this tile ----
   // case 1 (I != K, J != K): T <- A_{I,K}, C <- A_{J,K}; case 2 (J == K): T <- A_{I,K};
@@ -167,27 +228,27 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restri
     for (int e = tid; e < SB * SB; e += SW_THREADS) {
       const int a = e / SB, b = e % SB;
       const size_t src = (size_t)(X * SB + a) * mp + k0 + b;
-      Th[a][b] = sh_[src];
-      Tl[a][b] = sl_[src];
+      S.Th[a][b] = sh_[src];
+      S.Tl[a][b] = sl_[src];
     }
   }
   if (I != K && J != K) {
     for (int e = tid; e < SB * SB; e += SW_THREADS) {
       const int a = e / SB, b = e % SB;
       const size_t src = (size_t)(J * SB + a) * mp + k0 + b;
-      Ch[a][b] = sh_[src];
-      Cl[a][b] = sl_[src];
+      S.Ch[a][b] = sh_[src];
+      S.Cl[a][b] = sl_[src];
     }
   }
-  __syncthreads();
+  half_sync(bar);
 
   // ---- this thread's four outputs ----
   float oh[4], ol[4];
   if (I == K && J == K) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      oh[q] = Ph[r][c4 + q];  // -P^{-1}
-      ol[q] = Pl[r][c4 + q];
+      oh[q] = S.Ph[r][c4 + q];  // -P^{-1}
+      ol[q] = S.Pl[r][c4 + q];
     }
   } else {
     // U = A_{X,K} (-P^{-1}) = -(A_{X,K} P^{-1}) for this thread's row r
@@ -200,31 +261,31 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restri
     // row r of U for all 32 columns is needed in case 1: compute the full
     // 32 x 32 U into smem first (each thread its 4 entries), then use it
     for (int b = 0; b < SB; ++b) {
-      const float th = Th[r][b], tl = Tl[r][b];
+      const float th = S.Th[r][b], tl = S.Tl[r][b];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) df_mac(th, tl, Ph[b][c4 + q], Pl[b][c4 + q], uh4[q], ul4[q]);
+      for (int q = 0; q < 4; ++q) df_mac(th, tl, S.Ph[b][c4 + q], S.Pl[b][c4 + q], uh4[q], ul4[q]);
     }
-    __syncthreads();  // all reads of T done before it is overwritten with U
+    half_sync(bar);  // all reads of T done before it is overwritten with U
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       df_renorm(uh4[q], ul4[q]);
-      Th[r][c4 + q] = uh4[q];
-      Tl[r][c4 + q] = ul4[q];
+      S.Th[r][c4 + q] = uh4[q];
+      S.Tl[r][c4 + q] = ul4[q];
     }
-    __syncthreads();
+    half_sync(bar);
     if (J == K) {
       // A_IK P^{-1} = -U
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        oh[q] = -Th[r][c4 + q];
-        ol[q] = -Tl[r][c4 + q];
+        oh[q] = -S.Th[r][c4 + q];
+        ol[q] = -S.Tl[r][c4 + q];
       }
     } else if (I == K) {
       // P^{-1} A_KJ = (A_JK P^{-1})^T = -U^T
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        oh[q] = -Th[c4 + q][r];
-        ol[q] = -Tl[c4 + q][r];
+        oh[q] = -S.Th[c4 + q][r];
+        ol[q] = -S.Tl[c4 + q][r];
       }
     } else {
       // A_IJ - A_IK P^{-1} A_KJ = A_IJ + U A_{J,K}^T
@@ -235,9 +296,9 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep_step(const float* __restri
         ol[q] = sl_[src];
       }
       for (int b = 0; b < SB; ++b) {
-        const float th = Th[r][b], tl = Tl[r][b];
+        const float th = S.Th[r][b], tl = S.Tl[r][b];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) df_mac(th, tl, Ch[c4 + q][b], Cl[c4 + q][b], oh[q], ol[q]);
+        for (int q = 0; q < 4; ++q) df_mac(th, tl, S.Ch[c4 + q][b], S.Cl[c4 + q][b], oh[q], ol[q]);
       }
     }
   }
@@ -292,12 +353,13 @@ __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ 
 
 size_t sweep_scratch_floats(int m) {
   const size_t mp = (size_t)(m + SB - 1) / SB * SB;
-  return 4 * mp * mp + mp + 8 + 2 * SB * SB;
+  return 4 * mp * mp + mp + 8 + 4 * SB * SB;
 }
 
 // G: upper triangle of the column-major m x m Gram; qinv: m x m output
 cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double* qinv, float2* qinv_df,
-                                 DevScalars* sc, double rank_tol, int num_sms, cudaStream_t st) {
+                                 DevScalars* sc, double rank_tol, int num_sms, cudaStream_t st,
+                                 cudaStream_t st_aux, cudaEvent_t ev_x, cudaEvent_t ev_p) {
   const int mp = (m + SB - 1) / SB * SB;
   const size_t mm = (size_t)mp * mp;
   float* a0h = scratch;
@@ -307,19 +369,47 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   float* piv = scratch + 4 * mm;
   // the prescale 2^e, 8-byte aligned after the mp pivots (mp is a multiple of 32)
   double* scale_buf = reinterpret_cast<double*>(scratch + 4 * mm + mp);
-  float* qh = scratch + 4 * mm + mp + 8;  // the swept pivot block of the current step
-  float* ql = qh + SB * SB;
+  // the swept pivot blocks of steps K (even K: q[0], odd K: q[1]) as pairs
+  float* qbase = scratch + 4 * mm + mp + 8;
+  float* qh[2] = {qbase, qbase + 2 * SB * SB};
+  float* ql[2] = {qbase + SB * SB, qbase + 3 * SB * SB};
   const int g1 = (int)std::max<long long>(1, std::min<long long>(((long long)mm + 255) / 256, (long long)num_sms * 4));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sweep_init<<<g1, 256, 0, st>>>(g, m, mp, a0h, a0l, scale_buf);
   const int nt = mp / SB;
+  const int tile_smem = (int)(sizeof(TileSmem) * kTilesPerCta);
+  {
+    const cudaError_t es = ensure_smem((const void*)k_sweep_step, tile_smem);
+    if (es != cudaSuccess) return es;
+  }
+  // The pivot kernel of step K + 1 needs the iterate that step K reads and
+  // -P_K^{-1}, not step K's output, so with an auxiliary stream it runs beside
+  // step K's tile kernel: ev_x marks "the iterate step K reads is complete",
+  // ev_p "the pivot kernel of the next step is complete".  Without one, the
+  // same kernels run in the same order on st.
+  const bool two = st_aux && ev_x && ev_p;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_sweep_pivot<<<1, SB * SB, 0, st>>>(a0h, a0l, mp, 0, nullptr, nullptr, qh[0], ql[0], piv);
+  cudaError_t e = cudaSuccess;
+  if (two && (e = cudaEventRecord(ev_x, st)) != cudaSuccess) return e;
   for (int K = 0; K < nt; ++K) {
     const bool even = (K & 1) == 0;
+    const float* sh = even ? a0h : a1h;
+    const float* sl = even ? a0l : a1l;
+    if (K + 1 < nt) {
+      if (two && (e = cudaStreamWaitEvent(st_aux, ev_x, 0)) != cudaSuccess) return e;
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      k_sweep_pivot<<<1, SB * SB, 0, two ? st_aux : st>>>(sh, sl, mp, K + 1, qh[K & 1], ql[K & 1],
+                                                          qh[(K + 1) & 1], ql[(K + 1) & 1], piv);
+    }
+    if (two && K >= 1 && (e = cudaStreamWaitEvent(st, ev_p, 0)) != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_sweep_pivot<<<1, SB * SB, 0, st>>>(even ? a0h : a1h, even ? a0l : a1l, mp, K, qh, ql, piv);
-    k_sweep_step<<<nt * nt, SW_THREADS, 0, st>>>(even ? a0h : a1h, even ? a0l : a1l, even ? a1h : a0h,
-                                                 even ? a1l : a0l, mp, K, qh, ql);
+    k_sweep_step<<<(nt * nt + kTilesPerCta - 1) / kTilesPerCta, SW_THREADS * kTilesPerCta, tile_smem, st>>>(
+        sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1]);
+    if (two) {
+      if ((e = cudaEventRecord(ev_x, st)) != cudaSuccess) return e;
+      if (K + 1 < nt && (e = cudaEventRecord(ev_p, st_aux)) != cudaSuccess) return e;
+    }
   }
   const bool in0 = (nt & 1) == 0;
   g_launches.fetch_add(1, std::memory_order_relaxed);
