@@ -60,6 +60,14 @@ struct DevScalars {
 // ---------------------------------------------------------------------------
 // PTX wrappers
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel of its stream is still
+// running; pdl_wait() returns once that kernel has completed and its writes are
+// visible (at once when there is no such dependency), and pdl_trigger() lets
+// the next such kernel start launching.  Both are called first thing, before
+// any read of a previous kernel's results.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

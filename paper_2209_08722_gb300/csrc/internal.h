@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
+#include <utility>
 
 #include "common.cuh"
 #include "stream.cuh"
@@ -26,7 +27,26 @@ StreamPlan make_stream_plan(int m, long long n, int lda, int esz, int num_sms, i
 int fused_vpl(int lda, int esz);
 cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
                           const StreamPlan& p, cudaStream_t st);
-cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st);
+// pdl: launch with programmatic stream serialization (see pdl_wait in common.cuh)
+cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p, cudaStream_t st,
+                              bool pdl = false);
+
+// kernel launch with programmatic stream serialization when pdl is set
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 // FP64 n-vectors <-> FP32 pairs for the double-float streaming passes
 struct DfPackArgs {
   const double* src[4];
@@ -126,7 +146,7 @@ cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, 
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
                             cudaStream_t st, const double* y_add = nullptr,
-                            const float2* Mdf = nullptr);
+                            const float2* Mdf = nullptr, bool pdl = false);
 cudaError_t launch_gemv_rows(const double* M, int rows, int cols, const double* x, const double* y0,
                              double alpha, double beta, double* y, int num_sms, cudaStream_t st);
 cudaError_t launch_cheb_pre(int m, double* dy, const double* dir, DevScalars* sc, cudaStream_t st);

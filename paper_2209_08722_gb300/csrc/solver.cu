@@ -143,6 +143,7 @@ struct lp_handle {
   size_t ev_used = 0;
   long long k1_launches = 0;
   double k1_ms = 0.0;
+  unsigned long long k1_sample = 0;  // product launches seen by the profiling sampler
   long long launch_base = 0;
   std::vector<lp_iter_record> history;
   std::vector<void*> allocs;
@@ -191,12 +192,17 @@ struct lp_handle {
 
 namespace {
 
-int sync_read(lp_handle* h) {
-  CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
+// the device status word of the last copy of the scalars, as an error code
+int check_read(lp_handle* h) {
   if (h->hsc->err == ERR_TIMEOUT) return h->fail(LP_ERR_DEVICE_TIMEOUT, "device wait timed out");
   if (h->hsc->err == ERR_NUMERICAL) return h->fail(LP_ERR_NUMERICAL, "non-finite value in a reduction");
   return LP_OK;
+}
+
+int sync_read(lp_handle* h) {
+  CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return check_read(h);
 }
 
 int set_scalar(lp_handle* h, double* dev_field, double value) {
@@ -274,15 +280,33 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
   a.pcg_dy = h->dy;
   a.bvec = h->p;
   a.coef = h->coef;
+  // Inner-loop products (skip_level 1) and their GEMVs use programmatic
+  // dependent launch, which hides most of the launch latency between the two.
+  // With opt.profile, one run of 8 FP32 products in 8 (a whole block of CG
+  // steps) is launched plainly, and so are its GEMVs (events between the
+  // kernels would stop the overlap, and a single plain launch among
+  // overlapped ones would be timed with its dispatch); its products after the
+  // first (which follows a host synchronisation) are timed between CUDA
+  // events. The other blocks keep the overlap.
   EvPair* ev = nullptr;
+  bool pdl = skip_level == 1 && !use64;
   if (h->opt.profile && !use64) {
-    ev = ev_next(h);
-    if (ev) cudaEventRecord(ev->a, h->st);
+    const unsigned long long k = h->k1_sample++;
+    if (((k >> 3) & 7) == 0) {
+      pdl = false;
+      if ((k & 7) != 0) {
+        ev = ev_next(h);
+        if (ev) cudaEventRecord(ev->a, h->st);
+      }
+    }
   }
   cudaError_t e;
   if (h->sparse) e = launch_sparse(h->dtype, use64, M_ADAT, a, h->sp_grid, h->st);
-  else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st);
-  else if (h->use_df) e = launch_stream_df(h->dtype, M_ADAT, a, h->plan, h->st);
+  else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st, pdl);
+  else if (h->use_df) {
+    a.pdl = skip_level >= 1 ? 1 : 0;  // the refresh inside the inner loop follows a GEMV closely
+    e = launch_stream_df(h->dtype, M_ADAT, a, h->plan, h->st);
+  }
   else e = launch_stream(h->dtype, true, M_ADAT, a, h->plan, h->st);
   if (ev) cudaEventRecord(ev->b, h->st);
   if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "adat launch: %s", cudaGetErrorString(e));
@@ -290,25 +314,30 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
 }
 
 int precond_gemvs(lp_handle* h, const double* r, double* z, int epi, int skip_level) {
+  // inner-loop GEMVs follow their product closely (see launch_adat); those of
+  // a block sampled by opt.profile are launched plainly, like its products
+  const bool pdl = skip_level >= 1 && !(h->opt.profile && (((h->k1_sample - 1) >> 3) & 7) == 0);
   if (!h->opt.precondition) {  // Q = I: z = r, then the same CG / Chebyshev epilogue
     cudaError_t e = launch_gemv_tri(nullptr, h->m, 2, r, z, epi, skip_level, h->r, h->pdir, h->dy, h->sc,
-                                    h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st);
+                                    h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st,
+                                    nullptr, nullptr, pdl);
     if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
     return LP_OK;
   }
   if (h->qinv_ok) {  // one full GEMV with the explicit Q^{-1} (as pairs when the sweep formed it)
     cudaError_t e = launch_gemv_tri(h->qinv, h->m, 2, r, z, epi, skip_level, h->r, h->pdir, h->dy,
                                     h->sc, h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef,
-                                    h->num_sms, h->st, nullptr, h->qinv_df_ok ? h->qinv_df : nullptr);
+                                    h->num_sms, h->st, nullptr, h->qinv_df_ok ? h->qinv_df : nullptr, pdl);
     if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
     return LP_OK;
   }
   cudaError_t e = launch_gemv_tri(h->rinv_cm, h->m, 1, r, h->wv, GH_NONE, skip_level, nullptr,
                                   nullptr, nullptr, h->sc, h->tickets + 1, &h->sc->err, 0, nullptr,
-                                  h->num_sms, h->st);
+                                  h->num_sms, h->st, nullptr, nullptr, pdl);
   if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
   e = launch_gemv_tri(h->rinv_rm, h->m, 0, h->wv, z, epi, skip_level, h->r, h->pdir, h->dy, h->sc,
-                      h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st);
+                      h->tickets + 2, &h->sc->err, h->opt.t_max, h->coef, h->num_sms, h->st, nullptr,
+                      nullptr, pdl);
   if (e != cudaSuccess) return h->fail(LP_ERR_CUDA, "gemv: %s", cudaGetErrorString(e));
   return LP_OK;
 }
@@ -649,7 +678,7 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
       if (h->hsc->inner_done == 2) break;
       continue;
     }
-    RET(sync_read(h));
+    RET(check_read(h));  // the scalars were copied after the refresh just above
     if (h->opt.profile) ev_flush(h);
     if (h->hsc->inner_done == 3) {
       status = kInnerIndefinite;

@@ -228,6 +228,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adat_fused(const StreamArg
   float* v_s = reinterpret_cast<float*>(smem + L.v_off);
   double* red = reinterpret_cast<double*>(smem + L.red_off);
   __shared__ int s_flag;
+  pdl_wait();
+  pdl_trigger();
   if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -368,12 +370,13 @@ cudaError_t launch_stream_t(const StreamArgs& a, int grid, int smem, cudaStream_
 }
 
 template <typename TA, int VPL>
-cudaError_t launch_fused_t(const StreamArgs& a, int grid, int smem, cudaStream_t st) {
+cudaError_t launch_fused_t(const StreamArgs& a, int grid, int smem, cudaStream_t st, bool pdl) {
   auto k = k_adat_fused<TA, VPL>;
   cudaError_t e = ensure_smem((const void*)k, smem);
   if (e != cudaSuccess) return e;
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  k<<<grid, kFusedThreads, smem, st>>>(a);
+  e = launch_maybe_pdl(k, dim3(grid), dim3(kFusedThreads), (size_t)smem, st, pdl, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -390,13 +393,13 @@ cudaError_t dispatch_mode(int mode, const StreamArgs& a, int grid, int smem, cud
 }
 
 template <typename TA>
-cudaError_t dispatch_fused(int vpl, const StreamArgs& a, int grid, int smem, cudaStream_t st) {
+cudaError_t dispatch_fused(int vpl, const StreamArgs& a, int grid, int smem, cudaStream_t st, bool pdl) {
   switch (vpl) {
-    case 1: return launch_fused_t<TA, 1>(a, grid, smem, st);
-    case 2: return launch_fused_t<TA, 2>(a, grid, smem, st);
-    case 4: return launch_fused_t<TA, 4>(a, grid, smem, st);
-    case 8: return launch_fused_t<TA, 8>(a, grid, smem, st);
-    case 16: return launch_fused_t<TA, 16>(a, grid, smem, st);
+    case 1: return launch_fused_t<TA, 1>(a, grid, smem, st, pdl);
+    case 2: return launch_fused_t<TA, 2>(a, grid, smem, st, pdl);
+    case 4: return launch_fused_t<TA, 4>(a, grid, smem, st, pdl);
+    case 8: return launch_fused_t<TA, 8>(a, grid, smem, st, pdl);
+    case 16: return launch_fused_t<TA, 16>(a, grid, smem, st, pdl);
   }
   return cudaErrorInvalidValue;
 }
@@ -452,12 +455,12 @@ cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& 
 }
 
 cudaError_t launch_adat_fused(int dtype, const StreamArgs& a, const StreamPlan& p,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool pdl) {
   const int esz = dtype == 1 ? 4 : 2;
   const int vpl = fused_vpl(a.lda, esz);
   if (vpl == 0) return cudaErrorInvalidValue;
-  if (dtype == 1) return dispatch_fused<float>(vpl, a, p.grid, p.smem, st);
-  if (dtype == 2) return dispatch_fused<bf16raw>(vpl, a, p.grid, p.smem, st);
+  if (dtype == 1) return dispatch_fused<float>(vpl, a, p.grid, p.smem, st, pdl);
+  if (dtype == 2) return dispatch_fused<bf16raw>(vpl, a, p.grid, p.smem, st, pdl);
   return cudaErrorInvalidValue;
 }
 

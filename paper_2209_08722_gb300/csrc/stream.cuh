@@ -60,6 +60,7 @@ struct StreamArgs {
   const double* vin;  // m-vector for the column dots
   double* out_col[2];  // per-column FP64 outputs (n)
   float2* out_df[2];   // per-column double-float outputs (n) of the double-float kernels
+  int pdl;             // host side: launch with programmatic stream serialization
   float* out_colf;     // per-column FP32 output (n)
   void* partials;      // [grid][lda] of TC per accumulator (acc1 after acc0)
   double* red_partials;  // [grid][2] column reductions

@@ -58,6 +58,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
   float* vl_s = vh_s + a.lda;
   double* red = reinterpret_cast<double*>(smem + L.red_off);
   __shared__ int s_flag;
+  pdl_wait();
+  pdl_trigger();
   if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -267,7 +269,8 @@ cudaError_t df_launch(const StreamArgs& a, int grid, int smem, cudaStream_t st) 
     cudaError_t e = ensure_smem((const void*)k, smem);
     if (e != cudaSuccess) return e;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    k<<<grid, (CW + 1) * 32, smem, st>>>(a);
+    e = launch_maybe_pdl(k, dim3(grid), dim3((CW + 1) * 32), (size_t)smem, st, a.pdl != 0, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
 }

@@ -71,6 +71,8 @@ struct GemvArgs {
 __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
   __shared__ int s_flag;
   __shared__ __align__(16) double red[32];  // also read as float4 in the epilogue
+  pdl_wait();
+  pdl_trigger();
   if (a.skip_level > 0 && a.sc->inner_done >= a.skip_level) return;
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
 cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, double* y, int epi,
                             int skip_level, double* r, double* p, double* dy, DevScalars* sc,
                             unsigned* ticket, int* err, int t_max, double* coef, int num_sms,
-                            cudaStream_t st, const double* y_add, const float2* Mdf) {
+                            cudaStream_t st, const double* y_add, const float2* Mdf, bool pdl) {
   if ((Mdf || !M) && lower != 2) return cudaErrorInvalidValue;
   GemvArgs a{M, m, lower, x, y, epi, skip_level, r, p, dy, sc, ticket, err, t_max, coef, y_add, Mdf};
   const int warps = Mdf ? 4 : 8;
@@ -302,7 +304,8 @@ cudaError_t launch_gemv_tri(const double* M, int m, int lower, const double* x, 
     if (e != cudaSuccess) return e;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  k_gemv_tri<<<grid, warps * 32, smem, st>>>(a);
+  const cudaError_t e = launch_maybe_pdl(k_gemv_tri, dim3(grid), dim3(warps * 32), smem, st, pdl, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
