@@ -186,3 +186,39 @@ def test_two_rhs_adaptive_sigma_matches_oracle_and_cuts_iterations(col_scale):
     ref_sig = [h.sigma_used for h in ref.history[:-1]]
     k = min(5, len(sig), len(ref_sig))
     assert np.allclose(sig[:k], ref_sig[:k], rtol=1e-3, atol=1e-6)
+
+
+@pytest.mark.gpu
+def test_failed_sketch_draws_are_redrawn_and_inner_solves_stay_short():
+    """With s = 2, draws of W whose rows for the basic columns are dependent
+    leave PCG with a Ritz spread ~1e6 near the optimum (this LP once needed
+    2 x t_max = 1000 steps in one outer iteration); the solver redraws them, so
+    every outer iteration ends within a few dozen steps."""
+    torch_cuda()
+    lp = lpgen.planted_dense(64, 8192, seed=1000, storage="bf16")
+    with solver_for(lp, s=2) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+        assert info["status"] == 0, info
+        assert abs(lp.c @ x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+        assert info["inner_max"] <= 100, info
+        assert info["sketch_retries"] >= 1, info
+
+
+@pytest.mark.gpu
+def test_lp_whose_sketches_collapsed_near_the_optimum_is_solved():
+    """LP 23 of the batched family (284 x 53,392, s = 2): near mu ~ 1e-10 every
+    draw it tried had a singular W_B, kappa(ADW) ~ 1e9 against kappa(AD) ~ 600,
+    and the stored Q^{-1} turned indefinite; it stalled at gap 4.3e-8 before
+    the redraw and refactor rules."""
+    torch_cuda()
+    rng = np.random.default_rng(0)
+    for _ in range(24):  # the family's sizes, as lpgen.batch_family draws them
+        m = int(rng.integers(32, 513))
+        k = int(rng.integers(64, 257))
+    lp = lpgen.planted_dense(m, m * k, seed=23, storage="f32")
+    with solver_for(lp, s=2) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+        assert info["status"] == 0, info
+        assert info["rel_gap"] <= 1e-8
+        assert abs(lp.c @ x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+        assert info["inner_max"] <= 200, info

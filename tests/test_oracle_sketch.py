@@ -123,3 +123,44 @@ def test_gaussian_sketch_subspace_embedding():
     W = sketch.gaussian_matrix(8, 0, 0, n, w)
     G = (V.T @ W) @ (W.T @ V)
     assert np.linalg.norm(G - np.eye(m), 2) < 0.25
+
+
+def _basis_rows(cols, signs, basis, w, s):
+    """W_B: the rows of the CountSketch for the columns in `basis` (m x w)."""
+    wb = np.zeros((len(basis), w))
+    for b in range(s):
+        wb[np.arange(len(basis)), cols[b, basis]] += signs[b, basis] / np.sqrt(s)
+    return wb
+
+
+def test_countsketch_rank_on_a_coordinate_subspace_depends_on_s():
+    """Near an IPM optimum range((AD)^T) is close to the span of the m basic
+    coordinates, so W embeds it only if W_B (its rows for those columns) has
+    rank m.  With s = 1 two basic columns sharing a bucket already make W_B
+    singular (about m^2/(2w) shared pairs at w = 4m); with s = 2 a pair sharing
+    both buckets with equal sign products (or a longer cycle of shared buckets)
+    does, in a few per cent of draws; with s = 4 it takes far rarer
+    coincidences.  This is the failure the GPU path detects and redraws."""
+    m, n, w = 128, 16384, 512
+    basis = np.sort(np.random.default_rng(5).choice(n, m, replace=False))
+    draws = [(k, r) for k in range(10) for r in range(4)]
+    singular = {1: 0, 2: 0, 4: 0}
+    for s in (1, 2, 4):
+        for k, r in draws:
+            cols, signs = sketch.countsketch_hash(0, k, r, n, w, s)
+            sv = np.linalg.svd(_basis_rows(cols, signs, basis, w, s), compute_uv=False)
+            is_singular = sv[-1] < 1e-10 * sv[0]
+            singular[s] += int(is_singular)
+            if s == 2:
+                seen = {}
+                dependent_pair = False
+                for j in basis:
+                    key = (int(cols[0, j]), int(cols[1, j]))
+                    if key in seen:
+                        i = seen[key]
+                        dependent_pair |= signs[0, i] * signs[1, i] == signs[0, j] * signs[1, j]
+                    seen[key] = j
+                assert not dependent_pair or is_singular
+    assert singular[1] == len(draws)
+    assert 1 <= singular[2] <= 0.4 * len(draws), singular
+    assert singular[4] == 0, singular
