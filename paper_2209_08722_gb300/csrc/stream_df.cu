@@ -113,6 +113,16 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
           mbar_wait(&full[j % S], (uint32_t)((j / S) & 1), a.err);
     }
   } else {
+    // this lane's slice of v as pairs, in registers for the whole stream
+    float vrh[VPL][VEC], vrl[VPL][VEC];
+#pragma unroll
+    for (int c = 0; c < VPL; ++c)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        const int rv = c * 32 + lane;
+        vrh[c][e] = (rv < RV) ? vh_s[rv * VEC + e] : 0.0f;
+        vrl[c][e] = (rv < RV) ? vl_s[rv * VEC + e] : 0.0f;
+      }
     for (int i = 0; i < my_tiles; ++i) {
       const int st = i % S;
       if (!mbar_wait(&full[st], (uint32_t)((i / S) & 1), a.err)) {
@@ -126,21 +136,22 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_stream_df(const StreamArgs
       for (int jj = warp; jj < ncols; jj += CW) {
         const TA* col = At + (size_t)jj * a.lda;
         float av[VPL][VEC];
-        float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
+        float sh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int c = 0; c < VPL; ++c) {
           const int rv = c * 32 + lane;
           if (rv < RV) {
             ld16<float>(col + rv * VEC, av[c]);
 #pragma unroll
-            for (int e = 0; e < VEC; ++e)
-              df_fma(av[c][e], vh_s[rv * VEC + e], vl_s[rv * VEC + e], sh[e & 1], sl[e & 1]);
+            for (int e = 0; e < VEC; ++e) df_fma(av[c][e], vrh[c][e], vrl[c][e], sh[e & 3], sl[e & 3]);
           } else {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) av[c][e] = 0.0f;
           }
         }
         df_add(sh[0], sl[0], sh[1], sl[1]);
+        df_add(sh[2], sl[2], sh[3], sl[3]);
+        df_add(sh[0], sl[0], sh[2], sl[2]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const float oh = __shfl_xor_sync(0xffffffffu, sh[0], o);
@@ -250,7 +261,10 @@ constexpr int df_nacc() {
 
 template <int MODE>
 constexpr int df_cw(int elems) {
-  return df_nacc<MODE>() == 2 ? (elems <= 4 ? 16 : 8) : (elems <= 16 ? 16 : 8);
+  // one accumulated output (M_ADAT) keeps v as pairs in registers: 12 consumer
+  // warps so that its 128 registers per thread fit the register file
+  return df_nacc<MODE>() == 2 ? (elems <= 4 ? 16 : 8)
+                              : (elems <= 16 ? (df_nacc<MODE>() == 1 ? 12 : 16) : 8);
 }
 
 template <int MODE>
