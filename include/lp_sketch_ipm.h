@@ -48,7 +48,7 @@ typedef struct lp_handle lp_handle;
 #define LP_ERR_NOT_FEASIBLE    -5  /* feasible mode: start not strictly feasible / not in N(gamma) */
 #define LP_ERR_NUMERICAL       -6  /* NaN/Inf or a breakdown in a reduction */
 #define LP_ERR_DEVICE_TIMEOUT  -7  /* a bounded device-side wait gave up */
-#define LP_ERR_UNSUPPORTED     -8  /* valid request this build does not implement */
+#define LP_ERR_UNSUPPORTED     -8  /* valid request the library does not implement */
 #define LP_STATUS_MAX_ITER      1  /* lp_solve: k_max outer iterations reached */
 #define LP_WARN_INNER_MAXIT     2  /* an inner solve stopped at t_max */
 #define LP_STATUS_STALLED       3  /* lp_solve: step length reached zero, or mu fell far below the gap
@@ -274,7 +274,7 @@ int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
 
 /* u = A diag(d2) A^T v without any device allocation, for callers that own all
  * device memory themselves (a pre-sized arena, a serving loop with a fixed
- * memory budget, code that must not call the driver's allocator after start-up)
+ * memory budget, code that must not call the CUDA allocator after start-up)
  * and therefore cannot create a handle.  The paper has no counterpart: this is
  * the FP32 product of the solver's inner loop offered outside a handle.
  *   A   device pointer, column-major, leading dimension ld (elements) with

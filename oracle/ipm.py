@@ -11,7 +11,7 @@ Two normal-equation modes:
     correction v of eq. (compv), then the directions of eqs. (delxhat),
     (delshat) / (delxhat_i), (delshat_i).
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
   * alpha_max (Alg. 2 step 5, Alg. 3 step 6) is the first exit from N(gamma)
     along the direction: the largest alpha in [0,1] with the whole segment
     [0, alpha] inside N(gamma); positivity of (x, s) is enforced explicitly.

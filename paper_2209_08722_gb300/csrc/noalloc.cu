@@ -3,7 +3,7 @@
 //
 // Who needs this: code that embeds the product in a host application whose
 // device memory is fully owned by someone else -- a pre-sized arena, a
-// serving loop with a fixed memory budget, or a process where the driver
+// serving loop with a fixed memory budget, or a process where the CUDA
 // allocation calls must not be made after start-up (cudaMalloc and cudaFree
 // can block or implicitly synchronise the device, and fail once the budget
 // is spent).  Such callers cannot use lp_create, which allocates a handle's

@@ -1,8 +1,8 @@
 """End-to-end parity of lp_solve (Algorithms 2 and 3 on the GPU) with the CPU
 oracle and the planted closed-form optimum.
 
-Bar (BASELINE the benchmark spec): relative duality gap <= 1e-8 and FP64 objective
-agreement <= 1e-7 with the oracle and with c^T x*.
+Bar: relative duality gap <= 1e-8 and FP64 objective agreement <= 1e-7 with
+the oracle and with c^T x*.
 """
 
 import numpy as np

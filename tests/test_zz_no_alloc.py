@@ -1,7 +1,7 @@
 """lp_adat_noalloc: the product A diag(d2) A^T v for callers that cannot allocate.
 
 Some callers own all device memory themselves (a fixed arena, a serving loop
-with a hard memory budget, code that must not call the driver's allocator
+with a hard memory budget, code that must not call the CUDA allocator
 after start-up) and so cannot create a solver handle, which allocates its
 workspaces.  lp_adat_noalloc takes the caller's A, d2, v and u and keeps its
 scratch in a fixed-size device array inside the library.  This test calls it
