@@ -1,0 +1,82 @@
+"""Parity at the full size the bench times: the 512 x 131072 FP32 planted LP
+with columns scaled by 10^U(-2, 2) (seed 0), with the solver options of the
+bench (CountSketch w = 4m, s = 4).  The oracle checks every output of the
+product (one FP64 matrix product), sampled columns of the sketch (one bucket
+at a time, from the oracle's own hash), and the solve against the planted
+closed-form optimum.
+
+Tolerances as in test_gpu_kernels: the FP32 product to 4 (m + L + 64) 2^-24
+times |A| D^2 |A|^T |v| (L = n / 1216 + 64 columns summed in FP32 per warp),
+the double-float product to 8 (m + n) 2^-53 times the same bound, the
+double-float sketch to (32 n s / w + 64) 2^-48 times |A D| |W|.
+"""
+
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import sketch
+from tests.gpu_helpers import EPS32, EPS64, adat_bound, dev, host, solver_for, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+M, N, S_BLOCKS, W_FACTOR = 512, 131072, 4, 4.0
+DF_U = 2.0 ** -48
+
+
+@pytest.fixture(scope="module")
+def bench_lp():
+    return lpgen.planted_dense(M, N, seed=0, storage="f32", col_scale_log10=(-2.0, 2.0))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_product_matches_fp64(bench_lp, precision):
+    torch = torch_cuda()
+    lp = bench_lp
+    rng = np.random.default_rng(11)
+    d2 = np.exp(rng.uniform(-6, 6, N))
+    v = rng.standard_normal(M)
+    ref = lp.A @ (d2 * (lp.A.T @ v))
+    with solver_for(lp, s=S_BLOCKS, w_factor=W_FACTOR) as S:
+        u = host(S.adat(dev(torch, d2), dev(torch, v), precision))
+    bound = adat_bound(lp.A, d2, v)
+    if precision == 1:
+        tol = 8 * (M + N) * EPS64 * bound
+    else:
+        tol = 4 * (M + N // 1216 + 64 + 64) * EPS32 * bound
+    assert np.all(np.abs(u - ref) <= tol), np.max(np.abs(u - ref) / bound)
+
+
+def test_full_size_countsketch_sampled_columns(bench_lp):
+    torch = torch_cuda()
+    lp = bench_lp
+    rng = np.random.default_rng(12)
+    D = np.exp(rng.uniform(-3, 3, N))
+    seed, k, retry = 0, 5, 0
+    with solver_for(lp, s=S_BLOCKS, w_factor=W_FACTOR) as S:
+        w = S.sketch_width
+        adw = host(S.sketch(dev(torch, D), seed, k, retry))
+    assert adw.shape == (M, w)
+    cols, signs = sketch.countsketch_hash(seed, k, retry, N, w, S_BLOCKS)
+    eps = max(8 * N * EPS64, (32 * N * S_BLOCKS / w + 64) * DF_U)
+    for bucket in rng.choice(w, 24, replace=False):
+        b = bucket // (w // S_BLOCKS)  # the block this sketch column belongs to
+        members = np.nonzero(cols[b] == bucket)[0]
+        scale = signs[b, members] * D[members] / np.sqrt(S_BLOCKS)
+        ref = lp.A[:, members] @ scale
+        bound = np.abs(lp.A[:, members]) @ np.abs(scale)
+        assert np.all(np.abs(adw[:, bucket] - ref) <= eps * bound + 1e-300), bucket
+
+
+def test_full_size_solve_reaches_the_planted_optimum(bench_lp):
+    torch_cuda()
+    lp = bench_lp
+    with solver_for(lp, s=S_BLOCKS, w_factor=W_FACTOR) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+    assert info["status"] == 0, info
+    assert info["rel_gap"] <= 1e-8 and info["rp_rel"] <= 1e-8 and info["rd_rel"] <= 1e-8
+    assert abs(float(lp.c @ x) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert np.all(x > 0) and np.all(s > 0)
+    # the planted support is identified: the m largest x_j are the basic columns
+    basis = np.nonzero(lp.x_star > 0)[0]
+    assert set(np.argsort(-x)[:M]) == set(basis)

@@ -13,7 +13,7 @@ Tolerances: FP64 arithmetic is held to c * (length) * 2^-53 times the
 absolute-value bound of the same expression; the FP32 product to
 4 (m + L + 64) 2^-24 times |A| D^2 |A|^T |v| (forward error of a dot product of
 length m followed by FP32 sums of L columns per warp; the per-CTA partials
-are summed in FP64).
+are summed in double-float, ~2^-48).
 """
 
 import numpy as np
