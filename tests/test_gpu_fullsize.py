@@ -80,3 +80,26 @@ def test_full_size_solve_reaches_the_planted_optimum(bench_lp):
     # the planted support is identified: the m largest x_j are the basic columns
     basis = np.nonzero(lp.x_star > 0)[0]
     assert set(np.argsort(-x)[:M]) == set(basis)
+
+
+# ---- the sparse configuration at its full size --------------------------------
+# (the dense BF16 configuration, 2048 x 524288, shares its kernel launch
+# configuration, which depends on m, with the 2048-row cases of
+# test_gpu_kernels; generating its 10^9 entries here would take minutes)
+
+def test_c3_full_size_sparse_product_matches_fp64():
+    torch = torch_cuda()
+    # c3: CSC 4096 x 2,000,000, 8 nonzeros per column, 20 % Zipf rows, w = 3m, s = 2
+    lp = lpgen.config_small("c3", 1)
+    A = lp.scipy_csc()
+    rng = np.random.default_rng(14)
+    d2 = np.exp(rng.uniform(-5, 5, lp.n))
+    v = rng.standard_normal(lp.m)
+    ref = A @ (d2 * (A.T @ v))
+    absA = abs(A)
+    bound = absA @ (d2 * (absA.T @ np.abs(v)))
+    with solver_for(lp, s=2, w_factor=3.0) as S:
+        u = host(S.adat(dev(torch, d2), dev(torch, v), 0))
+    per_cta = lp.n // 304 + 1
+    tol = 4 * (8 + per_cta + 64) * EPS32 * bound
+    assert np.all(np.abs(u - ref) <= tol + 1e-300)
