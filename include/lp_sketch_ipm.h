@@ -91,11 +91,16 @@ typedef struct {
     int32_t t_max;         /* inner iteration limit per outer iteration; 500 */
     int32_t v_correction;  /* 1: apply eq. (compv); 0: v = 0 (Table 2 ablation) */
     int32_t cheb_lanczos;  /* CG steps used to estimate the Chebyshev interval; 10 */
-    int32_t profile;       /* 1: time the hot product kernel with CUDA events */
+    int32_t profile;       /* 1: time the hot product kernel with CUDA events: one
+                              block of 8 CG steps in 8 runs without the overlapped
+                              (programmatic) launches, and its products but the
+                              first are timed; 0 */
     double w_factor;       /* sketch width w = w_factor * m when w == 0; 4.0 */
     int64_t w;             /* explicit sketch width (multiple of s), or 0 */
     uint64_t seed;         /* seed of the sketch generator; 0 */
-    void* stream;          /* cudaStream_t to run on, or NULL for a private stream */
+    void* stream;          /* cudaStream_t to run on, or NULL for a private stream
+                              (the factor also uses a private second stream, joined
+                              back to this one by events before the factor ends) */
     int32_t tensor_sketch; /* Gaussian sketch with FP32/BF16 A: 1 = tcgen05 tensor-core GEMM,
                               0 = FP32 SIMT kernel; 1 */
     int32_t precondition;  /* 1 = the paper's method (sketch, Q^{-1}, correction v);
@@ -363,7 +368,8 @@ int lp_set_warm_start(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, f
 /* counters since lp_set_warm_start: recorded samples, proposals, accepted proposals */
 int lp_get_warm_start_stats(lp_handle* h, int64_t* recorded, int64_t* proposals, int64_t* accepted);
 
-/* Statistics of the hot product kernel (requires opt.profile = 1). */
+/* Statistics of the hot product kernel (requires opt.profile = 1; the timed
+ * launches are the sample described at lp_options.profile). */
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);
 int lp_reset_kernel_stats(lp_handle* h);
 
