@@ -357,11 +357,29 @@ def run_warm_start(args):
                      "accepted": acc, "proposals": props, "solve_s": secs}
     for S in solvers:
         S.close()
+    # the plain FP32 form of the same LPs (the BF16 values are exact in FP32), cold
+    f32 = [LPSolver(np.ascontiguousarray(lp.A.T, dtype=np.float32), lp.b, lp.c, m, n, dtype="f32", s=2)
+           for lp in tests]
+    f32[0].solve(tol=TOL)
+    torch.cuda.synchronize()
+    inner, outer, err, secs = 0, 0, 0.0, 0.0
+    for lp, S in zip(tests, f32):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, _, _, info = S.solve(tol=TOL)
+        secs += time.perf_counter() - t0
+        inner += info["inner_total"]
+        outer += info["outer_iterations"]
+        err = max(err, abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective)))
+        S.close()
+    out["fp32_cold"] = {"inner_total": inner, "outer_total": outer, "max_objective_rel_err": err, "solve_s": secs}
     print(json.dumps({"mode": "warm_start", "workload": f"planted dense BF16 m={m} n={n}, 24 training / 8 test LPs",
                       "samples": total, "params": net.num_params, "train_s": t_train, "final_loss": loss,
+                      "fp32_cold": out["fp32_cold"],
                       "cold": out["none"], "previous": out["previous"], "learned": out["model"],
                       "inner_saved_frac": 1.0 - out["model"]["inner_total"] / out["none"]["inner_total"],
-                      "time_saved_frac": 1.0 - out["model"]["solve_s"] / out["none"]["solve_s"]}),
+                      "time_saved_frac": 1.0 - out["model"]["solve_s"] / out["none"]["solve_s"],
+                      "learned_bf16_vs_fp32_cold_time": out["model"]["solve_s"] / out["fp32_cold"]["solve_s"]}),
           flush=True)
     return 0
 
