@@ -22,10 +22,11 @@ import numpy as np
 def bf16_bits(a: np.ndarray) -> np.ndarray:
     """Round FP64/FP32 values to bfloat16 (round to nearest even); uint16 bits."""
     f = np.ascontiguousarray(a, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
+    u = f.view(np.uint32)
     # NaN is not produced by the generators; plain RNE on the upper 16 bits.
-    rounding = 0x7FFF + ((u >> 16) & 1)
-    return ((u + rounding) >> 16).astype(np.uint16)
+    # For finite values u + 0x8000 stays below 2^32, so 32-bit arithmetic holds.
+    rounding = np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))
+    return ((u + rounding) >> np.uint32(16)).astype(np.uint16)
 
 
 def round_bf16(a: np.ndarray) -> np.ndarray:
@@ -101,12 +102,11 @@ class PlantedLP:
         uint16 bit pattern.
         """
         assert self.A is not None
-        At = np.ascontiguousarray(self.A.T)
         if self.storage == "f64":
-            return At
+            return np.ascontiguousarray(self.A.T)
         if self.storage == "f32":
-            return At.astype(np.float32)
-        return bf16_bits(At)
+            return np.ascontiguousarray(self.A.astype(np.float32).T)
+        return np.ascontiguousarray(bf16_bits(self.A).T)
 
 
 def _plant(rng: np.random.Generator, m: int, n: int):
