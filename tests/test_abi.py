@@ -80,3 +80,17 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_2209_08722_gb300 import _native
     with pytest.raises(ImportError):
         _native.load(str(tmp_path / "nope.so"))
+
+
+def test_status_codes_match_the_header():
+    """Every status and error code of the header has the same value in the
+    Python binding, and a name in its status table."""
+    from paper_2209_08722_gb300 import _native as nat
+    src = open(HEADER).read()
+    codes = dict((name, int(val)) for name, val in
+                 re.findall(r"^#define\s+(LP_(?:OK|ERR_\w+|STATUS_\w+|WARN_\w+))\s+(-?\d+)", src, flags=re.M))
+    assert "LP_OK" in codes and "LP_ERR_ARG" in codes and "LP_STATUS_STALLED" in codes
+    for name, val in codes.items():
+        assert getattr(nat, name) == val, name
+        assert nat.STATUS_NAMES[val] == name, name
+    assert set(nat.STATUS_NAMES) == set(codes.values())
