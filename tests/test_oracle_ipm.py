@@ -77,10 +77,10 @@ def test_planted_tiny_matches_vertex_enumeration():
 # per-step identities and invariants
 # ---------------------------------------------------------------------------
 
-def _trajectory(mode, solver="sketch", m=10, n=300, seed=7, k_max=40, v_corr=True):
+def _trajectory(mode, solver="sketch", m=10, n=300, seed=7, k_max=40, v_corr=True, sigma=0.5):
     lp = lpgen.planted_dense(m, n, seed=seed)
     opt = ipm.Options(mode=mode, solver=solver, s=2, w=4 * m, keep_vectors=True,
-                      k_max=k_max, v_correction=v_corr)
+                      k_max=k_max, v_correction=v_corr, sigma=sigma)
     if mode == "feasible":
         x0, y0, s0 = lpgen.feasible_start(lp, opt.gamma)
         res = ipm.solve(lp.A, lp.b, lp.c, opt, x0, y0, s0)
@@ -290,14 +290,17 @@ def test_first_exit_hand_built_quadratics():
     assert np.allclose(got, expect)
 
 
-@pytest.mark.parametrize("mode", ["feasible", "infeasible"])
-def test_step_length_against_grid(mode):
-    lp, opt, res = _trajectory(mode, k_max=12)
+@pytest.mark.parametrize("mode,sigma", [("feasible", 0.5), ("infeasible", 0.5), ("infeasible", 0.3)])
+def test_step_length_against_grid(mode, sigma):
+    # at sigma = 0.5 the residual condition of the infeasible neighbourhood
+    # never binds on this LP; at sigma = 0.3 it stops some steps
+    lp, opt, res = _trajectory(mode, k_max=12 if sigma == 0.5 else 6, sigma=sigma)
     feasible = mode == "feasible"
     r0 = np.sqrt(res.history[0].vectors["r_p"] @ res.history[0].vectors["r_p"]
                  + res.history[0].vectors["r_d"] @ res.history[0].vectors["r_d"])
     mu0 = res.history[0].mu
     grid = np.linspace(0, 1, 20001)
+    tight = 0
     for rec in res.history[:-1]:
         V = rec.vectors
         x, s, dx, ds = V["x"], V["s"], V["dx"], V["ds"]
@@ -317,6 +320,77 @@ def test_step_length_against_grid(mode):
         ab = rec.alpha_bar
         gap_ab = (x + ab * dx) @ (s + ab * ds)
         assert gap_ab <= min(gaps) * (1 + 1e-9) + 1e-15
+        if not feasible:
+            mu_a = (x + amax * dx) @ (s + amax * ds) / x.size
+            tight += abs(mu_a / mu0 - (1 - amax) * rr) <= 1e-7 * mu_a / mu0
+    if sigma < 0.5:
+        assert tight >= 1
+
+
+def _grid_membership(x, s, dx, ds, grid, gamma, feasible, rr, mu0, slack=1e-9):
+    """Brute force: is (x + a dx, s + a ds) in N(gamma) for every a of the
+    grid?  eq. neigh: x, s > 0 and x_i s_i >= (1 - gamma) mu; infeasible
+    (Section 5) adds ||r(a)||/||r0|| = (1 - a) rr <= mu(a)/mu0.  Also
+    returns the duality gap at every grid point."""
+    X = x[None, :] + grid[:, None] * dx[None, :]
+    S = s[None, :] + grid[:, None] * ds[None, :]
+    gap = (X * S).sum(axis=1)
+    mu = gap / x.size
+    ok = (X > 0).all(axis=1) & (S > 0).all(axis=1)
+    ok &= (X * S).min(axis=1) >= (1 - gamma) * mu * (1 - slack)
+    if not feasible:
+        ok &= (1 - grid) * rr <= mu / mu0 * (1 + slack)
+    return ok, gap
+
+
+@pytest.mark.parametrize("feasible", [True, False])
+def test_step_lengths_on_random_states_against_grid(feasible):
+    # Trajectories rarely make every condition bind (with gamma = 0.999 the
+    # neighbourhood hardly ever does, and the gap is usually smallest at
+    # alpha_max), so random states in N(gamma) with directions built to make
+    # each condition bind are checked too: alpha_max is the first exit from
+    # N(gamma) on a grid of 20001 steps, alpha_bar minimises the gap on
+    # [0, alpha_max].  Half the directions shrink one group of coordinates and
+    # grow the rest, which puts the gap's minimiser inside the interval.
+    rng = np.random.default_rng(50 + feasible)
+    grid = np.linspace(0, 1, 20001)
+    n = 40
+    interior = tight = 0
+    for trial in range(36):
+        gamma = (0.3, 0.6, 0.9)[trial % 3]
+        x = np.exp(rng.uniform(-1, 1, n))
+        s = (1 + 0.8 * gamma * rng.uniform(-1, 1, n)) / x
+        shrink = rng.uniform(0.2, 1.0) if feasible else rng.uniform(0.5, 1.0)
+        if trial % 4 < 2:
+            dx = x * (-shrink + rng.uniform(0.2, 1.2) * rng.standard_normal(n))
+            ds = s * (-shrink + rng.uniform(0.2, 1.2) * rng.standard_normal(n))
+        else:
+            grow = rng.random(n) < rng.uniform(0.15, 0.4)
+            u = np.where(grow, 1.0, -rng.uniform(0.6, 1.0)) * (1 + 0.1 * rng.standard_normal(n))
+            dx = x * u
+            ds = s * (u + 0.1 * rng.standard_normal(n))
+        mu = x @ s / n
+        mu0 = mu * rng.uniform(1, 3)
+        rr = 0.0 if feasible else mu / mu0 * rng.uniform(0.9, 1.0)
+        amax, abar = ipm.step_lengths(x, s, dx, ds, gamma, feasible, rr, mu0)
+        ok, gap = _grid_membership(x, s, dx, ds, grid, gamma, feasible, rr, mu0)
+        assert ok[0]
+        inside = grid <= amax
+        assert ok[inside].all(), trial
+        if amax < 1.0:
+            beyond = grid > amax * (1 + 1e-6) + 1e-9
+            assert not ok[beyond][:5].all(), trial
+        assert 0.0 <= abar <= amax
+        gap_ab = (x + abar * dx) @ (s + abar * ds)
+        assert gap_ab <= gap[inside].min() * (1 + 1e-9) + 1e-15, trial
+        interior += 1e-3 < abar < amax * (1 - 1e-3)
+        if not feasible:
+            mu_a = (x + amax * dx) @ (s + amax * ds) / n
+            tight += abs(mu_a / mu0 - (1 - amax) * rr) <= 1e-7 * mu_a / mu0
+    # the cases above really exercised the interior minimiser and, for the
+    # infeasible neighbourhood, the residual condition
+    assert interior >= 3
+    assert feasible or tight >= 3
 
 
 def test_feasible_start_is_strictly_feasible_and_central_enough():

@@ -145,6 +145,16 @@ def test_cg_residual_monotone_with_contraction_eq_rec():
     assert (rates <= pcg.cg_contraction(0.5) + 1e-12).all()
 
 
+@pytest.mark.parametrize("zeta", [0.1, 0.5, 0.9])
+def test_contraction_is_lemma_3_2_rate_at_the_lemma_3_1_band_edges(zeta):
+    # Lemma 3.1's band [(1 + zeta/2)^-1, (1 - zeta/2)^-1] for the squared
+    # singular values gives kappa^2 = (1 + zeta/2)/(1 - zeta/2), and Lemma
+    # 3.2's rate (kappa^2 - 1)/2 at that kappa is the eq. rec contraction
+    kappa2 = (1.0 / (1.0 - zeta / 2)) / (1.0 / (1.0 + zeta / 2))
+    assert pcg.cg_contraction(zeta) == pytest.approx((kappa2 - 1) / 2, rel=1e-14)
+    assert pcg.cg_contraction(zeta) < 1.0
+
+
 def test_theory_tolerance_and_iteration_count():
     n, gamma, sigma = 1000, 0.9, 0.5
     mu = 0.3
@@ -157,3 +167,25 @@ def test_theory_tolerance_and_iteration_count():
     assert np.sqrt(6) * n * 0.5 ** t * (1 + sigma / np.sqrt(1 - gamma)) <= gamma * sigma / 4
     assert np.sqrt(6) * n * 0.5 ** (t - 1) * (1 + sigma / np.sqrt(1 - gamma)) > gamma * sigma / 4
     assert t == int(np.ceil(np.log(n * psi) / np.log(2)))
+
+
+def test_lanczos_interval_recovers_the_spectrum():
+    # The Chebyshev interval comes from the Lanczos tridiagonal that CG's
+    # coefficients define.  Independent construction: Rayleigh-Ritz on an
+    # orthonormal basis of the Krylov space K_k(B, rhs), whose extreme Ritz
+    # values must equal those of the tridiagonal for every k, and after
+    # k = m steps are the extreme eigenvalues of B.
+    from oracle import ipm
+    m = 8
+    B, ev = _spd(m, 40.0, seed=15)
+    rhs = np.random.default_rng(16).standard_normal(m)
+    for k in range(1, m + 1):
+        alphas, betas = ipm._cg_coeffs(lambda z: B @ z, rhs, k)
+        lo, hi = ipm.lanczos_interval(alphas, betas)
+        K = np.column_stack([np.linalg.matrix_power(B, i) @ rhs for i in range(k)])
+        Qk, _ = np.linalg.qr(K)
+        ritz = np.linalg.eigvalsh(Qk.T @ B @ Qk)
+        assert lo == pytest.approx(ritz[0], rel=1e-7)
+        assert hi == pytest.approx(ritz[-1], rel=1e-7)
+        assert ev[0] * (1 - 1e-9) <= lo and hi <= ev[-1] * (1 + 1e-9)
+    assert lo == pytest.approx(ev[0], rel=1e-8) and hi == pytest.approx(ev[-1], rel=1e-8)

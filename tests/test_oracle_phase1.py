@@ -37,6 +37,23 @@ def test_negative_right_hand_sides_are_handled():
     A, b = lp.A * flip[:, None], lp.b * flip
     assert (b < 0).any()
     _check_start(A, b, phase1.phase1_start(A, b))
+    # the phase-1 data themselves: b1 >= 0, (0, b1) is feasible, and every
+    # feasible x of A x = b (here the planted optimum) gives the feasible
+    # point (x, 0) with objective 1^T z = 0
+    A1, b1, c1 = phase1.phase1_lp(A, b)
+    assert (b1 >= 0).all()
+    assert np.allclose(A1 @ np.concatenate([np.zeros(lp.n), b1]), b1)
+    xz = np.concatenate([lp.x_star, np.zeros(16)])
+    assert np.allclose(A1 @ xz, b1, atol=1e-10 * np.linalg.norm(b))
+    assert c1 @ xz == 0.0 and c1 @ np.concatenate([np.zeros(lp.n), b1]) == pytest.approx(b1.sum())
+
+
+def test_start_is_projected_onto_a_x_equals_b():
+    # with a loose phase-1 tolerance the IPM's x misses A x = b by far more
+    # than rounding; the minimum-norm correction must still land on it
+    lp = lpgen.planted_dense(20, 200, seed=8)
+    res = phase1.phase1_start(lp.A, lp.b, tol=1e-3)
+    assert np.linalg.norm(lp.A @ res.x0 - lp.b) <= 1e-11 * (1 + np.linalg.norm(lp.b)) * (1 + np.abs(res.x0).max())
 
 
 def test_random_lp_family_matches_highs_phase1_optimum():

@@ -164,3 +164,15 @@ def test_countsketch_rank_on_a_coordinate_subspace_depends_on_s():
     assert singular[1] == len(draws)
     assert 1 <= singular[2] <= 0.4 * len(draws), singular
     assert singular[4] == 0, singular
+
+
+def test_gaussian_uniforms_reach_both_ends_of_their_grids():
+    # u1 lives on {1, ..., 2^23} / 2^23 (never 0: it goes through a log) and
+    # u2 on {0, ..., 2^23 - 1} / 2^23.  Over 2^24 draws every end value turns
+    # up with probability 1 - e^-2 each; seed 0 shows all four, so a map that
+    # is off by one grid step at either end fails here.
+    u1, u2 = sketch.gaussian_uniforms(0, 0, 0, 4096, 4096)
+    step = 2.0 ** -23
+    assert u1.min() == step and u1.max() == 1.0
+    assert u2.min() == 0.0 and u2.max() == 1.0 - step
+    assert np.isfinite(np.log(u1)).all()
