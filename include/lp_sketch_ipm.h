@@ -79,7 +79,8 @@ enum { LP_RULE_THEORY = 0, LP_RULE_RELATIVE = 1 };
 enum { LP_FEASIBLE = 0, LP_INFEASIBLE = 1 };
 
 typedef struct {
-    double sigma;          /* centering parameter, (0, 4/5) (Algorithms 2, 3); 0.5 */
+    double sigma;          /* centering parameter in (0, 1); the analysis of Algorithms 2-3
+                              takes it in (0, 4/5); 0.5 */
     double gamma;          /* neighbourhood N(gamma) width, (0, 1) (eq. neigh); 0.999 */
     double tol_cg;         /* relative inner tolerance for LP_RULE_RELATIVE (Section 7); 1e-5 */
     int32_t inner_rule;    /* LP_RULE_THEORY: ||f|| <= gamma sigma sqrt(mu)/(4 sqrt(3n)) (Lemmas 4.2, 4.4) */
@@ -95,8 +96,9 @@ typedef struct {
                               block of 8 CG steps in 8 runs without the overlapped
                               (programmatic) launches, and its products but the
                               first are timed; 0 */
-    double w_factor;       /* sketch width w = w_factor * m when w == 0; 4.0 */
-    int64_t w;             /* explicit sketch width (multiple of s), or 0 */
+    double w_factor;       /* sketch width w = w_factor * m when w == 0, in (0, 1e6]; 4.0 */
+    int64_t w;             /* explicit sketch width (rounded up to a multiple of s), or 0;
+                              the width used must be >= m (Lemma 4.1 needs rank m) */
     uint64_t seed;         /* seed of the sketch generator; 0 */
     void* stream;          /* cudaStream_t to run on, or NULL for a private stream
                               (the factor also uses a private second stream, joined
@@ -175,8 +177,12 @@ void lp_options_default(lp_options* opt);
 /* Copies A (dense column-major or CSC), b (m) and c (n) to the device in the
  * handle's layout and allocates every workspace the solver needs.  `bc_on_device`
  * says where b and c live.  Errors: LP_ERR_ARG (sizes, m > n, bad CSC, bad
- * options), LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_UNSUPPORTED (shape outside this
- * build's kernels).  On error *h is NULL. */
+ * options, a sketch width below m), LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_UNSUPPORTED
+ * (shape outside this build's kernels).  On error *h is NULL and
+ * lp_create_error() says why.  Errors in the arguments themselves (pointers,
+ * sizes, the CSC structure of a host matrix, the options, the sketch width)
+ * are reported before any CUDA call is made; NaN/Inf in b or c is found on
+ * the device. */
 int lp_create(lp_handle** h, const lp_matrix* A, const double* b, const double* c,
               int32_t bc_on_device, const lp_options* opt);
 

@@ -1049,6 +1049,10 @@ void options_check(const lp_options* o, std::string* why) {
   else if (o->sigma_rule != 0 && o->sigma_rule != 1) *why = "sigma_rule must be 0 or 1";
   else if (o->inner != LP_INNER_CG && o->inner != LP_INNER_CHEBYSHEV) *why = "inner must be CG or Chebyshev";
   else if (o->t_max < 1 || o->k_max < 0) *why = "t_max >= 1 and k_max >= 0 required";
+  else if (o->inner_rule != LP_RULE_THEORY && o->inner_rule != LP_RULE_RELATIVE) *why = "unknown inner_rule";
+  else if (!(o->tol_cg >= 0 && std::isfinite(o->tol_cg))) *why = "tol_cg must be finite and >= 0";
+  else if (o->w < 0) *why = "w must be >= 0 (0: w = w_factor m)";
+  else if (o->w == 0 && !(o->w_factor > 0 && o->w_factor <= 1e6)) *why = "w_factor must be in (0, 1e6] when w = 0";
 }
 
 }  // namespace
@@ -1137,6 +1141,16 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   std::string why;
   options_check(&h->opt, &why);
   if (!why.empty()) return h->fail(LP_ERR_ARG, "%s", why.c_str());
+  // sketch width (host data only: every argument error is found before the
+  // first CUDA call)
+  h->s_blocks = h->opt.s;
+  long long w = h->opt.w > 0 ? h->opt.w : (long long)llround(h->opt.w_factor * A->m);
+  w = round_up_ll(std::max<long long>(w, h->s_blocks), h->s_blocks);
+  if (w < A->m) return h->fail(LP_ERR_ARG, "sketch width w=%lld < m=%d: A D W cannot have rank m", w, A->m);
+  if (w > (1 << 30)) return h->fail(LP_ERR_ARG, "sketch width too large");
+  h->w = (int)w;
+  if (A->fmt == LP_CSC && h->opt.sketch == LP_SKETCH_GAUSS)
+    return h->fail(LP_ERR_UNSUPPORTED, "the Gaussian sketch is built for dense A only");
   CK(cudaGetDevice(&h->dev));
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
   if (h->opt.stream) {
@@ -1156,15 +1170,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   const int vec = 16 / h->esz;
   h->lda = (int)round_up_ll(h->m, vec);
   h->npad = round_up_ll(h->n, 64);
-  h->s_blocks = h->opt.s;
-  long long w = h->opt.w > 0 ? h->opt.w : (long long)llround(h->opt.w_factor * h->m);
-  w = round_up_ll(std::max<long long>(w, h->s_blocks), h->s_blocks);
-  if (w < h->m) return h->fail(LP_ERR_ARG, "sketch width w=%lld < m=%d: A D W cannot have rank m", w, h->m);
-  if (w > (1 << 30)) return h->fail(LP_ERR_ARG, "sketch width too large");
-  h->w = (int)w;
   h->sparse = A->fmt == LP_CSC;
-  if (h->sparse && h->opt.sketch == LP_SKETCH_GAUSS)
-    return h->fail(LP_ERR_UNSUPPORTED, "the Gaussian sketch is built for dense A only");
   if (h->sparse) {
     h->lda = (int)round_up_ll(h->m, 4);
     if (h->lda * 3 * 8 > 200 * 1024)

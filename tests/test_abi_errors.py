@@ -1,0 +1,186 @@
+"""CPU checks of the C ABI's argument errors.
+
+Every case here is rejected before the library makes any CUDA call (the
+header promises that for errors in the arguments themselves), so these run
+without a GPU: each call returns the documented code, leaves the output
+handle NULL and says why in lp_create_error().
+"""
+
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from paper_2209_08722_gb300 import _native as nat
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2209_08722_gb300 import build_native
+    import os
+    if not os.path.exists(build_native.lib_path()):
+        build_native.build()
+    return nat.load()
+
+
+M, N = 8, 32
+_A = np.ones((N, M), dtype=np.float32)      # column-major m x n: column j = row j here
+_B = np.ones(M)
+_C = np.ones(N)
+
+
+def _dense(m=M, n=N, fmt=nat.LP_DENSE_COLMAJOR, dtype=nat.LP_F32, ld=M, val=_A):
+    A = nat.LpMatrix()
+    A.m, A.n, A.fmt, A.dtype, A.ld, A.on_device = m, n, fmt, dtype, ld, 0
+    A.val = val.ctypes.data if val is not None else None
+    return A
+
+
+def _csc(ptr, idx, val, m=M, n=N, dtype=nat.LP_F32):
+    A = nat.LpMatrix()
+    A.m, A.n, A.fmt, A.dtype, A.on_device = m, n, nat.LP_CSC, dtype, 0
+    A.ptr, A.idx, A.val = ptr.ctypes.data, idx.ctypes.data, val.ctypes.data
+    A.nnz = int(ptr[-1]) if len(ptr) else 0
+    return A
+
+
+def _opts(lib, **kw):
+    o = nat.LpOptions()
+    lib.lp_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _create(lib, A, b=_B, c=_C, opt=None):
+    h = ctypes.c_void_p(12345)           # must come back NULL
+    rc = lib.lp_create(ctypes.byref(h), ctypes.byref(A) if A is not None else None,
+                       b.ctypes.data if b is not None else None,
+                       c.ctypes.data if c is not None else None, 0,
+                       ctypes.byref(opt) if opt is not None else None)
+    assert h.value is None, "the handle must be NULL after a failed lp_create"
+    return rc, lib.lp_create_error().decode()
+
+
+def test_options_default_are_the_documented_defaults(lib):
+    o = _opts(lib)
+    assert (o.sigma, o.gamma, o.tol_cg) == (0.5, 0.999, 1e-5)
+    assert (o.inner_rule, o.sketch, o.s, o.inner) == (nat.LP_RULE_THEORY, nat.LP_SKETCH_COUNT, 2, nat.LP_INNER_CG)
+    assert (o.refine_every, o.k_max, o.t_max, o.v_correction, o.cheb_lanczos) == (8, 200, 500, 1, 10)
+    assert (o.profile, o.w_factor, o.w, o.seed, o.stream) == (0, 4.0, 0, 0, None)
+    assert (o.tensor_sketch, o.precondition, o.sigma_rule) == (1, 1, 0)
+
+
+def test_null_and_shape_errors(lib):
+    assert lib.lp_create(None, ctypes.byref(_dense()), _B.ctypes.data, _C.ctypes.data, 0, None) == nat.LP_ERR_ARG
+    rc, why = _create(lib, None)
+    assert rc == nat.LP_ERR_ARG and "required" in why
+    rc, why = _create(lib, _dense(), b=None)
+    assert rc == nat.LP_ERR_ARG and "required" in why
+    rc, why = _create(lib, _dense(m=N, n=M, ld=N))           # m > n
+    assert rc == nat.LP_ERR_ARG and "m <= n" in why
+    rc, why = _create(lib, _dense(m=0))
+    assert rc == nat.LP_ERR_ARG and "m <= n" in why
+    rc, why = _create(lib, _dense(fmt=7))
+    assert rc == nat.LP_ERR_ARG and "format" in why
+    rc, why = _create(lib, _dense(dtype=3))
+    assert rc == nat.LP_ERR_ARG and "dtype" in why
+    rc, why = _create(lib, _dense(ld=M - 1))
+    assert rc == nat.LP_ERR_ARG and "ld >= m" in why
+    rc, why = _create(lib, _dense(val=None))
+    assert rc == nat.LP_ERR_ARG and "ld >= m" in why
+
+
+def test_host_csc_structure_is_checked(lib):
+    ptr = np.arange(N + 1, dtype=np.int64)                  # one entry per column
+    idx = (np.arange(N) % M).astype(np.int32)
+    val = np.ones(N, dtype=np.float32)
+    bad_ptr = ptr.copy()
+    bad_ptr[5], bad_ptr[6] = 7, 6                           # not monotone
+    rc, why = _create(lib, _csc(bad_ptr, idx, val))
+    assert rc == nat.LP_ERR_ARG and "monotone" in why
+    bad_idx = idx.copy()
+    bad_idx[3] = M                                          # row index out of range
+    rc, why = _create(lib, _csc(ptr, bad_idx, val))
+    assert rc == nat.LP_ERR_ARG and "out of range" in why
+    A = _csc(ptr, idx, val)
+    A.nnz = N - 1                                           # ptr[n] != nnz
+    rc, why = _create(lib, A)
+    assert rc == nat.LP_ERR_ARG and "ptr[n]" in why
+    rc, why = _create(lib, _csc(ptr, idx, val.astype(np.float32), dtype=nat.LP_BF16))
+    assert rc == nat.LP_ERR_UNSUPPORTED and "FP32 or FP64" in why
+    rc, why = _create(lib, _csc(ptr, idx, val), opt=_opts(lib, sketch=nat.LP_SKETCH_GAUSS))
+    assert rc == nat.LP_ERR_UNSUPPORTED and "dense A only" in why
+
+
+@pytest.mark.parametrize("field,value,message", [
+    ("sigma", 0.0, "sigma"), ("sigma", 1.0, "sigma"), ("sigma", math.nan, "sigma"),
+    ("gamma", 0.0, "gamma"), ("gamma", 1.0, "gamma"),
+    ("s", 0, "s must be"), ("s", 17, "s must be"),
+    ("sketch", 2, "sketch"), ("precondition", 2, "precondition"), ("sigma_rule", 2, "sigma_rule"),
+    ("inner", 2, "inner must be"), ("t_max", 0, "t_max"), ("k_max", -1, "k_max"),
+    ("inner_rule", 2, "inner_rule"), ("tol_cg", -1e-3, "tol_cg"), ("tol_cg", math.inf, "tol_cg"),
+    ("w", -4, "w must be"), ("w_factor", 0.0, "w_factor"), ("w_factor", math.nan, "w_factor"),
+])
+def test_bad_options_are_rejected(lib, field, value, message):
+    rc, why = _create(lib, _dense(), opt=_opts(lib, **{field: value}))
+    assert rc == nat.LP_ERR_ARG and message in why, why
+
+
+@pytest.mark.parametrize("opts", [dict(w=4), dict(w_factor=0.5), dict(w=2**31)])
+def test_sketch_width_is_checked_before_any_device_work(lib, opts):
+    rc, why = _create(lib, _dense(), opt=_opts(lib, **opts))
+    assert rc == nat.LP_ERR_ARG and "sketch width" in why, why
+
+
+def test_null_handles_are_argument_errors(lib):
+    d = np.ones(N)
+    p = d.ctypes.data
+    assert lib.lp_destroy(None) == nat.LP_OK
+    assert lib.lp_last_error(None) == b""
+    assert lib.lp_adat(None, p, p, p, 0) == nat.LP_ERR_ARG
+    assert lib.lp_residual_rhs(None, p, p, p, 1, None, None, None, None) == nat.LP_ERR_ARG
+    assert lib.lp_sketch(None, p, 0, 0, 0, p, None) == nat.LP_ERR_ARG
+    assert lib.lp_precond_apply(None, p, p, p) == nat.LP_ERR_ARG
+    assert lib.lp_directions(None, p, p, p, p, p, 1.0, 1, p, p) == nat.LP_ERR_ARG
+    assert lib.lp_step_lengths(None, p, p, p, p, 1, 0.0, 1.0, p) == nat.LP_ERR_ARG
+    assert lib.lp_normal_solve(None, p, p, p, 0, 0.0, 0, p, p, None) == nat.LP_ERR_ARG
+    assert lib.lp_solve(None, 1e-8, 1, None, None, None, 0, None, None, None, None) == nat.LP_ERR_ARG
+    assert lib.lp_get_history(None, None, 0) == nat.LP_ERR_ARG
+    assert lib.lp_get_kernel_stats(None, None) == nat.LP_ERR_ARG
+    assert lib.lp_reset_kernel_stats(None) == nat.LP_ERR_ARG
+    assert lib.lp_set_warm_start(None, 0, None, None, None, 0) == nat.LP_ERR_ARG
+    assert lib.lp_get_warm_start_stats(None, None, None, None) == nat.LP_ERR_ARG
+    hs = (ctypes.c_void_p * 1)(None)
+    assert lib.lp_solve_batch(hs, 1, 1e-8, 1, 0, None, None, None, 1, None) == nat.LP_ERR_ARG
+    assert lib.lp_solve_batch(None, 1, 1e-8, 1, 0, None, None, None, 1, None) == nat.LP_ERR_ARG
+
+
+def test_mlp_and_standalone_entry_points_check_their_arguments(lib):
+    out = ctypes.c_void_p(None)
+    assert lib.lp_mlp_create(None, 4, 8, 4, 0, None) == nat.LP_ERR_ARG
+    for dims in ((0, 8, 4), (4, 0, 4), (4, 8, 0)):
+        assert lib.lp_mlp_create(ctypes.byref(out), *dims, 0, None) == nat.LP_ERR_ARG
+    assert lib.lp_mlp_destroy(None) == nat.LP_OK
+    assert lib.lp_mlp_num_params(None) == -1
+    buf = np.ones(16, dtype=np.float32)
+    assert lib.lp_mlp_get_params(None, buf.ctypes.data) == nat.LP_ERR_ARG
+    assert lib.lp_mlp_forward(None, buf.ctypes.data, 1, buf.ctypes.data) == nat.LP_ERR_ARG
+    # the allocation-free product: null pointers, FP64 storage, an ld that is
+    # not a 16-byte multiple, a misaligned A
+    d = np.ones(N)
+    A = np.ones(16 * N + 8, dtype=np.float32)
+    base = A.ctypes.data + (-A.ctypes.data) % 16            # a 16-byte-aligned start inside A
+    p = d.ctypes.data
+    assert lib.lp_adat_noalloc(None, nat.LP_F32, M, N, M, p, p, p, None) == nat.LP_ERR_ARG
+    assert lib.lp_adat_noalloc(base, nat.LP_F64, M, N, M, p, p, p, None) == nat.LP_ERR_ARG
+    assert lib.lp_adat_noalloc(base, nat.LP_F32, 6, N, 6, p, p, p, None) == nat.LP_ERR_ARG
+    assert lib.lp_adat_noalloc(base + 4, nat.LP_F32, M, N, M, p, p, p, None) == nat.LP_ERR_ARG
+    assert lib.lp_adat_noalloc(base, nat.LP_F32, M, N, M - 4, p, p, p, None) == nat.LP_ERR_ARG
+    # phase 1 wants a host matrix and tol > 0
+    x0 = np.zeros(N)
+    dense = _dense()
+    assert lib.lp_phase1_start(ctypes.byref(dense), _B.ctypes.data, None, 0.0, x0.ctypes.data, None) == nat.LP_ERR_ARG
+    dense.on_device = 1
+    assert lib.lp_phase1_start(ctypes.byref(dense), _B.ctypes.data, None, 1e-7, x0.ctypes.data, None) == nat.LP_ERR_ARG
