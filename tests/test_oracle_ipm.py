@@ -462,3 +462,18 @@ def test_two_rhs_adaptive_sigma_needs_fewer_outer_iterations(col_scale):
     assert out["adaptive"].iterations <= 0.7 * out["fixed"].iterations
     sig = [h.sigma_used for h in out["adaptive"].history if h.sigma_used > 0]
     assert min(sig) >= 0.1 and max(sig) <= 0.75
+
+
+@pytest.mark.parametrize("col_scale", [None, (-2, 2)])
+def test_gamma_sensitivity(col_scale):
+    # gamma is never given numerically; the default 0.999 is a reading.  On
+    # the planted family every gamma in {0.9, 0.99, 0.999} reaches the
+    # optimum, in outer iteration counts within 25 % of one another
+    lp = lpgen.planted_dense(64, 4096, seed=0, col_scale_log10=col_scale)
+    outer = []
+    for g in (0.9, 0.99, 0.999):
+        r = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(mode="infeasible", solver="sketch", gamma=g, s=2, w=256))
+        assert r.status == "optimal"
+        assert abs(lp.c @ r.x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+        outer.append(r.iterations)
+    assert max(outer) <= 1.25 * min(outer), outer
