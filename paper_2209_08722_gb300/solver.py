@@ -22,6 +22,10 @@ from . import _native as nat
 
 _DTYPES = {"f64": nat.LP_F64, "f32": nat.LP_F32, "bf16": nat.LP_BF16}
 _NP_DT = {"f64": np.float64, "f32": np.float32, "bf16": np.uint16}
+# torch dtypes accepted for each storage dtype (bf16 also as raw 16-bit patterns)
+_TORCH_DT = {"f64": ("torch.float64",), "f32": ("torch.float32",),
+             "bf16": ("torch.bfloat16", "torch.int16", "torch.uint16")}
+_MODES = {"feasible": nat.LP_FEASIBLE, "infeasible": nat.LP_INFEASIBLE}
 
 
 class LPError(RuntimeError):
@@ -52,12 +56,59 @@ def _on_device(x) -> bool:
     return _is_torch(x) and x.is_cuda
 
 
+def _numel(x) -> int:
+    return int(x.numel()) if _is_torch(x) else int(np.asarray(x).size)
+
+
+def _need(x, count: int, name: str):
+    """The library reads exactly ``count`` elements of every buffer it is
+    given: a shorter one would be read past its end, so sizes are checked here."""
+    if x is not None and _numel(x) != count:
+        raise ValueError(f"{name} must have {count} elements, got {_numel(x)}")
+
+
+def _mode(mode: str) -> int:
+    if mode not in _MODES:
+        raise ValueError(f"mode must be 'feasible' or 'infeasible', got {mode!r}")
+    return _MODES[mode]
+
+
 def _check_dev_f64(*xs):
     for x in xs:
         if x is None:
             continue
         if not (_is_torch(x) and x.is_cuda and str(x.dtype) == "torch.float64" and x.is_contiguous()):
             raise TypeError("kernel-level calls take contiguous float64 CUDA tensors")
+
+
+def _host_f64(x) -> bool:
+    """A writable host buffer of float64: a C-contiguous NumPy array, or a
+    contiguous CPU tensor (pinned or not)."""
+    if isinstance(x, np.ndarray):
+        return x.dtype == np.float64 and x.flags.c_contiguous and x.flags.writeable
+    return _is_torch(x) and not x.is_cuda and str(x.dtype) == "torch.float64" and x.is_contiguous()
+
+
+def _check_dev_f32(x, shape, name: str):
+    if not (_is_torch(x) and x.is_cuda and str(x.dtype) == "torch.float32" and x.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(x.shape)}")
+
+
+def _same_side(named):
+    """Host or device for a whole call: the library takes one flag for all of
+    a call's vectors, so a mix would hand it host pointers as device pointers
+    (or the reverse).  Device vectors must be contiguous float64 tensors.
+    Returns True when they are on the device."""
+    given = [(k, v) for k, v in named if v is not None]
+    dev = [_on_device(v) for _, v in given]
+    if any(dev) and not all(dev):
+        raise ValueError("pass all of " + ", ".join(k for k, _ in given)
+                         + " as CUDA tensors or all as host arrays")
+    if any(dev):
+        _check_dev_f64(*[v for _, v in given])
+    return any(dev)
 
 
 class LPSolver:
@@ -73,6 +124,8 @@ class LPSolver:
                  **options):
         self._lib = nat.load()
         self._h = ctypes.c_void_p()
+        if dtype not in _DTYPES:
+            raise ValueError(f"dtype must be one of {sorted(_DTYPES)}, got {dtype!r}")
         self.m, self.n, self.dtype = int(m), int(n), dtype
         opt = nat.LpOptions()
         self._lib.lp_options_default(ctypes.byref(opt))
@@ -91,6 +144,8 @@ class LPSolver:
                 ri = np.ascontiguousarray(ri, dtype=np.int32)
                 vals = np.ascontiguousarray(vals, dtype=_NP_DT[dtype])
             nnz = int(vals.shape[0])
+            _need(cp, self.n + 1, "col_ptr")
+            _need(ri, nnz, "row_idx")
             mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_CSC, dtype=_DTYPES[dtype],
                                val=_ptr(vals), ld=0, ptr=_ptr(cp), idx=_ptr(ri), nnz=nnz,
                                on_device=1 if _on_device(vals) else 0)
@@ -98,7 +153,11 @@ class LPSolver:
         elif _is_torch(A):
             if tuple(A.shape) != (self.n, self.m):
                 raise ValueError("A must have shape (n, m) (column-major)")
+            if str(A.dtype) not in _TORCH_DT[dtype]:
+                raise TypeError(f"A is {A.dtype}, storage dtype {dtype!r} takes {_TORCH_DT[dtype]}")
         else:
+            if dtype == "bf16" and np.asarray(A).dtype not in (np.uint16, np.int16):
+                raise TypeError("bf16 storage takes A as 16-bit patterns (uint16), not as values")
             A = np.ascontiguousarray(A, dtype=_NP_DT[dtype])
             if A.shape != (self.n, self.m):
                 raise ValueError("A must have shape (n, m) (column-major)")
@@ -106,10 +165,12 @@ class LPSolver:
             mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype],
                                val=_ptr(A), ld=self.m, ptr=None, idx=None, nnz=0,
                                on_device=1 if _on_device(A) else 0)
-        bc_dev = _on_device(b)
+        bc_dev = _same_side([("b", b), ("c", c)])
         if not bc_dev:
             b = np.ascontiguousarray(b, dtype=np.float64)
             c = np.ascontiguousarray(c, dtype=np.float64)
+        _need(b, self.m, "b")
+        _need(c, self.n, "c")
         self._keep = (A, b, c)
         rc = self._lib.lp_create(ctypes.byref(self._h), ctypes.byref(mat), _ptr(b), _ptr(c),
                                  1 if bc_dev else 0, ctypes.byref(opt))
@@ -135,8 +196,8 @@ class LPSolver:
     def __exit__(self, *exc):
         self.close()
 
-    def _check(self, rc: int, allow=(nat.LP_OK,)):
-        if rc < 0 or rc not in allow and rc < 0:
+    def _check(self, rc: int):
+        if rc < 0:
             raise LPError(rc, self._lib.lp_last_error(self._h).decode())
         return rc
 
@@ -145,9 +206,10 @@ class LPSolver:
               out=None):
         """lp_solve.  Host (NumPy) or device (torch CUDA) start/outputs."""
         m, n = self.m, self.n
-        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
-        dev = any(_on_device(v) for v in (x0, y0, s0) if v is not None) or (
-            out is not None and _on_device(out[0]))
+        mode_c = _mode(mode)
+        outs = [None, None, None] if out is None else list(out)
+        dev = _same_side([("x0", x0), ("y0", y0), ("s0", s0), ("x", outs[0]), ("y", outs[1]),
+                          ("s", outs[2])])
         if out is None:
             if dev:
                 import torch
@@ -159,6 +221,12 @@ class LPSolver:
         if not dev:
             x0, y0, s0 = [None if v is None else np.ascontiguousarray(v, dtype=np.float64)
                           for v in (x0, y0, s0)]
+            for name, o in zip(("x", "y", "s"), out):
+                if not _host_f64(o):
+                    raise TypeError(f"output {name} must be a contiguous float64 host array or tensor")
+        for name, v, k in (("x0", x0, n), ("y0", y0, m), ("s0", s0, n),
+                           ("x", out[0], n), ("y", out[1], m), ("s", out[2], n)):
+            _need(v, k, name)
         res = nat.LpResult()
         rc = self._lib.lp_solve(self._h, float(tol), mode_c, _ptr(x0), _ptr(y0), _ptr(s0),
                                 1 if dev else 0, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]),
@@ -171,7 +239,7 @@ class LPSolver:
 
     def normal_solve(self, D, p, xs=None, k: int = 0, tol_f: float = 0.0, want_v: bool = True):
         """lp_normal_solve: returns (dy, v or None, info dict)."""
-        dev = _on_device(D)
+        dev = _same_side([("D", D), ("p", p), ("xs", xs)])
         if dev:
             import torch
             dy = torch.empty(self.m, dtype=torch.float64, device="cuda")
@@ -182,6 +250,9 @@ class LPSolver:
             xs = None if xs is None else np.ascontiguousarray(xs, dtype=np.float64)
             dy = np.empty(self.m)
             v = np.empty(self.n) if (want_v and xs is not None) else None
+        _need(D, self.n, "D")
+        _need(p, self.m, "p")
+        _need(xs, self.n, "xs")
         info = nat.LpNsolveInfo()
         rc = self._lib.lp_normal_solve(self._h, _ptr(D), _ptr(p), _ptr(xs), int(k), float(tol_f),
                                        1 if dev else 0, _ptr(dy), _ptr(v), ctypes.byref(info))
@@ -195,6 +266,8 @@ class LPSolver:
     def adat(self, d2, v, precision: int = 0):
         import torch
         _check_dev_f64(d2, v)
+        _need(d2, self.n, "d2")
+        _need(v, self.m, "v")
         u = torch.empty(self.m, dtype=torch.float64, device="cuda")
         self._check(self._lib.lp_adat(self._h, _ptr(d2), _ptr(v), _ptr(u), int(precision)))
         return u
@@ -202,11 +275,13 @@ class LPSolver:
     def residual_rhs(self, x, y, s, mode: str = "infeasible"):
         import torch
         _check_dev_f64(x, y, s)
+        for name, t, k in (("x", x, self.n), ("y", y, self.m), ("s", s, self.n)):
+            _need(t, k, name)
         rp = torch.empty(self.m, dtype=torch.float64, device="cuda")
         rd = torch.empty(self.n, dtype=torch.float64, device="cuda")
         p = torch.empty(self.m, dtype=torch.float64, device="cuda")
         out5 = (ctypes.c_double * 5)()
-        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+        mode_c = _mode(mode)
         self._check(self._lib.lp_residual_rhs(self._h, _ptr(x), _ptr(y), _ptr(s), mode_c,
                                               _ptr(rp), _ptr(rd), _ptr(p), out5))
         keys = ("mu", "cx", "by", "rp_norm", "rd_norm")
@@ -215,6 +290,7 @@ class LPSolver:
     def sketch(self, D, seed: int, k: int, retry: int = 0):
         import torch
         _check_dev_f64(D)
+        _need(D, self.n, "D")
         w = self.sketch_width
         adw = torch.empty(self.m * w, dtype=torch.float64, device="cuda")
         wout = ctypes.c_int64()
@@ -232,6 +308,8 @@ class LPSolver:
     def precond_apply(self, adw, r):
         import torch
         _check_dev_f64(adw, r)
+        _need(adw, self.m * self.sketch_width, "adw")
+        _need(r, self.m, "r")
         z = torch.empty(self.m, dtype=torch.float64, device="cuda")
         self._check(self._lib.lp_precond_apply(self._h, _ptr(adw), _ptr(r), _ptr(z)))
         return z
@@ -239,9 +317,14 @@ class LPSolver:
     def directions(self, x, s, rd, dy, v, mu: float, mode: str = "infeasible"):
         import torch
         _check_dev_f64(x, s, rd, dy, v)
+        mode_c = _mode(mode)
+        if rd is None and mode_c == nat.LP_INFEASIBLE:
+            raise ValueError("the infeasible directions need rd")
+        for name, t, k in (("x", x, self.n), ("s", s, self.n), ("rd", rd, self.n), ("dy", dy, self.m),
+                           ("v", v, self.n)):
+            _need(t, k, name)
         dx = torch.empty(self.n, dtype=torch.float64, device="cuda")
         ds = torch.empty(self.n, dtype=torch.float64, device="cuda")
-        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
         self._check(self._lib.lp_directions(self._h, _ptr(x), _ptr(s), _ptr(rd), _ptr(dy), _ptr(v),
                                             float(mu), mode_c, _ptr(dx), _ptr(ds)))
         return dx, ds
@@ -249,8 +332,10 @@ class LPSolver:
     def step_lengths(self, x, s, dx, ds, mode: str = "infeasible", res_ratio: float = 0.0,
                      mu0: float = 1.0):
         _check_dev_f64(x, s, dx, ds)
+        for name, t in (("x", x), ("s", s), ("dx", dx), ("ds", ds)):
+            _need(t, self.n, name)
         out2 = (ctypes.c_double * 2)()
-        mode_c = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+        mode_c = _mode(mode)
         self._check(self._lib.lp_step_lengths(self._h, _ptr(x), _ptr(s), _ptr(dx), _ptr(ds), mode_c,
                                               float(res_ratio), float(mu0), out2))
         return out2[0], out2[1]
@@ -299,6 +384,8 @@ def phase1_start(A, b, m: int, n: int, dtype: str = "f64", csc=None, tol: float 
     (x0, info); raises LPError with code LP_ERR_NOT_FEASIBLE when the phase-1
     optimum shows A x = b, x >= 0 infeasible."""
     lib = nat.load()
+    if dtype not in _DTYPES:
+        raise ValueError(f"dtype must be one of {sorted(_DTYPES)}, got {dtype!r}")
     opt = nat.LpOptions()
     lib.lp_options_default(ctypes.byref(opt))
     for k, v in options.items():
@@ -309,10 +396,14 @@ def phase1_start(A, b, m: int, n: int, dtype: str = "f64", csc=None, tol: float 
         cp = np.ascontiguousarray(csc[0], dtype=np.int64)
         ri = np.ascontiguousarray(csc[1], dtype=np.int32)
         vals = np.ascontiguousarray(csc[2], dtype=_NP_DT[dtype])
+        _need(cp, n + 1, "col_ptr")
+        _need(ri, int(vals.shape[0]), "row_idx")
         keep = (cp, ri, vals)
         mat = nat.LpMatrix(m=m, n=n, fmt=nat.LP_CSC, dtype=_DTYPES[dtype], val=_ptr(vals), ld=0,
                            ptr=_ptr(cp), idx=_ptr(ri), nnz=int(vals.shape[0]), on_device=0)
     else:
+        if dtype == "bf16" and np.asarray(A).dtype not in (np.uint16, np.int16):
+            raise TypeError("bf16 storage takes A as 16-bit patterns (uint16), not as values")
         A = np.ascontiguousarray(A, dtype=_NP_DT[dtype])
         if A.shape != (n, m):
             raise ValueError("A must have shape (n, m) (column-major)")
@@ -320,6 +411,7 @@ def phase1_start(A, b, m: int, n: int, dtype: str = "f64", csc=None, tol: float 
         mat = nat.LpMatrix(m=m, n=n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype], val=_ptr(A),
                            ld=m, ptr=None, idx=None, nnz=0, on_device=0)
     b = np.ascontiguousarray(b, dtype=np.float64)
+    _need(b, m, "b")
     x0 = np.empty(n, dtype=np.float64)
     info = nat.LpPhase1Info()
     rc = lib.lp_phase1_start(ctypes.byref(mat), _ptr(b), ctypes.byref(opt), float(tol), _ptr(x0),
@@ -343,7 +435,7 @@ def solve_batch(solvers, tol: float = 1e-8, mode: str = "infeasible", max_thread
     ys = (ctypes.c_void_p * count)(*[o[1].ctypes.data for o in outs])
     ss = (ctypes.c_void_p * count)(*[o[2].ctypes.data for o in outs])
     res = (nat.LpResult * count)()
-    m = nat.LP_FEASIBLE if mode == "feasible" else nat.LP_INFEASIBLE
+    m = _mode(mode)
     rc = lib.lp_solve_batch(hs, count, float(tol), m, 0, xs, ys, ss, int(max_threads), res)
     if rc < 0:
         raise LPError(rc, "batched solve failed")
@@ -385,6 +477,7 @@ class Mlp:
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)
+        _need(flat, self.num_params, "params")
         self._check(self._lib.lp_mlp_set_params(self._h, flat.ctypes.data))
 
     def grads(self) -> np.ndarray:
@@ -394,16 +487,24 @@ class Mlp:
 
     def forward(self, X):
         import torch
+        _check_dev_f32(X, (X.shape[0], self.in_dim) if X.dim() == 2 else (-1,), "X")
         Y = torch.empty(X.shape[0], self.out_dim, dtype=torch.float32, device="cuda")
         self._check(self._lib.lp_mlp_forward(self._h, _ptr(X), int(X.shape[0]), _ptr(Y)))
         return Y
 
+    def _check_batch(self, X, T):
+        batch = int(X.shape[0]) if X.dim() == 2 else -1
+        _check_dev_f32(X, (batch, self.in_dim), "X")
+        _check_dev_f32(T, (batch, self.out_dim), "T")
+
     def loss_grad(self, X, T) -> float:
+        self._check_batch(X, T)
         loss = ctypes.c_double()
         self._check(self._lib.lp_mlp_loss_grad(self._h, _ptr(X), _ptr(T), int(X.shape[0]), ctypes.byref(loss)))
         return loss.value
 
     def train_step(self, X, T, lr: float) -> float:
+        self._check_batch(X, T)
         loss = ctypes.c_double()
         self._check(self._lib.lp_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]), float(lr),
                                                 ctypes.byref(loss)))
@@ -419,7 +520,18 @@ def _set_warm_start(self, mode: str = "none", model: Mlp = None, rec_X=None, rec
     rec_T (cap, m) float32 CUDA tensors receive (features, target) per outer
     iteration when given."""
     modes = {"none": 0, "previous": 1, "model": 2}
+    if mode not in modes:
+        raise ValueError(f"mode must be one of {sorted(modes)}, got {mode!r}")
+    if mode == "model" and model is None:
+        raise ValueError("mode 'model' needs a model")
+    if model is not None and (model.in_dim, model.out_dim) != (3 * self.m, self.m):
+        raise ValueError(f"the model must map 3m = {3 * self.m} features to m = {self.m} outputs")
+    if (rec_X is None) != (rec_T is None):
+        raise ValueError("give both rec_X and rec_T, or neither")
     cap = 0 if rec_X is None else int(rec_X.shape[0])
+    if rec_X is not None:
+        _check_dev_f32(rec_X, (cap, 3 * self.m), "rec_X")
+        _check_dev_f32(rec_T, (cap, self.m), "rec_T")
     self._warm_keep = (model, rec_X, rec_T)
     self._check(self._lib.lp_set_warm_start(self._h, modes[mode], model._h if model else None, _ptr(rec_X),
                                             _ptr(rec_T), cap))
