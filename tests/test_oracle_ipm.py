@@ -477,3 +477,41 @@ def test_gamma_sensitivity(col_scale):
         assert abs(lp.c @ r.x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
         outer.append(r.iterations)
     assert max(outer) <= 1.25 * min(outer), outer
+
+
+def test_orthonormal_rows_and_unit_scaling_give_the_identity_normal_matrix():
+    # A with orthonormal rows and D = I (x = s) make M = A A^T = I, so the
+    # inexact solve must return dy = p
+    rng = np.random.default_rng(60)
+    m, n = 10, 400
+    Qn, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    A = Qn.T
+    x = s = np.exp(rng.uniform(-1, 1, n))
+    p = rng.standard_normal(m)
+    opt = ipm.Options(solver="sketch", w=4 * m, s=2, t_max=100)
+    ns = ipm.normal_solve(A, x, s, p, opt, k=0, inner_tol=1e-12 * np.linalg.norm(p))
+    assert np.allclose(ns.dy, p, rtol=0, atol=1e-10 * np.linalg.norm(p))
+
+
+def test_identity_sketch_correction_is_the_min_norm_solution_of_ad():
+    # W = I: v = (XS)^{1/2} (AD)^+ r, and (AD)^+ r is the minimum-norm solution
+    # of (AD) z = r, here from a least-squares solver
+    rng = np.random.default_rng(61)
+    m, n = 6, 40
+    A = rng.standard_normal((m, n))
+    x, s = rng.uniform(0.1, 2, n), rng.uniform(0.1, 2, n)
+    r = rng.standard_normal(m)
+    AD = A * np.sqrt(x / s)
+    v = correction.correction_v(x, s, np.eye(n), AD, r)
+    z, *_ = np.linalg.lstsq(AD, r, rcond=None)
+    assert np.allclose(v, np.sqrt(x * s) * z, rtol=1e-10, atol=1e-12 * np.linalg.norm(v))
+
+
+def test_inner_solves_stop_at_the_theory_bound():
+    # with the default (theory) rule every inner solve ends at
+    # ||f|| <= gamma sigma sqrt(mu) / (4 sqrt(3 n)), the level Lemma 4.4 needs
+    lp, opt, res = _trajectory("infeasible", k_max=25)
+    n = lp.n
+    for rec in res.history[:-1]:
+        assert rec.inner_its < opt.t_max
+        assert rec.f_norm <= pcg.theory_inner_tol(rec.mu, n, opt.gamma, opt.sigma) * (1 + 1e-9)

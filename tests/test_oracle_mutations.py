@@ -81,6 +81,10 @@ PINS = {
     "ns_cholesky": ("test_oracle_ipm", "test_normal_solve_matches_cholesky_at_tight_tolerance", {}),
     "ns_plain": ("test_oracle_ipm", "test_unpreconditioned_normal_solve_is_cg_on_eq_normal", {}),
     "two_rhs": ("test_oracle_ipm", "test_two_rhs_combination_is_the_solve_with_p_sigma", {}),
+    "inner_theory_bound": ("test_oracle_ipm", "test_inner_solves_stop_at_the_theory_bound", {}),
+    "orthonormal_rows": ("test_oracle_ipm",
+                         "test_orthonormal_rows_and_unit_scaling_give_the_identity_normal_matrix", {}),
+    "v_identity_lstsq": ("test_oracle_ipm", "test_identity_sketch_correction_is_the_min_norm_solution_of_ad", {}),
     # oracle.phase1
     "p1_planted": ("test_oracle_phase1", "test_planted_lp_gets_a_strictly_feasible_start", {}),
     "p1_negative_b": ("test_oracle_phase1", "test_negative_right_hand_sides_are_handled", {}),
@@ -138,6 +142,8 @@ MUTANTS = [
      ["v_identity", "v_invariant"]),
     ("v_sign", "correction", "correction_v", "np.linalg.pinv(ADW) @ r_v", "np.linalg.pinv(ADW) @ (-r_v)",
      ["v_identity", "v_invariant"]),
+    ("v_q_inverse_dropped", "correction", "correction_v", "np.linalg.pinv(ADW) @ r_v",
+     "ADW.T @ r_v", ["v_identity_lstsq", "v_invariant"]),
     ("v_minnorm_scale", "correction", "correction_v_minnorm", "(A / s)", "(A * s)", ["v_identity"]),
     # --- residuals, right-hand side, directions (Sections 4-5) ---
     ("dual_residual_sign", "ipm", "residuals", "A.T @ y + s - c", "A.T @ y - s - c",
@@ -177,6 +183,8 @@ MUTANTS = [
      "r_v = p - A @ (d2 * (A.T @ dy))", ["v_invariant"]),
     ("ns_chebyshev_interval_too_small", "ipm", "normal_solve", "1.05 * tmax", "0.5 * tmax",
      ["ns_cholesky"]),
+    ("ns_inner_target_loosened", "ipm", "normal_solve", 'tol = inner_tol if opt.inner_rule == "theory"',
+     'tol = 10 * inner_tol if opt.inner_rule == "theory"', ["inner_theory_bound"]),
     ("plain_cg_d2_inverted", "ipm", "normal_solve_unpreconditioned", "d2 = x / s", "d2 = s / x",
      ["ns_plain"]),
     ("two_rhs_affine_part_kept", "ipm", "_adaptive_sigma_solve",
@@ -254,6 +262,9 @@ EQUIVALENT = [
      "p = A @ x - sigma * mu * (A @ (1.0 / s))", ["residual_linear", "lemma45_feas", "planted_exact"]),
     ("mu_dot_swapped", "ipm", "step_lengths", "c2 = (dx @ ds) / n", "c2 = (ds @ dx) / n",
      ["steps_feas", "steps_infeas"]),
+    # the pseudo-inverse as the CUDA path forms it, (ADW)^+ = (ADW)^T Q^{-1}
+    ("pinv_as_adw_t_q_inverse", "correction", "correction_v", "np.linalg.pinv(ADW) @ r_v",
+     "ADW.T @ np.linalg.solve(ADW @ ADW.T, r_v)", ["v_identity", "v_identity_lstsq", "v_invariant"]),
 ]
 
 
