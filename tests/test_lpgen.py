@@ -50,3 +50,55 @@ def test_storage_array_layout():
     assert bits.dtype == np.uint16
     vals = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     assert np.array_equal(vals.T, lpb.A)
+
+
+def test_bf16_rounding_ties_go_to_even():
+    # FP32 values exactly halfway between two bfloat16 neighbours (low 16 bits
+    # 0x8000) round to the neighbour with an even last bit, in both signs
+    hi = np.array([0x3F80, 0x3F81, 0x4049, 0x404A, 0xBF80, 0xBF81, 0x0001, 0x7F00], dtype=np.uint32)
+    f = ((hi << np.uint32(16)) | np.uint32(0x8000)).view(np.float32)
+    got = lpgen.bf16_bits(f).astype(np.uint32)
+    expect = np.where(hi % 2 == 0, hi, hi + 1)
+    assert np.array_equal(got, expect)
+    # just below and just above the halfway point
+    below = ((hi << np.uint32(16)) | np.uint32(0x7FFF)).view(np.float32)
+    above = ((hi << np.uint32(16)) | np.uint32(0x8001)).view(np.float32)
+    assert np.array_equal(lpgen.bf16_bits(below).astype(np.uint32), hi)
+    assert np.array_equal(lpgen.bf16_bits(above).astype(np.uint32), hi + 1)
+
+
+def test_column_scaling_is_log_uniform():
+    # col_scale_log10 = (-2, 2): column j is scaled by 10^U(-2, 2)
+    m, n = 16, 4000
+    plain = lpgen.planted_dense(m, n, seed=5)
+    scaled = lpgen.planted_dense(m, n, seed=5, col_scale_log10=(-2.0, 2.0))
+    lg = np.log10(np.linalg.norm(scaled.A, axis=0) / np.sqrt(m))
+    assert lg.min() < -1.8 and lg.max() > 1.8 and abs(lg.mean()) < 0.2
+    assert np.allclose(scaled.A @ scaled.x_star, scaled.b)
+    assert plain.A.shape == scaled.A.shape
+
+
+def test_batch_family_sizes_and_planted_optima():
+    lps = lpgen.batch_family(12, seed=4, m_range=(8, 24), k_range=(4, 9))
+    for lp in lps:
+        assert 8 <= lp.m <= 24 and lp.n % lp.m == 0 and 4 <= lp.n // lp.m <= 9
+        assert lp.storage == "f32"
+        assert np.allclose(lp.A @ lp.x_star, lp.b)
+        assert np.allclose(lp.c - lp.A.T @ lp.y_star, lp.s_star)
+        assert np.all(lp.x_star * lp.s_star == 0)
+    again = lpgen.batch_family(12, seed=4, m_range=(8, 24), k_range=(4, 9))
+    assert all(np.array_equal(a.A, b.A) and np.array_equal(a.b, b.b) for a, b in zip(lps, again))
+    assert len({(lp.m, lp.n) for lp in lps}) > 1           # the sizes vary across the family
+
+
+def test_named_workloads_and_the_bench_agree():
+    C = lpgen.CONFIGS
+    assert (C["c1"]["m"], C["c1"]["n"], C["c1"]["storage"], C["c1"]["mode"]) == (64, 4096, "f64", "feasible")
+    assert (C["c2"]["m"], C["c2"]["n"], C["c2"]["storage"], C["c2"]["col_scale"]) == (512, 131072, "f32", (-2.0, 2.0))
+    assert (C["c3"]["kind"], C["c3"]["m"], C["c3"]["n"], C["c3"]["nnz_per_col"]) == ("sparse", 4096, 2_000_000, 8)
+    assert (C["c4"]["m"], C["c4"]["n"], C["c4"]["storage"]) == (2048, 524288, "bf16")
+    import bench
+    assert (bench.M, bench.N_COLS, bench.S_BLOCKS, bench.W_FACTOR) == (
+        C["c2"]["m"], C["c2"]["n"], C["c2"]["s"], C["c2"]["w_factor"])
+    small = lpgen.config_small("c2", 64)
+    assert (small.m, small.n, small.storage) == (8, 2048, "f32")
