@@ -192,7 +192,8 @@ int lp_destroy(lp_handle* h);
 /* Message of the last error on `h` (empty string if none); valid until the next call. */
 const char* lp_last_error(const lp_handle* h);
 
-/* Message of the last lp_create failure in this process. */
+/* Message of the last lp_create failure on the calling thread (empty after a
+ * success); valid until that thread's next lp_create. */
 const char* lp_create_error(void);
 
 /* ---- solver ---------------------------------------------------------------- */

@@ -35,7 +35,8 @@
 using namespace lpk;
 
 namespace {
-std::string g_create_error;
+// per host thread, so that threads creating handles at once do not race on it
+thread_local std::string g_create_error;
 
 long long round_up_ll(long long x, long long a) { return (x + a - 1) / a * a; }
 

@@ -184,3 +184,24 @@ def test_mlp_and_standalone_entry_points_check_their_arguments(lib):
     assert lib.lp_phase1_start(ctypes.byref(dense), _B.ctypes.data, None, 0.0, x0.ctypes.data, None) == nat.LP_ERR_ARG
     dense.on_device = 1
     assert lib.lp_phase1_start(ctypes.byref(dense), _B.ctypes.data, None, 1e-7, x0.ctypes.data, None) == nat.LP_ERR_ARG
+
+
+def test_create_error_message_is_per_thread(lib):
+    # two threads fail lp_create with different argument errors at the same
+    # time; each reads back its own message
+    import threading
+    results = {}
+
+    def worker(tag, opt):
+        seen = set()
+        for _ in range(300):
+            rc, why = _create(lib, _dense(), opt=opt)
+            assert rc == nat.LP_ERR_ARG
+            seen.add(why)
+        results[tag] = seen
+
+    t1 = threading.Thread(target=worker, args=("sigma", _opts(lib, sigma=2.0)))
+    t2 = threading.Thread(target=worker, args=("t_max", _opts(lib, t_max=0)))
+    t1.start(); t2.start(); t1.join(); t2.join()
+    assert len(results["sigma"]) == 1 and "sigma" in next(iter(results["sigma"]))
+    assert len(results["t_max"]) == 1 and "t_max" in next(iter(results["t_max"]))
