@@ -16,7 +16,8 @@
  * Conventions for every entry point:
  *   - Return value: 0 = LP_OK; negative = error (LP_ERR_*); positive = a
  *     completed call with a warning status (LP_STATUS_*, LP_WARN_*).  After an
- *     error, lp_last_error(h) gives a one-line message.
+ *     error, lp_last_error(h) gives a one-line message.  No C++ exception
+ *     crosses this interface: a failed host allocation returns LP_ERR_OOM.
  *   - Ownership: the handle owns all device memory it allocates.  Caller
  *     buffers are never retained: lp_create copies A, b, c; outputs are written
  *     into caller-allocated buffers.

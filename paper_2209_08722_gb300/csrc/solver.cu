@@ -23,6 +23,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
+#include <stdexcept>
+#include <system_error>
 #include <string>
 #include <vector>
 
@@ -1061,6 +1064,27 @@ void options_check(const lp_options* o, std::string* why) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace {
+// C++ exceptions must not cross the C ABI: each entry point that allocates on
+// the host maps one to a status code (bad_alloc: LP_ERR_OOM; a size the
+// standard library refuses: LP_ERR_ARG) and records a message.
+template <typename F>
+int guarded(std::string* err, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    if (err) *err = "host allocation failed";
+    return LP_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (err) *err = std::string("invalid size: ") + e.what();
+    return LP_ERR_ARG;
+  } catch (...) {
+    if (err) *err = "unexpected host exception";
+    return LP_ERR_ARG;
+  }
+}
+}  // namespace
+
 extern "C" {
 
 void lp_options_default(lp_options* o) {
@@ -1307,8 +1331,12 @@ int lp_create(lp_handle** out, const lp_matrix* A, const double* b, const double
               int32_t bc_on_device, const lp_options* opt) {
   if (!out) return LP_ERR_ARG;
   *out = nullptr;
-  lp_handle* h = new lp_handle();
-  const int rc = create_impl(h, A, b, c, bc_on_device, opt);
+  lp_handle* h = new (std::nothrow) lp_handle();
+  if (!h) {
+    g_create_error = "host allocation failed";
+    return LP_ERR_OOM;
+  }
+  const int rc = guarded(&h->err, [&] { return create_impl(h, A, b, c, bc_on_device, opt); });
   if (rc != LP_OK) {
     g_create_error = h->err;
     lp_destroy(h);
@@ -1458,7 +1486,7 @@ int lp_reset_kernel_stats(lp_handle* h) {
 // ---------------------------------------------------------------------------
 // normal-equation solve (Algorithm 1 + eq. compv)
 // ---------------------------------------------------------------------------
-int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double* xs, int64_t k,
+static int normal_solve_impl(lp_handle* h, const double* D, const double* p, const double* xs, int64_t k,
                     double tol_f, int32_t io_on_device, double* dy, double* v, lp_nsolve_info* info) {
   if (!h || !D || !p || !dy || k < 0) return LP_ERR_ARG;
   h->err.clear();
@@ -1500,7 +1528,7 @@ int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double
 // ---------------------------------------------------------------------------
 // the IPM (Algorithm 2 / Algorithm 3)
 // ---------------------------------------------------------------------------
-int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const double* y0,
+static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, const double* y0,
              const double* s0, int32_t io_on_device, double* x, double* y, double* s,
              lp_result* info) {
   if (!h || !(tol > 0)) return LP_ERR_ARG;
@@ -1703,7 +1731,7 @@ int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const dou
   return status;
 }
 
-int lp_set_warm_start(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, float* rec_T,
+static int set_warm_start_impl(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, float* rec_T,
                       int32_t rec_capacity) {
   if (!h || mode < 0 || mode > 2 || (mode == 2 && !model) || rec_capacity < 0) return LP_ERR_ARG;
   if ((rec_X == nullptr) != (rec_T == nullptr)) return LP_ERR_ARG;
@@ -1762,7 +1790,13 @@ int lp_solve_batch(lp_handle* const* hs, int32_t count, double tol, int32_t mode
   int nt = max_threads > 0 ? max_threads : count;
   nt = std::max(1, std::min(std::min(nt, count), 64));
   std::vector<std::thread> pool;
-  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  for (int t = 1; t < nt; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (const std::system_error&) {
+      break;  // fewer host threads: the ones running take the remaining LPs
+    }
+  }
   worker();
   for (auto& t : pool) t.join();
   if (results)
@@ -1797,12 +1831,18 @@ void put_one(int dtype, void* dst, size_t idx) {
 }
 }  // namespace
 
-int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt_in, double tol,
-                    double* x0, lp_phase1_info* info) {
+static int phase1_start_impl(const lp_matrix* A, const double* b, const lp_options* opt_in, double tol,
+                             double* x0, lp_phase1_info* info) {
   if (!A || !b || !x0 || !(tol > 0) || A->on_device || A->m <= 0 || A->n <= 0) return LP_ERR_ARG;
   if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC) return LP_ERR_ARG;
   if (A->dtype != LP_F64 && A->dtype != LP_F32 && A->dtype != LP_BF16) return LP_ERR_ARG;
+  if (!A->val) return LP_ERR_ARG;
   if (A->fmt == LP_DENSE_COLMAJOR && A->ld < A->m) return LP_ERR_ARG;
+  if (A->fmt == LP_CSC) {  // the structure is read on the host below: check it first
+    if (!A->ptr || !A->idx || A->ptr[0] < 0) return LP_ERR_ARG;
+    for (long long j = 0; j < A->n; ++j)
+      if (A->ptr[j + 1] < A->ptr[j]) return LP_ERR_ARG;
+  }
   const int m = A->m;
   const long long n = A->n, n1 = n + m;
   const int esz = A->dtype == LP_F64 ? 8 : (A->dtype == LP_F32 ? 4 : 2);
@@ -1912,6 +1952,30 @@ int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt_i
   inf.x0_min = xmin;
   if (info) *info = inf;
   return xmin > 0.0 ? LP_OK : LP_ERR_NUMERICAL;
+}
+
+int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double* xs, int64_t k,
+                    double tol_f, int32_t io_on_device, double* dy, double* v, lp_nsolve_info* info) {
+  return guarded(h ? &h->err : nullptr,
+                 [&] { return normal_solve_impl(h, D, p, xs, k, tol_f, io_on_device, dy, v, info); });
+}
+
+int lp_solve(lp_handle* h, double tol, int32_t mode, const double* x0, const double* y0,
+             const double* s0, int32_t io_on_device, double* x, double* y, double* s,
+             lp_result* info) {
+  return guarded(h ? &h->err : nullptr,
+                 [&] { return solve_impl(h, tol, mode, x0, y0, s0, io_on_device, x, y, s, info); });
+}
+
+int lp_set_warm_start(lp_handle* h, int32_t mode, lp_mlp* model, float* rec_X, float* rec_T,
+                      int32_t rec_capacity) {
+  return guarded(h ? &h->err : nullptr,
+                 [&] { return set_warm_start_impl(h, mode, model, rec_X, rec_T, rec_capacity); });
+}
+
+int lp_phase1_start(const lp_matrix* A, const double* b, const lp_options* opt_in, double tol,
+                    double* x0, lp_phase1_info* info) {
+  return guarded(nullptr, [&] { return phase1_start_impl(A, b, opt_in, tol, x0, info); });
 }
 
 }  // extern "C"

@@ -205,3 +205,27 @@ def test_create_error_message_is_per_thread(lib):
     t1.start(); t2.start(); t1.join(); t2.join()
     assert len(results["sigma"]) == 1 and "sigma" in next(iter(results["sigma"]))
     assert len(results["t_max"]) == 1 and "t_max" in next(iter(results["t_max"]))
+
+
+def test_phase1_checks_a_host_matrix_before_reading_it(lib):
+    x0 = np.zeros(N)
+    b = _B.ctypes.data
+
+    def call(A):
+        return lib.lp_phase1_start(ctypes.byref(A), b, None, 1e-7, x0.ctypes.data, None)
+
+    assert call(_dense(val=None)) == nat.LP_ERR_ARG          # no values
+    ptr = np.arange(N + 1, dtype=np.int64)
+    idx = (np.arange(N) % M).astype(np.int32)
+    val = np.ones(N, dtype=np.float32)
+    A = _csc(ptr, idx, val)
+    A.ptr = None
+    assert call(A) == nat.LP_ERR_ARG                           # no column pointers
+    A = _csc(ptr, idx, val)
+    A.idx = None
+    assert call(A) == nat.LP_ERR_ARG                           # no row indices
+    back = ptr.copy()
+    back[-1] = 0                                               # ptr[n] < ptr[0]: negative nnz
+    assert call(_csc(back, idx, val)) == nat.LP_ERR_ARG
+    neg = ptr - 1                                              # ptr[0] < 0
+    assert call(_csc(neg, idx, val)) == nat.LP_ERR_ARG
