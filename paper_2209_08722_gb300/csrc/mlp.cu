@@ -16,6 +16,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <vector>
 
 #include "../../include/lp_sketch_ipm.h"
@@ -140,7 +142,12 @@ struct lp_mlp {
   bool alloc(T** p, size_t count) {
     void* q = nullptr;
     if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
-    allocs.push_back(q);
+    try {
+      allocs.push_back(q);
+    } catch (const std::bad_alloc&) {  // never throw out of a C ABI call
+      cudaFree(q);
+      return false;
+    }
     *p = static_cast<T*>(q);
     return true;
   }
@@ -189,25 +196,24 @@ struct lp_mlp {
 
 extern "C" {
 
-int lp_mlp_create(lp_mlp** out, int32_t in, int32_t hidden, int32_t outdim, uint64_t seed, void* stream) {
-  if (!out || in <= 0 || hidden <= 0 || outdim <= 0) return LP_ERR_ARG;
-  *out = nullptr;
-  lp_mlp* M = new lp_mlp();
+static int mlp_create_impl(lp_mlp** out, int32_t in, int32_t hidden, int32_t outdim, uint64_t seed,
+                           void* stream) {
+  std::unique_ptr<lp_mlp> M(new lp_mlp());  // freed on every early return
   M->in = in;
   M->hid = hidden;
   M->out = outdim;
   M->st = static_cast<cudaStream_t>(stream);
   int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&M->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&M->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    return LP_ERR_CUDA;
+  }
   if (cublasCreate(&M->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(M->blas, M->st) != CUBLAS_STATUS_SUCCESS) {
-    delete M;
     return LP_ERR_CUDA;
   }
   M->nparam = (long long)hidden * in + hidden + (long long)hidden * hidden + hidden + (long long)outdim * hidden + outdim;
   if (!M->alloc(&M->param, M->nparam) || !M->alloc(&M->grad, M->nparam) || !M->alloc(&M->adam_m, M->nparam) ||
       !M->alloc(&M->adam_v, M->nparam) || !M->alloc(&M->loss, 1)) {
-    delete M;
     return LP_ERR_OOM;
   }
   // He-style initialisation from SplitMix64 (host), biases zero; the output
@@ -227,11 +233,23 @@ int lp_mlp_create(lp_mlp** out, int32_t in, int32_t hidden, int32_t outdim, uint
   if (cudaMemcpy(M->param, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(M->adam_m, 0, sizeof(float) * M->nparam) != cudaSuccess ||
       cudaMemset(M->adam_v, 0, sizeof(float) * M->nparam) != cudaSuccess) {
-    delete M;
     return LP_ERR_CUDA;
   }
-  *out = M;
+  *out = M.release();
   return LP_OK;
+}
+
+// no C++ exception crosses the C ABI: a failed host allocation is LP_ERR_OOM
+int lp_mlp_create(lp_mlp** out, int32_t in, int32_t hidden, int32_t outdim, uint64_t seed, void* stream) {
+  if (!out || in <= 0 || hidden <= 0 || outdim <= 0) return LP_ERR_ARG;
+  *out = nullptr;
+  try {
+    return mlp_create_impl(out, in, hidden, outdim, seed, stream);
+  } catch (const std::bad_alloc&) {
+    return LP_ERR_OOM;
+  } catch (...) {
+    return LP_ERR_ARG;
+  }
 }
 
 int lp_mlp_destroy(lp_mlp* M) {
