@@ -166,6 +166,35 @@ def oracle_sample(lp, budget_s: float = 20.0):
     return per_it * outer, desc, os.cpu_count()
 
 
+def oracle_sketched_sample(lp, outer: int, inner: int):
+    """Times the CPU sketched oracle (the paper's method in FP64: CountSketch W,
+    SVD preconditioner, CG, correction v) on the full LP.  Two outer
+    iterations from the default start, one with exactly 1 CG step and one with
+    21, separate the per-outer-iteration cost (sketch, SVD, v, residuals,
+    directions, step lengths) from the cost of one CG step; the solve's cost
+    is estimated at this GPU solve's own outer and inner counts.  Returns
+    (seconds per solve, description, cores)."""
+    from oracle import ipm
+
+    def one(t_max):
+        opt = ipm.Options(mode="infeasible", solver="sketch", s=S_BLOCKS, w=int(W_FACTOR * M), k_max=1,
+                          inner_rule="relative", tol_cg=0.0, t_max=t_max)
+        t0 = time.perf_counter()
+        r = ipm.solve(lp.A, lp.b, lp.c, opt)
+        return time.perf_counter() - t0, r.history[0].inner_its
+
+    ta, ia = one(1)
+    tb, ib = one(21)
+    t_cg = max(tb - ta, 0.0) / max(ib - ia, 1)
+    t_outer = max(ta - ia * t_cg, 0.0)
+    value = outer * t_outer + inner * t_cg
+    desc = (f"the FP64 sketched oracle on the full 512x131072 LP: {t_outer:.3f} s per outer iteration "
+            f"(sketch, SVD, v, residuals, directions, steps) and {t_cg * 1e3:.2f} ms per CG step, "
+            f"measured from outer iterations with 1 and 21 CG steps, at this solve's {outer} outer "
+            f"and {inner} inner iterations")
+    return value, desc, os.cpu_count()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -491,10 +520,13 @@ def main():
     achieved = stats["bytes_per_launch"] / (k_ms * 1e-3) / 1e9 if launches else None
     traffic = traffic_record()
     gpu_launches = stats["all_launches"]
-    cpu = None
+    cpu = cpu_sk = None
     if not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(lp, budget_s=20.0)
         cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": desc}
+        v, desc, cores = oracle_sketched_sample(lp, infos[-1]["outer_iterations"], infos[-1]["inner_total"])
+        cpu_sk = {"value": v, "unit": "s", "cores": cores, "kind": "oracle (sketched method)",
+                  "sample": desc}
     value = ms_per_step / 1000.0 / world
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -512,6 +544,7 @@ def main():
                      "bytes_per_launch": stats["bytes_per_launch"], "launches": launches,
                      "mean_launch_ms": k_ms},
         "cpu_baseline": cpu,
+        "cpu_sketched": cpu_sk,
         "e2e": {"value": e2e / 1000.0 / world, "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": gpu_launches,
