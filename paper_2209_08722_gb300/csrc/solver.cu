@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "../../include/lp_sketch_ipm.h"
+#include "host_math.h"
 #include "internal.h"
 
 #include <atomic>
@@ -498,43 +499,10 @@ int sketch_and_factor(lp_handle* h, const double* dvec, int is_d2, long long k, 
   return rc;
 }
 
-// Symmetric tridiagonal eigenvalue bounds by bisection on Sturm counts.
-void tridiag_extremes(const std::vector<double>& dg, const std::vector<double>& off, double* lo,
-                      double* hi) {
-  const int k = (int)dg.size();
-  double gl = 1e300, gu = -1e300;
-  for (int i = 0; i < k; ++i) {
-    const double r = (i > 0 ? fabs(off[i - 1]) : 0.0) + (i + 1 < k ? fabs(off[i]) : 0.0);
-    gl = std::min(gl, dg[i] - r);
-    gu = std::max(gu, dg[i] + r);
-  }
-  auto count_below = [&](double x) {
-    int cnt = 0;
-    double q = 1.0;
-    for (int i = 0; i < k; ++i) {
-      const double o2 = i > 0 ? off[i - 1] * off[i - 1] : 0.0;
-      q = dg[i] - x - (i > 0 ? o2 / q : 0.0);
-      if (q == 0.0) q = -1e-300;
-      if (q < 0) ++cnt;
-    }
-    return cnt;
-  };
-  auto kth = [&](int idx) {  // idx-th smallest eigenvalue (0-based)
-    double a = gl, b = gu;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (count_below(mid) > idx) b = mid;
-      else a = mid;
-    }
-    return 0.5 * (a + b);
-  };
-  *lo = kth(0);
-  *hi = kth(k - 1);
-}
-
 // Extreme Ritz values of Q^{-1} M from the first kk CG steps: the Lanczos
 // tridiagonal has diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal
 // sqrt(beta_j)/alpha_j (alpha_j at coef[2j], beta_j at coef[2j+1]).
+// (lanczos_extremes in host_math.h; a broken recurrence keeps the defaults)
 int ritz_extremes(lp_handle* h, int kk, double* lo, double* hi) {
   *lo = 0.5;
   *hi = 2.0;
@@ -542,15 +510,7 @@ int ritz_extremes(lp_handle* h, int kk, double* lo, double* hi) {
   std::vector<double> coef(2 * (size_t)kk);
   CK(cudaMemcpyAsync(coef.data(), h->coef, sizeof(double) * 2 * kk, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  std::vector<double> dg(kk), off(std::max(0, kk - 1));
-  for (int j = 0; j < kk; ++j) {
-    const double al = coef[2 * j], be_prev = j > 0 ? coef[2 * (j - 1) + 1] : 0.0;
-    const double al_prev = j > 0 ? coef[2 * (j - 1)] : 1.0;
-    if (!(al > 0.0) || !(al_prev > 0.0) || !(be_prev >= 0.0)) return LP_OK;  // broken recurrence
-    dg[j] = 1.0 / al + (j > 0 ? be_prev / al_prev : 0.0);
-    if (j + 1 < kk) off[j] = sqrt(std::max(coef[2 * j + 1], 0.0)) / al;
-  }
-  tridiag_extremes(dg, off, lo, hi);
+  lanczos_extremes(coef.data(), kk, lo, hi);
   return LP_OK;
 }
 
