@@ -67,4 +67,28 @@ inline bool lanczos_extremes(const double* coef, int kk, double* lo, double* hi)
   return true;
 }
 
+// The inner solve's target at the Lemma 4.4 level: Lemma 4.2 bounds
+// ||v|| <= sqrt(3 n mu) ||f||, and Lemma 4.4 needs ||v|| <= gamma sigma mu / 4,
+// so ||f|| <= gamma sigma sqrt(mu) / (4 sqrt(3 n)).
+inline double theory_inner_tol(double mu, long long n, double gamma, double sigma) {
+  return gamma * sigma * std::sqrt(mu) / (4.0 * std::sqrt(3.0 * (double)n));
+}
+
+// The outer loop's stopping measures: the relative duality gap
+// |c^T x - b^T y| / (1 + |c^T x|) and the relative residuals
+// ||r_p|| / (1 + ||b||), ||r_d|| / (1 + ||c||); the solve stops when all three
+// are at most tol.
+struct StopMeasures {
+  double gap, rp_rel, rd_rel;
+};
+
+inline StopMeasures stop_measures(double cx, double by, double rp2, double rd2, double bnorm, double cnorm) {
+  return {std::fabs(cx - by) / (1.0 + std::fabs(cx)), std::sqrt(rp2) / (1.0 + bnorm),
+          std::sqrt(rd2) / (1.0 + cnorm)};
+}
+
+inline bool stop_reached(const StopMeasures& s, double tol) {
+  return s.gap <= tol && s.rp_rel <= tol && s.rd_rel <= tol;
+}
+
 }  // namespace lpk

@@ -1535,8 +1535,8 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     ms_res += ms_since(t0);
     const DevScalars& S = *h->hsc;
     const double rp = sqrt(S.rp2), rd = sqrt(S.rd2);
-    const double gap = fabs(S.cx - S.by) / (1.0 + fabs(S.cx));
-    const double rp_rel = rp / (1.0 + h->bnorm), rd_rel = rd / (1.0 + h->cnorm);
+    const StopMeasures sm = stop_measures(S.cx, S.by, S.rp2, S.rd2, h->bnorm, h->cnorm);
+    const double gap = sm.gap, rp_rel = sm.rp_rel, rd_rel = sm.rd_rel;
     if (k > 0 && !h->history.empty()) {
       h->history.back().alpha_max = S.alpha_max;
       h->history.back().alpha_bar = S.alpha_bar;
@@ -1567,7 +1567,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     res.mu = S.mu;
     if (!std::isfinite(gap) || !std::isfinite(rp) || !std::isfinite(rd))
       return h->fail(LP_ERR_NUMERICAL, "non-finite residuals at iteration %d", k);
-    if (gap <= tol && rp_rel <= tol && rd_rel <= tol) {
+    if (stop_reached(sm, tol)) {
       status = LP_OK;
       break;
     }
@@ -1594,8 +1594,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     const bool adaptive = h->opt.sigma_rule == 1;
     const double sig_lo = 0.1, sig_hi = 0.75;  // inside the analysis range (0, 4/5)
     const double tol_f = h->opt.inner_rule == LP_RULE_THEORY
-                             ? h->opt.gamma * (adaptive ? sig_lo : h->opt.sigma) * sqrt(mu) /
-                                   (4.0 * sqrt(3.0 * (double)n))
+                             ? theory_inner_tol(mu, n, h->opt.gamma, adaptive ? sig_lo : h->opt.sigma)
                              : 0.0;
     double sigma_k = h->opt.sigma;
     int iters = 0, ist = 0;

@@ -12,7 +12,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from oracle import ipm
+from oracle import ipm, pcg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2209_08722_gb300", "csrc")
@@ -32,6 +32,10 @@ def shim(tmp_path_factory):
     lib.shim_lanczos_extremes.restype = ctypes.c_int
     lib.shim_tridiag_extremes.argtypes = [dp, dp, ctypes.c_int, dp, dp]
     lib.shim_tridiag_extremes.restype = None
+    lib.shim_theory_inner_tol.argtypes = [ctypes.c_double, ctypes.c_longlong, ctypes.c_double, ctypes.c_double]
+    lib.shim_theory_inner_tol.restype = ctypes.c_double
+    lib.shim_stop.argtypes = [ctypes.c_double] * 7 + [dp]
+    lib.shim_stop.restype = ctypes.c_int
     return lib
 
 
@@ -81,3 +85,49 @@ def test_broken_recurrence_is_reported(shim):
                  np.array([np.nan, 0.1])):
         assert shim.shim_lanczos_extremes(_ptr(coef), len(coef) // 2, ctypes.byref(lo), ctypes.byref(hi)) == 0
         assert lo.value == -7.0 and hi.value == -7.0    # left alone
+
+
+def test_theory_inner_target_matches_the_oracle(shim):
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        mu, n = 10.0 ** rng.uniform(-12, 2), int(rng.integers(1, 10 ** 7))
+        gamma, sigma = rng.uniform(0.01, 0.999), rng.uniform(0.05, 0.8)
+        ref = pcg.theory_inner_tol(mu, n, gamma, sigma)
+        assert shim.shim_theory_inner_tol(mu, n, gamma, sigma) == pytest.approx(ref, rel=1e-15)
+
+
+def test_stopping_measures_match_the_oracle(shim):
+    # the oracle's test on random iterates, and at a planted optimum moved so
+    # that exactly one of the three measures sits at 0.5 or 2 times tol
+    import lpgen
+    rng = np.random.default_rng(8)
+    tol = 1e-8
+    lp = lpgen.planted_dense(6, 40, seed=8)
+    A, b, c, n = lp.A, lp.b, lp.c, lp.n
+    x0, y0, s0 = lp.x_star, lp.y_star, lp.s_star
+    cases = [(rng.uniform(0, 2, n), rng.standard_normal(lp.m), rng.uniform(0, 2, n)) for _ in range(10)]
+    cases.append((x0, y0, s0))
+    null = np.eye(n) - np.linalg.pinv(A) @ A                    # A (null u) = 0
+    for scale in (0.5, 2.0):
+        u = rng.standard_normal(n)
+        u -= (u @ c) / (c @ c) * c                              # keeps c^T x: only r_p moves
+        t = scale * tol * (1 + np.linalg.norm(b)) / np.linalg.norm(A @ u)
+        cases.append((x0 + t * u, y0, s0))
+        e = np.eye(n)[0]                                        # only r_d moves
+        cases.append((x0, y0, s0 + scale * tol * (1 + np.linalg.norm(c)) * e))
+        g = null @ rng.standard_normal(n)                       # only the gap moves
+        t = scale * tol * (1 + abs(c @ x0)) / abs(c @ g)
+        cases.append((x0 + t * g, y0, s0))
+    out = np.empty(3)
+    outcomes = set()
+    for x, y, s in cases:
+        r_p, r_d = ipm.residuals(A, b, c, x, y, s)
+        done_ref, gap_ref = ipm.converged(A, b, c, x, y, r_p, r_d, tol)
+        done = shim.shim_stop(c @ x, b @ y, r_p @ r_p, r_d @ r_d, np.linalg.norm(b), np.linalg.norm(c), tol,
+                              _ptr(out))
+        assert out[0] == pytest.approx(gap_ref, rel=1e-12, abs=1e-15)
+        assert out[1] == pytest.approx(np.linalg.norm(r_p) / (1 + np.linalg.norm(b)), rel=1e-12, abs=1e-300)
+        assert out[2] == pytest.approx(np.linalg.norm(r_d) / (1 + np.linalg.norm(c)), rel=1e-12, abs=1e-300)
+        assert bool(done) == bool(done_ref)
+        outcomes.add(bool(done))
+    assert outcomes == {True, False}
