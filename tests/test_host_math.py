@@ -19,13 +19,14 @@ CSRC = os.path.join(ROOT, "paper_2209_08722_gb300", "csrc")
 SHIM = os.path.join(ROOT, "tests", "host_math_shim.cpp")
 
 
-@pytest.fixture(scope="module")
-def shim(tmp_path_factory):
+def _build_shim(out_dir, include_dir):
+    """Compile the shim against the host_math.h found in include_dir."""
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("g++ not available")
-    out = str(tmp_path_factory.mktemp("shim") / "libhostmath.so")
-    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, SHIM, "-o", out], check=True)
+    out = os.path.join(str(out_dir), "libhostmath.so")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", str(include_dir), SHIM, "-o", out],
+                   check=True)
     lib = ctypes.CDLL(out)
     dp = ctypes.POINTER(ctypes.c_double)
     lib.shim_lanczos_extremes.argtypes = [dp, ctypes.c_int, dp, dp]
@@ -37,6 +38,11 @@ def shim(tmp_path_factory):
     lib.shim_stop.argtypes = [ctypes.c_double] * 7 + [dp]
     lib.shim_stop.restype = ctypes.c_int
     return lib
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    return _build_shim(tmp_path_factory.mktemp("shim"), CSRC)
 
 
 def _ptr(a):
@@ -131,3 +137,44 @@ def test_stopping_measures_match_the_oracle(shim):
         assert bool(done) == bool(done_ref)
         outcomes.add(bool(done))
     assert outcomes == {True, False}
+
+
+# One mistake at a time planted in a copy of host_math.h; the tests above,
+# run against a shim built from that copy, must catch each of them.
+HEADER_MUTANTS = [
+    ("diagonal_index", "be_prev / al_prev", "be_prev / al", "lanczos"),
+    ("offdiagonal_sqrt_dropped", "std::sqrt(std::max(coef[2 * j + 1], 0.0)) / al",
+     "std::max(coef[2 * j + 1], 0.0) / al", "lanczos"),
+    ("breakdown_test_strict", "!(be_prev >= 0.0)", "!(be_prev > 0.0)", "lanczos"),
+    ("sturm_pivot_sign", "q = dg[i] - x - (i > 0 ? o2 / q : 0.0);", "q = dg[i] - x + (i > 0 ? o2 / q : 0.0);",
+     "tridiag"),
+    ("gershgorin_radius_dropped", "gl = std::min(gl, dg[i] - r);", "gl = std::min(gl, dg[i]);", "tridiag"),
+    ("theory_factor_3_dropped", "std::sqrt(3.0 * (double)n)", "std::sqrt((double)n)", "theory"),
+    ("gap_normalised_by_dual", "(1.0 + std::fabs(cx))", "(1.0 + std::fabs(by))", "stop"),
+    ("primal_residual_by_c", "std::sqrt(rp2) / (1.0 + bnorm)", "std::sqrt(rp2) / (1.0 + cnorm)", "stop"),
+    ("dual_residual_test_dropped", "s.rd_rel <= tol", "s.rp_rel <= tol", "stop"),
+]
+
+
+def _run_checks(lib, which):
+    if which == "lanczos":
+        for m, cond, steps in ((12, 30.0, 5), (40, 1e3, 12)):
+            test_lanczos_extremes_match_the_oracle(lib, m, cond, steps)
+    elif which == "tridiag":
+        test_tridiagonal_extremes_match_a_dense_eigensolver(lib)
+    elif which == "theory":
+        test_theory_inner_target_matches_the_oracle(lib)
+    else:
+        test_stopping_measures_match_the_oracle(lib)
+
+
+@pytest.mark.parametrize("mid,old,new,which", HEADER_MUTANTS, ids=[m[0] for m in HEADER_MUTANTS])
+def test_planted_mistake_in_host_math_is_caught(tmp_path, mid, old, new, which):
+    src = open(os.path.join(CSRC, "host_math.h")).read()
+    assert src.count(old) == 1, (mid, src.count(old))
+    inc = tmp_path / "inc"
+    inc.mkdir()
+    (inc / "host_math.h").write_text(src.replace(old, new))
+    lib = _build_shim(tmp_path, inc)
+    with pytest.raises(AssertionError):
+        _run_checks(lib, which)
