@@ -81,6 +81,8 @@ PINS = {
     "ns_cholesky": ("test_oracle_ipm", "test_normal_solve_matches_cholesky_at_tight_tolerance", {}),
     "ns_plain": ("test_oracle_ipm", "test_unpreconditioned_normal_solve_is_cg_on_eq_normal", {}),
     "two_rhs": ("test_oracle_ipm", "test_two_rhs_combination_is_the_solve_with_p_sigma", {}),
+    "two_rhs_fewer_outer": ("test_oracle_ipm", "test_two_rhs_adaptive_sigma_needs_fewer_outer_iterations",
+                            {"col_scale": None}),
     "inner_theory_bound": ("test_oracle_ipm", "test_inner_solves_stop_at_the_theory_bound", {}),
     "orthonormal_rows": ("test_oracle_ipm",
                          "test_orthonormal_rows_and_unit_scaling_give_the_identity_normal_matrix", {}),
@@ -187,6 +189,10 @@ MUTANTS = [
      'tol = 10 * inner_tol if opt.inner_rule == "theory"', ["inner_theory_bound"]),
     ("plain_cg_d2_inverted", "ipm", "normal_solve_unpreconditioned", "d2 = x / s", "d2 = s / x",
      ["ns_plain"]),
+    ("adaptive_sigma_ratio_inverted", "ipm", "_adaptive_sigma_solve", "(mu_aff / mu) ** 3",
+     "(mu / mu_aff) ** 3", ["two_rhs_fewer_outer"]),
+    ("neighbourhood_residual_ratio_inverted", "ipm", "in_neighbourhood", "res_ratio > (mu / mu0)",
+     "res_ratio > (mu0 / mu)", ["grid_infeas_binding", "steps_infeas"]),
     ("two_rhs_affine_part_kept", "ipm", "_adaptive_sigma_solve",
      "rhs(A, x, s, r_p, r_d, 1.0, mu, feasible) - p_aff", "rhs(A, x, s, r_p, r_d, 1.0, mu, feasible)",
      ["two_rhs"]),
@@ -198,6 +204,8 @@ MUTANTS = [
     ("p1_b_not_flipped", "phase1", "phase1_lp", "b1 = b * sign", "b1 = b", ["p1_negative_b"]),
     ("p1_costs_swapped", "phase1", "phase1_lp", "[np.zeros(n), np.ones(m)]", "[np.ones(n), np.zeros(m)]",
      ["p1_highs", "p1_infeasible"]),
+    ("p1_feasibility_test_inverted", "phase1", "phase1_start", "feasible = z_sum <=", "feasible = z_sum >=",
+     ["p1_planted"]),
     ("p1_projection_sign", "phase1", "phase1_start", "x0 = x + A.T", "x0 = x - A.T",
      ["p1_planted", "p1_projection"]),
     # --- the warm-start model ---
@@ -207,6 +215,8 @@ MUTANTS = [
     ("loss_batch_mean_dropped", "mlp", "loss_and_grads", "d3 = R / B", "d3 = R", ["mlp_fd"]),
     ("backprop_transpose_dropped", "mlp", "loss_and_grads", "(W2.T @ d2)", "(W2 @ d2)", ["mlp_fd"]),
     ("forward_activation_dropped", "mlp", "forward", "A2 = gelu(Z2)", "A2 = Z2", ["mlp_fd"]),
+    ("adam_second_moment_unsquared", "mlp", "adam_step", "(1 - b2) * grad * grad", "(1 - b2) * grad",
+     ["mlp_adam"]),
     ("adam_bias_correction_dropped", "mlp", "adam_step", "mh = m / (1 - b1 ** step)", "mh = m",
      ["mlp_adam"]),
     ("unflatten_row_major", "mlp", "unflatten", ".reshape(cols, rows).T", ".reshape(rows, cols)",
