@@ -413,6 +413,47 @@ def run_warm_start(args):
     return 0
 
 
+def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk):
+    """The JSON line of the default run: BASELINE-style keys plus roofline,
+    cpu_baseline, cpu_sketched, e2e, gpu_launches, clocks and the solve's
+    counts.  Pure host code (reads the measured peaks and the traffic record)."""
+    peak, peak_kind = load_peaks()
+    launches = stats["launches"]
+    k_ms = stats["ms"] / max(1, launches)
+    achieved = stats["bytes_per_launch"] / (k_ms * 1e-3) / 1e9 if launches else None
+    traffic = traffic_record()
+    gpu_launches = stats["all_launches"]
+    value = ms_per_step / 1000.0 / world
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "dtype_detail": "A stored FP32; products FP32 with FP32 accumulation in the inner loop, "
+                        "FP64 residual refresh, FP64 vectors, sketch, QR and step lengths",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (A = 268 MB FP32)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_adat_fused (A diag(d2) A^T v, FP32)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "bytes_per_launch": stats["bytes_per_launch"], "launches": launches,
+                     "mean_launch_ms": k_ms},
+        "cpu_baseline": cpu,
+        "cpu_sketched": cpu_sk,
+        "e2e": {"value": e2e / 1000.0 / world, "unit": "s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "solve": {"outer_iterations": infos[-1]["outer_iterations"],
+                  "inner_total": infos[-1]["inner_total"], "inner_max": infos[-1]["inner_max"],
+                  "rel_gap": infos[-1]["rel_gap"], "objective_rel_err": obj_err,
+                  "ms_phases": {k: infos[-1][k] for k in ("ms_residual", "ms_factor", "ms_inner",
+                                                          "ms_correction", "ms_step")}},
+    }
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,12 +555,6 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return 0
-    peak, peak_kind = load_peaks()
-    launches = stats["launches"]
-    k_ms = stats["ms"] / max(1, launches)
-    achieved = stats["bytes_per_launch"] / (k_ms * 1e-3) / 1e9 if launches else None
-    traffic = traffic_record()
-    gpu_launches = stats["all_launches"]
     cpu = cpu_sk = None
     if not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(lp, budget_s=20.0)
@@ -531,34 +566,7 @@ def main():
                       "sample": desc}
         except Exception as e:  # noqa: BLE001
             cpu_sk = {"value": None, "error": f"{type(e).__name__}: {e}"}
-    value = ms_per_step / 1000.0 / world
-    line = {
-        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "dtype_detail": "A stored FP32; products FP32 with FP32 accumulation in the inner loop, "
-                        "FP64 residual refresh, FP64 vectors, sketch, QR and step lengths",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (A = 268 MB FP32)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_adat_fused (A diag(d2) A^T v, FP32)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None,
-                     "peak_kind": peak_kind, "traffic": traffic,
-                     "bytes_per_launch": stats["bytes_per_launch"], "launches": launches,
-                     "mean_launch_ms": k_ms},
-        "cpu_baseline": cpu,
-        "cpu_sketched": cpu_sk,
-        "e2e": {"value": e2e / 1000.0 / world, "unit": "s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-        "gpu_launches": gpu_launches,
-        "clocks": clk,
-        "solve": {"outer_iterations": infos[-1]["outer_iterations"],
-                  "inner_total": infos[-1]["inner_total"], "inner_max": infos[-1]["inner_max"],
-                  "rel_gap": infos[-1]["rel_gap"], "objective_rel_err": obj_err,
-                  "ms_phases": {k: infos[-1][k] for k in ("ms_residual", "ms_factor", "ms_inner",
-                                                          "ms_correction", "ms_step")}},
-    }
+    line = ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
