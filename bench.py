@@ -414,7 +414,7 @@ def run_warm_start(args):
 
 
 def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk):
-    """The JSON line of the default run: BASELINE-style keys plus roofline,
+    """The JSON line of the default run: the metric and its run keys plus roofline,
     cpu_baseline, cpu_sketched, e2e, gpu_launches, clocks and the solve's
     counts.  Pure host code (reads the measured peaks and the traffic record)."""
     peak, peak_kind = load_peaks()
