@@ -179,7 +179,7 @@ void lp_options_default(lp_options* opt);
  * handle's layout and allocates every workspace the solver needs.  `bc_on_device`
  * says where b and c live.  Errors: LP_ERR_ARG (sizes, m > n, bad CSC, bad
  * options, a sketch width below m), LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_UNSUPPORTED
- * (shape outside this build's kernels).  On error *h is NULL and
+ * (a shape the library's kernels do not cover).  On error *h is NULL and
  * lp_create_error() says why.  Errors in the arguments themselves (pointers,
  * sizes, the CSC structure of a host matrix, the options, the sketch width)
  * are reported before any CUDA call is made; NaN/Inf in b or c is found on
