@@ -176,3 +176,33 @@ def test_gaussian_uniforms_reach_both_ends_of_their_grids():
     assert u1.min() == step and u1.max() == 1.0
     assert u2.min() == 0.0 and u2.max() == 1.0 - step
     assert np.isfinite(np.log(u1)).all()
+
+
+def test_preconditioned_condition_number_by_sketch_and_regime():
+    # kappa(Q^{-1} M) of Q^{-1/2} A D at w = 4m: with spread D every sketch
+    # sits near the Marchenko-Pastur value ((1 + 1/2)/(1 - 1/2))^2 = 9; near
+    # the optimum (m dominant columns of D) one nonzero per row collapses
+    # (two basic columns in one bucket make W_B singular) while s = 4 stays
+    # within twice the Gaussian sketch
+    from oracle import pcg
+    m, n, w = 64, 8192, 256
+    rng = np.random.default_rng(100)
+    A = rng.standard_normal((m, n))
+
+    def kappa2(AD, W):
+        ADW = np.asarray((W.T @ AD.T).T) if hasattr(W, "tocsc") else AD @ W
+        sv = np.linalg.svd(pcg.preconditioner(ADW).Q_mhalf @ AD, compute_uv=False)
+        return (sv[0] / sv[-1]) ** 2
+
+    spread = A * np.exp(rng.uniform(-3, 3, n))
+    d = np.exp(rng.uniform(-8, -4, n))
+    d[rng.choice(n, m, replace=False)] = np.exp(rng.uniform(3, 6, m))
+    near = A * d
+    sketches = {s: sketch.countsketch_matrix(0, 0, 0, n, w, s) for s in (1, 2, 4)}
+    gauss = sketch.gaussian_matrix(0, 0, 0, n, w)
+    for W in list(sketches.values()) + [gauss]:
+        assert 5.0 < kappa2(spread, W) < 12.0
+    k_gauss = kappa2(near, gauss)
+    assert kappa2(near, sketches[1]) > 1e4
+    assert kappa2(near, sketches[4]) < 2.0 * k_gauss
+    assert kappa2(near, sketches[2]) > kappa2(near, sketches[4])
