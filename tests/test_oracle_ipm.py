@@ -515,3 +515,5 @@ def test_inner_solves_stop_at_the_theory_bound():
     for rec in res.history[:-1]:
         assert rec.inner_its < opt.t_max
         assert rec.f_norm <= pcg.theory_inner_tol(rec.mu, n, opt.gamma, opt.sigma) * (1 + 1e-9)
+        # and so, by Lemma 4.2, the correction meets Lemma 4.4's ||v|| <= gamma sigma mu / 4
+        assert rec.v_norm <= opt.gamma * opt.sigma * rec.mu / 4 * (1 + 1e-9)
