@@ -322,7 +322,12 @@ int lp_adat_noalloc(const void* A, int32_t dtype, int32_t m, int64_t n, int64_t 
  * found feasible.  Returns LP_OK with x0 > 0 and A x0 = b to rounding,
  * LP_ERR_NOT_FEASIBLE when the phase-1 optimum 1^T z exceeds
  * 1e-6 (1 + ||b||) (info->z_sum holds it), LP_ERR_NUMERICAL when the
- * correction leaves some x0_j <= 0, or the error of the inner calls. */
+ * correction leaves some x0_j <= 0, or the error of the inner calls.
+ * LP_ERR_ARG, before anything is read or any CUDA call is made: a NULL
+ * argument, tol <= 0, a device matrix, m or n < 1, a bad format or dtype, a
+ * NULL value array, ld < m (dense), or a CSC matrix without pointers or
+ * indices, with ptr[0] < 0 or with decreasing column pointers (a row index
+ * out of range is found while the phase-1 matrix is built). */
 typedef struct {
     double z_sum;               /* 1^T z at the phase-1 solution */
     double residual;            /* ||A x0 - b|| after the correction */
