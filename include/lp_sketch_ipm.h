@@ -220,7 +220,10 @@ int lp_solve(lp_handle* h, double tol, int32_t mode,
  * have different sizes.  Returns LP_OK when every solve returned a
  * non-negative status (per-LP statuses are in results[i].status), else the
  * first error in index order.  Handles must not be shared between batches
- * running at the same time. */
+ * running at the same time.  LP_ERR_ARG for hs NULL, count < 0, tol <= 0, a
+ * NULL handle or the same handle twice.  If the system refuses to start a
+ * host worker, the workers already running (and the calling thread) take its
+ * LPs. */
 int lp_solve_batch(lp_handle* const* hs, int32_t count, double tol, int32_t mode,
                    int32_t io_on_device, double* const* x, double* const* y, double* const* s,
                    int32_t max_threads, lp_result* results);
