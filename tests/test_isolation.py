@@ -68,3 +68,14 @@ def test_committed_code_does_not_read_the_working_folder():
         src = open(path, encoding="utf-8").read()
         assert not work.search(src), path
         assert "/root/reference" not in src, path
+
+
+def test_smoke_refuses_to_run_without_a_gpu():
+    # no CPU fallback anywhere: without a CUDA device smoke() stops at once
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: smoke() runs for real there")
+    import __graft_entry__
+    with pytest.raises(AssertionError, match="cuda"):
+        __graft_entry__.smoke()
