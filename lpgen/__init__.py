@@ -20,6 +20,8 @@ When A is stored in a reduced precision, b and c are formed in FP64 from the
 from .planted import (  # noqa: F401
     PlantedLP,
     planted_dense,
+    planted_dense_blocked,
+    make,
     planted_sparse,
     round_bf16,
     bf16_bits,

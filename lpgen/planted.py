@@ -10,6 +10,7 @@ and stand in for its l1-SVM data sets, which are not available here.
 from __future__ import annotations
 
 import dataclasses
+import os
 from typing import Optional
 
 import numpy as np
@@ -71,6 +72,7 @@ class PlantedLP:
     col_ptr: Optional[np.ndarray] = None
     row_idx: Optional[np.ndarray] = None
     val: Optional[np.ndarray] = None
+    cols: Optional[np.ndarray] = None   # blocked dense problems: (n, m) storage array
 
     @property
     def sparse(self) -> bool:
@@ -83,6 +85,14 @@ class PlantedLP:
 
     def dense(self) -> np.ndarray:
         if self.A is not None:
+            return self.A
+        if self.cols is not None:
+            # FP64 values of the stored (already rounded) entries, (m, n)
+            if self.storage == "bf16":
+                vals = (self.cols.astype(np.uint32) << np.uint32(16)).view(np.float32)
+            else:
+                vals = self.cols
+            self.A = np.ascontiguousarray(vals.T, dtype=np.float64)
             return self.A
         A = np.zeros((self.m, self.n))
         for j in range(self.n):
@@ -101,6 +111,8 @@ class PlantedLP:
         column-major layout with leading dimension m; bf16 is returned as its
         uint16 bit pattern.
         """
+        if self.cols is not None:
+            return self.cols
         assert self.A is not None
         if self.storage == "f64":
             return np.ascontiguousarray(self.A.T)
@@ -138,6 +150,68 @@ def planted_dense(m: int, n: int, seed: int = 0, storage: str = "f64",
     c = A.T @ y_star + s_star
     return PlantedLP(m=m, n=n, b=b, c=c, x_star=x_star, y_star=y_star,
                      s_star=s_star, basis=basis, storage=storage, A=A)
+
+
+def _storage_cols(block: np.ndarray, storage: str) -> np.ndarray:
+    """(cols, m) float32 draws -> the storage dtype (bf16 as uint16 bits)."""
+    if storage == "bf16":
+        return bf16_bits(block)
+    if storage == "f32":
+        return block
+    return block.astype(np.float64)
+
+
+def _cols_values(cols: np.ndarray, storage: str) -> np.ndarray:
+    """Stored entries of a column block as FP64 values."""
+    if storage == "bf16":
+        return (cols.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+    return cols.astype(np.float64)
+
+
+def planted_dense_blocked(m: int, n: int, seed: int = 0, storage: str = "bf16",
+                          col_scale_log10: Optional[tuple] = None, block: int = 8192,
+                          threads: Optional[int] = None) -> PlantedLP:
+    """Dense planted LP with iid N(0,1) entries, drawn column block by column
+    block so that 10^9-entry instances are generated in seconds.
+
+    Block q (columns q*block ... q*block+block-1) is drawn from its own
+    generator ``default_rng([seed, 1, q])`` as float32 normals, one row per
+    column (the column-major storage order), then multiplied by its columns'
+    10**U(lo, hi) scales (drawn after the normals from the same generator)
+    and rounded to ``storage``.  The planted optimum comes from
+    ``default_rng([seed, 2])``.  b = A x* (only the m basic columns enter) and
+    c = A^T y* + s* are formed in FP64 from the stored values.  The blocks are
+    independent, so the result does not depend on ``threads``.
+
+    The stored matrix is kept only in its storage dtype (``cols``, an (n, m)
+    array = column-major with leading dimension m); ``dense()`` expands it to
+    FP64 on request.
+    """
+    import concurrent.futures as cf
+    if storage not in ("f64", "f32", "bf16"):
+        raise ValueError(f"unknown storage {storage!r}")
+    sdt = {"bf16": np.uint16, "f32": np.float32, "f64": np.float64}[storage]
+    cols = np.empty((n, m), dtype=sdt)
+    basis, x_star, y_star, s_star = _plant(np.random.default_rng([seed, 2]), m, n)
+    c = np.empty(n)
+    nblocks = (n + block - 1) // block
+
+    def fill(q):
+        j0, j1 = q * block, min(n, (q + 1) * block)
+        rng = np.random.default_rng([seed, 1, q])
+        blk = rng.standard_normal((j1 - j0, m), dtype=np.float32)
+        if col_scale_log10 is not None:
+            lo, hi = col_scale_log10
+            blk *= (10.0 ** rng.uniform(lo, hi, size=j1 - j0)).astype(np.float32)[:, None]
+        cols[j0:j1] = _storage_cols(blk, storage)
+        c[j0:j1] = _cols_values(cols[j0:j1], storage) @ y_star + s_star[j0:j1]
+
+    workers = threads or min(32, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        list(ex.map(fill, range(nblocks)))
+    b = _cols_values(cols[basis], storage).T @ x_star[basis]
+    return PlantedLP(m=m, n=n, b=b, c=c, x_star=x_star, y_star=y_star,
+                     s_star=s_star, basis=basis, storage=storage, cols=cols)
 
 
 def planted_sparse(m: int, n: int, nnz_per_col: int = 8, seed: int = 0,
@@ -256,8 +330,9 @@ CONFIGS = {
     # 20% Zipf(1.2) rows, CountSketch w=3m, s=2
     "c3": dict(kind="sparse", m=4096, n=2_000_000, storage="f32", nnz_per_col=8,
                mode="infeasible", w_factor=3.0, s=2, seed=0),
-    # BF16 storage, dense 2048 x 524288, CountSketch w=4m, s=2
-    "c4": dict(kind="dense", m=2048, n=524288, storage="bf16", col_scale=None,
+    # BF16 storage, dense 2048 x 524288, CountSketch w=4m, s=2; drawn column
+    # block by column block (10^9 entries)
+    "c4": dict(kind="dense_blocked", m=2048, n=524288, storage="bf16", col_scale=None,
                mode="infeasible", w_factor=4.0, s=2, seed=0),
 }
 
@@ -270,6 +345,9 @@ def make(cfg: dict, m: Optional[int] = None, n: Optional[int] = None,
     if cfg["kind"] == "dense":
         return planted_dense(m, n, seed=seed, storage=cfg["storage"],
                              col_scale_log10=cfg.get("col_scale"))
+    if cfg["kind"] == "dense_blocked":
+        return planted_dense_blocked(m, n, seed=seed, storage=cfg["storage"],
+                                     col_scale_log10=cfg.get("col_scale"))
     return planted_sparse(m, n, nnz_per_col=cfg.get("nnz_per_col", 8), seed=seed,
                           storage=cfg["storage"])
 

@@ -33,7 +33,7 @@ def _check(lp, x, y, s, info, ref=None):
 def test_infeasible_solve_small_configs(name, div):
     lp = lpgen.config_small(name, div)
     cfg = lpgen.CONFIGS[name]
-    ref = ipm.solve(lp.A, lp.b, lp.c, ipm.Options(mode="infeasible"))
+    ref = ipm.solve(lp.dense(), lp.b, lp.c, ipm.Options(mode="infeasible"))
     with solver_for(lp, s=cfg["s"], w_factor=cfg["w_factor"]) as S:
         x, y, s, info = S.solve(tol=1e-8, mode="infeasible")
     _check(lp, x, y, s, info, ref)

@@ -102,3 +102,43 @@ def test_named_workloads_and_the_bench_agree():
         C["c2"]["m"], C["c2"]["n"], C["c2"]["s"], C["c2"]["w_factor"])
     small = lpgen.config_small("c2", 64)
     assert (small.m, small.n, small.storage) == (8, 2048, "f32")
+
+
+@pytest.mark.parametrize("storage,scale", [("bf16", None), ("f32", (-2.0, 2.0)), ("f64", None)])
+def test_blocked_dense_generator_is_planted_and_thread_independent(storage, scale):
+    # the column-block generator of the 10^9-entry workload: every block has its
+    # own seeded stream, so the matrix does not depend on the worker count
+    m, n = 12, 1000
+    one = lpgen.planted_dense_blocked(m, n, seed=7, storage=storage, col_scale_log10=scale,
+                                      block=96, threads=1)
+    many = lpgen.planted_dense_blocked(m, n, seed=7, storage=storage, col_scale_log10=scale,
+                                       block=96, threads=5)
+    assert np.array_equal(one.storage_array(), many.storage_array())
+    assert np.array_equal(one.b, many.b) and np.array_equal(one.c, many.c)
+    st = one.storage_array()
+    assert st.shape == (n, m)
+    A = one.dense()
+    assert A.shape == (m, n) and A.dtype == np.float64
+    if storage == "bf16":
+        assert st.dtype == np.uint16
+        assert np.array_equal(A, lpgen.round_bf16(A))        # values are bf16-representable
+    if storage == "f32":
+        assert np.array_equal(A, A.astype(np.float32).astype(np.float64))
+        lg = np.log10(np.linalg.norm(A, axis=0) / np.sqrt(m))
+        assert lg.min() < -1.5 and lg.max() > 1.5
+    # the planted optimum is exact for the stored values
+    assert np.allclose(A @ one.x_star, one.b, rtol=1e-13, atol=1e-12)
+    assert np.allclose(one.c - A.T @ one.y_star, one.s_star, rtol=1e-13, atol=1e-12)
+    assert np.all(one.x_star * one.s_star == 0) and np.count_nonzero(one.x_star) == m
+    # the entries look like N(0, 1) draws and differ across seeds and blocks
+    if scale is None:
+        assert abs(A.mean()) < 0.05 and abs(A.std() - 1) < 0.05
+    other = lpgen.planted_dense_blocked(m, n, seed=8, storage=storage, block=96)
+    assert not np.array_equal(other.storage_array(), st)
+    assert not np.array_equal(st[:96], st[96:192])
+
+
+def test_c4_workload_uses_the_blocked_generator():
+    small = lpgen.config_small("c4", 64)
+    assert small.cols is not None and small.storage == "bf16"
+    assert (small.m, small.n) == (32, 8192)
