@@ -1,20 +1,30 @@
 """Benchmark: seconds per LP solve to a relative duality gap of 1e-8 on one GB300.
 
 Workload (one "step" = one full lp_solve from the infeasible start x0 = s0 = 1,
-y0 = 0): a planted dense LP with m = 512 constraints and n = 131072 variables,
-N(0,1) entries with every column scaled by 10**U(-2, 2), stored in FP32
-(268 MB, larger than the 129 MB L2, so every A-pass streams from HBM);
-CountSketch with w = 4m = 2048 and s = 4 nonzeros per row.
+y0 = 0), chosen with --config:
+  c4 (default)  planted dense LP, m = 2048 constraints, n = 524288 variables,
+                N(0,1) entries stored in BF16 (2.15 GB, far larger than the
+                129 MB L2, so every A-pass streams from HBM); CountSketch with
+                w = 4m = 8192 and s = 2 nonzeros per row
+  c2            planted dense LP, m = 512, n = 131072, N(0,1) entries with
+                every column scaled by 10**U(-2, 2), stored in FP32 (268 MB);
+                CountSketch w = 2048, s = 4
 
 Printed JSON line (rank 0):
-  value       device-timed seconds per LP solve (inputs resident in HBM)
+  value       device-timed seconds per LP solve (inputs resident in HBM); with
+              --gpus N the slowest replica's (every rank solves its own LP)
   e2e         the same through the C ABI with host buffers: lp_create from
               pinned host A, b, c + lp_solve + copy of x, y, s back, per step
-  roofline    the hot kernel (fused FP32 A diag(d2) A^T v): algorithmic bytes per
-              launch / mean CUDA-event duration of its launches inside the timed
-              solves, against the measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle (exact-Cholesky IPM, FP64 NumPy) timed on this
-              host on a bounded sample of the same LP, scaled to one solve
+  roofline    the hot kernel (the inner-loop product A diag(d2) A^T v in FP32
+              arithmetic): algorithmic bytes per launch / mean CUDA-event
+              duration of its launches inside the timed solves, against the
+              measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle (exact-Cholesky IPM, FP64 NumPy) on this host:
+              one whole timed solve of the same LP where that fits the run
+              (c2); for c4, outer iterations of the same LP timed live and
+              scaled by the oracle's own outer-iteration count on that LP
+              (tests/golden/oracle_solves.json), marked as an estimate
+  oracle      the GPU objective against the oracle's objective on the same LP
   clocks      nvidia-smi samples taken during the timed region
 
 --impl reference times that CPU oracle as the reference arm.
@@ -39,11 +49,35 @@ import numpy as np  # noqa: E402
 
 import lpgen  # noqa: E402
 
-M, N_COLS, W_FACTOR, S_BLOCKS = 512, 131072, 4.0, 4
 TOL = 1e-8
 METRIC = "LP solve s to rel gap 1e-8"
-WORKLOAD = ("planted dense LP m=512 n=131072 FP32 storage, columns scaled 10^U(-2,2), "
-            "infeasible start x0=s0=1 y0=0, CountSketch w=2048 s=4")
+DEFAULT_CONFIG = "c4"
+ORACLE_RECORDS = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+
+# the workloads the bench times; sizes and solver options as in lpgen.CONFIGS
+BENCH = {
+    "c4": dict(
+        m=2048, n=524288, dtype="bf16", s=2, w_factor=4.0, whole_oracle=False,
+        workload=("planted dense LP m=2048 n=524288 BF16 storage, N(0,1) entries, "
+                  "infeasible start x0=s0=1 y0=0, CountSketch w=8192 s=2"),
+        l2="inputs larger than L2 (A = 2.15 GB BF16)",
+        dtype_detail=("A stored BF16; inner-loop products in FP32 with FP32 accumulation; residual "
+                      "refresh, residuals, directions, sketch sums and factor in double-float "
+                      "(FP64-class); FP64 vectors, dots and step lengths"),
+        kernel="k_rows (A diag(d2) A^T v, BF16 storage, FP32 arithmetic, row-split)",
+        sources=("stream_rows.cu", "stream_dev.cuh", "stream.cuh", "common.cuh", "df.cuh"),
+        traffic="traffic_k_rows_m2048_n524288_bf16.json"),
+    "c2": dict(
+        m=512, n=131072, dtype="f32", s=4, w_factor=4.0, whole_oracle=True,
+        workload=("planted dense LP m=512 n=131072 FP32 storage, columns scaled 10^U(-2,2), "
+                  "infeasible start x0=s0=1 y0=0, CountSketch w=2048 s=4"),
+        l2="inputs larger than L2 (A = 268 MB FP32)",
+        dtype_detail=("A stored FP32; products FP32 with FP32 accumulation in the inner loop, "
+                      "FP64-class residual refresh, FP64 vectors, sketch, factor and step lengths"),
+        kernel="k_adat_fused (A diag(d2) A^T v, FP32)",
+        sources=("stream.cu", "stream_dev.cuh", "stream.cuh", "common.cuh", "df.cuh"),
+        traffic="traffic_k_adat_fused_m512_n131072.json"),
+}
 
 
 def load_peaks():
@@ -54,26 +88,23 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# the translation unit of the hot kernel and the headers it is built from
-HOT_KERNEL_SOURCES = ("stream.cu", "stream_dev.cuh", "stream.cuh", "common.cuh", "df.cuh")
-
-
-def hot_kernel_source_hash() -> str:
+def hot_kernel_source_hash(sources) -> str:
+    """sha256 over the hot kernel's translation unit and the headers it is built from."""
     import hashlib
     h = hashlib.sha256()
-    for f in HOT_KERNEL_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2209_08722_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
 
-def traffic_record():
+def traffic_record(cfg):
     """Per-launch DRAM bytes of the hot kernel from the committed ncu summary,
     valid only while the kernel's sources are unchanged."""
-    p = os.path.join(ROOT, "profiles", "traffic_k_adat_fused_m512_n131072.json")
+    p = os.path.join(ROOT, "profiles", cfg["traffic"])
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    if hot_kernel_source_hash() != rec.get("kernel_sources_sha256"):
+    if hot_kernel_source_hash(cfg["sources"]) != rec.get("kernel_sources_sha256"):
         return None
     return float(rec["dram_bytes_per_launch"])
 
@@ -120,8 +151,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_lp(seed: int):
-    return lpgen.planted_dense(M, N_COLS, seed=seed, storage="f32", col_scale_log10=(-2.0, 2.0))
+def make_lp(name: str, seed: int):
+    return lpgen.make(lpgen.CONFIGS[name], seed=seed)
 
 
 def replica_seed(rank: int) -> int:
@@ -139,34 +170,74 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
-def oracle_sample(lp, budget_s: float = 20.0):
-    """Times the CPU oracle (exact-Cholesky IPM) on the full LP for a bounded
-    number of outer iterations, and counts the outer iterations it needs on the
-    same LP family at 1/8 size; returns (seconds per solve, description, cores)."""
+def oracle_record(name: str, lp):
+    """The oracle's own whole solve of this LP, recorded by
+    tests/golden/make_oracle_records.py (None when absent or for another LP)."""
+    if not os.path.exists(ORACLE_RECORDS):
+        return None
+    rec = json.load(open(ORACLE_RECORDS)).get(name)
+    if not rec or (rec["m"], rec["n"], rec["seed"]) != (lp.m, lp.n, lpgen.CONFIGS[name]["seed"]):
+        return None
+    if abs(rec["planted_objective"] - lp.objective) > 1e-9 * (1 + abs(lp.objective)):
+        return None
+    return rec
+
+
+def oracle_whole_solve(lp):
+    """One whole timed solve of the CPU oracle (exact-Cholesky FP64 IPM,
+    Algorithm 3 from x0 = s0 = 1, y0 = 0); returns (seconds, outer
+    iterations, objective)."""
     from oracle import ipm
-    A = lp.A
+    A = lp.dense()
     t0 = time.perf_counter()
-    its = 0
-    opt = ipm.Options(mode="infeasible", solver="exact", k_max=1)
-    # time outer iterations one at a time until the budget is used (>= 2)
-    x = y = s = None
-    while True:
-        res = ipm.solve(A, lp.b, lp.c, opt, x, y, s)
-        x, y, s = res.x, res.y, res.s
-        its += 1
-        if time.perf_counter() - t0 > budget_s or its >= 30:
-            break
-    per_it = (time.perf_counter() - t0) / its
-    small = lpgen.planted_dense(M // 8, N_COLS // 8, seed=0, storage="f32", col_scale_log10=(-2.0, 2.0))
-    full = ipm.solve(small.A, small.b, small.c, ipm.Options(mode="infeasible", solver="exact"))
-    outer = full.iterations
-    desc = (f"{its} outer iterations of the exact-Cholesky FP64 oracle on the full 512x131072 LP "
-            f"({per_it:.3f} s each) x {outer} outer iterations (the oracle's count on the same "
-            f"LP family at m/8, n/8)")
-    return per_it * outer, desc, os.cpu_count()
+    res = ipm.solve(A, lp.b, lp.c, ipm.Options(mode="infeasible", solver="exact", tol=TOL))
+    return time.perf_counter() - t0, res.iterations, float(lp.c @ res.x)
 
 
-def oracle_sketched_sample(lp, outer: int, inner: int):
+class OracleStepper:
+    """The CPU oracle run one outer iteration at a time along its own
+    trajectory from the default start (each call continues from the iterate
+    the previous call left)."""
+
+    def __init__(self, lp):
+        from oracle import ipm
+        self.ipm = ipm
+        self.lp = lp
+        self.A = lp.dense()
+        self.state = (None, None, None)
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        res = self.ipm.solve(self.A, self.lp.b, self.lp.c,
+                             self.ipm.Options(mode="infeasible", solver="exact", tol=TOL, k_max=1),
+                             *self.state)
+        dt = time.perf_counter() - t0
+        self.state = (res.x, res.y, res.s)
+        return dt
+
+
+def oracle_estimate(name: str, lp, budget_s: float, gpu_outer: int):
+    """Seconds per oracle solve of an LP too large to solve whole within the
+    run: outer iterations timed live (at least one, until budget_s) times the
+    oracle's own outer-iteration count on this LP from its recorded whole solve
+    (the GPU solve's count when no record exists).  Returns (seconds,
+    description, cores, record)."""
+    st = OracleStepper(lp)
+    times = []
+    t0 = time.perf_counter()
+    while not times or time.perf_counter() - t0 < budget_s:
+        times.append(st.step())
+    per_it = float(np.mean(times))
+    rec = oracle_record(name, lp)
+    outer = rec["outer_iterations"] if rec else gpu_outer
+    src = ("the oracle's own count on this LP, from its recorded whole solve" if rec
+           else "the GPU solve's count on this LP: no recorded oracle solve")
+    desc = (f"estimate: {len(times)} outer iteration(s) of the exact-Cholesky FP64 oracle on the full "
+            f"{lp.m}x{lp.n} LP timed here ({per_it:.2f} s each) x {outer} outer iterations ({src})")
+    return per_it * outer, desc, os.cpu_count(), rec
+
+
+def oracle_sketched_sample(lp, cfg, outer: int, inner: int):
     """Times the CPU sketched oracle (the paper's method in FP64: CountSketch W,
     SVD preconditioner, CG, correction v) on the full LP.  Two outer
     iterations from the default start, one with exactly 1 CG step and one with
@@ -177,8 +248,8 @@ def oracle_sketched_sample(lp, outer: int, inner: int):
     from oracle import ipm
 
     def one(t_max):
-        opt = ipm.Options(mode="infeasible", solver="sketch", s=S_BLOCKS, w=int(W_FACTOR * M), k_max=1,
-                          inner_rule="relative", tol_cg=0.0, t_max=t_max)
+        opt = ipm.Options(mode="infeasible", solver="sketch", s=cfg["s"], w=int(cfg["w_factor"] * lp.m),
+                          k_max=1, inner_rule="relative", tol_cg=0.0, t_max=t_max)
         t0 = time.perf_counter()
         r = ipm.solve(lp.A, lp.b, lp.c, opt)
         return time.perf_counter() - t0, r.history[0].inner_its
@@ -188,7 +259,7 @@ def oracle_sketched_sample(lp, outer: int, inner: int):
     t_cg = max(tb - ta, 0.0) / max(ib - ia, 1)
     t_outer = max(ta - ia * t_cg, 0.0)
     value = outer * t_outer + inner * t_cg
-    desc = (f"the FP64 sketched oracle on the full 512x131072 LP: {t_outer:.3f} s per outer iteration "
+    desc = (f"the FP64 sketched oracle on the full {lp.m}x{lp.n} LP: {t_outer:.3f} s per outer iteration "
             f"(sketch, SVD, v, residuals, directions, steps) and {t_cg * 1e3:.2f} ms per CG step, "
             f"measured from outer iterations with 1 and 21 CG steps, at this solve's {outer} outer "
             f"and {inner} inner iterations")
@@ -196,23 +267,44 @@ def oracle_sketched_sample(lp, outer: int, inner: int):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on this host's cores.
+    Where a whole oracle solve fits the run (c2) every step is one whole
+    solve; otherwise (c4) every step is one outer iteration of the same LP
+    (continuing along the oracle's trajectory) and the value scales the mean
+    step by the oracle's recorded outer-iteration count on that LP.  The
+    oracle has no state to warm, so the warm-up steps are not run."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    lp = make_lp(0)
-    per_steps = []
-    desc, cores = "", os.cpu_count()
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state worth timing separately
-    for _ in range(args.steps):
-        v, desc, cores = oracle_sample(lp, budget_s=max(5.0, 60.0 / max(1, args.steps)))
-        per_steps.append(v)
-    value = float(np.median(per_steps))
+    cfg = BENCH[args.config]
+    lp = make_lp(args.config, 0)
+    cores = os.cpu_count()
+    if cfg["whole_oracle"]:
+        per = [oracle_whole_solve(lp)[0] for _ in range(args.steps)]
+        value = float(np.mean(per))
+        ms_step = value * 1000.0
+        desc = f"{args.steps} whole solves of the exact-Cholesky FP64 oracle on the full {lp.m}x{lp.n} LP"
+    else:
+        st = OracleStepper(lp)
+        per = [st.step() for _ in range(args.steps)]
+        ms_step = float(np.mean(per)) * 1000.0
+        rec = oracle_record(args.config, lp)
+        outer = rec["outer_iterations"] if rec else None
+        if outer is None:
+            print(json.dumps({"impl": "reference", "unavailable": "no recorded oracle solve of this LP "
+                              "(tests/golden/oracle_solves.json) to scale the timed outer iterations"}))
+            return 0
+        value = ms_step / 1000.0 * outer
+        desc = (f"estimate: {args.steps} outer iterations of the exact-Cholesky FP64 oracle on the full "
+                f"{lp.m}x{lp.n} LP, one per step ({ms_step / 1000.0:.2f} s each), x {outer} outer "
+                f"iterations (the oracle's own count on this LP, from its recorded whole solve)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": value * 1000.0, "higher_is_better": False, "scaling": "weak",
+            "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (A = 268 MB FP32)"},
+            "config": {"workload": cfg["workload"], "l2": cfg["l2"]},
+            "step": ("one whole oracle solve" if cfg["whole_oracle"]
+                     else "one outer iteration of the oracle; value = mean step x outer iterations"),
             "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -221,15 +313,17 @@ def run_reference(args):
 
 
 def run_kernel(args):
-    """Microbenchmark of the fused FP32 product on the bench's A (used for the
-    ncu captures in profiles/): W warm-up launches, then K timed launches."""
+    """Microbenchmark of the inner-loop FP32 product on the configured workload's
+    A (used for the ncu captures in profiles/): W warm-up launches, then K timed
+    launches."""
     import torch
     from paper_2209_08722_gb300 import LPSolver
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    lp = make_lp(0)
+    cfg = BENCH[args.config]
+    lp = make_lp(args.config, 0)
     stream = torch.cuda.current_stream()
-    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=S_BLOCKS,
-                      w_factor=W_FACTOR, profile=1, stream=stream.cuda_stream)
+    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype=cfg["dtype"], s=cfg["s"],
+                      w_factor=cfg["w_factor"], profile=1, stream=stream.cuda_stream)
     rng = np.random.default_rng(0)
     d2 = torch.from_numpy(np.exp(rng.uniform(-5, 5, lp.n))).cuda()
     v = torch.from_numpy(rng.standard_normal(lp.m)).cuda()
@@ -242,7 +336,7 @@ def run_kernel(args):
     peak, kind = load_peaks()
     ms = st["ms"] / max(1, st["launches"])
     gbs = st["bytes_per_launch"] / (ms * 1e-3) / 1e9
-    print(json.dumps({"kernel": "k_adat_fused", "workload": WORKLOAD, "launches": st["launches"],
+    print(json.dumps({"kernel": cfg["kernel"], "workload": cfg["workload"], "launches": st["launches"],
                       "mean_ms": ms, "bytes_per_launch": st["bytes_per_launch"],
                       "achieved_gbs": gbs, "peak_gbs": peak, "peak_kind": kind,
                       "frac": gbs / peak}), flush=True)
@@ -251,18 +345,19 @@ def run_kernel(args):
 
 
 def run_gauss_kernel(args):
-    """Microbenchmark of the Gaussian sketch A D W_G (Section 6) on the bench's A,
-    w = 2048: the tcgen05 split-TF32 product ("gauss") or the FP32 SIMT product
+    """Microbenchmark of the Gaussian sketch A D W_G (Section 6) on the configured
+    workload's A, w = 4m: the tcgen05 split-TF32 product ("gauss") or the FP32 SIMT product
     ("gauss-simt").  Each timed call is lp_sketch: zero-fill, the product, and a
     device copy of the m x w FP64 result.  Algorithmic FLOPs = 2 m n w."""
     import torch
     from paper_2209_08722_gb300 import LPSolver
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    lp = make_lp(0)
+    cfg = BENCH[args.config]
+    lp = make_lp(args.config, 0)
     stream = torch.cuda.current_stream()
     tensor = 1 if args.kernel == "gauss" else 0
-    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", sketch=1,
-                      w_factor=W_FACTOR, tensor_sketch=tensor, stream=stream.cuda_stream)
+    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype=cfg["dtype"], sketch=1,
+                      w_factor=cfg["w_factor"], tensor_sketch=tensor, stream=stream.cuda_stream)
     rng = np.random.default_rng(0)
     D = torch.from_numpy(np.exp(rng.uniform(-3, 3, lp.n))).cuda()
     for i in range(args.warmup):
@@ -413,35 +508,39 @@ def run_warm_start(args):
     return 0
 
 
-def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk):
+def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk,
+              oracle=None, cfg=None):
     """The JSON line of the default run: the metric and its run keys plus roofline,
-    cpu_baseline, cpu_sketched, e2e, gpu_launches, clocks and the solve's
-    counts.  Pure host code (reads the measured peaks and the traffic record)."""
+    cpu_baseline, e2e, gpu_launches, clocks, the solve's counts and the
+    comparison with the oracle's objective.  Pure host code (reads the
+    measured peaks and the traffic record).  `value` is the slowest replica's
+    seconds per solve at any number of GPUs (each rank solves its own LP);
+    the replicas' combined rate is given beside it."""
+    cfg = cfg or BENCH[getattr(args, "config", DEFAULT_CONFIG)]
     peak, peak_kind = load_peaks()
     launches = stats["launches"]
     k_ms = stats["ms"] / max(1, launches)
     achieved = stats["bytes_per_launch"] / (k_ms * 1e-3) / 1e9 if launches else None
-    traffic = traffic_record()
+    traffic = traffic_record(cfg)
     gpu_launches = stats["all_launches"]
-    value = ms_per_step / 1000.0 / world
+    value = ms_per_step / 1000.0
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "dtype_detail": "A stored FP32; products FP32 with FP32 accumulation in the inner loop, "
-                        "FP64 residual refresh, FP64 vectors, sketch, QR and step lengths",
+        "scaling": "weak", "vs_baseline": None, "dtype": cfg["dtype"],
+        "dtype_detail": cfg["dtype_detail"],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (A = 268 MB FP32)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_adat_fused (A diag(d2) A^T v, FP32)",
+        "config": {"workload": cfg["workload"], "l2": cfg["l2"],
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "replicas": {"count": world, "lps_per_s": world / value if value > 0 else None},
+        "roofline": {"bound": "hbm", "kernel": cfg["kernel"],
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "bytes_per_launch": stats["bytes_per_launch"], "launches": launches,
                      "mean_launch_ms": k_ms},
         "cpu_baseline": cpu,
-        "cpu_sketched": cpu_sk,
-        "e2e": {"value": e2e / 1000.0 / world, "unit": "s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e2e / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": gpu_launches,
         "clocks": clk,
@@ -451,6 +550,10 @@ def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, cl
                   "ms_phases": {k: infos[-1][k] for k in ("ms_residual", "ms_factor", "ms_inner",
                                                           "ms_correction", "ms_step")}},
     }
+    if cpu_sk is not None:
+        line["cpu_sketched"] = cpu_sk
+    if oracle is not None:
+        line["oracle"] = oracle
     return line
 
 
@@ -459,6 +562,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", choices=sorted(BENCH), default=DEFAULT_CONFIG,
+                    help="workload: c4 (2048 x 524288 BF16, default) or c2 (512 x 131072 FP32)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warm-start", action="store_true",
@@ -466,7 +571,7 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="time N LPs of the batched family one at a time and batched")
     ap.add_argument("--kernel", choices=["adat", "gauss", "gauss-simt"], default=None,
-                    help="time one kernel on the same A: the hot product (lp_adat, FP32), or the "
+                    help="time one kernel on the workload's A: the hot product (lp_adat, FP32), or the "
                          "Gaussian sketch on the tensor cores / FP32 SIMT")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -483,6 +588,7 @@ def main():
     import torch
     from paper_2209_08722_gb300 import LPSolver
 
+    cfg = BENCH[args.config]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -497,10 +603,11 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    lp = make_lp(replica_seed(rank))
+    lp = make_lp(args.config, replica_seed(rank))
+    opts = dict(dtype=cfg["dtype"], s=cfg["s"], w_factor=cfg["w_factor"])
     stream = torch.cuda.current_stream()
-    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=S_BLOCKS,
-                      w_factor=W_FACTOR, profile=1, stream=stream.cuda_stream)
+    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, profile=1, stream=stream.cuda_stream,
+                      **opts)
     info = None
     for _ in range(args.warmup):
         x, y, s, info = solver.solve(tol=TOL)
@@ -522,7 +629,8 @@ def main():
     stats = solver.kernel_stats()
     ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
-    obj_err = abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective))
+    obj = float(lp.c @ x)
+    obj_err = abs(obj - lp.objective) / (1 + abs(lp.objective))
     assert all(i["status"] == 0 for i in infos), infos
     assert obj_err <= 1e-7, obj_err
 
@@ -540,8 +648,7 @@ def main():
     for it in range(args.warmup + args.steps):
         barrier()
         t0 = time.perf_counter()
-        sv = LPSolver(pinA, pinb, pinc, lp.m, lp.n, dtype="f32", s=S_BLOCKS, w_factor=W_FACTOR,
-                      stream=stream.cuda_stream)
+        sv = LPSolver(pinA, pinb, pinc, lp.m, lp.n, stream=stream.cuda_stream, **opts)
         _, _, _, inf2 = sv.solve(tol=TOL, out=outs)
         sv.close()
         torch.cuda.synchronize()
@@ -550,23 +657,38 @@ def main():
         if it >= args.warmup:
             e2e_ms.append(dt)
     e2e = max_over_ranks(float(np.mean(e2e_ms)), dist, "cuda")
+    del pinA
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
-    cpu = cpu_sk = None
-    if not args.no_cpu_baseline:
-        v, desc, cores = oracle_sample(lp, budget_s=20.0)
-        cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": desc}
-        try:  # context only: a failure here must not cost the line
-            v, desc, cores = oracle_sketched_sample(lp, infos[-1]["outer_iterations"],
-                                                    infos[-1]["inner_total"])
-            cpu_sk = {"value": v, "unit": "s", "cores": cores, "kind": "oracle (sketched method)",
-                      "sample": desc}
-        except Exception as e:  # noqa: BLE001
-            cpu_sk = {"value": None, "error": f"{type(e).__name__}: {e}"}
-    line = ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk)
+    cpu = cpu_sk = oracle = None
+    if not args.no_cpu_baseline and world == 1:
+        if cfg["whole_oracle"]:
+            secs, its, o_obj = oracle_whole_solve(lp)
+            cpu = {"value": secs, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"one whole timed solve of the exact-Cholesky FP64 oracle on the same "
+                             f"{lp.m}x{lp.n} LP ({its} outer iterations)", "estimate": False}
+            oracle = {"objective": o_obj, "outer_iterations": its, "source": "whole solve in this run",
+                      "gpu_objective_rel_diff": abs(obj - o_obj) / (1 + abs(o_obj))}
+            try:  # context only: a failure here must not cost the line
+                v, desc, cores = oracle_sketched_sample(lp, cfg, infos[-1]["outer_iterations"],
+                                                        infos[-1]["inner_total"])
+                cpu_sk = {"value": v, "unit": "s", "cores": cores, "kind": "oracle (sketched method)",
+                          "sample": desc}
+            except Exception as e:  # noqa: BLE001
+                cpu_sk = {"value": None, "error": f"{type(e).__name__}: {e}"}
+        else:
+            v, desc, cores, rec = oracle_estimate(args.config, lp, 20.0, infos[-1]["outer_iterations"])
+            cpu = {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": desc,
+                   "estimate": True}
+            if rec:
+                oracle = {"objective": rec["objective"], "outer_iterations": rec["outer_iterations"],
+                          "source": "recorded whole solve (tests/golden/oracle_solves.json)",
+                          "gpu_objective_rel_diff": abs(obj - rec["objective"]) / (1 + abs(rec["objective"]))}
+    line = ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk,
+                     oracle, cfg)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

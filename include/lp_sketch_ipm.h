@@ -56,7 +56,7 @@ typedef struct lp_handle lp_handle;
                                       tolerance while a residual test still fails */
 
 /* ---- matrix description -------------------------------------------------- */
-typedef enum { LP_DENSE_COLMAJOR = 0, LP_CSC = 1 } lp_format;
+typedef enum { LP_DENSE_COLMAJOR = 0, LP_CSC = 1, LP_CSR = 2 } lp_format;
 typedef enum { LP_F64 = 0, LP_F32 = 1, LP_BF16 = 2 } lp_dtype;
 
 typedef struct {
@@ -65,11 +65,12 @@ typedef struct {
     int32_t fmt;          /* lp_format */
     int32_t dtype;        /* lp_dtype of the stored values; the LP solved is the one
                              with these (rounded) values */
-    const void* val;      /* dense: column j at val + j*ld; CSC: nnz values */
-    int64_t ld;           /* dense: leading dimension (>= m); ignored for CSC */
-    const int64_t* ptr;   /* CSC: n+1 column pointers (ptr[0] = 0) */
-    const int32_t* idx;   /* CSC: nnz row indices in [0, m) */
-    int64_t nnz;          /* CSC: number of stored entries */
+    const void* val;      /* dense: column j at val + j*ld; CSC/CSR: nnz values */
+    int64_t ld;           /* dense: leading dimension (>= m); ignored for CSC/CSR */
+    const int64_t* ptr;   /* CSC: n+1 column pointers; CSR: m+1 row pointers (ptr[0] = 0) */
+    const int32_t* idx;   /* CSC: nnz row indices in [0, m); CSR: nnz column indices in
+                             [0, n) (so n < 2^31) */
+    int64_t nnz;          /* CSC/CSR: number of stored entries */
     int32_t on_device;    /* 1: val/ptr/idx are device pointers */
 } lp_matrix;
 
@@ -175,17 +176,36 @@ typedef struct {
 /* Fills `opt` with the defaults listed above. */
 void lp_options_default(lp_options* opt);
 
-/* Copies A (dense column-major or CSC), b (m) and c (n) to the device in the
- * handle's layout and allocates every workspace the solver needs.  `bc_on_device`
- * says where b and c live.  Errors: LP_ERR_ARG (sizes, m > n, bad CSC, bad
- * options, a sketch width below m), LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_UNSUPPORTED
- * (a shape the library's kernels do not cover).  On error *h is NULL and
- * lp_create_error() says why.  Errors in the arguments themselves (pointers,
- * sizes, the CSC structure of a host matrix, the options, the sketch width)
- * are reported before any CUDA call is made; NaN/Inf in b or c is found on
- * the device. */
+/* Copies A (dense column-major, CSC or CSR), b (m) and c (n) to the device in
+ * the handle's layout and allocates every workspace the solver needs.  The
+ * sparse kernels stream A by columns (the product A D^2 A^T v of eq. normal
+ * gathers a_j^T v and scatters a_j t_j per column), so a CSR matrix is sorted
+ * into CSC on the host (a device CSR is first read back); each column's entries
+ * then come in increasing row order, and the handle is the same as the one
+ * created from the equivalent CSC input with sorted rows.  CSR and CSC values
+ * are FP32 or FP64.  `bc_on_device` says where b and c live.  Errors:
+ * LP_ERR_ARG (sizes, m > n, bad CSC or CSR structure, bad options, a sketch
+ * width below m), LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_UNSUPPORTED (a shape the
+ * library's kernels do not cover, BF16 sparse values, the Gaussian sketch with
+ * a sparse A).  On error *h is NULL and lp_create_error() says why.  Errors in
+ * the arguments themselves (pointers, sizes, the CSC or CSR structure of a host
+ * matrix, the options, the sketch width) are reported before any CUDA call is
+ * made; the structure of a device CSR is checked after it is read back;
+ * NaN/Inf in b or c is found on the device. */
 int lp_create(lp_handle** h, const lp_matrix* A, const double* b, const double* c,
               int32_t bc_on_device, const lp_options* opt);
+
+/* The CSR -> CSC sort that lp_create applies to an LP_CSR matrix, offered on
+ * its own (host memory only, no CUDA call; the paper has no counterpart: it
+ * states the problem for a given A, Section 1).  row_ptr (m+1, row_ptr[0] = 0,
+ * row_ptr[m] = nnz, non-decreasing), col_idx (nnz, in [0, n)), val (nnz
+ * values of `dtype`) -> col_ptr (n+1), row_idx (nnz), val_out (nnz), all
+ * caller-owned.  A stable counting sort on the column index: every column's
+ * entries come out in increasing row order (entries of one row keep their
+ * order), duplicates are kept.  Returns LP_OK, or LP_ERR_ARG for NULL
+ * pointers, sizes out of range (n < 2^31) or an invalid CSR structure. */
+int lp_csr_to_csc(int32_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                  const void* val, int32_t dtype, int64_t* col_ptr, int32_t* row_idx, void* val_out);
 
 /* Frees the handle and everything it owns.  NULL is accepted. */
 int lp_destroy(lp_handle* h);
@@ -250,6 +270,21 @@ int lp_normal_solve(lp_handle* h, const double* D, const double* p, const double
  * (FP32/BF16 storage; FP64 storage always computes in FP64); 1: FP64. */
 int lp_adat(lp_handle* h, const double* d2, const double* v, double* u, int32_t precision);
 
+/* Health check of the bounded device-side waits (the paper has no
+ * counterpart: this is the failure detection of the GPU pipelines).  Every
+ * pipeline wait on an mbarrier gives up after a spin limit (about 1 s),
+ * records the timeout in the handle's device status word, waits (again
+ * bounded) for its own copies in flight and returns, and the call that
+ * launched it returns LP_ERR_DEVICE_TIMEOUT.  This call runs that same wait in
+ * one thread on the handle's stream with a spin limit of `spin_cycles`
+ * clock64 cycles (1 .. 2^31): with complete = 1 the thread completes the
+ * barrier's phase first and the call returns LP_OK; with complete = 0 nothing
+ * completes it, so the wait gives up after spin_cycles cycles and the call
+ * returns LP_ERR_DEVICE_TIMEOUT.  Nothing else runs and nothing is left in
+ * flight; the handle stays usable (every call starts from a clear status
+ * word).  LP_ERR_ARG for a NULL handle or arguments out of range. */
+int lp_wait_probe(lp_handle* h, int64_t spin_cycles, int32_t complete);
+
 /* Residuals and right-hand side of Algorithm 3 step 3 (Section 5) or eq. pdef:
  * r_p = A x - b (m), r_d = A^T y + s - c (n), mu = x^T s / n, and
  *   infeasible: p = -r_p - sigma mu A S^{-1} 1 + A x - A D^2 r_d
@@ -295,18 +330,22 @@ int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
  * the FP32 product of the solver's inner loop offered outside a handle.
  *   A   device pointer, column-major, leading dimension ld (elements) with
  *       ld * element size a multiple of 16 bytes, 16-byte aligned, holding
- *       n * ld elements; dtype LP_F32 or LP_BF16.
+ *       n * ld elements; dtype LP_F32 or LP_BF16.  Rows m .. ld-1 of each
+ *       column are padding: they are read but never used, whatever they hold.
  *   d2 (n), v (m), u (m): FP64 device vectors owned by the caller.
- *   stream: cudaStream_t or NULL.  The call returns after the product is done.
+ *   stream: cudaStream_t or NULL.
+ * The call is synchronous: it returns after the product is done (it reads a
+ * status word back and synchronises the stream), so it must not be called
+ * while a stream is being captured into a CUDA graph.
  * Scratch lives in one fixed 4 MiB __device__ array inside the library, kept by
  * every device that used it until the library is unloaded; its address is
- * looked up on the first call on a device, so make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller.  Sizes whose scratch would not fit (about ld > 5000) and m beyond the
- * kernel's register tile (2048 rows in FP32, 4096 in BF16) return LP_ERR_ARG;
- * nothing is allocated in any case.  Returns LP_OK, LP_ERR_ARG, LP_ERR_CUDA or
- * LP_ERR_DEVICE_TIMEOUT. */
+ * looked up on the first call on each device.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  The limit is on the leading dimension,
+ * not on m: ld up to 2048 in FP32 and 4096 in BF16 (the kernel's register
+ * tile; the fixed array holds the partial sums of any such ld); a larger ld
+ * returns LP_ERR_ARG.  Nothing is allocated in any case.  Returns LP_OK, LP_ERR_ARG,
+ * LP_ERR_CUDA or LP_ERR_DEVICE_TIMEOUT. */
 int lp_adat_noalloc(const void* A, int32_t dtype, int32_t m, int64_t n, int64_t ld,
                     const double* d2, const double* v, double* u, void* stream);
 
@@ -320,7 +359,8 @@ int lp_adat_noalloc(const void* A, int32_t dtype, int32_t m, int64_t n, int64_t 
  * optimum has z = 0; the interior x > 0 it returns is then moved onto A x = b by
  * the minimum-norm correction x0 = x + A^T (A A^T)^{-1} (b - A x), computed with
  * the sketched normal-equation solver (D = I).
- * A: host matrix (dense column-major or CSC, any storage dtype); b: host m-vector;
+ * A: host matrix (dense column-major, CSC or CSR, any storage dtype; CSR is
+ * sorted into CSC first); b: host m-vector;
  * opt: NULL for defaults; x0: caller-owned host n-vector, written when the LP is
  * found feasible.  Returns LP_OK with x0 > 0 and A x0 = b to rounding,
  * LP_ERR_NOT_FEASIBLE when the phase-1 optimum 1^T z exceeds
@@ -328,9 +368,10 @@ int lp_adat_noalloc(const void* A, int32_t dtype, int32_t m, int64_t n, int64_t 
  * correction leaves some x0_j <= 0, or the error of the inner calls.
  * LP_ERR_ARG, before anything is read or any CUDA call is made: a NULL
  * argument, tol <= 0, a device matrix, m or n < 1, a bad format or dtype, a
- * NULL value array, ld < m (dense), or a CSC matrix without pointers or
+ * NULL value array, ld < m (dense), a CSC matrix without pointers or
  * indices, with ptr[0] < 0 or with decreasing column pointers (a row index
- * out of range is found while the phase-1 matrix is built). */
+ * out of range is found while the phase-1 matrix is built), or a CSR matrix
+ * whose structure is not valid. */
 typedef struct {
     double z_sum;               /* 1^T z at the phase-1 solution */
     double residual;            /* ||A x0 - b|| after the correction */

@@ -25,7 +25,7 @@ LP_STATUS_MAX_ITER = 1
 LP_WARN_INNER_MAXIT = 2
 LP_STATUS_STALLED = 3
 
-LP_DENSE_COLMAJOR, LP_CSC = 0, 1
+LP_DENSE_COLMAJOR, LP_CSC, LP_CSR = 0, 1, 2
 LP_F64, LP_F32, LP_BF16 = 0, 1, 2
 LP_SKETCH_COUNT, LP_SKETCH_GAUSS = 0, 1
 LP_INNER_CG, LP_INNER_CHEBYSHEV = 0, 1
@@ -121,6 +121,8 @@ SIGNATURES = {
     "lp_step_lengths": (c_int32, [P, P, P, P, P, c_int32, c_double, c_double, P]),
     "lp_get_history": (c_int32, [P, POINTER(LpIterRecord), c_int32]),
     "lp_adat_noalloc": (c_int32, [P, c_int32, c_int32, c_int64, c_int64, P, P, P, P]),
+    "lp_wait_probe": (c_int32, [P, c_int64, c_int32]),
+    "lp_csr_to_csc": (c_int32, [c_int32, c_int64, c_int64, P, P, P, c_int32, P, P, P]),
     "lp_phase1_start": (c_int32, [POINTER(LpMatrix), P, POINTER(LpOptions), c_double, P,
                                   POINTER(LpPhase1Info)]),
     "lp_solve_batch": (c_int32, [POINTER(P), c_int32, c_double, c_int32, c_int32, POINTER(P),

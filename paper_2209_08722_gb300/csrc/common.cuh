@@ -118,17 +118,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on phase `parity`; false (and err = ERR_TIMEOUT) after ~1 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Bounded wait on phase `parity`: false (and err = ERR_TIMEOUT) once `limit`
+// clock64 cycles have passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* err, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kSpinCycles) {
+    if (clock64() - t0 > limit) {
       atomicExch(err, ERR_TIMEOUT);
       return false;
     }
   }
   return true;
+}
+
+// The wait every pipeline uses: gives up after kSpinCycles (~1 s).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  return mbar_wait_for(bar, parity, err, kSpinCycles);
 }
 
 // ---------------------------------------------------------------------------

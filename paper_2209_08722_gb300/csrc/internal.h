@@ -72,13 +72,32 @@ struct DfUnpackArgs {
 cudaError_t launch_df_pack(const DfPackArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_df_unpack(const DfUnpackArgs& a, int num_sms, cudaStream_t st);
 
-// the warm-start model's forward pass for one sample on stream st (mlp.cu)
-int mlp_predict(::lp_mlp* M, cublasHandle_t blas, const float* X, float* scratch, float* Y,
-                cudaStream_t st);
+// the warm-start model's forward pass for one sample on stream st into
+// scratch of mlp_predict_scratch_floats floats (mlp.cu)
+int mlp_predict(::lp_mlp* M, const float* X, float* scratch, float* Y, cudaStream_t st);
+size_t mlp_predict_scratch_floats(const ::lp_mlp* M);
 void mlp_dims(const ::lp_mlp* M, int* in, int* out, int* hid);
+// the model's contractions (mlp_gemm.cu): C = op(A) op(B), column-major FP32,
+// split-TF32 on the tcgen05 tensor cores; y-partials of a column-major GEMV
+// over gemv_slices(cols) column slices ([slice][rows])
+cudaError_t launch_gemm_tf32x3(bool ta, bool tb, int M, int N, int K, const float* A, int lda, const float* B,
+                               int ldb, float* C, int ldc, int* err, cudaStream_t st);
+int gemv_slices(int cols);
+cudaError_t launch_gemv_cm(int rows, int cols, const float* W, const float* x, float* part, cudaStream_t st);
 
 // raise (never lower) a kernel's dynamic shared-memory limit; thread-safe
 cudaError_t ensure_smem(const void* func, int bytes);
+
+// Row-split streaming kernels for tall columns (stream_rows.cu): FP32 M_ADAT
+// (df = false) and the double-float passes M_ADAT, M_RESID, M_DIR (df = true)
+// with their own tile width (nb = 4 x column groups) and stage count.
+struct RowsPlan {
+  int rpt = 0, nb = 0, ntiles = 0, stages = 0, grid = 0, smem = 0;
+  bool ok = false;
+};
+RowsPlan make_rows_plan(int lda, long long n, int esz, int num_sms);
+cudaError_t launch_rows(int dtype, bool df, int mode, const StreamArgs& a, const RowsPlan& p,
+                        cudaStream_t st, bool pdl);
 
 // double-float streaming passes (M_ADAT, M_RESID, M_DIR) for FP32/BF16 storage
 cudaError_t launch_stream_df(int dtype, int mode, const StreamArgs& a, const StreamPlan& p,
@@ -161,6 +180,10 @@ cudaError_t launch_update(long long n, int m, double* x, double* s, double* y, c
                           const double* ds, const double* dy, DevScalars* sc, double* part,
                           unsigned* ticket, int num_sms, cudaStream_t st);
 cudaError_t launch_fill(long long n, double* x, double v, int num_sms, cudaStream_t st);
+// one thread waits (mbar_wait_for, limit in clock64 cycles) on a shared-memory
+// mbarrier that it completes first when `complete` is set, and that nothing
+// completes otherwise; a wait that gives up sets *err = ERR_TIMEOUT
+cudaError_t launch_wait_probe(int* err, long long limit, int complete, cudaStream_t st);
 cudaError_t launch_axpby(long long n, double alpha, const double* x, double beta, const double* y,
                          double* out, int num_sms, cudaStream_t st);
 cudaError_t launch_ws_features(int m, const double* dy_prev, int have_prev, const double* u,

@@ -5,14 +5,14 @@
 //
 // Layout: a batch of B samples is a column-major (features x B) matrix, i.e.
 // each sample is contiguous; weights are column-major (rows = outputs).  The
-// three matrix products per pass are plain library GEMMs (cuBLAS SGEMM); the
-// element-wise work is in this file's kernels: bias + GELU (keeping Z for the
-// backward pass), the GELU derivative fused with the bias-gradient row sums,
-// the loss and its gradient, and the Adam update.  GELU is the exact
+// three matrix products of a forward pass and the six of a backward pass run
+// on the project's tcgen05 GEMM (mlp_gemm.cu: split-TF32 operands, FP32
+// accumulation in tensor memory), single-sample prediction on its FP32 GEMV;
+// the element-wise work is in this file's kernels: bias + GELU (keeping Z for
+// the backward pass), the GELU derivative fused with the bias-gradient row
+// sums, the loss and its gradient, and the Adam update.  GELU is the exact
 // 0.5 z (1 + erf(z / sqrt 2)) with derivative Phi(z) + z phi(z).
 #include "internal.h"
-
-#include <cublas_v2.h>
 
 #include <cmath>
 #include <cstring>
@@ -69,6 +69,18 @@ __global__ void k_act_back(int rows, int cols, const float* __restrict__ z, floa
   }
 }
 
+// y = sum of the GEMV's column-slice partials (in slice order) + b, then the
+// activation (single-sample prediction)
+__global__ void k_slices_bias_act(int rows, int slices, const float* __restrict__ part,
+                                  const float* __restrict__ b, float* __restrict__ y, int act) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  float s = 0.0f;
+  for (int q = 0; q < slices; ++q) s += part[(size_t)q * rows + r];
+  const float v = s + b[r];
+  y[r] = act ? gelu(v) : v;
+}
+
 // dY = (Y - T) / B; loss partial sums
 __global__ void k_mse(long long total, int batch, const float* __restrict__ y, const float* __restrict__ t,
                       float* __restrict__ dy, double* __restrict__ loss) {
@@ -110,8 +122,9 @@ using namespace lpk;
 struct lp_mlp {
   int in = 0, hid = 0, out = 0;
   int num_sms = 1;
-  cublasHandle_t blas = nullptr;
   cudaStream_t st = nullptr;
+  int* err = nullptr;        // device status word of the GEMMs' bounded waits
+  int* herr = nullptr;       // pinned host copy
   // parameters: W1 (hid x in), b1, W2 (hid x hid), b2, W3 (out x hid), b3, in one buffer
   float* param = nullptr;
   float* grad = nullptr;
@@ -136,7 +149,7 @@ struct lp_mlp {
 
   ~lp_mlp() {
     for (void* p : allocs) cudaFree(p);
-    if (blas) cublasDestroy(blas);
+    if (herr) cudaFreeHost(herr);
   }
   template <typename T>
   bool alloc(T** p, size_t count) {
@@ -160,19 +173,29 @@ struct lp_mlp {
     cap = B;
     return true;
   }
-  bool gemm(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const float* A, int lda,
-            const float* B, int ldb, float beta, float* C, int ldc) {
-    const float one = 1.0f;
-    return cublasSgemm(blas, ta, tb, m, n, k, &one, A, lda, B, ldb, &beta, C, ldc) == CUBLAS_STATUS_SUCCESS;
+  // C = op(A) op(B) on the tensor cores (ta / tb: transpose A / B)
+  bool gemm(bool ta, bool tb, int m, int n, int k, const float* A, int lda, const float* B, int ldb, float* C,
+            int ldc) {
+    return launch_gemm_tf32x3(ta, tb, m, n, k, A, lda, B, ldb, C, ldc, err, st) == cudaSuccess;
+  }
+  // the GEMMs' status word after the stream is done: LP_ERR_DEVICE_TIMEOUT
+  // when a wait gave up (the word is cleared again)
+  int status() {
+    if (cudaMemcpyAsync(herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return LP_ERR_CUDA;
+    if (*herr == ERR_NONE) return LP_OK;
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return LP_ERR_CUDA;
+    return LP_ERR_DEVICE_TIMEOUT;
   }
   // Y (out x B) from X (in x B); activations kept for backward
   int forward(const float* X, int B) {
     if (!ensure_batch(B)) return LP_ERR_OOM;
-    if (!gemm(CUBLAS_OP_N, CUBLAS_OP_N, hid, B, in, W1(), hid, X, in, 0.0f, z1, hid)) return LP_ERR_CUDA;
+    if (!gemm(false, false, hid, B, in, W1(), hid, X, in, z1, hid)) return LP_ERR_CUDA;
     k_bias_act<<<grid_for((long long)hid * B, num_sms), 256, 0, st>>>(hid, B, b1(), z1, a1, 1);
-    if (!gemm(CUBLAS_OP_N, CUBLAS_OP_N, hid, B, hid, W2(), hid, a1, hid, 0.0f, z2, hid)) return LP_ERR_CUDA;
+    if (!gemm(false, false, hid, B, hid, W2(), hid, a1, hid, z2, hid)) return LP_ERR_CUDA;
     k_bias_act<<<grid_for((long long)hid * B, num_sms), 256, 0, st>>>(hid, B, b2(), z2, a2, 1);
-    if (!gemm(CUBLAS_OP_N, CUBLAS_OP_N, out, B, hid, W3(), out, a2, hid, 0.0f, y, out)) return LP_ERR_CUDA;
+    if (!gemm(false, false, out, B, hid, W3(), out, a2, hid, y, out)) return LP_ERR_CUDA;
     k_bias_act<<<grid_for((long long)out * B, num_sms), 256, 0, st>>>(out, B, b3(), y, nullptr, 0);
     g_launches.fetch_add(3, std::memory_order_relaxed);
     return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
@@ -181,14 +204,14 @@ struct lp_mlp {
   int backward(const float* X, int B) {
     const int wg = std::max(1, std::min(num_sms * 4, (out + 7) / 8));
     k_act_back<<<wg, 256, 0, st>>>(out, B, y, d3, g(b3()), 0);
-    if (!gemm(CUBLAS_OP_N, CUBLAS_OP_T, out, hid, B, d3, out, a2, hid, 0.0f, g(W3()), out)) return LP_ERR_CUDA;
-    if (!gemm(CUBLAS_OP_T, CUBLAS_OP_N, hid, B, out, W3(), out, d3, out, 0.0f, d2, hid)) return LP_ERR_CUDA;
+    if (!gemm(false, true, out, hid, B, d3, out, a2, hid, g(W3()), out)) return LP_ERR_CUDA;
+    if (!gemm(true, false, hid, B, out, W3(), out, d3, out, d2, hid)) return LP_ERR_CUDA;
     const int hg = std::max(1, std::min(num_sms * 4, (hid + 7) / 8));
     k_act_back<<<hg, 256, 0, st>>>(hid, B, z2, d2, g(b2()), 1);
-    if (!gemm(CUBLAS_OP_N, CUBLAS_OP_T, hid, hid, B, d2, hid, a1, hid, 0.0f, g(W2()), hid)) return LP_ERR_CUDA;
-    if (!gemm(CUBLAS_OP_T, CUBLAS_OP_N, hid, B, hid, W2(), hid, d2, hid, 0.0f, d1, hid)) return LP_ERR_CUDA;
+    if (!gemm(false, true, hid, hid, B, d2, hid, a1, hid, g(W2()), hid)) return LP_ERR_CUDA;
+    if (!gemm(true, false, hid, B, hid, W2(), hid, d2, hid, d1, hid)) return LP_ERR_CUDA;
     k_act_back<<<hg, 256, 0, st>>>(hid, B, z1, d1, g(b1()), 1);
-    if (!gemm(CUBLAS_OP_N, CUBLAS_OP_T, hid, in, B, d1, hid, X, in, 0.0f, g(W1()), hid)) return LP_ERR_CUDA;
+    if (!gemm(false, true, hid, in, B, d1, hid, X, in, g(W1()), hid)) return LP_ERR_CUDA;
     g_launches.fetch_add(3, std::memory_order_relaxed);
     return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
   }
@@ -208,12 +231,13 @@ static int mlp_create_impl(lp_mlp** out, int32_t in, int32_t hidden, int32_t out
       cudaDeviceGetAttribute(&M->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     return LP_ERR_CUDA;
   }
-  if (cublasCreate(&M->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(M->blas, M->st) != CUBLAS_STATUS_SUCCESS) {
-    return LP_ERR_CUDA;
+  if (cudaMallocHost(&M->herr, sizeof(int)) != cudaSuccess) {
+    M->herr = nullptr;
+    return LP_ERR_OOM;
   }
   M->nparam = (long long)hidden * in + hidden + (long long)hidden * hidden + hidden + (long long)outdim * hidden + outdim;
   if (!M->alloc(&M->param, M->nparam) || !M->alloc(&M->grad, M->nparam) || !M->alloc(&M->adam_m, M->nparam) ||
-      !M->alloc(&M->adam_v, M->nparam) || !M->alloc(&M->loss, 1)) {
+      !M->alloc(&M->adam_v, M->nparam) || !M->alloc(&M->loss, 1) || !M->alloc(&M->err, 1)) {
     return LP_ERR_OOM;
   }
   // He-style initialisation from SplitMix64 (host), biases zero; the output
@@ -232,6 +256,7 @@ static int mlp_create_impl(lp_mlp** out, int32_t in, int32_t hidden, int32_t out
   fill(o3, outdim, hidden, 0.01 * std::sqrt(1.0 / hidden));
   if (cudaMemcpy(M->param, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(M->adam_m, 0, sizeof(float) * M->nparam) != cudaSuccess ||
+      cudaMemset(M->err, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(M->adam_v, 0, sizeof(float) * M->nparam) != cudaSuccess) {
     return LP_ERR_CUDA;
   }
@@ -287,7 +312,7 @@ int lp_mlp_forward(lp_mlp* M, const float* X, int32_t batch, float* Y) {
   if (cudaMemcpyAsync(Y, M->y, sizeof(float) * (size_t)M->out * batch, cudaMemcpyDeviceToDevice, M->st) !=
       cudaSuccess)
     return LP_ERR_CUDA;
-  return cudaStreamSynchronize(M->st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+  return M->status();
 }
 
 int lp_mlp_loss_grad(lp_mlp* M, const float* X, const float* T, int32_t batch, double* loss) {
@@ -302,7 +327,7 @@ int lp_mlp_loss_grad(lp_mlp* M, const float* X, const float* T, int32_t batch, d
   if (rc != LP_OK) return rc;
   if (loss && cudaMemcpyAsync(loss, M->loss, sizeof(double), cudaMemcpyDeviceToHost, M->st) != cudaSuccess)
     return LP_ERR_CUDA;
-  return cudaStreamSynchronize(M->st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+  return M->status();
 }
 
 int lp_mlp_train_step(lp_mlp* M, const float* X, const float* T, int32_t batch, float lr, double* loss) {
@@ -319,10 +344,10 @@ int lp_mlp_train_step(lp_mlp* M, const float* X, const float* T, int32_t batch, 
 
 }  // extern "C"
 
-// used by the solver's warm start: Y (out x 1) from X (in x 1) on the caller's
-// cuBLAS handle (bound to the caller's stream) and scratch (2 hid floats), so
-// the model is only read: handles solving concurrently may share it, and no
-// cuBLAS stream switch (which resets its workspace) happens per call.
+// used by the solver's warm start: Y (out x 1) from X (in x 1) into the
+// caller's scratch (mlp_predict_scratch_floats floats) on the caller's
+// stream, so the model is only read and handles solving concurrently may
+// share it.
 namespace lpk {
 void mlp_dims(const lp_mlp* M, int* in, int* out, int* hid) {
   *in = M->in;
@@ -330,23 +355,24 @@ void mlp_dims(const lp_mlp* M, int* in, int* out, int* hid) {
   if (hid) *hid = M->hid;
 }
 
-int mlp_predict(lp_mlp* M, cublasHandle_t blas, const float* X, float* scratch, float* Y,
-                cudaStream_t st) {
-  const float one = 1.0f, zero = 0.0f;
+size_t mlp_predict_scratch_floats(const lp_mlp* M) {
+  return 2 * (size_t)M->hid + (size_t)32 * std::max(M->hid, M->out);
+}
+
+int mlp_predict(lp_mlp* M, const float* X, float* scratch, float* Y, cudaStream_t st) {
   float* h1 = scratch;
   float* h2 = scratch + M->hid;
+  float* part = scratch + 2 * (size_t)M->hid;
   const int hid = M->hid, in = M->in, out = M->out;
-  auto gemv = [&](int rows, int cols, const float* W, const float* x, float* y) {
-    return cublasSgemv(blas, CUBLAS_OP_N, rows, cols, &one, W, rows, x, 1, &zero, y, 1) ==
-           CUBLAS_STATUS_SUCCESS;
+  auto layer = [&](int rows, int cols, const float* W, const float* b, const float* x, float* y, int act) {
+    if (launch_gemv_cm(rows, cols, W, x, part, st) != cudaSuccess) return false;
+    k_slices_bias_act<<<(rows + 127) / 128, 128, 0, st>>>(rows, gemv_slices(cols), part, b, y, act);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError() == cudaSuccess;
   };
-  if (!gemv(hid, in, M->W1(), X, h1)) return LP_ERR_CUDA;
-  k_bias_act<<<grid_for(hid, M->num_sms), 256, 0, st>>>(hid, 1, M->b1(), h1, h1, 1);
-  if (!gemv(hid, hid, M->W2(), h1, h2)) return LP_ERR_CUDA;
-  k_bias_act<<<grid_for(hid, M->num_sms), 256, 0, st>>>(hid, 1, M->b2(), h2, h2, 1);
-  if (!gemv(out, hid, M->W3(), h2, Y)) return LP_ERR_CUDA;
-  k_bias_act<<<grid_for(out, M->num_sms), 256, 0, st>>>(out, 1, M->b3(), Y, nullptr, 0);
-  g_launches.fetch_add(3, std::memory_order_relaxed);
-  return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+  if (!layer(hid, in, M->W1(), M->b1(), X, h1, 1)) return LP_ERR_CUDA;
+  if (!layer(hid, hid, M->W2(), M->b2(), h1, h2, 1)) return LP_ERR_CUDA;
+  if (!layer(out, hid, M->W3(), M->b3(), h2, Y, 0)) return LP_ERR_CUDA;
+  return LP_OK;
 }
 }  // namespace lpk

@@ -130,6 +130,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_adat_noalloc(const NaArgs 
           const int rv = c * 32 + lane;
           if (rv < RV) {
             ld16<float>(col + rv * VEC, av[c]);
+            // rows m .. ld-1 are the caller's padding and may hold anything
+            // (NaN or Inf included): they must not reach the dot product
+            if ((rv + 1) * VEC > a.m) {
+#pragma unroll
+              for (int e = 0; e < VEC; ++e)
+                if (rv * VEC + e >= a.m) av[c][e] = 0.0f;
+            }
           } else {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) av[c][e] = 0.0f;

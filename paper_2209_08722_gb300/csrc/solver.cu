@@ -47,6 +47,42 @@ long long round_up_ll(long long x, long long a) { return (x + a - 1) / a * a; }
 struct EvPair {
   cudaEvent_t a, b;
 };
+
+// A matrix given by rows (CSR) in the column form the sparse kernels stream
+// (CSC), built on the host by a counting sort on the column index: one pass
+// counts each column's entries, a prefix sum gives the column pointers, and a
+// second pass over the rows in order places every entry, so each column's
+// entries come out in increasing row order (a stable sort: the result depends
+// only on the matrix).  Returns an empty string, or the structural error found
+// in the CSR arrays (row pointers not starting at 0, decreasing, or not ending
+// at nnz; a column index outside [0, n)).
+struct CscCopy {
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> idx;
+  std::vector<char> val;
+};
+std::string csr_to_csc(int m, long long n, long long nnz, const int64_t* rp, const int32_t* ci,
+                       const void* val, int esz, CscCopy* out) {
+  if (rp[0] != 0 || rp[m] != nnz) return "CSR ptr[0] != 0 or ptr[m] != nnz";
+  for (int i = 0; i < m; ++i)
+    if (rp[i + 1] < rp[i]) return "CSR row pointers not monotone";
+  for (long long q = 0; q < nnz; ++q)
+    if (ci[q] < 0 || ci[q] >= n) return "CSR column index out of range";
+  out->ptr.assign((size_t)n + 1, 0);
+  for (long long q = 0; q < nnz; ++q) ++out->ptr[(size_t)ci[q] + 1];
+  for (long long j = 0; j < n; ++j) out->ptr[j + 1] += out->ptr[j];
+  std::vector<int64_t> cursor(out->ptr.begin(), out->ptr.end() - 1);
+  out->idx.resize((size_t)std::max<long long>(nnz, 1));
+  out->val.resize((size_t)std::max<long long>(nnz, 1) * esz);
+  const char* v = static_cast<const char*>(val);
+  for (int i = 0; i < m; ++i)
+    for (long long q = rp[i]; q < rp[i + 1]; ++q) {
+      const int64_t dst = cursor[ci[q]]++;
+      out->idx[dst] = i;
+      std::memcpy(out->val.data() + (size_t)dst * esz, v + (size_t)q * esz, esz);
+    }
+  return std::string();
+}
 }  // namespace
 
 struct lp_handle {
@@ -110,7 +146,7 @@ struct lp_handle {
   double *ws_v = nullptr, *ws_w = nullptr, *ws_dots = nullptr;  // proposal, M v_i (2 m), dots
   bool warm_r_ready = false;  // h->r already holds p - M dy^0 for the warm start
   float *ws_X = nullptr, *ws_Y = nullptr;
-  float* ws_hid = nullptr;  // 2 x hidden floats: the model's activations (per handle)
+  float* ws_hid = nullptr;  // the model's activations and GEMV partials (per handle)
   long long ws_hid_cap = 0;
   // n-vectors (padded)
   double *c = nullptr, *x = nullptr, *y = nullptr, *s = nullptr, *rd = nullptr, *d2d = nullptr,
@@ -142,6 +178,8 @@ struct lp_handle {
   int* hinfo = nullptr;       // pinned
   double* hval = nullptr;     // pinned staging for scalars
   StreamPlan plan;
+  RowsPlan rplan;          // row-split kernels for tall columns (stream_rows.cu)
+  bool use_rows = false;   // the FP32 product and the double-float passes use them
   std::string err;
   // profiling of the hot product kernel
   std::vector<EvPair> ev_pool;
@@ -208,6 +246,14 @@ int sync_read(lp_handle* h) {
   CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   return check_read(h);
+}
+
+// A call starts from a clear device status word, so that an error reported by
+// an earlier call (a wait that gave up, a non-finite reduction) does not stick
+// to the handle.
+int clear_status(lp_handle* h) {
+  CK(cudaMemsetAsync(&h->sc->err, 0, sizeof(int), h->st));
+  return LP_OK;
 }
 
 int set_scalar(lp_handle* h, double* dev_field, double value) {
@@ -307,8 +353,12 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
   }
   cudaError_t e;
   if (h->sparse) e = launch_sparse(h->dtype, use64, M_ADAT, a, h->sp_grid, h->st);
+  else if (!use64 && h->use_rows) e = launch_rows(h->dtype, false, M_ADAT, a, h->rplan, h->st, pdl);
   else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st, pdl);
-  else if (h->use_df) {
+  else if (h->use_rows) {
+    // the refresh inside the inner loop follows a GEMV closely
+    e = launch_rows(h->dtype, true, M_ADAT, a, h->rplan, h->st, skip_level >= 1);
+  } else if (h->use_df) {
     a.pdl = skip_level >= 1 ? 1 : 0;  // the refresh inside the inner loop follows a GEMV closely
     e = launch_stream_df(h->dtype, M_ADAT, a, h->plan, h->st);
   }
@@ -838,7 +888,7 @@ int warm_start_prepare(lp_handle* h, double mu_ratio, bool* warm) {
   const double* v[2];
   int nv = 0;
   if (h->ws_mode == 2 && h->ws_model) {
-    if (mlp_predict(h->ws_model, h->blas, h->ws_X, h->ws_hid, h->ws_Y, h->st) != LP_OK)
+    if (mlp_predict(h->ws_model, h->ws_X, h->ws_hid, h->ws_Y, h->st) != LP_OK)
       return h->fail(LP_ERR_CUDA, "warm-start model forward failed");
     CK(launch_ws_scale(m, 0, h->ws_Y, nullptr, h->sc, h->ws_v, nullptr, h->st));
     v[nv++] = h->ws_v;
@@ -947,7 +997,8 @@ int residual_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
     a.out_df[0] = h->dfout[0];
     a.out_df[1] = h->d2df;
     a.red_partials = nullptr;
-    CK(launch_stream_df(h->dtype, M_RESID, a, h->plan, h->st));
+    if (h->use_rows) CK(launch_rows(h->dtype, true, M_RESID, a, h->rplan, h->st, false));
+    else CK(launch_stream_df(h->dtype, M_RESID, a, h->plan, h->st));
     DfUnpackArgs up{0, h->n, h->dfout[0], h->d2df, h->rd, h->d2d, h->d2f, h->x, h->s, h->c, h->sc,
                     h->vpart, h->tickets + 7};
     CK(launch_df_unpack(up, h->num_sms, h->st));
@@ -989,7 +1040,8 @@ int direction_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
     a.out_df[0] = h->dfout[0];
     a.out_df[1] = h->dfout[1];
     a.red_partials = nullptr;
-    CK(launch_stream_df(h->dtype, M_DIR, a, h->plan, h->st));
+    if (h->use_rows) CK(launch_rows(h->dtype, true, M_DIR, a, h->rplan, h->st, false));
+    else CK(launch_stream_df(h->dtype, M_DIR, a, h->plan, h->st));
     DfUnpackArgs up{1, h->n, h->dfout[0], h->dfout[1], h->dx, h->ds, nullptr, h->x, h->s, nullptr, h->sc,
                     h->vpart, h->tickets + 7};
     CK(launch_df_unpack(up, h->num_sms, h->st));
@@ -1105,10 +1157,17 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
                        int bc_on_device, const lp_options* opt) {
   if (!A || !b || !c) return h->fail(LP_ERR_ARG, "A, b and c are required");
   if (A->m < 1 || A->n < A->m) return h->fail(LP_ERR_ARG, "need 1 <= m <= n (m=%d n=%lld)", A->m, (long long)A->n);
-  if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC) return h->fail(LP_ERR_ARG, "bad format");
+  if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC && A->fmt != LP_CSR)
+    return h->fail(LP_ERR_ARG, "bad format");
   if (A->dtype < LP_F64 || A->dtype > LP_BF16) return h->fail(LP_ERR_ARG, "bad dtype");
   if (A->fmt == LP_DENSE_COLMAJOR && (!A->val || A->ld < A->m))
     return h->fail(LP_ERR_ARG, "dense A needs val and ld >= m");
+  if (A->fmt == LP_CSR) {
+    if (!A->val || !A->ptr || !A->idx || A->nnz < 0) return h->fail(LP_ERR_ARG, "CSR A needs ptr, idx, val");
+    if (A->dtype == LP_BF16) return h->fail(LP_ERR_UNSUPPORTED, "CSR values must be FP32 or FP64");
+    if (A->nnz >= (1LL << 40)) return h->fail(LP_ERR_ARG, "nnz too large");
+    if (A->n > INT32_MAX) return h->fail(LP_ERR_ARG, "CSR column indices are 32-bit: n too large");
+  }
   if (A->fmt == LP_CSC) {
     if (!A->val || !A->ptr || !A->idx || A->nnz < 0) return h->fail(LP_ERR_ARG, "CSC A needs ptr, idx, val");
     if (A->dtype == LP_BF16) return h->fail(LP_ERR_UNSUPPORTED, "CSC values must be FP32 or FP64");
@@ -1134,8 +1193,43 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   if (w < A->m) return h->fail(LP_ERR_ARG, "sketch width w=%lld < m=%d: A D W cannot have rank m", w, A->m);
   if (w > (1 << 30)) return h->fail(LP_ERR_ARG, "sketch width too large");
   h->w = (int)w;
-  if (A->fmt == LP_CSC && h->opt.sketch == LP_SKETCH_GAUSS)
+  if (A->fmt != LP_DENSE_COLMAJOR && h->opt.sketch == LP_SKETCH_GAUSS)
     return h->fail(LP_ERR_UNSUPPORTED, "the Gaussian sketch is built for dense A only");
+  // CSR input: the sparse kernels stream columns, so the rows are sorted into
+  // CSC here (a device CSR is read back to the host first)
+  lp_matrix csc_view;
+  CscCopy conv;
+  if (A->fmt == LP_CSR) {
+    const int esz_in = A->dtype == LP_F64 ? 8 : 4;
+    const int64_t* rp = A->ptr;
+    const int32_t* ci = A->idx;
+    const void* vv = A->val;
+    std::vector<int64_t> rp_h;
+    std::vector<int32_t> ci_h;
+    std::vector<char> vv_h;
+    if (A->on_device) {
+      rp_h.resize((size_t)A->m + 1);
+      ci_h.resize((size_t)std::max<long long>(A->nnz, 1));
+      vv_h.resize((size_t)std::max<long long>(A->nnz, 1) * esz_in);
+      CK(cudaMemcpy(rp_h.data(), A->ptr, sizeof(int64_t) * ((size_t)A->m + 1), cudaMemcpyDeviceToHost));
+      if (A->nnz > 0) {
+        CK(cudaMemcpy(ci_h.data(), A->idx, sizeof(int32_t) * (size_t)A->nnz, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(vv_h.data(), A->val, (size_t)esz_in * A->nnz, cudaMemcpyDeviceToHost));
+      }
+      rp = rp_h.data();
+      ci = ci_h.data();
+      vv = vv_h.data();
+    }
+    const std::string bad = csr_to_csc(A->m, A->n, A->nnz, rp, ci, vv, esz_in, &conv);
+    if (!bad.empty()) return h->fail(LP_ERR_ARG, "%s", bad.c_str());
+    csc_view = *A;
+    csc_view.fmt = LP_CSC;
+    csc_view.ptr = conv.ptr.data();
+    csc_view.idx = conv.idx.data();
+    csc_view.val = conv.val.data();
+    csc_view.on_device = 0;
+    A = &csc_view;
+  }
   CK(cudaGetDevice(&h->dev));
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
   if (h->opt.stream) {
@@ -1169,8 +1263,17 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   h->use_df = !h->sparse && h->dtype != LP_F64 && stream_df_supported(M_ADAT, h->lda, h->esz, h->plan);
   h->use_df_resid = !h->sparse && h->dtype != LP_F64 && stream_df_supported(M_RESID, h->lda, h->esz, h->plan);
   h->use_df_dir = !h->sparse && h->dtype != LP_F64 && stream_df_supported(M_DIR, h->lda, h->esz, h->plan);
+  // Tall columns (16-byte vectors per lane per column >= 8: m > 512 in FP32,
+  // m > 1024 in BF16) go to the row-split kernels, whose per-lane state does
+  // not grow with m; the warp-per-column kernels would spill there.
+  if (!h->sparse && h->dtype != LP_F64) {
+    const int vpl = fused_vpl(h->lda, h->esz);
+    h->rplan = make_rows_plan(h->lda, h->n, h->esz, h->num_sms);
+    h->use_rows = h->rplan.ok && (vpl == 0 || vpl >= 8);
+    if (h->use_rows) h->use_df = h->use_df_resid = h->use_df_dir = true;
+  }
   if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
-  if (!h->sparse && h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0)
+  if (!h->sparse && h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0 && !h->use_rows)
     return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the fused product kernel", h->m);
   if (!h->sparse && h->lda / vec > 4 * kThreads)
     return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the FP64 streaming kernel", h->m);
@@ -1250,8 +1353,9 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->uw, (size_t)h->w));
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));
-  RET(h->alloc(reinterpret_cast<char**>(&h->partials), (size_t)h->plan.grid * 2 * h->lda * 8));
-  RET(h->alloc(&h->gpart, (size_t)((h->plan.grid + kGroup - 1) / kGroup) * 2 * h->lda));
+  const int max_grid = std::max(h->plan.grid, h->use_rows ? h->rplan.grid : 0);
+  RET(h->alloc(reinterpret_cast<char**>(&h->partials), (size_t)max_grid * 2 * h->lda * 8));
+  RET(h->alloc(&h->gpart, (size_t)((max_grid + kGroup - 1) / kGroup) * 2 * h->lda));
   RET(h->alloc(&h->gtickets, kMaxGroups + 1));
   RET(h->alloc(&h->red_partials, (size_t)h->plan.grid * 2 + 2));
   RET(h->alloc(&h->tickets, 16));
@@ -1313,6 +1417,7 @@ int lp_create(lp_handle** out, const lp_matrix* A, const double* b, const double
 int lp_adat(lp_handle* h, const double* d2, const double* v, double* u, int32_t precision) {
   if (!h || !d2 || !v || !u) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   CK(cudaMemcpyAsync(h->d2d, d2, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st));
   h->d2df_valid = false;
   CK(launch_to_f32(h->n, h->d2d, h->d2f, 0, h->num_sms, h->st));
@@ -1325,10 +1430,40 @@ int lp_adat(lp_handle* h, const double* d2, const double* v, double* u, int32_t 
   return LP_OK;
 }
 
+int lp_csr_to_csc(int32_t m, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                  const void* val, int32_t dtype, int64_t* col_ptr, int32_t* row_idx, void* val_out) {
+  if (m < 1 || n < 1 || n > INT32_MAX || nnz < 0 || !row_ptr || (nnz > 0 && (!col_idx || !val)) ||
+      !col_ptr || (nnz > 0 && (!row_idx || !val_out)))
+    return LP_ERR_ARG;
+  if (dtype != LP_F64 && dtype != LP_F32 && dtype != LP_BF16) return LP_ERR_ARG;
+  const int esz = dtype == LP_F64 ? 8 : (dtype == LP_F32 ? 4 : 2);
+  std::string err;
+  return guarded(&err, [&] {
+    CscCopy conv;
+    if (!csr_to_csc(m, n, nnz, row_ptr, col_idx, val, esz, &conv).empty()) return LP_ERR_ARG;
+    std::memcpy(col_ptr, conv.ptr.data(), sizeof(int64_t) * ((size_t)n + 1));
+    if (nnz > 0) {
+      std::memcpy(row_idx, conv.idx.data(), sizeof(int32_t) * (size_t)nnz);
+      std::memcpy(val_out, conv.val.data(), (size_t)esz * nnz);
+    }
+    return LP_OK;
+  });
+}
+
+int lp_wait_probe(lp_handle* h, int64_t spin_cycles, int32_t complete) {
+  if (!h || spin_cycles < 1 || spin_cycles > (1LL << 31) || (complete != 0 && complete != 1))
+    return LP_ERR_ARG;
+  h->err.clear();
+  RET(clear_status(h));
+  CK(launch_wait_probe(&h->sc->err, (long long)spin_cycles, complete, h->st));
+  return sync_read(h);
+}
+
 int lp_residual_rhs(lp_handle* h, const double* x, const double* y, const double* s, int32_t mode,
                     double* r_p, double* r_d, double* p, double* out5) {
   if (!h || !x || !y || !s) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   RET(copy_in(h, h->x, x, h->n, 1));
   RET(copy_in(h, h->s, s, h->n, 1));
   RET(copy_in(h, h->y, y, h->m, 1));
@@ -1352,6 +1487,7 @@ int lp_sketch(lp_handle* h, const double* D, uint64_t seed, int64_t k, int32_t r
               int64_t* w_out) {
   if (!h || !D || !adw || retry < 0 || retry >= kMaxRetry || k < 0) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   RET(copy_in(h, h->nb0, D, h->n, 1));
   CK(launch_sketch(h, h->nb0, 0, seed, k, retry));
   CK(cudaMemcpyAsync(adw, h->adw, sizeof(double) * (size_t)h->m * h->w, cudaMemcpyDeviceToDevice, h->st));
@@ -1363,6 +1499,7 @@ int lp_sketch(lp_handle* h, const double* D, uint64_t seed, int64_t k, int32_t r
 int lp_precond_apply(lp_handle* h, const double* adw, const double* r, double* z) {
   if (!h || !adw || !r || !z) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   CK(cudaMemcpyAsync(h->adw, adw, sizeof(double) * (size_t)h->m * h->w, cudaMemcpyDeviceToDevice, h->st));
   RET(factor(h));
   RET(copy_in(h, h->mb0, r, h->m, 1));
@@ -1378,6 +1515,7 @@ int lp_directions(lp_handle* h, const double* x, const double* s, const double* 
   const bool feasible = mode == LP_FEASIBLE;
   if (!feasible && !rd) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   RET(copy_in(h, h->x, x, h->n, 1));
   RET(copy_in(h, h->s, s, h->n, 1));
   RET(copy_in(h, h->v, v, h->n, 1));
@@ -1395,6 +1533,7 @@ int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double
                     int32_t mode, double res_ratio, double mu0, double* out2) {
   if (!h || !x || !s || !dx || !ds || !out2) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   RET(copy_in(h, h->x, x, h->n, 1));
   RET(copy_in(h, h->s, s, h->n, 1));
   RET(copy_in(h, h->dx, dx, h->n, 1));
@@ -1450,6 +1589,7 @@ static int normal_solve_impl(lp_handle* h, const double* D, const double* p, con
                     double tol_f, int32_t io_on_device, double* dy, double* v, lp_nsolve_info* info) {
   if (!h || !D || !p || !dy || k < 0) return LP_ERR_ARG;
   h->err.clear();
+  RET(clear_status(h));
   RET(copy_in(h, h->nb0, D, h->n, io_on_device));
   RET(copy_in(h, h->p, p, h->m, io_on_device));
   CK(launch_square(h->n, h->nb0, h->d2d, h->num_sms, h->st));
@@ -1698,12 +1838,12 @@ static int set_warm_start_impl(lp_handle* h, int32_t mode, lp_mlp* model, float*
     int in = 0, out = 0, hid = 0;
     mlp_dims(model, &in, &out, &hid);
     if (in != 3 * h->m || out != h->m) return LP_ERR_ARG;  // features 3m -> dy (m)
-    if (!h->blas) return LP_ERR_UNSUPPORTED;
-    if (2LL * hid > h->ws_hid_cap) {
+    const long long need = (long long)mlp_predict_scratch_floats(model);
+    if (need > h->ws_hid_cap) {
       if (cudaStreamSynchronize(h->st) != cudaSuccess) return LP_ERR_CUDA;
       h->err.clear();
-      if (h->alloc(&h->ws_hid, 2 * (size_t)hid) != LP_OK) return LP_ERR_OOM;
-      h->ws_hid_cap = 2LL * hid;
+      if (h->alloc(&h->ws_hid, (size_t)need) != LP_OK) return LP_ERR_OOM;
+      h->ws_hid_cap = need;
     }
   }
   h->ws_mode = mode;
@@ -1793,9 +1933,22 @@ void put_one(int dtype, void* dst, size_t idx) {
 static int phase1_start_impl(const lp_matrix* A, const double* b, const lp_options* opt_in, double tol,
                              double* x0, lp_phase1_info* info) {
   if (!A || !b || !x0 || !(tol > 0) || A->on_device || A->m <= 0 || A->n <= 0) return LP_ERR_ARG;
-  if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC) return LP_ERR_ARG;
+  if (A->fmt != LP_DENSE_COLMAJOR && A->fmt != LP_CSC && A->fmt != LP_CSR) return LP_ERR_ARG;
   if (A->dtype != LP_F64 && A->dtype != LP_F32 && A->dtype != LP_BF16) return LP_ERR_ARG;
   if (!A->val) return LP_ERR_ARG;
+  lp_matrix csc_view;
+  CscCopy conv;
+  if (A->fmt == LP_CSR) {  // rows sorted into columns on the host, as lp_create does
+    if (!A->ptr || !A->idx || A->nnz < 0 || A->n > INT32_MAX) return LP_ERR_ARG;
+    const int esz_in = A->dtype == LP_F64 ? 8 : (A->dtype == LP_F32 ? 4 : 2);
+    if (!csr_to_csc(A->m, A->n, A->nnz, A->ptr, A->idx, A->val, esz_in, &conv).empty()) return LP_ERR_ARG;
+    csc_view = *A;
+    csc_view.fmt = LP_CSC;
+    csc_view.ptr = conv.ptr.data();
+    csc_view.idx = conv.idx.data();
+    csc_view.val = conv.val.data();
+    A = &csc_view;
+  }
   if (A->fmt == LP_DENSE_COLMAJOR && A->ld < A->m) return LP_ERR_ARG;
   if (A->fmt == LP_CSC) {  // the structure is read on the host below: check it first
     if (!A->ptr || !A->idx || A->ptr[0] < 0) return LP_ERR_ARG;

@@ -636,6 +636,24 @@ cudaError_t launch_fill(long long n, double* x, double v, int num_sms, cudaStrea
   return cudaGetLastError();
 }
 
+// Health check of the bounded waits: the wait every pipeline uses, on a
+// barrier whose phase completes only if this thread arrives on it first.
+__global__ void k_wait_probe(int* err, long long limit, int complete) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (complete) mbar_arrive(&bar);
+    mbar_wait_for(&bar, 0u, err, limit);
+  }
+}
+
+cudaError_t launch_wait_probe(int* err, long long limit, int complete, cudaStream_t st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_wait_probe<<<1, 32, 0, st>>>(err, limit, complete);
+  return cudaGetLastError();
+}
+
 // *out = min_i x_i y_i
 __global__ void k_min_prod(long long n, const double* __restrict__ x, const double* __restrict__ y,
                            double* part, unsigned* ticket, double* out) {

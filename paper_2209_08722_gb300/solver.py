@@ -117,11 +117,14 @@ class LPSolver:
     ``A`` is column-major: an (n, m) C-contiguous array whose row j is column
     a_j (NumPy on the host, or a torch CUDA tensor), in the storage dtype
     ``dtype`` ("f64", "f32" or "bf16"; bf16 given as uint16 bit patterns or a
-    torch.bfloat16 tensor).
+    torch.bfloat16 tensor).  A sparse A is given instead as
+    ``csc=(col_ptr, row_idx, values)`` or ``csr=(row_ptr, col_idx, values)``
+    (int64 pointers, int32 indices, "f32" or "f64" values; host arrays or
+    CUDA tensors), with ``A=None``; the library sorts CSR into CSC.
     """
 
     def __init__(self, A, b, c, m: int, n: int, dtype: str = "f32", stream=None, csc=None,
-                 **options):
+                 csr=None, **options):
         self._lib = nat.load()
         self._h = ctypes.c_void_p()
         if dtype not in _DTYPES:
@@ -136,19 +139,27 @@ class LPSolver:
         if stream is not None:
             opt.stream = stream
         self.options = opt
-        if csc is not None:
-            # sparse A in CSC form: (col_ptr int64 [n+1], row_idx int32 [nnz], values [nnz])
-            cp, ri, vals = csc
+        if csc is not None and csr is not None:
+            raise ValueError("give A as csc or as csr, not both")
+        sparse = csc if csc is not None else csr
+        if sparse is not None:
+            # sparse A: CSC (col_ptr int64 [n+1], row_idx int32 [nnz], values [nnz])
+            # or CSR (row_ptr int64 [m+1], col_idx int32 [nnz], values [nnz])
+            cp, ri, vals = sparse
             if not _is_torch(cp):
                 cp = np.ascontiguousarray(cp, dtype=np.int64)
                 ri = np.ascontiguousarray(ri, dtype=np.int32)
                 vals = np.ascontiguousarray(vals, dtype=_NP_DT[dtype])
             nnz = int(vals.shape[0])
-            _need(cp, self.n + 1, "col_ptr")
-            _need(ri, nnz, "row_idx")
-            mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_CSC, dtype=_DTYPES[dtype],
-                               val=_ptr(vals), ld=0, ptr=_ptr(cp), idx=_ptr(ri), nnz=nnz,
-                               on_device=1 if _on_device(vals) else 0)
+            if csc is not None:
+                _need(cp, self.n + 1, "col_ptr")
+                _need(ri, nnz, "row_idx")
+            else:
+                _need(cp, self.m + 1, "row_ptr")
+                _need(ri, nnz, "col_idx")
+            mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_CSC if csc is not None else nat.LP_CSR,
+                               dtype=_DTYPES[dtype], val=_ptr(vals), ld=0, ptr=_ptr(cp), idx=_ptr(ri),
+                               nnz=nnz, on_device=1 if _on_device(vals) else 0)
             A = (cp, ri, vals)
         elif _is_torch(A):
             if tuple(A.shape) != (self.n, self.m):
@@ -161,7 +172,7 @@ class LPSolver:
             A = np.ascontiguousarray(A, dtype=_NP_DT[dtype])
             if A.shape != (self.n, self.m):
                 raise ValueError("A must have shape (n, m) (column-major)")
-        if csc is None:
+        if sparse is None:
             mat = nat.LpMatrix(m=self.m, n=self.n, fmt=nat.LP_DENSE_COLMAJOR, dtype=_DTYPES[dtype],
                                val=_ptr(A), ld=self.m, ptr=None, idx=None, nnz=0,
                                on_device=1 if _on_device(A) else 0)
@@ -272,6 +283,12 @@ class LPSolver:
         self._check(self._lib.lp_adat(self._h, _ptr(d2), _ptr(v), _ptr(u), int(precision)))
         return u
 
+    def wait_probe(self, spin_cycles: int, complete: bool) -> int:
+        """lp_wait_probe: runs the pipelines' bounded device wait once on this
+        handle's stream; returns the library's status code (LP_OK when the
+        barrier was completed, LP_ERR_DEVICE_TIMEOUT when the wait gave up)."""
+        return int(self._lib.lp_wait_probe(self._h, int(spin_cycles), 1 if complete else 0))
+
     def residual_rhs(self, x, y, s, mode: str = "infeasible"):
         import torch
         _check_dev_f64(x, y, s)
@@ -373,6 +390,28 @@ def from_planted(lp, device: bool = False, **options) -> LPSolver:
         b = torch.from_numpy(np.ascontiguousarray(b)).cuda()
         c = torch.from_numpy(np.ascontiguousarray(c)).cuda()
     return LPSolver(A, b, c, lp.m, lp.n, dtype=lp.storage, **options)
+
+
+def csr_to_csc(row_ptr, col_idx, values, m: int, n: int, dtype: str = "f32"):
+    """lp_csr_to_csc: the CSR -> CSC sort lp_create applies to CSR input, on
+    host arrays.  Returns (col_ptr int64 [n+1], row_idx int32 [nnz], values)."""
+    lib = nat.load()
+    if dtype not in _DTYPES:
+        raise ValueError(f"dtype must be one of {sorted(_DTYPES)}, got {dtype!r}")
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    vals = np.ascontiguousarray(values, dtype=_NP_DT[dtype])
+    nnz = int(vals.shape[0])
+    _need(rp, m + 1, "row_ptr")
+    _need(ci, nnz, "col_idx")
+    cp = np.empty(n + 1, dtype=np.int64)
+    ri = np.empty(nnz, dtype=np.int32)
+    vo = np.empty(nnz, dtype=_NP_DT[dtype])
+    rc = lib.lp_csr_to_csc(m, n, nnz, _ptr(rp), _ptr(ci), _ptr(vals), _DTYPES[dtype], _ptr(cp), _ptr(ri),
+                           _ptr(vo))
+    if rc != nat.LP_OK:
+        raise LPError(rc, "invalid CSR structure or sizes")
+    return cp, ri, vo
 
 
 def phase1_start(A, b, m: int, n: int, dtype: str = "f64", csc=None, tol: float = 1e-7, **options):

@@ -30,3 +30,14 @@ def solver_for(lp, **opts):
 def adat_bound(A, d2, v):
     """|A| diag(d2) |A|^T |v|: the scale of the rounding error of A diag(d2) A^T v."""
     return np.abs(A) @ (d2 * (np.abs(A).T @ np.abs(v)))
+
+
+def fp32_lane_columns(m, n, storage):
+    """Bound on the columns one lane sums in FP32 in the inner-loop product:
+    the warp-per-column kernel (columns of at most 7 16-byte vectors per lane,
+    m <= 512 in FP32, m <= 1024 in BF16) spreads a CTA's columns over 16 warps
+    (n / 1216 + 64); the row-split kernel for taller columns gives each lane
+    4 columns of every tile of its CTA (n / 152 + 64)."""
+    vec = 4 if storage == "f32" else 8
+    vpl = -(-((m + vec - 1) // vec) // 32)
+    return n // 1216 + 64 if vpl < 8 else n // 152 + 64

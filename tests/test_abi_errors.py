@@ -45,6 +45,14 @@ def _csc(ptr, idx, val, m=M, n=N, dtype=nat.LP_F32):
     return A
 
 
+def _csr(ptr, idx, val, m=M, n=N, dtype=nat.LP_F32):
+    A = nat.LpMatrix()
+    A.m, A.n, A.fmt, A.dtype, A.on_device = m, n, nat.LP_CSR, dtype, 0
+    A.ptr, A.idx, A.val = ptr.ctypes.data, idx.ctypes.data, val.ctypes.data
+    A.nnz = int(ptr[-1]) if len(ptr) else 0
+    return A
+
+
 def _opts(lib, **kw):
     o = nat.LpOptions()
     lib.lp_options_default(ctypes.byref(o))
@@ -111,6 +119,35 @@ def test_host_csc_structure_is_checked(lib):
     rc, why = _create(lib, _csc(ptr, idx, val.astype(np.float32), dtype=nat.LP_BF16))
     assert rc == nat.LP_ERR_UNSUPPORTED and "FP32 or FP64" in why
     rc, why = _create(lib, _csc(ptr, idx, val), opt=_opts(lib, sketch=nat.LP_SKETCH_GAUSS))
+    assert rc == nat.LP_ERR_UNSUPPORTED and "dense A only" in why
+
+
+def test_host_csr_structure_is_checked(lib):
+    ptr = np.arange(0, 4 * M + 1, 4, dtype=np.int64)        # four entries per row
+    idx = (np.arange(4 * M) * 3 % N).astype(np.int32)
+    val = np.ones(4 * M, dtype=np.float32)
+    bad_ptr = ptr.copy()
+    bad_ptr[2], bad_ptr[3] = 13, 11                         # not monotone
+    rc, why = _create(lib, _csr(bad_ptr, idx, val))
+    assert rc == nat.LP_ERR_ARG and "monotone" in why
+    bad_idx = idx.copy()
+    bad_idx[5] = N                                          # column index out of range
+    rc, why = _create(lib, _csr(ptr, bad_idx, val))
+    assert rc == nat.LP_ERR_ARG and "out of range" in why
+    bad_idx[5] = -1
+    rc, why = _create(lib, _csr(ptr, bad_idx, val))
+    assert rc == nat.LP_ERR_ARG and "out of range" in why
+    A = _csr(ptr, idx, val)
+    A.nnz = 4 * M - 1                                       # ptr[m] != nnz
+    rc, why = _create(lib, A)
+    assert rc == nat.LP_ERR_ARG and "ptr[m]" in why
+    A = _csr(ptr, idx, val)
+    A.ptr = None
+    rc, why = _create(lib, A)
+    assert rc == nat.LP_ERR_ARG and "CSR A needs" in why
+    rc, why = _create(lib, _csr(ptr, idx, val, dtype=nat.LP_BF16))
+    assert rc == nat.LP_ERR_UNSUPPORTED and "FP32 or FP64" in why
+    rc, why = _create(lib, _csr(ptr, idx, val), opt=_opts(lib, sketch=nat.LP_SKETCH_GAUSS))
     assert rc == nat.LP_ERR_UNSUPPORTED and "dense A only" in why
 
 
@@ -229,3 +266,46 @@ def test_phase1_checks_a_host_matrix_before_reading_it(lib):
     assert call(_csc(back, idx, val)) == nat.LP_ERR_ARG
     neg = ptr - 1                                              # ptr[0] < 0
     assert call(_csc(neg, idx, val)) == nat.LP_ERR_ARG
+    csr_ptr = np.arange(0, 4 * M + 1, 4, dtype=np.int64)
+    csr_idx = (np.arange(4 * M) * 3 % N).astype(np.int32)
+    csr_val = np.ones(4 * M, dtype=np.float32)
+    bad = csr_idx.copy()
+    bad[0] = N                                                 # CSR column index out of range
+    assert call(_csr(csr_ptr, bad, csr_val)) == nat.LP_ERR_ARG
+    A = _csr(csr_ptr, csr_idx, csr_val)
+    A.idx = None
+    assert call(A) == nat.LP_ERR_ARG                           # no column indices
+
+
+def test_wait_probe_rejects_a_null_handle(lib):
+    assert lib.lp_wait_probe(None, 1000, 0) == nat.LP_ERR_ARG
+
+
+def test_csr_to_csc_is_a_stable_column_sort(lib):
+    # the conversion lp_create applies to CSR input, on the host (no CUDA call):
+    # identical to SciPy's CSR -> CSC (column-major, rows ascending in each
+    # column), for a matrix with unsorted and duplicate column indices in rows
+    sp = pytest.importorskip("scipy.sparse")
+    from paper_2209_08722_gb300.solver import LPError, csr_to_csc
+    rng = np.random.default_rng(3)
+    m, n = 37, 500
+    counts = rng.integers(0, 30, size=m)
+    rp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    ci = rng.integers(0, n, size=int(rp[-1])).astype(np.int32)
+    val = rng.standard_normal(int(rp[-1]))
+    for dtype, vals in (("f64", val), ("f32", val.astype(np.float32))):
+        cp, ri, vo = csr_to_csc(rp, ci, vals, m, n, dtype)
+        ref = sp.csr_matrix((vals, ci, rp), shape=(m, n)).tocsc()
+        assert np.array_equal(cp, ref.indptr) and np.array_equal(ri, ref.indices)
+        assert np.array_equal(vo, ref.data)
+    # each column's rows ascend, and the entries are the CSR's
+    cp, ri, vo = csr_to_csc(rp, ci, val, m, n, "f64")
+    for j in range(n):
+        assert np.all(np.diff(ri[cp[j]:cp[j + 1]]) >= 0)
+    assert sorted(zip(ri.tolist(), np.repeat(np.arange(n), np.diff(cp)).tolist(), vo.tolist())) == \
+        sorted(zip(np.repeat(np.arange(m), counts).tolist(), ci.tolist(), val.tolist()))
+    bad = ci.copy()
+    bad[0] = n
+    with pytest.raises(LPError):
+        csr_to_csc(rp, bad, val, m, n, "f64")
+    assert lib.lp_csr_to_csc(m, n, 0, None, None, None, nat.LP_F64, None, None, None) == nat.LP_ERR_ARG

@@ -1,6 +1,7 @@
-"""Parity at the full size the bench times: the 512 x 131072 FP32 planted LP
-with columns scaled by 10^U(-2, 2) (seed 0), with the solver options of the
-bench (CountSketch w = 4m, s = 4).  The oracle checks every output of the
+"""Parity at the full sizes of the workloads: the 512 x 131072 FP32 planted LP
+with columns scaled by 10^U(-2, 2) (seed 0) with its solver options
+(CountSketch w = 4m, s = 4); the 2048 x 524288 BF16 LP (CountSketch w = 4m,
+s = 2), which the bench times; the 4096 x 2,000,000 sparse LP (w = 3m, s = 2).  The oracle checks every output of the
 product (one FP64 matrix product), sampled columns of the sketch (one bucket
 at a time, from the oracle's own hash), and the solve against the planted
 closed-form optimum.
@@ -16,7 +17,7 @@ import pytest
 
 import lpgen
 from oracle import sketch
-from tests.gpu_helpers import EPS32, EPS64, adat_bound, dev, host, solver_for, torch_cuda
+from tests.gpu_helpers import EPS32, EPS64, adat_bound, dev, fp32_lane_columns, host, solver_for, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -83,9 +84,6 @@ def test_full_size_solve_reaches_the_planted_optimum(bench_lp):
 
 
 # ---- the sparse configuration at its full size --------------------------------
-# (the dense BF16 configuration, 2048 x 524288, shares its kernel launch
-# configuration, which depends on m, with the 2048-row cases of
-# test_gpu_kernels; generating its 10^9 entries here would take minutes)
 
 def test_c3_full_size_sparse_product_matches_fp64():
     torch = torch_cuda()
@@ -103,3 +101,94 @@ def test_c3_full_size_sparse_product_matches_fp64():
     per_cta = lp.n // 304 + 1
     tol = 4 * (8 + per_cta + 64) * EPS32 * bound
     assert np.all(np.abs(u - ref) <= tol + 1e-300)
+
+
+# ---- the other full-size workloads ----------------------------------------------
+
+def _blocked_product(lp, d2, v, block=32768):
+    """A (d2 o (A^T v)) and |A| (d2 o (|A|^T |v|)) in FP64 from the stored
+    values, one column block at a time (the FP64 copy of a 10^9-entry A would
+    take 8.6 GB)."""
+    u = np.zeros(lp.m)
+    bound = np.zeros(lp.m)
+    cols = lp.storage_array()
+    for j0 in range(0, lp.n, block):
+        blk = cols[j0:j0 + block]
+        if lp.storage == "bf16":
+            blk = (blk.astype(np.uint32) << np.uint32(16)).view(np.float32)
+        blk = blk.astype(np.float64)                     # (cols, m) = A[:, j0:j1]^T
+        u += blk.T @ (d2[j0:j0 + block] * (blk @ v))
+        ab = np.abs(blk)
+        bound += ab.T @ (d2[j0:j0 + block] * (ab @ np.abs(v)))
+    return u, bound
+
+
+@pytest.fixture(scope="module")
+def c4_lp():
+    return lpgen.make(lpgen.CONFIGS["c4"])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c4_full_size_product_matches_fp64(c4_lp, precision):
+    # 2048 x 524288 BF16 (2.1 GB): the row-split kernels, every output
+    torch = torch_cuda()
+    lp = c4_lp
+    rng = np.random.default_rng(15)
+    d2 = np.exp(rng.uniform(-6, 6, lp.n))
+    v = rng.standard_normal(lp.m)
+    ref, bound = _blocked_product(lp, d2, v)
+    cfg = lpgen.CONFIGS["c4"]
+    with solver_for(lp, s=cfg["s"], w_factor=cfg["w_factor"]) as S:
+        u = host(S.adat(dev(torch, d2), dev(torch, v), precision))
+    if precision == 1:
+        tol = 8 * (lp.m + lp.n) * EPS64 * bound
+    else:
+        tol = 4 * (lp.m + fp32_lane_columns(lp.m, lp.n, "bf16") + 64) * EPS32 * bound
+    assert np.all(np.abs(u - ref) <= tol), np.max(np.abs(u - ref) / bound)
+
+
+def test_c4_full_size_solve_reaches_the_planted_optimum(c4_lp):
+    # BF16 storage, FP32 products, FP64-class refinement; CountSketch w = 4m, s = 2
+    torch_cuda()
+    lp = c4_lp
+    cfg = lpgen.CONFIGS["c4"]
+    with solver_for(lp, s=cfg["s"], w_factor=cfg["w_factor"]) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+    assert info["status"] == 0, info
+    assert info["rel_gap"] <= 1e-8 and info["rp_rel"] <= 1e-8 and info["rd_rel"] <= 1e-8
+    assert abs(float(lp.c @ x) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert abs(float(lp.b @ y) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert np.all(x > 0) and np.all(s > 0)
+    basis = np.nonzero(lp.x_star > 0)[0]
+    assert set(np.argsort(-x)[:lp.m]) == set(basis)
+
+
+def test_c3_full_size_solve_from_csr_reaches_the_planted_objective():
+    # 4096 x 2,000,000 with 16 M nonzeros, given as CSR (the configured format):
+    # lp_create sorts it into exactly the CSC the generator built (checked on
+    # the host with the same sort), and the solve reaches the planted
+    # objective; A_B may be singular (empty rows), so only the objective and
+    # the residuals are compared (several optimal x may exist).  The sparse
+    # kernels scatter with shared-memory atomics, so the CSR and CSC solves
+    # agree to rounding, not bitwise.
+    torch_cuda()
+    import scipy.sparse as sp
+    from paper_2209_08722_gb300 import LPSolver, csr_to_csc
+    lp = lpgen.config_small("c3", 1)
+    vals = lp.val.astype(np.float32)
+    csr = sp.csc_matrix((vals, lp.row_idx, lp.col_ptr), shape=(lp.m, lp.n)).tocsr()
+    rp, ci = csr.indptr.astype(np.int64), csr.indices.astype(np.int32)
+    cp, ri, vo = csr_to_csc(rp, ci, csr.data, lp.m, lp.n, "f32")
+    assert np.array_equal(cp, lp.col_ptr) and np.array_equal(ri, lp.row_idx) and np.array_equal(vo, vals)
+    opts = dict(s=2, w_factor=3.0)
+    with LPSolver(None, lp.b, lp.c, lp.m, lp.n, dtype="f32", csr=(rp, ci, csr.data), **opts) as S:
+        x, y, s, info = S.solve(tol=1e-8)
+    assert info["status"] == 0, info
+    assert info["rel_gap"] <= 1e-8 and info["rp_rel"] <= 1e-8 and info["rd_rel"] <= 1e-8
+    assert abs(float(lp.c @ x) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert abs(float(lp.b @ y) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert np.all(x > 0) and np.all(s > 0)
+    with solver_for(lp, **opts) as S:
+        x2, _, _, info2 = S.solve(tol=1e-8)
+    assert info2["status"] == 0
+    assert abs(float(lp.c @ x2) - float(lp.c @ x)) <= 1e-8 * (1 + abs(lp.objective))

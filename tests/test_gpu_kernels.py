@@ -21,7 +21,7 @@ import pytest
 
 import lpgen
 from oracle import correction, ipm, pcg, sketch
-from tests.gpu_helpers import EPS32, EPS64, adat_bound, dev, host, solver_for, torch_cuda
+from tests.gpu_helpers import EPS32, EPS64, adat_bound, dev, fp32_lane_columns, host, solver_for, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +35,14 @@ SHAPES = [
     (256, 9000, "bf16"),
     (19, 1000, "bf16"),
     (2048, 3000, "bf16"),
+    # tall columns: the row-split kernels (several column groups, one group,
+    # and two slabs per warp), with ragged row vectors and a ragged last tile
+    (600, 5003, "f32"),
+    (1500, 7001, "f32"),
+    (2048, 3001, "f32"),
+    (1100, 4003, "bf16"),
+    (4096, 6007, "bf16"),
+    (5000, 6001, "bf16"),
 ]
 
 
@@ -58,13 +66,14 @@ def test_adat_matches_fp64_product(m, n, storage, precision):
     if storage == "f64" or precision == 1:
         tol = 8 * (m + n) * EPS64 * bound
     else:
-        L = n // 1216 + 64
+        L = fp32_lane_columns(m, n, storage)
         tol = 4 * (m + L + 64) * EPS32 * bound
     assert np.all(np.abs(u - ref) <= tol + 1e-300), np.max(np.abs(u - ref) / bound)
 
 
 @pytest.mark.parametrize("mode", ["infeasible", "feasible"])
-@pytest.mark.parametrize("m,n,storage", [(64, 4099, "f64"), (512, 20011, "f32"), (37, 2000, "bf16")])
+@pytest.mark.parametrize("m,n,storage", [(64, 4099, "f64"), (512, 20011, "f32"), (37, 2000, "bf16"),
+                                         (700, 4001, "f32"), (2048, 3001, "bf16"), (5000, 6001, "bf16")])
 def test_residual_rhs(mode, m, n, storage):
     torch = torch_cuda()
     lp = _lp(m, n, storage, seed=2)
@@ -199,10 +208,10 @@ def test_normal_solve_fixed_iterations_matches_oracle_cg(storage):
     assert np.linalg.norm(v) <= np.sqrt(3 * n * mu) * info["f_norm"] * (1 + 1e-6)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("storage,m,n", [("f64", 96, 12000), ("f32", 96, 12000), ("bf16", 96, 12000),
+                                         ("f32", 700, 30000), ("bf16", 1100, 40000)])
 @pytest.mark.parametrize("inner", [0, 1])
-def test_normal_solve_converges_to_cholesky(storage, inner):
-    m, n = 96, 12000
+def test_normal_solve_converges_to_cholesky(storage, m, n, inner):
     lp = _lp(m, n, storage, seed=11)
     rng = np.random.default_rng(12)
     D = np.exp(rng.uniform(-3, 3, n))
@@ -217,7 +226,8 @@ def test_normal_solve_converges_to_cholesky(storage, inner):
 
 
 @pytest.mark.parametrize("mode", ["infeasible", "feasible"])
-@pytest.mark.parametrize("m,n,storage", [(64, 4099, "f64"), (512, 20011, "f32"), (33, 3000, "bf16")])
+@pytest.mark.parametrize("m,n,storage", [(64, 4099, "f64"), (512, 20011, "f32"), (33, 3000, "bf16"),
+                                         (700, 4001, "f32"), (2048, 3001, "bf16"), (5000, 6001, "bf16")])
 def test_directions(mode, m, n, storage):
     torch = torch_cuda()
     lp = _lp(m, n, storage, seed=13)

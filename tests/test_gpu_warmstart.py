@@ -37,6 +37,40 @@ def test_mlp_forward_gradients_and_adam_match_oracle():
     assert np.abs(M.params() - po).max() <= 1e-5
 
 
+def test_mlp_tensor_core_contractions_at_several_tiles_match_oracle():
+    # widths that span several 128 x 128 tiles of the tcgen05 GEMM with ragged
+    # edges, and K lengths over many 16-wide chunks, in all three operand forms
+    # (forward NN, weight gradients NT, input gradients TN): the FP32-class
+    # split-TF32 products against the FP64 oracle; the bound grows with the
+    # contraction length (FP32 accumulation over K = B for the weight gradients)
+    torch = torch_cuda()
+    from paper_2209_08722_gb300 import Mlp
+    n_in, hid, n_out, B = 300, 200, 150, 333
+    M = Mlp(n_in, hid, n_out, seed=4)
+    rng = np.random.default_rng(1)
+    flat = (rng.standard_normal(M.num_params) * 0.1).astype(np.float32)
+    M.set_params(flat)
+    X = rng.standard_normal((B, n_in)).astype(np.float32)
+    T = rng.standard_normal((B, n_out)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    P = omlp.unflatten(flat.astype(np.float64), n_in, hid, n_out)
+    Yo, _ = omlp.forward(P, X.T.astype(np.float64))
+    Y = M.forward(Xd).cpu().numpy()
+    assert np.abs(Y - Yo.T).max() <= 1e-5 * np.abs(Yo).max()
+    loss = M.loss_grad(Xd, Td)
+    lo, go = omlp.loss_and_grads(P, X.T.astype(np.float64), T.T.astype(np.float64))
+    gof = omlp.flatten(go)
+    assert abs(loss - lo) <= 1e-5 * lo
+    g = M.grads()
+    # per block (W1, b1, W2, b2, W3, b3): within 4e-5 of the block's largest gradient
+    sizes = [hid * n_in, hid, hid * hid, hid, n_out * hid, n_out]
+    off = 0
+    for size in sizes:
+        blk, ref = g[off:off + size], gof[off:off + size]
+        assert np.abs(blk - ref).max() <= 4e-5 * np.abs(ref).max(), off
+        off += size
+
+
 def test_learned_warm_start_keeps_the_solution_and_saves_inner_iterations():
     torch = torch_cuda()
     from paper_2209_08722_gb300 import Mlp

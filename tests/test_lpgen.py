@@ -98,8 +98,10 @@ def test_named_workloads_and_the_bench_agree():
     assert (C["c3"]["kind"], C["c3"]["m"], C["c3"]["n"], C["c3"]["nnz_per_col"]) == ("sparse", 4096, 2_000_000, 8)
     assert (C["c4"]["m"], C["c4"]["n"], C["c4"]["storage"]) == (2048, 524288, "bf16")
     import bench
-    assert (bench.M, bench.N_COLS, bench.S_BLOCKS, bench.W_FACTOR) == (
-        C["c2"]["m"], C["c2"]["n"], C["c2"]["s"], C["c2"]["w_factor"])
+    for name in ("c2", "c4"):
+        b = bench.BENCH[name]
+        assert (b["m"], b["n"], b["s"], b["w_factor"], b["dtype"]) == (
+            C[name]["m"], C[name]["n"], C[name]["s"], C[name]["w_factor"], C[name]["storage"])
     small = lpgen.config_small("c2", 64)
     assert (small.m, small.n, small.storage) == (8, 2048, "f32")
 
