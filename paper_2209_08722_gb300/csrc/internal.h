@@ -95,7 +95,7 @@ struct RowsPlan {
   int rpt = 0, nb = 0, ntiles = 0, stages = 0, grid = 0, smem = 0;
   bool ok = false;
 };
-RowsPlan make_rows_plan(int lda, long long n, int esz, int num_sms);
+RowsPlan make_rows_plan(int lda, long long n, int esz, int num_sms, bool df);
 cudaError_t launch_rows(int dtype, bool df, int mode, const StreamArgs& a, const RowsPlan& p,
                         cudaStream_t st, bool pdl);
 

@@ -178,7 +178,8 @@ struct lp_handle {
   int* hinfo = nullptr;       // pinned
   double* hval = nullptr;     // pinned staging for scalars
   StreamPlan plan;
-  RowsPlan rplan;          // row-split kernels for tall columns (stream_rows.cu)
+  RowsPlan rplan;          // row-split kernels for tall columns (stream_rows.cu): FP32 product
+  RowsPlan rplan_df;       // ... and the double-float passes
   bool use_rows = false;   // the FP32 product and the double-float passes use them
   std::string err;
   // profiling of the hot product kernel
@@ -357,7 +358,7 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
   else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st, pdl);
   else if (h->use_rows) {
     // the refresh inside the inner loop follows a GEMV closely
-    e = launch_rows(h->dtype, true, M_ADAT, a, h->rplan, h->st, skip_level >= 1);
+    e = launch_rows(h->dtype, true, M_ADAT, a, h->rplan_df, h->st, skip_level >= 1);
   } else if (h->use_df) {
     a.pdl = skip_level >= 1 ? 1 : 0;  // the refresh inside the inner loop follows a GEMV closely
     e = launch_stream_df(h->dtype, M_ADAT, a, h->plan, h->st);
@@ -997,7 +998,7 @@ int residual_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
     a.out_df[0] = h->dfout[0];
     a.out_df[1] = h->d2df;
     a.red_partials = nullptr;
-    if (h->use_rows) CK(launch_rows(h->dtype, true, M_RESID, a, h->rplan, h->st, false));
+    if (h->use_rows) CK(launch_rows(h->dtype, true, M_RESID, a, h->rplan_df, h->st, false));
     else CK(launch_stream_df(h->dtype, M_RESID, a, h->plan, h->st));
     DfUnpackArgs up{0, h->n, h->dfout[0], h->d2df, h->rd, h->d2d, h->d2f, h->x, h->s, h->c, h->sc,
                     h->vpart, h->tickets + 7};
@@ -1040,7 +1041,7 @@ int direction_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
     a.out_df[0] = h->dfout[0];
     a.out_df[1] = h->dfout[1];
     a.red_partials = nullptr;
-    if (h->use_rows) CK(launch_rows(h->dtype, true, M_DIR, a, h->rplan, h->st, false));
+    if (h->use_rows) CK(launch_rows(h->dtype, true, M_DIR, a, h->rplan_df, h->st, false));
     else CK(launch_stream_df(h->dtype, M_DIR, a, h->plan, h->st));
     DfUnpackArgs up{1, h->n, h->dfout[0], h->dfout[1], h->dx, h->ds, nullptr, h->x, h->s, nullptr, h->sc,
                     h->vpart, h->tickets + 7};
@@ -1268,8 +1269,9 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   // not grow with m; the warp-per-column kernels would spill there.
   if (!h->sparse && h->dtype != LP_F64) {
     const int vpl = fused_vpl(h->lda, h->esz);
-    h->rplan = make_rows_plan(h->lda, h->n, h->esz, h->num_sms);
-    h->use_rows = h->rplan.ok && (vpl == 0 || vpl >= 8);
+    h->rplan = make_rows_plan(h->lda, h->n, h->esz, h->num_sms, false);
+    h->rplan_df = make_rows_plan(h->lda, h->n, h->esz, h->num_sms, true);
+    h->use_rows = h->rplan.ok && h->rplan_df.ok && (vpl == 0 || vpl >= 8);
     if (h->use_rows) h->use_df = h->use_df_resid = h->use_df_dir = true;
   }
   if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
@@ -1353,7 +1355,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->uw, (size_t)h->w));
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));
-  const int max_grid = std::max(h->plan.grid, h->use_rows ? h->rplan.grid : 0);
+  const int max_grid = std::max(h->plan.grid, h->use_rows ? std::max(h->rplan.grid, h->rplan_df.grid) : 0);
   RET(h->alloc(reinterpret_cast<char**>(&h->partials), (size_t)max_grid * 2 * h->lda * 8));
   RET(h->alloc(&h->gpart, (size_t)((max_grid + kGroup - 1) / kGroup) * 2 * h->lda));
   RET(h->alloc(&h->gtickets, kMaxGroups + 1));

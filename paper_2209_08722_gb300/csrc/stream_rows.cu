@@ -8,9 +8,10 @@
 // whole stream:
 //
 //   * rows come in slabs of 32 16-byte row vectors (one per lane); a warp owns
-//     RPT consecutive slabs, nsw warps cover a column, and the 16 consumer
-//     warps form L = 16 / nsw column groups;
-//   * a tile holds CPT = 4 columns per group (nb = 4 L columns, about 32 KB),
+//     RPT consecutive slabs (two for the FP32 product, one for the
+//     double-float passes where the rows allow), nsw warps cover a column, and
+//     the 16 consumer warps form L = 16 / nsw column groups;
+//   * a tile holds CPT = 4 columns per group (nb = 4 L columns, 32-64 KB),
 //     streamed by one producer lane with cp.async.bulk into a ring of stages
 //     (full/empty mbarriers, as in the other streaming kernels);
 //   * phase 1: each warp forms its slab's partial of a_j^T v for the group's
@@ -21,9 +22,10 @@
 //     formulas) are summed over the nsw partials in a fixed order by lane c of
 //     every warp of the group (so all of them get identical values) and
 //     broadcast by shuffles;
-//   * phase 2: each lane adds a_j t_j to the accumulators of its rows, using
-//     the column slices kept in registers since phase 1 (raw 16-byte vectors,
-//     converted on use), so shared memory is read once per element;
+//   * phase 2: each lane adds a_j t_j to the accumulators of its rows, reading
+//     its column slices from the stage again (shared memory is read twice per
+//     element; keeping them in registers would not leave room for the
+//     accumulators);
 //   * the L groups' accumulators of the same rows are combined at the end and
 //     go through the deterministic two-level reduction and the mode epilogues
 //     shared with the other streaming kernels.
@@ -54,6 +56,7 @@ __host__ __device__ inline void rows_geom(int lda, int esz, int rpt, int* nsw, i
 struct RowsLayout {
   SmemLayout s;    // stages (A tile + per-column vector tiles), barriers, reduction buffer
   int part_off;    // [2][nsw][nb] float2 partial dots
+  int v_off;       // v as FP32 (hi) and, for the double-float passes, its low parts: [2][lda]
   int total;
 };
 
@@ -61,7 +64,8 @@ __host__ __device__ inline RowsLayout rows_layout(int lda, int esz, int nb, int 
   RowsLayout R;
   R.s = make_layout(lda, esz, nb, stages, 0);
   R.part_off = R.s.total;
-  R.total = R.part_off + align_up_i(2 * nsw * nb * 8, 128);
+  R.v_off = R.part_off + align_up_i(2 * nsw * nb * 8, 128);
+  R.total = R.v_off + align_up_i(2 * lda * 4, 128);
   return R;
 }
 
@@ -109,9 +113,6 @@ __device__ __forceinline__ dfl cv_pair(const char* stage, const SmemLayout& L, i
 
 template <typename TA, bool DF, int MODE, int RPT>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
-  // the FP32 product pipelines its tiles; the double-float passes keep one
-  // tile's columns in registers (their accumulator pairs need the room)
-  constexpr bool PIPE = !DF;
   constexpr int VEC = VecOf<TA>::N;
   constexpr int CPT = kRowsCPT;
   constexpr int NACC = (MODE == M_RESID) ? 2 : ((MODE == M_ADAT) ? 1 : 0);
@@ -151,40 +152,45 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
   }
   __syncthreads();
 
+  // v in shared memory (read once per tile per lane): v_hi[lda], v_lo[lda]
+  float* v_hi = reinterpret_cast<float*>(smem + R.v_off);
+  float* v_lo = v_hi + a.lda;
+  for (int i = tid; i < a.lda; i += blockDim.x) {
+    const double v = i < a.m ? a.vin[i] : 0.0;
+    v_hi[i] = (float)v;
+    v_lo[i] = (float)(v - (double)v_hi[i]);
+  }
+  __syncthreads();
   // this lane's rows: row vector (qs * RPT + k) * 32 + lane, k < RPT
-  float vh[RPT][VEC], vl[DF ? RPT : 1][VEC];
   float ah[NA][RPT][VEC], al[DF ? NA : 1][DF ? RPT : 1][VEC];
 #pragma unroll
-  for (int k = 0; k < RPT; ++k) {
-    const int rv = (qs * RPT + k) * 32 + lane;
+  for (int k = 0; k < RPT; ++k)
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-      const int i = rv * VEC + e;
-      const double v = (active && rv < RV && i < a.m) ? a.vin[i] : 0.0;
-      vh[k][e] = (float)v;
-      if (DF) vl[DF ? k : 0][e] = (float)(v - (double)vh[k][e]);
+    for (int e = 0; e < VEC; ++e)
 #pragma unroll
       for (int t = 0; t < NA; ++t) {
         ah[t][k][e] = 0.0f;
         if (DF) al[DF ? t : 0][DF ? k : 0][e] = 0.0f;
       }
-    }
-  }
   bool aborted = false;
 
   if (warp == kConsumerWarps) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0, st = 0;
+      uint32_t parity = 1u;  // phase of empty[st] to wait for (the first pass waits for none)
       for (int i = 0; i < my_tiles; ++i) {
-        const int st = i % S;
-        if (i >= S && !mbar_wait(&empty[st], (uint32_t)(((i / S) - 1) & 1), a.err)) {
+        if (i >= S && !mbar_wait(&empty[st], parity, a.err)) {
           aborted = true;
           break;
         }
         fence_proxy_async_smem();
         issue_tile<TA>(a, R.s, smem, full, st, (int)blockIdx.x + i * (int)gridDim.x);
         issued = i + 1;
+        if (++st == S) {
+          st = 0;
+          parity ^= 1u;
+        }
       }
       if (aborted || *a.err != ERR_NONE)
         for (int j = (issued > S ? issued - S : 0); j < issued; ++j)
@@ -192,43 +198,62 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
     }
   } else {
     // ---------------- consumers ----------------
-    // phase 1 of tile i: wait for its stage, load this warp's slab of the
-    // group's four columns into `raw`, and publish the slab partials of
-    // a_j^T v in pbuf[i & 1]; returns whether the stage's wait succeeded
-    auto phase1 = [&](int i, uint4 (&raw)[CPT][RPT]) -> bool {
-      const int st = i % S;
-      const bool ok = mbar_wait(&full[st], (uint32_t)((i / S) & 1), a.err);
-      const long long j0 = (long long)((int)blockIdx.x + i * (int)gridDim.x) * a.nb;
-      const int ncols = (int)min((long long)a.nb, a.n - j0);
+    // phase 1 of a tile: wait for its stage, form this warp's slab partials
+    // of a_j^T v for the group's four columns and write them to partial
+    // buffer pb; returns whether the stage's wait succeeded
+    auto phase1 = [&](int st, uint32_t parity, int ncols, int pb) -> bool {
+      const bool ok = mbar_wait(&full[st], parity, a.err);
       const TA* At = reinterpret_cast<const TA*>(smem + (size_t)st * R.s.stage_bytes);
+      // partial dots of the four columns: two interleaved sums per column
+      float ph[CPT][2], pl[CPT][2];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) ph[c][0] = ph[c][1] = pl[c][0] = pl[c][1] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int rv = (qs * RPT + k) * 32 + lane;
+        const bool row_ok = ok && active && rv < RV;
+        float vk[VEC], vkl[DF ? VEC : 1];
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4) {
+          const float4 t4 = row_ok ? *reinterpret_cast<const float4*>(v_hi + rv * VEC + e)
+                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          vk[e] = t4.x;
+          vk[e + 1] = t4.y;
+          vk[e + 2] = t4.z;
+          vk[e + 3] = t4.w;
+          if (DF) {
+            const float4 l4 = row_ok ? *reinterpret_cast<const float4*>(v_lo + rv * VEC + e)
+                                     : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            vkl[DF ? e : 0] = l4.x;
+            vkl[DF ? e + 1 : 0] = l4.y;
+            vkl[DF ? e + 2 : 0] = l4.z;
+            vkl[DF ? e + 3 : 0] = l4.w;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          const int jj = grp * CPT + c;
+          uint4 raw = make_uint4(0u, 0u, 0u, 0u);
+          if (row_ok && jj < ncols)
+            raw = *reinterpret_cast<const uint4*>(At + (size_t)jj * a.lda + (size_t)rv * VEC);
+          float av[VEC];
+          unpack16<TA>(raw, av);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            if (DF) df_fma(av[e], vk[e], vkl[DF ? e : 0], ph[c][e & 1], pl[c][e & 1]);
+            else ph[c][e & 1] = fmaf(av[e], vk[e], ph[c][e & 1]);
+          }
+        }
+      }
       float dh[CPT], dl[CPT];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
-        const int jj = grp * CPT + c;
-        const bool col_ok = ok && active && jj < ncols;
-        float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f}, pl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-          const int rv = (qs * RPT + k) * 32 + lane;
-          raw[c][k] = make_uint4(0u, 0u, 0u, 0u);
-          if (col_ok && rv < RV)
-            raw[c][k] = *reinterpret_cast<const uint4*>(At + (size_t)jj * a.lda + (size_t)rv * VEC);
-          float av[VEC];
-          unpack16<TA>(raw[c][k], av);
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) {
-            if (DF) df_fma(av[e], vh[k][e], vl[DF ? k : 0][e], ph[e & 3], pl[e & 3]);
-            else ph[e & 3] = fmaf(av[e], vh[k][e], ph[e & 3]);
-          }
-        }
         if (DF) {
-          df_add(ph[0], pl[0], ph[1], pl[1]);
-          df_add(ph[2], pl[2], ph[3], pl[3]);
-          df_add(ph[0], pl[0], ph[2], pl[2]);
-          dh[c] = ph[0];
-          dl[c] = pl[0];
+          df_add(ph[c][0], pl[c][0], ph[c][1], pl[c][1]);
+          dh[c] = ph[c][0];
+          dl[c] = pl[c][0];
         } else {
-          dh[c] = (ph[0] + ph[1]) + (ph[2] + ph[3]);
+          dh[c] = ph[c][0] + ph[c][1];
           dl[c] = 0.0f;
         }
       }
@@ -262,18 +287,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
       const int c = 2 * (lane >> 4) + ((lane >> 3) & 1);
       const int jj = grp * CPT + c;
       if (ok && active && (lane & 7) == 0 && jj < ncols)
-        part_s[(size_t)(i & 1) * nsw * a.nb + (size_t)qs * a.nb + jj] = make_float2(yh, DF ? yl : 0.0f);
+        part_s[(size_t)pb * nsw * a.nb + (size_t)qs * a.nb + jj] = make_float2(yh, DF ? yl : 0.0f);
       return ok;
     };
-    // the rest of tile i once its partials are published: the column scalars
+    // the rest of the tile once its partials are published: the column scalars
     // (lanes 8c .. 8c+7 sum column c's nsw slab partials by a fixed tree, lane
     // 8c forms t_c), then acc += a_j t_j from `raw`, then release the stage
-    auto finish = [&](int i, const uint4 (&raw)[CPT][RPT]) {
-      const int st = i % S;
-      const long long j0 = (long long)((int)blockIdx.x + i * (int)gridDim.x) * a.nb;
-      const int ncols = (int)min((long long)a.nb, a.n - j0);
+    auto finish = [&](int st, long long j0, int ncols, int pb) {
       const char* stage = smem + (size_t)st * R.s.stage_bytes;
-      const float2* pbuf = part_s + (size_t)(i & 1) * nsw * a.nb;
+      const float2* pbuf = part_s + (size_t)pb * nsw * a.nb;
       const int c = lane >> 3, q0 = lane & 7;
       const int jj = grp * CPT + c;
       const bool col_ok = active && jj < ncols;
@@ -343,10 +365,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
             uh = __shfl_sync(0xffffffffu, t1h, cc * 8);
             ul = __shfl_sync(0xffffffffu, t1l, cc * 8);
           }
+          const int jj2 = grp * CPT + cc;
 #pragma unroll
           for (int k = 0; k < RPT; ++k) {
+            // the column slice again from the stage (still held: this warp
+            // has not released it), rather than kept in registers
+            const int rv = (qs * RPT + k) * 32 + lane;
+            uint4 raw = make_uint4(0u, 0u, 0u, 0u);
+            if (active && rv < RV && jj2 < ncols)
+              raw = *reinterpret_cast<const uint4*>(reinterpret_cast<const TA*>(stage) + (size_t)jj2 * a.lda +
+                                                    (size_t)rv * VEC);
             float av[VEC];
-            unpack16<TA>(raw[cc][k], av);
+            unpack16<TA>(raw, av);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
               if (DF) {
@@ -362,33 +392,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
     };
-    uint4 rawA[CPT][RPT], rawB[CPT][RPT];
-    if (!PIPE) {
-      // phase 1, publish, finish: one tile at a time
-      for (int i = 0; i < my_tiles; ++i) {
-        const bool ok = phase1(i, rawA);
-        if (consumers_bar_or(!ok)) {
-          aborted = true;
-          break;
-        }
-        finish(i, rawA);
+    // phase 1, publish, finish, one tile at a time; the stage index, its
+    // parity and the tile's first column advance incrementally
+    int st = 0, pb = 0;
+    uint32_t parity = 0;
+    long long j0 = (long long)blockIdx.x * a.nb;
+    const long long jstep = (long long)gridDim.x * a.nb;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int ncols = (int)min((long long)a.nb, a.n - j0);
+      const bool ok = phase1(st, parity, ncols, pb);
+      if (consumers_bar_or(!ok)) {
+        aborted = true;
+        break;
       }
-    } else if (my_tiles > 0) {
-      // software pipelined: phase 1 of tile i + 1 runs before tile i is
-      // finished, so the column-sum latency overlaps the next tile's loads;
-      // the partial buffers alternate, and the barrier after phase 1 of tile
-      // i + 1 comes after every warp finished reading those of tile i - 1
-      auto step = [&](int i, const uint4 (&cur)[CPT][RPT], uint4 (&nxt)[CPT][RPT]) -> bool {
-        const bool has_next = i + 1 < my_tiles;
-        bool ok = true;
-        if (has_next) ok = phase1(i + 1, nxt);
-        finish(i, cur);
-        return has_next && consumers_bar_or(!ok);
-      };
-      aborted = consumers_bar_or(!phase1(0, rawA));
-      for (int i = 0; !aborted && i < my_tiles; i += 2) {
-        if (step(i, rawA, rawB)) aborted = true;
-        else if (i + 1 < my_tiles && step(i + 1, rawB, rawA)) aborted = true;
+      finish(st, j0, ncols, pb);
+      j0 += jstep;
+      pb ^= 1;
+      if (++st == S) {
+        st = 0;
+        parity ^= 1u;
       }
     }
   }
@@ -434,12 +456,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_rows(const StreamArgs a) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-RowsPlan make_rows_plan(int lda, long long n, int esz, int num_sms) {
+RowsPlan make_rows_plan(int lda, long long n, int esz, int num_sms, bool df) {
   RowsPlan p;
   if (esz != 4 && esz != 2) return p;
   const int rv = lda / (16 / esz);
   const int ns = (rv + 31) / 32;
+  // slabs per warp: as few as cover the rows with 16 warps; the FP32 product
+  // takes two when it can, so that each lane's share of a column (and of the
+  // per-column overhead: addressing, reductions) doubles, while the
+  // double-float passes need the registers for their accumulator pairs
   p.rpt = (ns + kConsumerWarps - 1) / kConsumerWarps;
+  if (!df && ns >= 2) p.rpt = std::max(p.rpt, 2);
   if (p.rpt < 1 || p.rpt > 2) return p;
   int nsw = 0, groups = 0;
   rows_geom(lda, esz, p.rpt, &nsw, &groups);
