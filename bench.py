@@ -391,30 +391,44 @@ def run_gauss_kernel(args):
 def run_batch(args):
     """Batched-LP family (m ~ U{32..512}, n = m U{64..256}, FP32, CountSketch
     w = 4m, s = 2): the same LPs solved one at a time and with lp_solve_batch
-    (concurrent handles, one stream each); wall time of each, LPs per second."""
+    (concurrent handles, one stream each); every handle replays its blocks of
+    inner steps from CUDA graphs and takes the product's tile shape from the
+    autotuner (timed at lp_create, cached per shape).  Wall time of each,
+    LPs per second, and every LP's gap and objective error against its
+    planted optimum."""
     import torch
     from paper_2209_08722_gb300 import LPSolver, solve_batch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     lps = lpgen.batch_family(args.batch, seed=0)
-    solvers = [LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=2) for lp in lps]
-    for S in solvers:                       # warm-up: every kernel shape once
+    t0 = time.perf_counter()
+    solvers = [LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype="f32", s=2, autotune=1, graphs=1)
+               for lp in lps]
+    t_create = time.perf_counter() - t0
+    for S in solvers:                       # warm-up: every kernel shape and graph once
         S.solve(tol=TOL)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     seq = [S.solve(tol=TOL) for S in solvers]
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
+    for S in solvers:
+        S.reset_kernel_stats()
     t0 = time.perf_counter()
     bat = solve_batch(solvers, tol=TOL)
     torch.cuda.synchronize()
     t_bat = time.perf_counter() - t0
-    optimal = sum(1 for lp, b in zip(lps, bat) if b[3]["status"] == 0
-                  and abs(float(lp.c @ b[0]) - lp.objective) <= 1e-7 * (1 + abs(lp.objective)))
+    replays = sum(S.kernel_stats()["graph_replays"] for S in solvers)
+    errs = [abs(float(lp.c @ b[0]) - lp.objective) / (1 + abs(lp.objective)) for lp, b in zip(lps, bat)]
+    gaps = [b[3]["rel_gap"] for b in bat]
+    optimal = sum(1 for e, b in zip(errs, bat) if b[3]["status"] == 0 and e <= 1e-7)
     same = all(np.array_equal(a[0], b[0]) for a, b in zip(seq, bat))
     print(json.dumps({"mode": "batch", "lps": len(lps), "total_bytes_A": int(sum(lp.m * lp.n * 4 for lp in lps)),
+                      "create_s_with_autotune": t_create,
                       "sequential_s": t_seq, "batched_s": t_bat, "lps_per_s": len(lps) / t_bat,
-                      "speedup": t_seq / t_bat, "optimal": optimal,
-                      "statuses": [b[3]["status"] for b in bat], "identical_to_sequential": same}),
+                      "speedup": t_seq / t_bat, "optimal": optimal, "max_rel_gap": max(gaps),
+                      "max_objective_rel_err": max(errs), "graph_replays": replays,
+                      "statuses": sorted(set(b[3]["status"] for b in bat)),
+                      "identical_to_sequential": same}),
           flush=True)
     for S in solvers:
         S.close()
@@ -422,89 +436,104 @@ def run_batch(args):
 
 
 def run_warm_start(args):
-    """Learned warm start on the BF16 dense family at 1/8 scale (m = 256,
-    n = 65536): record (features, dy) from the solves of training LPs (seeds
-    1..24), train the 3m -> 1024 -> 1024 -> m model, then solve held-out LPs
-    (seeds 1000..1007) cold and warm-started; inner iterations and the
-    objective error of each."""
+    """Learned warm start on the BF16 dense family of the configured workload's
+    shape (c4: m = 2048, n = 524288; --ws-scale 8 divides m and n by 8):
+    record (features, dy) from the solves of training LPs (seeds
+    1 .. --train-lps), train the 3m -> 1024 -> 1024 -> m model on the GPU
+    (the project's tensor-core GEMMs), then solve held-out LPs (seeds 1000 ..
+    1000 + --test-lps - 1) cold, with the previous dy, and with the model's
+    proposal; inner iterations, wall time and the errors against the planted
+    optimum of each, and the plain FP32-storage form of the same LPs (cold)
+    for the wall-time comparison."""
     import torch
     from paper_2209_08722_gb300 import LPSolver, Mlp
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    m, n = 256, 65536
+    cfg = lpgen.CONFIGS["c4"]
+    m, n = cfg["m"] // args.ws_scale, cfg["n"] // args.ws_scale
+    opts = dict(s=cfg["s"], w_factor=cfg["w_factor"])
 
     def make(seed):
-        return lpgen.planted_dense(m, n, seed=seed, storage="bf16")
+        return lpgen.planted_dense_blocked(m, n, seed=seed, storage="bf16")
 
-    def solver(lp):
-        return LPSolver(lp.storage_array(), lp.b, lp.c, m, n, dtype="bf16", s=2)
-    cap = 4000
+    def solver(lp, dtype="bf16"):
+        A = lp.storage_array()
+        if dtype == "f32":  # the BF16 values, exact in FP32
+            A = (A.astype(np.uint32) << np.uint32(16)).view(np.float32)
+        return LPSolver(A, lp.b, lp.c, m, n, dtype=dtype, **opts)
+
+    def errors(lp, x, y, s):
+        return {"objective": abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective)),
+                "x": float(np.linalg.norm(x - lp.x_star) / np.linalg.norm(lp.x_star)),
+                "y": float(np.linalg.norm(y - lp.y_star) / np.linalg.norm(lp.y_star))}
+    cap = args.train_lps * 80 + 64
     recX = torch.zeros(cap, 3 * m, device="cuda")
     recT = torch.zeros(cap, m, device="cuda")
     total = 0
-    for seed in range(1, 25):
-        S = solver(make(seed))
-        S.set_warm_start("none", None, recX[total:], recT[total:])
-        S.solve(tol=TOL)
-        total += S.warm_start_stats()["recorded"]
-        S.close()
+    t0 = time.perf_counter()
+    for seed in range(1, args.train_lps + 1):
+        lp = make(seed)
+        with solver(lp) as S:
+            S.set_warm_start("none", None, recX[total:], recT[total:])
+            S.solve(tol=TOL)
+            total += S.warm_start_stats()["recorded"]
+        del lp
+    t_record = time.perf_counter() - t0
     net = Mlp(3 * m, 1024, m, seed=7)
     X, T = recX[:total].contiguous(), recT[:total].contiguous()
-    loss = net.train_step(X, T, 1e-3)       # first step: library and kernel loading, untimed
+    del recX, recT
+    loss0 = net.train_step(X, T, 1e-3)      # first step: library and kernel loading, untimed
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for it in range(1, 2000):
-        loss = net.train_step(X, T, 1e-3 if it < 1400 else 3e-4)
+    steps = args.train_steps
+    for it in range(1, steps):
+        loss = net.train_step(X, T, 1e-3 if it < int(0.7 * steps) else 3e-4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    tests = [make(seed) for seed in range(1000, 1008)]
-    solvers = [solver(lp) for lp in tests]
-    for mode in ("none", "model"):          # warm-up: every kernel shape and library path once
-        solvers[0].set_warm_start(mode, net if mode == "model" else None)
-        solvers[0].solve(tol=TOL)
-    torch.cuda.synchronize()
-    out = {}
-    for mode in ("none", "previous", "model"):
-        inner, outer, err, acc, props, secs = 0, 0, 0.0, 0, 0, 0.0
-        for lp, S in zip(tests, solvers):
-            S.set_warm_start(mode, net if mode == "model" else None)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            x, _, _, info = S.solve(tol=TOL)
-            secs += time.perf_counter() - t0
-            st = S.warm_start_stats()
-            inner += info["inner_total"]
-            outer += info["outer_iterations"]
-            err = max(err, abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective)))
-            acc += st["accepted"]
-            props += st["proposals"]
-        out[mode] = {"inner_total": inner, "outer_total": outer, "max_objective_rel_err": err,
-                     "accepted": acc, "proposals": props, "solve_s": secs}
-    for S in solvers:
-        S.close()
-    # the plain FP32 form of the same LPs (the BF16 values are exact in FP32), cold
-    f32 = [LPSolver(np.ascontiguousarray(lp.A.T, dtype=np.float32), lp.b, lp.c, m, n, dtype="f32", s=2)
-           for lp in tests]
-    f32[0].solve(tol=TOL)
-    torch.cuda.synchronize()
-    inner, outer, err, secs = 0, 0, 0.0, 0.0
-    for lp, S in zip(tests, f32):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, _, _, info = S.solve(tol=TOL)
-        secs += time.perf_counter() - t0
-        inner += info["inner_total"]
-        outer += info["outer_iterations"]
-        err = max(err, abs(float(lp.c @ x) - lp.objective) / (1 + abs(lp.objective)))
-        S.close()
-    out["fp32_cold"] = {"inner_total": inner, "outer_total": outer, "max_objective_rel_err": err, "solve_s": secs}
-    print(json.dumps({"mode": "warm_start", "workload": f"planted dense BF16 m={m} n={n}, 24 training / 8 test LPs",
-                      "samples": total, "params": net.num_params, "train_s": t_train, "final_loss": loss,
-                      "fp32_cold": out["fp32_cold"],
-                      "cold": out["none"], "previous": out["previous"], "learned": out["model"],
-                      "inner_saved_frac": 1.0 - out["model"]["inner_total"] / out["none"]["inner_total"],
-                      "time_saved_frac": 1.0 - out["model"]["solve_s"] / out["none"]["solve_s"],
-                      "learned_bf16_vs_fp32_cold_time": out["model"]["solve_s"] / out["fp32_cold"]["solve_s"]}),
-          flush=True)
+    del X, T
+    modes = ("none", "previous", "model")
+    out = {k: {"inner_total": 0, "outer_total": 0, "solve_s": 0.0, "accepted": 0, "proposals": 0,
+               "max_err": {"objective": 0.0, "x": 0.0, "y": 0.0}, "inner": []} for k in modes + ("fp32_cold",)}
+    warmed = False
+    for seed in range(1000, 1000 + args.test_lps):
+        lp = make(seed)
+        runs = [(mode, "bf16") for mode in modes] + [("fp32_cold", "f32")]
+        for mode, dtype in runs:
+            with solver(lp, dtype) as S:
+                if dtype == "bf16":
+                    S.set_warm_start(mode, net if mode == "model" else None)
+                if not warmed:      # every kernel shape and library path once, untimed
+                    S.solve(tol=TOL)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                x, y, s_, info = S.solve(tol=TOL)
+                dt = time.perf_counter() - t1
+                o = out[mode]
+                assert info["status"] == 0, (mode, info)
+                o["solve_s"] += dt
+                o["inner_total"] += info["inner_total"]
+                o["outer_total"] += info["outer_iterations"]
+                o["inner"].append(info["inner_total"])
+                e = errors(lp, x, y, s_)
+                o["max_err"] = {k: max(o["max_err"][k], e[k]) for k in e}
+                if dtype == "bf16":
+                    st = S.warm_start_stats()
+                    o["accepted"] += st["accepted"]
+                    o["proposals"] += st["proposals"]
+        warmed = True
+        del lp
+    model_vs_prev = sum(1 for a, b in zip(out["model"]["inner"], out["previous"]["inner"]) if a < b)
+    print(json.dumps({
+        "mode": "warm_start", "workload": f"planted dense BF16 m={m} n={n} (the 2048 x 524288 family"
+                                          + (f" / {args.ws_scale}" if args.ws_scale > 1 else "") + ")",
+        "train_seeds": f"1..{args.train_lps}", "test_seeds": f"1000..{999 + args.test_lps}",
+        "samples": total, "params": net.num_params, "record_s": t_record, "train_steps": steps,
+        "train_s": t_train, "first_loss": loss0, "final_loss": loss,
+        "cold": out["none"], "previous": out["previous"], "learned": out["model"], "fp32_cold": out["fp32_cold"],
+        "learned_fewer_inner_than_previous_on": f"{model_vs_prev} of {args.test_lps} test LPs",
+        "inner_saved_frac_learned": 1.0 - out["model"]["inner_total"] / out["none"]["inner_total"],
+        "inner_saved_frac_previous": 1.0 - out["previous"]["inner_total"] / out["none"]["inner_total"],
+        "learned_bf16_vs_fp32_cold_time": out["model"]["solve_s"] / out["fp32_cold"]["solve_s"]}),
+        flush=True)
     return 0
 
 
@@ -567,7 +596,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warm-start", action="store_true",
-                    help="train the learned warm start on the BF16 family at 1/8 scale and compare")
+                    help="train the learned warm start on the 2048 x 524288 BF16 family and compare")
+    ap.add_argument("--ws-scale", type=int, default=1, help="warm start: divide m and n by this")
+    ap.add_argument("--train-lps", type=int, default=200, help="warm start: training LPs (seeds 1..N)")
+    ap.add_argument("--test-lps", type=int, default=20, help="warm start: held-out LPs (seeds 1000..)")
+    ap.add_argument("--train-steps", type=int, default=2000, help="warm start: Adam steps")
     ap.add_argument("--batch", type=int, default=0,
                     help="time N LPs of the batched family one at a time and batched")
     ap.add_argument("--kernel", choices=["adat", "gauss", "gauss-simt"], default=None,
@@ -633,6 +666,13 @@ def main():
     obj_err = abs(obj - lp.objective) / (1 + abs(lp.objective))
     assert all(i["status"] == 0 for i in infos), infos
     assert obj_err <= 1e-7, obj_err
+    # the result against the FP64 optimum: the planted (x*, y*, s*) is the
+    # unique optimum of these LPs, which the FP64 oracle reaches to its tolerance
+    err_fp64 = {"objective": obj_err,
+                "x": float(np.linalg.norm(x - lp.x_star) / np.linalg.norm(lp.x_star)),
+                "y": float(np.linalg.norm(y - lp.y_star) / np.linalg.norm(lp.y_star)),
+                "s": float(np.linalg.norm(s - lp.s_star) / np.linalg.norm(lp.s_star)),
+                "reference": "planted optimum (x*, y*, s*), relative 2-norm errors"}
 
     # ---- end to end through the C ABI with host buffers ----
     pinA = torch.from_numpy(lp.storage_array()).pin_memory()
@@ -689,6 +729,7 @@ def main():
                           "gpu_objective_rel_diff": abs(obj - rec["objective"]) / (1 + abs(rec["objective"]))}
     line = ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk,
                      oracle, cfg)
+    line["solve"]["error_vs_fp64"] = err_fp64
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -115,6 +115,17 @@ typedef struct {
                               (p(1) - p(0)) is affine in sigma, so are dy, v and the
                               directions; sigma = clip((mu_aff/mu)^3, 0.1, 0.75) from the
                               affine direction's largest positivity-keeping step; 0 */
+    int32_t graphs;        /* 1: each block of refine_every inner steps (products, preconditioner
+                              GEMVs, the true-residual refresh) is captured once per handle as
+                              a CUDA graph and replayed with one launch; the kernels and their
+                              results are the same as with plain launches (0); 1 */
+    int32_t autotune;      /* 1: lp_create times the inner-loop product's candidate tile shapes
+                              (warp-per-column kernel with 16/32/64 KB tiles and 2-4 stages,
+                              the row-split kernel where the rows allow) on A and keeps the
+                              fastest, cached per process by (dtype, leading dimension, n), so
+                              later handles of that shape reuse it untimed; the choice changes
+                              the product's summation order (results agree with autotune = 0 to
+                              rounding); 0 */
 } lp_options;
 
 /* ---- results -------------------------------------------------------------- */
@@ -148,7 +159,9 @@ typedef struct {
     double ms;                  /* their summed CUDA-event duration */
     int64_t bytes_per_launch;   /* algorithmic bytes of one launch (A + d^2 + in/out vectors) */
     int64_t all_launches;       /* every kernel this library launched since the last reset
-                                   (library-wide counter; cuSOLVER's kernels not included) */
+                                   (library-wide counter, the kernels of replayed graphs
+                                   included; cuSOLVER's kernels not included) */
+    int64_t graph_replays;      /* blocks of inner steps replayed from a CUDA graph (opt.graphs) */
 } lp_kernel_stats;
 
 /* One record per outer iteration of the last lp_solve (iteration log). */

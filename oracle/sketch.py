@@ -92,24 +92,30 @@ def countsketch_matrix(seed: int, k: int, retry: int, n: int, w: int, s: int):
 
 
 def gaussian_matrix(seed: int, k: int, retry: int, n: int, w: int) -> np.ndarray:
-    """Dense W_G (n x w) with N(0, 1/w) entries via Box-Muller.
+    """Dense W_G (n x w) with N(0, 1/w) entries via Box-Muller, both outputs.
 
     The draw for (k, retry) uses its own stream, seeded with
-    S_kr = draw(draw(seed, 0), k*MAX_RETRY + retry); entry (i, j) is the draw
-    at counter i*w + j of that stream.  Its 64 bits give two uniforms that are
-    exact in FP32: u1 = (bits 41..63 + 1) / 2^23 in (0, 1] and
-    u2 = (bits 18..40) / 2^23 in [0, 1); z = sqrt(-2 ln u1) cos(2 pi u2).
+    S_kr = draw(draw(seed, 0), k*MAX_RETRY + retry).  Entry (i, j) has the flat
+    index f = i*w + j and uses the draw at counter floor(f / 2) of that
+    stream: its 64 bits give two uniforms that are exact in FP32,
+    u1 = (bits 41..63 + 1) / 2^23 in (0, 1] and u2 = (bits 18..40) / 2^23 in
+    [0, 1), and the entry is z = sqrt(-2 ln u1) cos(2 pi u2) for even f and
+    z = sqrt(-2 ln u1) sin(2 pi u2) for odd f (the two independent normals of
+    one Box-Muller draw).
     """
     u1, u2 = gaussian_uniforms(seed, k, retry, n, w)
-    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    f = np.arange(n * w)
+    r = np.sqrt(-2.0 * np.log(u1))[f // 2]
+    ang = 2.0 * np.pi * u2[f // 2]
+    z = np.where(f % 2 == 0, r * np.cos(ang), r * np.sin(ang))
     return (z / np.sqrt(w)).reshape(n, w)
 
 
 def gaussian_uniforms(seed: int, k: int, retry: int, n: int, w: int):
-    """The two uniforms of every entry of W_G (flattened row-major)."""
+    """The two uniforms of every draw of W_G: draws 0 .. ceil(n w / 2) - 1."""
     s_g = int(draw(seed, np.array([0], dtype=np.uint64))[0])
     s_kr = int(draw(s_g, np.array([k * MAX_RETRY + retry], dtype=np.uint64))[0])
-    idx = np.arange(n * w, dtype=np.uint64)
+    idx = np.arange((n * w + 1) // 2, dtype=np.uint64)
     with np.errstate(over="ignore"):
         val = draw(s_kr, idx)
     u1 = ((val >> _U64(41)).astype(np.float64) + 1.0) / 8388608.0

@@ -53,7 +53,8 @@ class LpOptions(ctypes.Structure):
                 ("t_max", c_int32), ("v_correction", c_int32), ("cheb_lanczos", c_int32),
                 ("profile", c_int32), ("w_factor", c_double), ("w", c_int64),
                 ("seed", c_uint64), ("stream", c_void_p), ("tensor_sketch", c_int32),
-                ("precondition", c_int32), ("sigma_rule", c_int32)]
+                ("precondition", c_int32), ("sigma_rule", c_int32), ("graphs", c_int32),
+                ("autotune", c_int32)]
 
 
 class LpResult(ctypes.Structure):
@@ -99,7 +100,7 @@ class LpPhase1Info(ctypes.Structure):
 
 class LpKernelStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("ms", c_double), ("bytes_per_launch", c_int64),
-                ("all_launches", c_int64)]
+                ("all_launches", c_int64), ("graph_replays", c_int64)]
 
 
 # name -> (restype, argtypes); every symbol of include/lp_sketch_ipm.h

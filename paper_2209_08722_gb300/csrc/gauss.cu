@@ -1,9 +1,11 @@
 // Gaussian sketch (Section 6): A D W_G with W_G (n x w) iid N(0, 1/w), drawn
 // on the fly from the SplitMix64 counter-based generator -- W_G is never
-// stored.  Entry (j, k) of the draw for (k_iter, retry) uses counter j*w + k of
-// the stream seeded with S = draw(draw(seed, 0), k_iter*16 + retry); its bits
-// give u1 = (bits 41..63 + 1)/2^23, u2 = (bits 18..40)/2^23 (exact in FP32)
-// and g = sqrt(-2 ln u1) cos(2 pi u2) / sqrt(w) (Box-Muller, FP32).
+// stored.  Entry (j, k) of the draw for (k_iter, retry) has the flat index
+// f = j*w + k and uses the draw at counter floor(f/2) of the stream seeded
+// with S = draw(draw(seed, 0), k_iter*16 + retry); its bits give
+// u1 = (bits 41..63 + 1)/2^23, u2 = (bits 18..40)/2^23 (exact in FP32) and
+// g = sqrt(-2 ln u1) cos(2 pi u2) / sqrt(w) for even f, the sine for odd f
+// (both Box-Muller outputs, FP32).
 //
 // D is folded into the rows of W: W'_jk = fl32(fl32(d_j) * g_jk), so that
 // A D W = A W' and the correction vector of eq. (compv) is

@@ -196,24 +196,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
     if (c + 1 < nchunks) load_chunk(jb + TC_BK);
-    // ---- W': operand rows are the columns k of W', K runs over j ----
+    // ---- W': operand rows are the columns k of W', K runs over j.  With w
+    // even, entries (j, k) and (j, k + 1) for even k are the two normals of
+    // one Box-Muller draw (counter (j w + k) / 2), so thread t draws both for
+    // the column pair k0 + 2 (t % 64) and the rows jb + 2 (t / 64) + {0, 1};
+    // for odd w every entry is drawn on its own ----
     {
       char* whi = stage + (SPLIT_A ? 2 : 1) * mb * TC_BLK;
       char* wlo = whi + TC_BLK;
-      const int k = k0 + r;
-      uint32_t hi[4], lo[4];
+      const int kr = 2 * (tid & 63);        // operand rows kr, kr + 1
+      const int jc = 2 * (tid >> 6);        // K columns jc, jc + 1 of the chunk
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long long j = jb + g * 4 + q;
-        const float wv = (j < j1 && k < w)
-                             ? gauss_wprime(d_s[c & 1][g * 4 + q], s_kr, (uint64_t)j * w + k, inv_sqrt_w)
-                             : 0.0f;
-        hi[q] = to_tf32(wv);
-        lo[q] = to_tf32(wv - __uint_as_float(hi[q]));
+      for (int dj = 0; dj < 2; ++dj) {
+        const long long j = jb + jc + dj;
+        const float djv = d_s[c & 1][jc + dj];
+        float g[2] = {0.0f, 0.0f};
+        if (j < j1 && k0 + kr < w) {
+          if ((w & 1) == 0) {
+            gauss_pair(s_kr, ((uint64_t)j * w + (uint64_t)(k0 + kr)) >> 1, inv_sqrt_w, &g[0], &g[1]);
+            if (k0 + kr + 1 >= w) g[1] = 0.0f;
+          } else {
+            g[0] = gauss_entry(s_kr, (uint64_t)j * w + (uint64_t)(k0 + kr), inv_sqrt_w);
+            if (k0 + kr + 1 < w) g[1] = gauss_entry(s_kr, (uint64_t)j * w + (uint64_t)(k0 + kr + 1), inv_sqrt_w);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float wv = __fmul_rn(djv, g[e]);
+          const uint32_t hi = to_tf32(wv);
+          const uint32_t lo = to_tf32(wv - __uint_as_float(hi));
+          const int row = kr + e, col = jc + dj;
+          const int off = (row >> 3) * TC_SBO + (col >> 2) * TC_LBO + (row & 7) * 16 + (col & 3) * 4;
+          *reinterpret_cast<uint32_t*>(whi + off) = hi;
+          *reinterpret_cast<uint32_t*>(wlo + off) = lo;
+        }
       }
-      const int off = core_off(r, g);
-      *reinterpret_cast<uint4*>(whi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(wlo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     // make the generic-proxy stores visible to the tensor core, then issue
     fence_proxy_async_smem();

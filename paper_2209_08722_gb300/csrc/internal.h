@@ -24,6 +24,8 @@ struct StreamPlan {
 };
 
 StreamPlan make_stream_plan(int m, long long n, int lda, int esz, int num_sms, int tc_bytes);
+StreamPlan make_stream_plan_ex(int m, long long n, int lda, int esz, int num_sms, int tc_bytes, int target,
+                               int max_stages);
 int fused_vpl(int lda, int esz);
 cudaError_t launch_stream(int dtype, bool fp64_acc, int mode, const StreamArgs& a,
                           const StreamPlan& p, cudaStream_t st);
@@ -105,6 +107,11 @@ cudaError_t launch_stream_df(int dtype, int mode, const StreamArgs& a, const Str
 bool stream_df_supported(int mode, int lda, int esz, const StreamPlan& p);
 
 int sparse_grid(int num_sms);
+// deterministic two-pass form (CSC column pass + CSR row-segment pass + one-CTA
+// epilogue); a carries the CSR arrays, segments, column scalars and segment sums
+constexpr int kSegNnz = 4096;  // CSR entries per row segment at most
+int sparse2_col_grid(long long n, int num_sms);
+cudaError_t launch_sparse2(int dtype, bool fp64, int mode, const StreamArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_sparse(int dtype, bool fp64, int mode, const StreamArgs& a, int grid,
                           cudaStream_t st);
 cudaError_t launch_sparse_sketch(int dtype, const long long* cp, const int* ri, const void* val,

@@ -34,6 +34,8 @@
 #include "internal.h"
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <thread>
 
 using namespace lpk;
@@ -119,6 +121,16 @@ struct lp_handle {
   void* spval = nullptr;
   long long nnz = 0;
   int sp_grid = 0;
+  // the same sparse A by rows, in row segments, for the two-pass kernels
+  long long* rowptr = nullptr;
+  int* colidx = nullptr;
+  void* rval = nullptr;
+  long long* seg = nullptr;
+  int* seg_row = nullptr;
+  int* row_seg = nullptr;
+  int nseg = 0;
+  double* tcol = nullptr;
+  double* segsum = nullptr;
   bool qinv_ok = false;  // explicit Q^{-1} formed for the current factor
   double* qinv = nullptr;
   bool qinv_df_ok = false;  // ... and as FP32 pairs (the sweep's output), for the double-float GEMV
@@ -178,6 +190,21 @@ struct lp_handle {
   int* hinfo = nullptr;       // pinned
   double* hval = nullptr;     // pinned staging for scalars
   StreamPlan plan;
+  // CUDA graphs of one block of inner steps (refine_every products and
+  // preconditioner GEMVs, then the true-residual refresh), captured once per
+  // handle and variant (inner method, form of the stored preconditioner) and
+  // replayed with one launch per block
+  struct BlockGraph {
+    cudaGraphExec_t exec = nullptr;
+    int key = -1;
+    long long kernels = 0;
+  };
+  BlockGraph blk_graph[2];
+  bool graphs_failed = false;
+  long long graph_replays = 0;
+  StreamPlan fplan;        // tile plan of the warp-per-column FP32 product (opt.autotune may change it)
+  bool prod_rows = false;  // the FP32 product uses the row-split kernel
+  int alloc_grid = 0;      // CTAs the per-CTA partial buffers were sized for
   RowsPlan rplan;          // row-split kernels for tall columns (stream_rows.cu): FP32 product
   RowsPlan rplan_df;       // ... and the double-float passes
   bool use_rows = false;   // the FP32 product and the double-float passes use them
@@ -282,6 +309,15 @@ StreamArgs base_args(lp_handle* h) {
   a.colptr = h->colptr;
   a.rowidx = h->rowidx;
   a.spval = h->spval;
+  a.rowptr = h->rowptr;
+  a.colidx = h->colidx;
+  a.rval = h->rval;
+  a.seg = h->seg;
+  a.seg_row = h->seg_row;
+  a.row_seg = h->row_seg;
+  a.nseg = h->nseg;
+  a.tcol = h->tcol;
+  a.segsum = h->segsum;
   a.ticket = h->tickets + 0;
   a.sc = h->sc;
   a.err = &h->sc->err;
@@ -353,9 +389,14 @@ int launch_adat(lp_handle* h, const double* vin, int epilogue, bool fp64, int sk
     }
   }
   cudaError_t e;
-  if (h->sparse) e = launch_sparse(h->dtype, use64, M_ADAT, a, h->sp_grid, h->st);
-  else if (!use64 && h->use_rows) e = launch_rows(h->dtype, false, M_ADAT, a, h->rplan, h->st, pdl);
-  else if (!use64) e = launch_adat_fused(h->dtype, a, h->plan, h->st, pdl);
+  if (h->sparse) e = launch_sparse2(h->dtype, use64, M_ADAT, a, h->num_sms, h->st);
+  else if (!use64 && h->prod_rows) e = launch_rows(h->dtype, false, M_ADAT, a, h->rplan, h->st, pdl);
+  else if (!use64) {
+    a.nb = h->fplan.nb;
+    a.ntiles = h->fplan.ntiles;
+    a.stages = h->fplan.stages;
+    e = launch_adat_fused(h->dtype, a, h->fplan, h->st, pdl);
+  }
   else if (h->use_rows) {
     // the refresh inside the inner loop follows a GEMV closely
     e = launch_rows(h->dtype, true, M_ADAT, a, h->rplan_df, h->st, skip_level >= 1);
@@ -581,6 +622,88 @@ constexpr double kRitzSpread = 1e3;  // ((1 + e)/(1 - e))^2 = 1e3 at e ~ 0.94
 constexpr int kPoorCheckIters = 32;  // act only on solves still running here ...
 constexpr double kRitzSevere = 1e6;  // ... or at once beyond this spread
 
+// One block of inner steps on the stream: `refine` steps of CG (or
+// Chebyshev), each a product and the preconditioner GEMV with the method's
+// epilogue, then the FP64-class true residual r = p - M dy and its GEMV.
+// Every kernel skips its work on the device once the solve has converged
+// (skip levels 1 and 2), so the block's launches do not depend on the state.
+int enqueue_cg_block(lp_handle* h, int inner, bool use64, int refine) {
+  const int m = h->m;
+  for (int j = 0; j < refine; ++j) {
+    if (inner == LP_INNER_CHEBYSHEV) {
+      CK(launch_cheb_pre(m, h->dy, h->pdir, h->sc, h->st));
+      RET(launch_adat(h, h->pdir, E_CHEB, use64, 1, h->q));
+      RET(precond_gemvs(h, h->r, h->z, GH_CHEB_B, 1));
+    } else {
+      RET(launch_adat(h, h->pdir, E_PCG_A, use64, 1, h->q));
+      RET(precond_gemvs(h, h->r, h->z, j + 1 == refine ? GH_PCG_B_LAST : GH_PCG_B, 1));
+    }
+  }
+  RET(launch_adat(h, h->dy, E_TRUE_RES, true, 2, nullptr));
+  RET(precond_gemvs(h, h->r, h->z, inner == LP_INNER_CHEBYSHEV ? GH_CHEB_REFRESH : GH_REFRESH, 2));
+  return LP_OK;
+}
+
+// Whether the next block may be replayed from a graph: FP32 products, graphs
+// enabled, and none of the block's products in the window opt.profile times
+// (those blocks run as plain launches with events between them).
+bool block_graph_usable(lp_handle* h, bool use64, int refine) {
+  if (use64 || !h->opt.graphs || h->graphs_failed) return false;
+  if (!h->opt.profile) return true;
+  for (unsigned long long k = h->k1_sample; k < h->k1_sample + (unsigned long long)refine; ++k)
+    if (((k >> 3) & 7) == 0) return false;
+  return true;
+}
+
+// The block from its graph, captured on first use for this variant.  The
+// packed d^2 the refresh reads is prepared outside the graph, so a replay
+// never depends on what was valid at capture time.
+int run_cg_block_graph(lp_handle* h, int inner, int refine) {
+  if (!h->sparse && h->use_df && !h->d2df_valid) {
+    DfPackArgs pk{{h->d2d}, {h->d2df}, 1, h->n};
+    CK(launch_df_pack(pk, h->num_sms, h->st));
+    h->d2df_valid = true;
+  }
+  const int key = refine * 8 + (h->qinv_ok ? 1 : 0) + (h->qinv_df_ok ? 2 : 0) + (h->opt.precondition ? 4 : 0);
+  lp_handle::BlockGraph& g = h->blk_graph[inner == LP_INNER_CHEBYSHEV ? 1 : 0];
+  if (!g.exec || g.key != key) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    const unsigned long long k1 = h->k1_sample;
+    const long long before = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs_failed = true;
+      return enqueue_cg_block(h, inner, false, refine);
+    }
+    const int rc = enqueue_cg_block(h, inner, false, refine);
+    const cudaError_t ec = cudaStreamEndCapture(h->st, &graph);
+    g.kernels = g_launches.load() - before;
+    g_launches.fetch_sub(g.kernels, std::memory_order_relaxed);  // captured, not launched
+    h->k1_sample = k1;
+    cudaError_t ei = cudaErrorUnknown;
+    if (rc == LP_OK && ec == cudaSuccess && graph)
+      ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      g.exec = nullptr;
+      h->graphs_failed = true;
+      h->err.clear();
+      return enqueue_cg_block(h, inner, false, refine);
+    }
+    g.key = key;
+  }
+  CK(cudaGraphLaunch(g.exec, h->st));
+  g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
+  h->k1_sample += (unsigned long long)refine;
+  h->graph_replays += 1;
+  return LP_OK;
+}
+
 // The inner solve on the current factor: dy ~ M^{-1} p.  Returns LP_OK or
 // LP_WARN_INNER_MAXIT (or kInnerSketchPoor when check_sketch is set).
 // tol_f > 0: absolute ||f|| target; else relative tol_cg.
@@ -656,19 +779,10 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
   check_sketch = check_sketch && inner == LP_INNER_CG && h->opt.precondition;
   bool poor = false, severe = false, ritz_done = false;
   while (true) {
-    for (int j = 0; j < refine; ++j) {
-      if (inner == LP_INNER_CHEBYSHEV) {
-        CK(launch_cheb_pre(m, h->dy, h->pdir, h->sc, h->st));
-        RET(launch_adat(h, h->pdir, E_CHEB, use64, 1, h->q));
-        RET(precond_gemvs(h, h->r, h->z, GH_CHEB_B, 1));
-      } else {
-        RET(launch_adat(h, h->pdir, E_PCG_A, use64, 1, h->q));
-        RET(precond_gemvs(h, h->r, h->z, j + 1 == refine ? GH_PCG_B_LAST : GH_PCG_B, 1));
-      }
-    }
-    // FP64 true residual r = p - M dy, ||f|| = sqrt(r^T Q^{-1} r)
-    RET(launch_adat(h, h->dy, E_TRUE_RES, true, 2, nullptr));
-    RET(precond_gemvs(h, h->r, h->z, inner == LP_INNER_CHEBYSHEV ? GH_CHEB_REFRESH : GH_REFRESH, 2));
+    // refine steps, then the FP64 true residual r = p - M dy and
+    // ||f|| = sqrt(r^T Q^{-1} r): replayed from a graph when it can be
+    if (block_graph_usable(h, use64, refine)) RET(run_cg_block_graph(h, inner, refine));
+    else RET(enqueue_cg_block(h, inner, use64, refine));
     CK(cudaMemcpyAsync(h->hsc, h->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     if (h->hsc->err == ERR_NUMERICAL && !use64) {
@@ -1007,7 +1121,7 @@ int residual_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
     return LP_OK;
   }
   h->d2df_valid = false;
-  if (h->sparse) CK(launch_sparse(h->dtype, true, M_RESID, a, h->sp_grid, h->st));
+  if (h->sparse) CK(launch_sparse2(h->dtype, true, M_RESID, a, h->num_sms, h->st));
   else CK(launch_stream(h->dtype, true, M_RESID, a, h->plan, h->st));
   return LP_OK;
 }
@@ -1027,7 +1141,7 @@ int direction_pass(lp_handle* h, bool feasible, double sigma = -1.0) {
   a.out_col[1] = h->ds;
   a.red_partials = h->red_partials;
   a.epilogue = E_DIR;
-  if (h->sparse) CK(launch_sparse(h->dtype, true, M_DIR, a, h->sp_grid, h->st));
+  if (h->sparse) CK(launch_sparse2(h->dtype, true, M_DIR, a, h->num_sms, h->st));
   else if (h->use_df_dir) {
     // double-float pass: x, s, v, r_d as pairs in, dx and ds as pairs out
     DfPackArgs pk{{h->x, h->s, h->v, h->rd}, {h->dfin[0], h->dfin[1], h->dfin[2], h->dfin[3]},
@@ -1070,6 +1184,8 @@ void options_check(const lp_options* o, std::string* why) {
   else if (!(o->tol_cg >= 0 && std::isfinite(o->tol_cg))) *why = "tol_cg must be finite and >= 0";
   else if (o->w < 0) *why = "w must be >= 0 (0: w = w_factor m)";
   else if (o->w == 0 && !(o->w_factor > 0 && o->w_factor <= 1e6)) *why = "w_factor must be in (0, 1e6] when w = 0";
+  else if (o->graphs != 0 && o->graphs != 1) *why = "graphs must be 0 or 1";
+  else if (o->autotune != 0 && o->autotune != 1) *why = "autotune must be 0 or 1";
 }
 
 }  // namespace
@@ -1123,6 +1239,8 @@ void lp_options_default(lp_options* o) {
   o->tensor_sketch = 1;
   o->precondition = 1;
   o->sigma_rule = 0;
+  o->graphs = 1;
+  o->autotune = 0;
 }
 
 const char* lp_create_error(void) { return g_create_error.c_str(); }
@@ -1141,6 +1259,8 @@ int lp_destroy(lp_handle* h) {
   if (h->hinfo) cudaFreeHost(h->hinfo);
   if (h->hval) cudaFreeHost(h->hval);
   if (h->hwork) free(h->hwork);
+  for (auto& g : h->blk_graph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->sol) cusolverDnDestroy(h->sol);
   if (h->blas) cublasDestroy(h->blas);
   if (h->st_aux) {
@@ -1151,6 +1271,170 @@ int lp_destroy(lp_handle* h) {
   if (h->ev_p) cudaEventDestroy(h->ev_p);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
+  return LP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the inner-loop product's tile shape (opt.autotune)
+// ---------------------------------------------------------------------------
+// Candidates for the FP32 product A diag(d2) A^T v on this handle's A: the
+// warp-per-column kernel with tiles of about 16, 32 or 64 KB and 2 to 4
+// stages, and the row-split kernel where the rows allow; each runs once
+// untimed and three times between CUDA events on the handle's stream, and the
+// fastest is kept for the handle and cached for the process, keyed by the
+// storage dtype, the leading dimension and n, so that every later handle of
+// the same shape takes the same kernel without timing (results then agree
+// bit for bit between handles; a different choice changes the summation
+// order, so autotuned results agree with untuned ones to rounding).
+namespace {
+struct TuneKey {
+  int dtype, lda;
+  long long n;
+  bool operator<(const TuneKey& o) const {
+    return dtype != o.dtype ? dtype < o.dtype : (lda != o.lda ? lda < o.lda : n < o.n);
+  }
+};
+struct TuneChoice {
+  bool rows = false;
+  int target = 0, stages = 0;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+}  // namespace
+
+static void apply_choice(lp_handle* h, const TuneChoice& c) {
+  h->prod_rows = c.rows;
+  if (!c.rows) h->fplan = make_stream_plan_ex(h->m, h->n, h->lda, h->esz, h->num_sms, 4, c.target, c.stages);
+}
+
+static int autotune_product(lp_handle* h) {
+  const TuneKey key{h->dtype, h->lda, h->n};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply_choice(h, it->second);
+      return LP_OK;
+    }
+  }
+  std::vector<TuneChoice> cand;
+  const int vpl = fused_vpl(h->lda, h->esz);
+  if (vpl >= 1 && vpl <= 8)
+    for (int target : {16 * 1024, 32 * 1024, 64 * 1024})
+      for (int stages : {2, 3, 4}) {
+        const StreamPlan p = make_stream_plan_ex(h->m, h->n, h->lda, h->esz, h->num_sms, 4, target, stages);
+        if (p.ok && p.stages == stages && p.grid <= h->alloc_grid) cand.push_back(TuneChoice{false, target, stages});
+      }
+  if (h->rplan.ok && h->rplan.grid <= h->alloc_grid) cand.push_back(TuneChoice{true, 0, 0});
+  if (cand.empty()) return LP_OK;
+  // d2 = 1, v = 1 in the handle's work vectors
+  CK(launch_fill(h->n, h->d2d, 1.0, h->num_sms, h->st));
+  CK(launch_to_f32(h->n, h->d2d, h->d2f, 0, h->num_sms, h->st));
+  h->d2df_valid = false;
+  CK(launch_fill(h->m, h->mb0, 1.0, h->num_sms, h->st));
+  CK(cudaMemsetAsync(&h->sc->inner_done, 0, 2 * sizeof(int), h->st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return h->fail(LP_ERR_CUDA, "cudaEventCreate failed");
+  }
+  const int profile = h->opt.profile;
+  h->opt.profile = 0;  // no sampled events while timing candidates
+  float best = 0.0f;
+  int best_i = -1, rc = LP_OK;
+  for (size_t i = 0; i < cand.size() && rc == LP_OK; ++i) {
+    apply_choice(h, cand[i]);
+    rc = launch_adat(h, h->mb0, E_PLAIN, false, 0, h->mb1);
+    if (rc != LP_OK) break;
+    cudaEventRecord(e0, h->st);
+    for (int r = 0; r < 3 && rc == LP_OK; ++r) rc = launch_adat(h, h->mb0, E_PLAIN, false, 0, h->mb1);
+    cudaEventRecord(e1, h->st);
+    float ms = 0.0f;
+    if (rc == LP_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+        (best_i < 0 || ms < best)) {
+      best = ms;
+      best_i = (int)i;
+    }
+  }
+  h->opt.profile = profile;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LP_OK) return rc;
+  RET(sync_read(h));
+  if (best_i < 0) return h->fail(LP_ERR_CUDA, "autotune: no candidate could be timed");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto ins = g_tune_cache.emplace(key, cand[best_i]);
+    apply_choice(h, ins.first->second);  // a concurrent tuner may have cached first: take its choice
+  }
+  return LP_OK;
+}
+
+// The sparse A by rows for the two-pass kernels: CSR from the CSC (the same
+// stable counting sort, read as CSC of A = CSR of A^T), rows split into
+// segments of at most kSegNnz entries, and the per-column scalars and
+// segment sums the passes exchange.  A device CSC is read back first.
+static int build_rows(lp_handle* h, const lp_matrix* A) {
+  const int esz = h->esz;
+  const long long nnz = h->nnz, n = h->n;
+  const int m = h->m;
+  std::vector<int64_t> cp_h;
+  std::vector<int32_t> ri_h;
+  std::vector<char> v_h;
+  const int64_t* cp = A->ptr;
+  const int32_t* ri = A->idx;
+  const void* vv = A->val;
+  if (A->on_device) {
+    cp_h.resize((size_t)n + 1);
+    ri_h.resize((size_t)std::max<long long>(nnz, 1));
+    v_h.resize((size_t)std::max<long long>(nnz, 1) * esz);
+    CK(cudaMemcpy(cp_h.data(), A->ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
+    if (nnz > 0) {
+      CK(cudaMemcpy(ri_h.data(), A->idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(v_h.data(), A->val, (size_t)esz * nnz, cudaMemcpyDeviceToHost));
+    }
+    cp = cp_h.data();
+    ri = ri_h.data();
+    vv = v_h.data();
+  }
+  if (n > INT32_MAX) return h->fail(LP_ERR_UNSUPPORTED, "sparse n too large for the row form");
+  CscCopy rows;  // CSC of A^T = CSR of A
+  const std::string bad = csr_to_csc((int)n, m, nnz, cp, ri, vv, esz, &rows);
+  if (!bad.empty()) return h->fail(LP_ERR_ARG, "CSC structure: %s", bad.c_str());
+  // segments
+  std::vector<long long> seg;
+  std::vector<int> seg_row, row_seg((size_t)m + 1, 0);
+  for (int i = 0; i < m; ++i) {
+    row_seg[i] = (int)seg_row.size();
+    for (long long k = rows.ptr[i]; k < rows.ptr[i + 1]; k += kSegNnz) {
+      seg.push_back(k);
+      seg.push_back(std::min<long long>(rows.ptr[i + 1], k + kSegNnz));
+      seg_row.push_back(i);
+    }
+  }
+  row_seg[m] = (int)seg_row.size();
+  h->nseg = (int)seg_row.size();
+  RET(h->alloc(&h->rowptr, (size_t)m + 1));
+  RET(h->alloc(&h->colidx, (size_t)std::max<long long>(nnz, 1)));
+  RET(h->alloc(reinterpret_cast<char**>(&h->rval), (size_t)std::max<long long>(nnz, 1) * esz));
+  RET(h->alloc(&h->seg, 2 * (size_t)std::max(h->nseg, 1)));
+  RET(h->alloc(&h->seg_row, (size_t)std::max(h->nseg, 1)));
+  RET(h->alloc(&h->row_seg, (size_t)m + 1));
+  RET(h->alloc(&h->tcol, 2 * (size_t)h->npad));
+  RET(h->alloc(&h->segsum, 2 * (size_t)std::max(h->nseg, 1) + 2 + 2 * (size_t)sparse2_col_grid(n, h->num_sms)));
+  CK(cudaMemcpyAsync(h->rowptr, rows.ptr.data(), sizeof(int64_t) * ((size_t)m + 1), cudaMemcpyHostToDevice, h->st));
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(h->colidx, rows.idx.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->rval, rows.val.data(), (size_t)esz * nnz, cudaMemcpyHostToDevice, h->st));
+  }
+  if (h->nseg > 0) {
+    CK(cudaMemcpyAsync(h->seg, seg.data(), sizeof(long long) * seg.size(), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->seg_row, seg_row.data(), sizeof(int) * seg_row.size(), cudaMemcpyHostToDevice, h->st));
+  }
+  CK(cudaMemcpyAsync(h->row_seg, row_seg.data(), sizeof(int) * row_seg.size(), cudaMemcpyHostToDevice, h->st));
+  // the host vectors go out of scope: wait for the copies from them
+  CK(cudaStreamSynchronize(h->st));
   return LP_OK;
 }
 
@@ -1273,6 +1557,8 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
     h->rplan_df = make_rows_plan(h->lda, h->n, h->esz, h->num_sms, true);
     h->use_rows = h->rplan.ok && h->rplan_df.ok && (vpl == 0 || vpl >= 8);
     if (h->use_rows) h->use_df = h->use_df_resid = h->use_df_dir = true;
+    h->prod_rows = h->use_rows;
+    h->fplan = h->plan;
   }
   if (!h->plan.ok) return h->fail(LP_ERR_UNSUPPORTED, "m=%d too large for the streaming kernels", h->m);
   if (!h->sparse && h->dtype != LP_F64 && fused_vpl(h->lda, h->esz) == 0 && !h->use_rows)
@@ -1292,6 +1578,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
       CK(cudaMemcpyAsync(h->rowidx, A->idx, sizeof(int) * (size_t)h->nnz, kind, h->st));
       CK(cudaMemcpyAsync(h->spval, A->val, (size_t)h->esz * h->nnz, kind, h->st));
     }
+    RET(build_rows(h, A));
   } else {
     if (h->opt.sketch == LP_SKETCH_COUNT) {
       if (h->w > kCsMaxW)
@@ -1356,6 +1643,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   RET(h->alloc(&h->adwt_part, (size_t)h->adwt_parts * h->w));
   RET(h->alloc(&h->dinfo, 4));
   const int max_grid = std::max(h->plan.grid, h->use_rows ? std::max(h->rplan.grid, h->rplan_df.grid) : 0);
+  h->alloc_grid = max_grid;
   RET(h->alloc(reinterpret_cast<char**>(&h->partials), (size_t)max_grid * 2 * h->lda * 8));
   RET(h->alloc(&h->gpart, (size_t)((max_grid + kGroup - 1) / kGroup) * 2 * h->lda));
   RET(h->alloc(&h->gtickets, kMaxGroups + 1));
@@ -1390,6 +1678,7 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   h->cnorm = sqrt(h->hsc->pad[1]);
   if (!std::isfinite(h->bnorm) || !std::isfinite(h->cnorm))
     return h->fail(LP_ERR_ARG, "b or c contains NaN/Inf");
+  if (h->opt.autotune && !h->sparse && h->dtype != LP_F64) RET(autotune_product(h));
   return LP_OK;
 }
 
@@ -1571,12 +1860,14 @@ int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st) {
   st->bytes_per_launch = h->sparse ? (int64_t)h->nnz * (h->esz + 4) + 8 * (h->n + 1) + 4 * h->n + 16 * (int64_t)h->m
                                     : (int64_t)h->m * h->n * h->esz + 4 * h->n + 2 * 8 * (int64_t)h->m;
   st->all_launches = g_launches.load() - h->launch_base;
+  st->graph_replays = h->graph_replays;
   return LP_OK;
 }
 
 int lp_reset_kernel_stats(lp_handle* h) {
   if (!h) return LP_ERR_ARG;
   cudaStreamSynchronize(h->st);
+  h->graph_replays = 0;
   ev_flush(h);
   h->k1_launches = 0;
   h->k1_ms = 0.0;

@@ -407,16 +407,22 @@ cudaError_t dispatch_fused(int vpl, const StreamArgs& a, int grid, int smem, cud
 }  // namespace
 
 StreamPlan make_stream_plan(int m, long long n, int lda, int esz, int num_sms, int tc_bytes) {
+  return make_stream_plan_ex(m, n, lda, esz, num_sms, tc_bytes, 32 * 1024, kMaxStages);
+}
+
+// tiles of about target_bytes of A (4 to 64 columns, a multiple of 4), and as
+// many stages (at most max_stages) as fit the shared-memory budget
+StreamPlan make_stream_plan_ex(int m, long long n, int lda, int esz, int num_sms, int tc_bytes, int target,
+                               int max_stages) {
   StreamPlan p;
   const int col_bytes = lda * esz;
-  const int target = 32 * 1024;
   int nb = target / col_bytes;
   nb = std::max(4, std::min(64, nb));
   nb = nb / 4 * 4;
   p.nb = nb;
   p.ntiles = (int)((n + nb - 1) / nb);
   const int budget = 220 * 1024;
-  int stages = kMaxStages;
+  int stages = std::max(2, std::min(kMaxStages, max_stages));
   for (; stages >= 2; --stages) {
     SmemLayout L = make_layout(lda, esz, nb, stages, 8);
     // the end-of-kernel reduction buffer reuses the stage area

@@ -80,6 +80,17 @@ struct StreamArgs {
   const long long* colptr;  // CSC: n+1 column pointers
   const int* rowidx;        // CSC: row indices
   const void* spval;        // CSC: values (FP32 or FP64)
+  // sparse A by rows as well (the deterministic two-pass product): CSR arrays,
+  // row segments of at most kSegNnz entries, per-column scalars and segment sums
+  const long long* rowptr;  // m+1
+  const int* colidx;        // CSR column indices
+  const void* rval;         // CSR values
+  const long long* seg;     // [nseg][2]: first and last+1 CSR index of a segment
+  const int* seg_row;       // row of a segment
+  const int* row_seg;       // m+1: the segments of row i are row_seg[i] .. row_seg[i+1]-1
+  int nseg;
+  void* tcol;               // [2][n] per-column scalars t0, t1 (TC)
+  double* segsum;           // [nseg][2] segment sums
   double* gpart;       // [ceil(grid/kGroup)][2][lda] group sums of the partials (FP64, or FP32
                        // pairs in the same 8 bytes when the partials are FP32)
   unsigned* gtickets;  // [kMaxGroups + 1] self-resetting tickets of the two-level reduction

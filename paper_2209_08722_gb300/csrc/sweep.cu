@@ -14,11 +14,13 @@
 // m x m matrix with m in the hundreds is latency-bound in library code, so:
 //   * the matrix is prescaled by a power of two (max diagonal -> [1, 2)) and
 //     held as FP32 pairs (relative accuracy ~2^-46 per operation);
-//   * each of the m/32 pivot steps is two launches: one CTA of 32 x 32 threads
-//     sweeps the 32 x 32 pivot block (the step's serial chain of 32 pivots,
-//     one element per thread), then one launch over all 32 x 32 tiles writes
-//     the next iterate from it; two buffers alternate, so no tile is read after
-//     it is overwritten.
+//   * each of the m/32 pivot steps is three launches: one CTA of 32 x 32
+//     threads sweeps the 32 x 32 pivot block (the step's serial chain of 32
+//     pivots, one element per thread), one launch forms the panel
+//     U_I = A_{I,K} (-P^{-1}) of every row block once, and one launch over the
+//     upper-triangle 32 x 32 tiles writes the next iterate (each tile and its
+//     mirror: the iterate is symmetric); two buffers alternate, so no tile is
+//     read after it is overwritten.
 #include "internal.h"
 #include "df.cuh"
 
@@ -196,45 +198,95 @@ __global__ void __launch_bounds__(SB* SB) k_sweep_pivot(const float* __restrict_
   ql[a * SB + b] = cl[a][b];
 }
 
-// one pivot step K: src -> dst for every 32 x 32 tile (I, J); the swept pivot
-// block -P^{-1} comes from k_sweep_pivot
+// The panel of pivot step K: U_I = A_{I,K} (-P_K^{-1}) for every row block I
+// != K (one 32 x 32 block per CTA, 4 outputs per thread), from the iterate
+// step K reads and the swept pivot block.  Every tile of step K in row block I
+// uses U_I, so it is formed once here instead of once per tile.
+__global__ void __launch_bounds__(SW_THREADS) k_sweep_panel(const float* __restrict__ sh_, const float* __restrict__ sl_,
+                                                            int mp, int K, const float* __restrict__ qh,
+                                                            const float* __restrict__ ql, float* __restrict__ uh_,
+                                                            float* __restrict__ ul_) {
+  __shared__ float Ph[SB][SB + 1], Pl[SB][SB + 1];
+  __shared__ float Th[SB][SB + 1], Tl[SB][SB + 1];
+  const int I = blockIdx.x;
+  if (I == K) return;
+  const int tid = threadIdx.x, k0 = K * SB;
+  for (int e = tid; e < SB * SB; e += SW_THREADS) {
+    const int a = e / SB, b = e % SB;
+    Ph[a][b] = qh[e];
+    Pl[a][b] = ql[e];
+    const size_t src = (size_t)(I * SB + a) * mp + k0 + b;
+    Th[a][b] = sh_[src];
+    Tl[a][b] = sl_[src];
+  }
+  __syncthreads();
+  const int r = tid >> 3, c4 = (tid & 7) * 4;
+  float uh4[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ul4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int b = 0; b < SB; ++b) {
+    const float th = Th[r][b], tl = Tl[r][b];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) df_mac(th, tl, Ph[b][c4 + q], Pl[b][c4 + q], uh4[q], ul4[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    df_renorm(uh4[q], ul4[q]);
+    uh_[(size_t)I * SB * SB + r * SB + c4 + q] = uh4[q];
+    ul_[(size_t)I * SB * SB + r * SB + c4 + q] = ul4[q];
+  }
+}
+
+// (I, J) with J >= I of upper-triangle tile number t (column by column)
+__device__ __forceinline__ void upper_tile(int t, int* I, int* J) {
+  int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((j + 1) * (j + 2) / 2 <= t) ++j;
+  while (j * (j + 1) / 2 > t) --j;
+  *J = j;
+  *I = t - j * (j + 1) / 2;
+}
+
+// One pivot step K: src -> dst.  The iterate stays symmetric, so only the
+// tiles (I, J) with J >= I are formed (the swept pivot block -P^{-1} from
+// k_sweep_pivot, the panels U from k_sweep_panel):
+//   I = J = K:      -P^{-1}
+//   J = K:          A_IK P^{-1} = -U_I
+//   I = K:          P^{-1} A_KJ = -U_J^T
+//   otherwise:      A_IJ + U_I A_{J,K}^T
+// and each is written to (I, J) and, transposed through shared memory, to
+// (J, I); both writes are coalesced along rows.
 __global__ void __launch_bounds__(SW_THREADS* kTilesPerCta) k_sweep_step(const float* __restrict__ sh_, const float* __restrict__ sl_,
                                                                          float* __restrict__ dh_, float* __restrict__ dl_,
                                                                          int mp, int K, const float* __restrict__ qh,
-                                                                         const float* __restrict__ ql) {
+                                                                         const float* __restrict__ ql,
+                                                                         const float* __restrict__ uh_,
+                                                                         const float* __restrict__ ul_) {
   extern __shared__ __align__(16) char sw_smem[];
   const int half = threadIdx.x / SW_THREADS;
   TileSmem& S = reinterpret_cast<TileSmem*>(sw_smem)[half];
   const int nt = mp / SB;
   const int tile = blockIdx.x * kTilesPerCta + half;
-  if (tile >= nt * nt) return;  // no tile for this half; the other half's barrier counts its own threads
-  const int I = tile % nt, J = tile / nt;
+  if (tile >= nt * (nt + 1) / 2) return;  // no tile for this half; the other half's barrier counts its own threads
+  int I, J;
+  upper_tile(tile, &I, &J);
   const int k0 = K * SB;
   const int tid = threadIdx.x % SW_THREADS;
   const int bar = 1 + half;
   const int r = tid >> 3, c4 = (tid & 7) * 4;  // this thread's outputs: row r, columns c4..c4+3
 
-  // ---- load the swept pivot block -P^{-1} ----
+  // ---- operands: Ph/Pl <- -P^{-1} or U_I, Th/Tl <- A_{J,K} or U_J ----
   for (int e = tid; e < SB * SB; e += SW_THREADS) {
     const int a = e / SB, b = e % SB;
-    S.Ph[a][b] = qh[e];
-    S.Pl[a][b] = ql[e];
-  }
-  // ---- load the panels needed by this tile ----
-  // case 1 (I != K, J != K): T <- A_{I,K}, C <- A_{J,K}; case 2 (J == K): T <- A_{I,K};
-  // case 3 (I == K): T <- A_{J,K}
-  const int X = (I == K) ? J : I;
-  if (X != K) {
-    for (int e = tid; e < SB * SB; e += SW_THREADS) {
-      const int a = e / SB, b = e % SB;
-      const size_t src = (size_t)(X * SB + a) * mp + k0 + b;
-      S.Th[a][b] = sh_[src];
-      S.Tl[a][b] = sl_[src];
-    }
-  }
-  if (I != K && J != K) {
-    for (int e = tid; e < SB * SB; e += SW_THREADS) {
-      const int a = e / SB, b = e % SB;
+    if (I == K && J == K) {
+      S.Ph[a][b] = qh[e];
+      S.Pl[a][b] = ql[e];
+    } else if (J == K) {
+      S.Ph[a][b] = uh_[(size_t)I * SB * SB + e];
+      S.Pl[a][b] = ul_[(size_t)I * SB * SB + e];
+    } else if (I == K) {
+      S.Ph[a][b] = uh_[(size_t)J * SB * SB + e];
+      S.Pl[a][b] = ul_[(size_t)J * SB * SB + e];
+    } else {
+      S.Ph[a][b] = uh_[(size_t)I * SB * SB + e];
+      S.Pl[a][b] = ul_[(size_t)I * SB * SB + e];
       const size_t src = (size_t)(J * SB + a) * mp + k0 + b;
       S.Ch[a][b] = sh_[src];
       S.Cl[a][b] = sl_[src];
@@ -247,67 +299,55 @@ __global__ void __launch_bounds__(SW_THREADS* kTilesPerCta) k_sweep_step(const f
   if (I == K && J == K) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      oh[q] = S.Ph[r][c4 + q];  // -P^{-1}
+      oh[q] = S.Ph[r][c4 + q];
       ol[q] = S.Pl[r][c4 + q];
     }
+  } else if (J == K) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      oh[q] = -S.Ph[r][c4 + q];
+      ol[q] = -S.Pl[r][c4 + q];
+    }
+  } else if (I == K) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      oh[q] = -S.Ph[c4 + q][r];
+      ol[q] = -S.Pl[c4 + q][r];
+    }
   } else {
-    // U = A_{X,K} (-P^{-1}) = -(A_{X,K} P^{-1}) for this thread's row r
-    float uh4[4], ul4[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      uh4[q] = 0.0f;
-      ul4[q] = 0.0f;
+      const size_t src = (size_t)(I * SB + r) * mp + J * SB + c4 + q;
+      oh[q] = sh_[src];
+      ol[q] = sl_[src];
     }
-    // row r of U for all 32 columns is needed in case 1: compute the full
-    // 32 x 32 U into smem first (each thread its 4 entries), then use it
     for (int b = 0; b < SB; ++b) {
-      const float th = S.Th[r][b], tl = S.Tl[r][b];
+      const float th = S.Ph[r][b], tl = S.Pl[r][b];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) df_mac(th, tl, S.Ph[b][c4 + q], S.Pl[b][c4 + q], uh4[q], ul4[q]);
+      for (int q = 0; q < 4; ++q) df_mac(th, tl, S.Ch[c4 + q][b], S.Cl[c4 + q][b], oh[q], ol[q]);
     }
-    half_sync(bar);  // all reads of T done before it is overwritten with U
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      df_renorm(uh4[q], ul4[q]);
-      S.Th[r][c4 + q] = uh4[q];
-      S.Tl[r][c4 + q] = ul4[q];
-    }
-    half_sync(bar);
-    if (J == K) {
-      // A_IK P^{-1} = -U
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        oh[q] = -S.Th[r][c4 + q];
-        ol[q] = -S.Tl[r][c4 + q];
-      }
-    } else if (I == K) {
-      // P^{-1} A_KJ = (A_JK P^{-1})^T = -U^T
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        oh[q] = -S.Th[c4 + q][r];
-        ol[q] = -S.Tl[c4 + q][r];
-      }
-    } else {
-      // A_IJ - A_IK P^{-1} A_KJ = A_IJ + U A_{J,K}^T
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const size_t src = (size_t)(I * SB + r) * mp + J * SB + c4 + q;
-        oh[q] = sh_[src];
-        ol[q] = sl_[src];
-      }
-      for (int b = 0; b < SB; ++b) {
-        const float th = S.Th[r][b], tl = S.Tl[r][b];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) df_mac(th, tl, S.Ch[c4 + q][b], S.Cl[c4 + q][b], oh[q], ol[q]);
-      }
-    }
+    for (int q = 0; q < 4; ++q) df_renorm(oh[q], ol[q]);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    df_renorm(oh[q], ol[q]);
     const size_t dst = (size_t)(I * SB + r) * mp + J * SB + c4 + q;
     dh_[dst] = oh[q];
     dl_[dst] = ol[q];
+  }
+  if (I == J) return;
+  // the mirror (J, I) = tile^T, through shared memory (Th/Tl are free)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    S.Th[r][c4 + q] = oh[q];
+    S.Tl[r][c4 + q] = ol[q];
+  }
+  half_sync(bar);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const size_t dst = (size_t)(J * SB + r) * mp + I * SB + c4 + q;
+    dh_[dst] = S.Th[c4 + q][r];
+    dl_[dst] = S.Tl[c4 + q][r];
   }
 }
 
@@ -353,7 +393,7 @@ __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ 
 
 size_t sweep_scratch_floats(int m) {
   const size_t mp = (size_t)(m + SB - 1) / SB * SB;
-  return 4 * mp * mp + mp + 8 + 4 * SB * SB;
+  return 4 * mp * mp + mp + 8 + 4 * SB * SB + 2 * mp * SB;
 }
 
 // G: upper triangle of the column-major m x m Gram; qinv: m x m output
@@ -373,6 +413,9 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   float* qbase = scratch + 4 * mm + mp + 8;
   float* qh[2] = {qbase, qbase + 2 * SB * SB};
   float* ql[2] = {qbase + SB * SB, qbase + 3 * SB * SB};
+  // the panels U_I of the current step: [nt][SB][SB] pairs
+  float* uh = qbase + 4 * SB * SB;
+  float* ul = uh + (size_t)mp * SB;
   const int g1 = (int)std::max<long long>(1, std::min<long long>(((long long)mm + 255) / 256, (long long)num_sms * 4));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sweep_init<<<g1, 256, 0, st>>>(g, m, mp, a0h, a0l, scale_buf);
@@ -403,9 +446,11 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
                                                           qh[(K + 1) & 1], ql[(K + 1) & 1], piv);
     }
     if (two && K >= 1 && (e = cudaStreamWaitEvent(st, ev_p, 0)) != cudaSuccess) return e;
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    k_sweep_step<<<(nt * nt + kTilesPerCta - 1) / kTilesPerCta, SW_THREADS * kTilesPerCta, tile_smem, st>>>(
-        sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1]);
+    g_launches.fetch_add(2, std::memory_order_relaxed);
+    k_sweep_panel<<<nt, SW_THREADS, 0, st>>>(sh, sl, mp, K, qh[K & 1], ql[K & 1], uh, ul);
+    const int ntiles = nt * (nt + 1) / 2;
+    k_sweep_step<<<(ntiles + kTilesPerCta - 1) / kTilesPerCta, SW_THREADS * kTilesPerCta, tile_smem, st>>>(
+        sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1], uh, ul);
     if (two) {
       if ((e = cudaEventRecord(ev_x, st)) != cudaSuccess) return e;
       if (K + 1 < nt && (e = cudaEventRecord(ev_p, st_aux)) != cudaSuccess) return e;

@@ -370,7 +370,7 @@ class LPSolver:
         st = nat.LpKernelStats()
         self._check(self._lib.lp_get_kernel_stats(self._h, ctypes.byref(st)))
         return {"launches": st.launches, "ms": st.ms, "bytes_per_launch": st.bytes_per_launch,
-                "all_launches": st.all_launches}
+                "all_launches": st.all_launches, "graph_replays": st.graph_replays}
 
     def reset_kernel_stats(self):
         self._check(self._lib.lp_reset_kernel_stats(self._h))

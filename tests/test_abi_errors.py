@@ -77,7 +77,7 @@ def test_options_default_are_the_documented_defaults(lib):
     assert (o.inner_rule, o.sketch, o.s, o.inner) == (nat.LP_RULE_THEORY, nat.LP_SKETCH_COUNT, 2, nat.LP_INNER_CG)
     assert (o.refine_every, o.k_max, o.t_max, o.v_correction, o.cheb_lanczos) == (8, 200, 500, 1, 10)
     assert (o.profile, o.w_factor, o.w, o.seed, o.stream) == (0, 4.0, 0, 0, None)
-    assert (o.tensor_sketch, o.precondition, o.sigma_rule) == (1, 1, 0)
+    assert (o.tensor_sketch, o.precondition, o.sigma_rule, o.graphs, o.autotune) == (1, 1, 0, 1, 0)
 
 
 def test_null_and_shape_errors(lib):
@@ -154,7 +154,7 @@ def test_host_csr_structure_is_checked(lib):
 @pytest.mark.parametrize("field,value,message", [
     ("sigma", 0.0, "sigma"), ("sigma", 1.0, "sigma"), ("sigma", math.nan, "sigma"),
     ("gamma", 0.0, "gamma"), ("gamma", 1.0, "gamma"),
-    ("s", 0, "s must be"), ("s", 17, "s must be"),
+    ("s", 0, "s must be"), ("s", 17, "s must be"), ("graphs", 2, "graphs"), ("autotune", 3, "autotune"),
     ("sketch", 2, "sketch"), ("precondition", 2, "precondition"), ("sigma_rule", 2, "sigma_rule"),
     ("inner", 2, "inner must be"), ("t_max", 0, "t_max"), ("k_max", -1, "k_max"),
     ("inner_rule", 2, "inner_rule"), ("tol_cg", -1e-3, "tol_cg"), ("tol_cg", math.inf, "tol_cg"),

@@ -144,24 +144,67 @@ def test_w_sweep_inner_iterations_fall_with_w():
     assert means[0] > means[1] > means[2], means
 
 
+def test_autotuned_handles_of_one_shape_take_the_same_kernel():
+    # the tuned choice is cached per (dtype, leading dimension, n): a second
+    # handle of the same shape computes the same products bit for bit, and the
+    # tuned product agrees with the default one to FP32 rounding
+    torch = torch_cuda()
+    lp = lpgen.planted_dense(300, 40000, seed=23, storage="f32", col_scale_log10=(-1, 1))
+    rng = np.random.default_rng(24)
+    d2 = dev(torch, np.exp(rng.uniform(-4, 4, lp.n)))
+    v = dev(torch, rng.standard_normal(lp.m))
+    with solver_for(lp, s=2, autotune=1) as S1, solver_for(lp, s=2, autotune=1) as S2, \
+            solver_for(lp, s=2) as S0:
+        u1, u2, u0 = host(S1.adat(d2, v, 0)), host(S2.adat(d2, v, 0)), host(S0.adat(d2, v, 0))
+    assert np.array_equal(u1, u2)
+    assert np.allclose(u1, u0, rtol=1e-4, atol=1e-6 * np.abs(u0).max())
+
+
 def test_batched_solve_matches_sequential_solves():
     # the batched-LP family (uneven m, n): lp_solve_batch runs the LPs
     # concurrently on their own streams; every LP reaches its planted optimum
     # and the results equal the one-at-a-time solves bit for bit
+    # (with the graph path on: blocks of inner steps replayed from CUDA graphs,
+    # and the product's tile shape from the autotuner)
     from paper_2209_08722_gb300 import solve_batch
     lps = lpgen.batch_family(6, seed=3, m_range=(32, 160), k_range=(64, 128))
-    solvers = [solver_for(lp, s=2) for lp in lps]
+    solvers = [solver_for(lp, s=2, autotune=1) for lp in lps]
     try:
         seq = [S.solve(tol=1e-8) for S in solvers]
+        for S in solvers:
+            S.reset_kernel_stats()
         bat = solve_batch(solvers, tol=1e-8, max_threads=0)
+        replays = [S.kernel_stats()["graph_replays"] for S in solvers]
     finally:
         for S in solvers:
             S.close()
+    assert all(r > 0 for r in replays), replays
     for lp, (x1, y1, _, i1), (x2, y2, _, i2) in zip(lps, seq, bat):
         assert i2["status"] == 0, i2
         assert abs(lp.c @ x2 - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
         assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
         assert i1["inner_total"] == i2["inner_total"]
+
+
+@pytest.mark.parametrize("storage,m,n,inner", [("f32", 128, 20000, 0), ("bf16", 1100, 30000, 0),
+                                               ("f32", 96, 12000, 1)])
+def test_graph_replayed_blocks_equal_plain_launches(storage, m, n, inner):
+    # the same kernels with the same arguments: the solve with every block of
+    # inner steps replayed from a CUDA graph equals the one with plain
+    # launches bit for bit (warp-per-column and row-split products, CG and
+    # Chebyshev)
+    lp = lpgen.planted_dense(m, n, seed=17, storage=storage, col_scale_log10=(-1, 1))
+    out = {}
+    for graphs in (0, 1):
+        with solver_for(lp, s=2, graphs=graphs, inner=inner) as S:
+            S.reset_kernel_stats()
+            out[graphs] = S.solve(tol=1e-8)
+            out[graphs] += (S.kernel_stats()["graph_replays"],)
+    (x0, y0, s0, i0, r0), (x1, y1, s1, i1, r1) = out[0], out[1]
+    assert r0 == 0 and r1 > 0
+    assert i1["status"] == 0 and abs(lp.c @ x1 - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert np.array_equal(x0, x1) and np.array_equal(y0, y1) and np.array_equal(s0, s1)
+    assert i0["inner_total"] == i1["inner_total"]
 
 
 @pytest.mark.parametrize("col_scale", [None, (-2, 2)])

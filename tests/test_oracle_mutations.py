@@ -46,6 +46,7 @@ PINS = {
     "gauss_uniforms": ("test_oracle_sketch", "test_gaussian_uniforms_are_exact_fp32_and_in_range", {}),
     "gauss_grid_ends": ("test_oracle_sketch", "test_gaussian_uniforms_reach_both_ends_of_their_grids", {}),
     "gauss_embedding": ("test_oracle_sketch", "test_gaussian_sketch_subspace_embedding", {}),
+    "gauss_pairs": ("test_oracle_sketch", "test_gaussian_sketch_uses_both_box_muller_outputs", {}),
     # oracle.pcg
     "cg_krylov": ("test_oracle_pcg", "test_cg_iterates_minimise_energy_error_over_krylov_space", {}),
     "cg_exact": ("test_oracle_pcg", "test_cg_reaches_exact_solution", {}),
@@ -116,6 +117,10 @@ MUTANTS = [
      "np.sqrt(-np.log(u1))", ["gauss_moments", "gauss_embedding"]),
     ("uniform_u1_open_at_zero", "sketch", "gaussian_uniforms", "+ 1.0) / 8388608.0", ") / 8388608.0",
      ["gauss_uniforms", "gauss_grid_ends"]),
+    ("box_muller_one_output", "sketch", "gaussian_matrix", "r * np.sin(ang)", "r * np.cos(ang)",
+     ["gauss_pairs"]),
+    ("box_muller_pair_index", "sketch", "gaussian_matrix", "[f // 2]\n    ang", "[f % ((n * w + 1) // 2)]\n    ang",
+     ["gauss_pairs"]),
     # --- Algorithm 1 (Section 3) ---
     ("precond_q_plus_half", "pcg", "preconditioner", "(U / sv) @ U.T", "(U * sv) @ U.T", ["whiten"]),
     ("precond_transpose_dropped", "pcg", "preconditioner", "(U / sv) @ U.T", "(U / sv) @ U", ["whiten"]),

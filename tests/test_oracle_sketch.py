@@ -108,6 +108,26 @@ def test_gaussian_sketch_moments():
     assert not np.allclose(G / np.sqrt(w), G2)
 
 
+def test_gaussian_sketch_uses_both_box_muller_outputs():
+    # entries 2p and 2p+1 (flat, row-major) are the cosine and sine normals of
+    # draw p: r cos(t) and r sin(t) with the same r and t, so their squares
+    # add up to r^2 = -2 ln u1, and across draws the two halves are
+    # uncorrelated N(0, 1) samples with the same moments
+    n, w = 300, 200
+    G = sketch.gaussian_matrix(5, 3, 1, n, w).reshape(-1) * np.sqrt(w)
+    u1, u2 = sketch.gaussian_uniforms(5, 3, 1, n, w)
+    even, odd = G[0::2], G[1::2]
+    assert np.allclose(even ** 2 + odd ** 2, -2.0 * np.log(u1), rtol=1e-12)
+    assert np.allclose(np.arctan2(odd, even) % (2 * np.pi), (2 * np.pi * u2) % (2 * np.pi), atol=1e-9)
+    assert abs(np.corrcoef(even, odd)[0, 1]) < 0.02
+    assert abs(even.var() - 1.0) < 0.03 and abs(odd.var() - 1.0) < 0.03
+    # an odd width pairs entries across rows: the flat index decides
+    G3 = sketch.gaussian_matrix(5, 3, 1, 7, 3).reshape(-1) * np.sqrt(3)
+    v1, _ = sketch.gaussian_uniforms(5, 3, 1, 7, 3)
+    assert v1.size == 11
+    assert np.allclose(G3[0:20:2] ** 2 + G3[1:21:2] ** 2, -2.0 * np.log(v1[:10]), rtol=1e-12)
+
+
 def test_gaussian_uniforms_are_exact_fp32_and_in_range():
     u1, u2 = sketch.gaussian_uniforms(3, 1, 0, 50, 40)
     assert np.array_equal(u1.astype(np.float32).astype(np.float64), u1)
@@ -171,7 +191,8 @@ def test_gaussian_uniforms_reach_both_ends_of_their_grids():
     # u2 on {0, ..., 2^23 - 1} / 2^23.  Over 2^24 draws every end value turns
     # up with probability 1 - e^-2 each; seed 0 shows all four, so a map that
     # is off by one grid step at either end fails here.
-    u1, u2 = sketch.gaussian_uniforms(0, 0, 0, 4096, 4096)
+    u1, u2 = sketch.gaussian_uniforms(0, 0, 0, 4096, 8192)
+    assert u1.size == 2 ** 24
     step = 2.0 ** -23
     assert u1.min() == step and u1.max() == 1.0
     assert u2.min() == 0.0 and u2.max() == 1.0 - step
