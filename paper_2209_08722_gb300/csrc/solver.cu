@@ -709,7 +709,7 @@ int run_cg_block_graph(lp_handle* h, int inner, int refine) {
 // tol_f > 0: absolute ||f|| target; else relative tol_cg.
 // warm: h->dy holds the starting point (CG only); otherwise dy^0 = 0 (Alg. 1)
 int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
-                bool check_sketch = false) {
+                bool check_sketch = false, bool start64 = false) {
   const int m = h->m;
   int inner = h->opt.inner;
   if (warm && inner != LP_INNER_CG) warm = false;
@@ -772,7 +772,7 @@ int inner_solve(lp_handle* h, double tol_f, int* iters_out, bool warm = false,
   int status = LP_OK;
   // FP32 products until a refresh shows the true residual stalled (the FP32
   // product's precision floor); then FP64 products for the rest of this solve.
-  bool use64 = false;
+  bool use64 = start64;
   double f_prev = h->hsc->f_true;
   // sketch check: Ritz values of the first refine-block of CG steps (one
   // unbroken Lanczos run from dy^0)
@@ -924,7 +924,10 @@ int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out, bool warm = f
       tf = h->opt.tol_cg * sqrt(std::max(h->hsc->pad[1], 0.0));
     }
     int more = 0;
-    st = inner_solve(h, tf, &more, true, sk != nullptr && redraws < kPoorRedraws);
+    // after an indefinite Q^{-1} (kappa(Q)^2 u_DF >~ 1) the FP32 product's
+    // error, about 2^-24 kappa(Q) in the preconditioned norm, is as large as
+    // the operator: continue with the double-float product from the start
+    st = inner_solve(h, tf, &more, true, sk != nullptr && redraws < kPoorRedraws, h->factor_kind != 0);
     *iters_out += more;
     tol_f = tf;
   }
@@ -942,7 +945,8 @@ int inner_solve_robust(lp_handle* h, double tol_f, int* iters_out, bool warm = f
   }
   if (rc != LP_OK) return rc;
   int more = 0;
-  st = inner_solve(h, tol_f, &more);
+  // the second attempt: FP64 factor of (ADW)^T and the double-float product
+  st = inner_solve(h, tol_f, &more, false, false, true);
   *iters_out += more;
   return st == kInnerIndefinite ? LP_WARN_INNER_MAXIT : st;
 }

@@ -1,7 +1,7 @@
 """Parity at the full sizes of the workloads: the 512 x 131072 FP32 planted LP
 with columns scaled by 10^U(-2, 2) (seed 0) with its solver options
 (CountSketch w = 4m, s = 4); the 2048 x 524288 BF16 LP (CountSketch w = 4m,
-s = 2), which the bench times; the 4096 x 2,000,000 sparse LP (w = 3m, s = 2).  The oracle checks every output of the
+s = 4), which the bench times; the 4096 x 2,000,000 sparse LP (w = 3m, s = 2).  The oracle checks every output of the
 product (one FP64 matrix product), sampled columns of the sketch (one bucket
 at a time, from the oracle's own hash), and the solve against the planted
 closed-form optimum.
@@ -148,7 +148,7 @@ def test_c4_full_size_product_matches_fp64(c4_lp, precision):
 
 
 def test_c4_full_size_solve_reaches_the_planted_optimum(c4_lp):
-    # BF16 storage, FP32 products, FP64-class refinement; CountSketch w = 4m, s = 2
+    # BF16 storage, FP32 products, FP64-class refinement; CountSketch w = 4m, s = 4
     torch_cuda()
     lp = c4_lp
     cfg = lpgen.CONFIGS["c4"]
