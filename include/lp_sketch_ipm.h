@@ -336,6 +336,52 @@ int lp_step_lengths(lp_handle* h, const double* x, const double* s, const double
  * available (>= 0) or LP_ERR_ARG. */
 int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
 
+/* ---- checkpoint / resume ----
+ * The state of the outer iteration (Algorithm 3, or Algorithm 2 in feasible
+ * mode) between two outer steps.  The sketch of outer iteration k is drawn
+ * from (seed, k, retry) (Section 6, Algorithm 1 step 1), so a solve resumed
+ * from the state taken after k steps draws the same W sequence as the
+ * uninterrupted solve and, the rest of the path being deterministic, takes
+ * the same iterates.  The neighbourhood of the infeasible method
+ * (||r|| / ||r^0|| <= mu / mu_0, Algorithm 3) and the stalling test refer to
+ * the start point's mu_0 and ||r^0||, which the state carries along.
+ *   k            outer iterations done (the iterate is x_k, y_k, s_k)
+ *   mode         LP_FEASIBLE / LP_INFEASIBLE of the solve the state is from
+ *   has_dy_prev  1 when dy_prev holds the last outer iteration's dy (kept for
+ *                the warm start's "previous" proposal, lp_set_warm_start)
+ *   mu0, r0      mu and ||(r_p, r_d)|| at the solve's start point
+ *   ratio_ref    the factor check's reference ratio max/min |R_ii| (0: none)
+ *   seed         the sketch seed (lp_options.seed) of that solve */
+typedef struct {
+    int32_t k;
+    int32_t mode;
+    int32_t has_dy_prev;
+    int32_t reserved;  /* 0 */
+    double mu0;
+    double r0;
+    double ratio_ref;
+    uint64_t seed;
+} lp_state;
+
+/* The state of the last lp_solve on `h` (whatever status >= 0 it returned):
+ * `st` (host) and the iterate x (n), y (m), s (n) and dy_prev (m, nullable),
+ * host or device buffers by io_on_device.  LP_ERR_ARG when no solve has ended
+ * with a status >= 0 since the handle was created, a state was set, or another
+ * entry point overwrote the handle's iterate (lp_residual_rhs). */
+int lp_get_state(lp_handle* h, lp_state* st, double* x, double* y, double* s, double* dy_prev,
+                 int32_t io_on_device);
+
+/* Loads a state (from lp_get_state, on this handle or another one created on
+ * the same LP) for the next lp_solve, which then must be called with
+ * x0 = y0 = s0 = NULL and the state's mode: it starts at outer iteration
+ * st->k from (x, y, s), counts k towards k_max, and takes mu_0, ||r^0||, the
+ * factor reference and the sketch seed from the state (the handle's seed is
+ * replaced by st->seed).  dy_prev is needed when st->has_dy_prev is 1.
+ * LP_ERR_ARG for a null pointer, k < 0, an unknown mode, mu0 <= 0, a
+ * negative or non-finite r0 or ratio_ref, or reserved != 0. */
+int lp_set_state(lp_handle* h, const lp_state* st, const double* x, const double* y,
+                 const double* s, const double* dy_prev, int32_t io_on_device);
+
 /* u = A diag(d2) A^T v without any device allocation, for callers that own all
  * device memory themselves (a pre-sized arena, a serving loop with a fixed
  * memory budget, code that must not call the CUDA allocator after start-up)

@@ -98,6 +98,14 @@ class LpPhase1Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class LpState(ctypes.Structure):
+    _fields_ = [("k", c_int32), ("mode", c_int32), ("has_dy_prev", c_int32), ("reserved", c_int32),
+                ("mu0", c_double), ("r0", c_double), ("ratio_ref", c_double), ("seed", c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LpKernelStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("ms", c_double), ("bytes_per_launch", c_int64),
                 ("all_launches", c_int64), ("graph_replays", c_int64)]
@@ -121,6 +129,8 @@ SIGNATURES = {
     "lp_directions": (c_int32, [P, P, P, P, P, P, c_double, c_int32, P, P]),
     "lp_step_lengths": (c_int32, [P, P, P, P, P, c_int32, c_double, c_double, P]),
     "lp_get_history": (c_int32, [P, POINTER(LpIterRecord), c_int32]),
+    "lp_get_state": (c_int32, [P, POINTER(LpState), P, P, P, P, c_int32]),
+    "lp_set_state": (c_int32, [P, POINTER(LpState), P, P, P, P, c_int32]),
     "lp_adat_noalloc": (c_int32, [P, c_int32, c_int32, c_int64, c_int64, P, P, P, P]),
     "lp_wait_probe": (c_int32, [P, c_int64, c_int32]),
     "lp_csr_to_csc": (c_int32, [c_int32, c_int64, c_int64, P, P, P, c_int32, P, P, P]),

@@ -218,6 +218,12 @@ struct lp_handle {
   long long launch_base = 0;
   std::vector<lp_iter_record> history;
   std::vector<void*> allocs;
+  // checkpoint / resume: the state of the last solve (valid while x, y, s
+  // still hold its iterate) and a state loaded for the next solve
+  bool state_valid = false;
+  lp_state last_state{};
+  bool resume_pending = false;
+  lp_state resume{};
 
   int fail(int code, const char* fmt, ...) {
     char buf[512];
@@ -1759,6 +1765,7 @@ int lp_residual_rhs(lp_handle* h, const double* x, const double* y, const double
   if (!h || !x || !y || !s) return LP_ERR_ARG;
   h->err.clear();
   RET(clear_status(h));
+  h->state_valid = false;  // the handle's iterate is overwritten
   RET(copy_in(h, h->x, x, h->n, 1));
   RET(copy_in(h, h->s, s, h->n, 1));
   RET(copy_in(h, h->y, y, h->m, 1));
@@ -1855,6 +1862,55 @@ int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records) {
   return cnt;
 }
 
+static int get_state_impl(lp_handle* h, lp_state* st, double* x, double* y, double* s, double* dy_prev,
+                          int32_t io_on_device) {
+  if (!h || !st || !x || !y || !s) return LP_ERR_ARG;
+  h->err.clear();
+  if (!h->state_valid) return h->fail(LP_ERR_ARG, "no solve state: no solve ended since the iterate was last set");
+  RET(copy_out(h, x, h->x, h->n, io_on_device));
+  RET(copy_out(h, y, h->y, h->m, io_on_device));
+  RET(copy_out(h, s, h->s, h->n, io_on_device));
+  if (dy_prev) RET(copy_out(h, dy_prev, h->dy_prev, h->m, io_on_device));
+  CK(cudaStreamSynchronize(h->st));
+  *st = h->last_state;
+  if (!dy_prev) st->has_dy_prev = 0;
+  return LP_OK;
+}
+
+static int set_state_impl(lp_handle* h, const lp_state* st, const double* x, const double* y, const double* s,
+                          const double* dy_prev, int32_t io_on_device) {
+  if (!h || !st || !x || !y || !s) return LP_ERR_ARG;
+  h->err.clear();
+  if (st->k < 0 || (st->mode != LP_FEASIBLE && st->mode != LP_INFEASIBLE) || st->reserved != 0 ||
+      !(st->mu0 > 0) || !std::isfinite(st->mu0) || !(st->r0 >= 0) || !std::isfinite(st->r0) ||
+      !(st->ratio_ref >= 0) || !std::isfinite(st->ratio_ref) || (st->has_dy_prev != 0 && st->has_dy_prev != 1) ||
+      (st->has_dy_prev && !dy_prev))
+    return h->fail(LP_ERR_ARG, "invalid state");
+  h->state_valid = false;
+  h->resume_pending = false;
+  RET(copy_in(h, h->x, x, h->n, io_on_device));
+  RET(copy_in(h, h->y, y, h->m, io_on_device));
+  RET(copy_in(h, h->s, s, h->n, io_on_device));
+  if (st->has_dy_prev) RET(copy_in(h, h->dy_prev, dy_prev, h->m, io_on_device));
+  CK(cudaStreamSynchronize(h->st));
+  h->resume = *st;
+  h->opt.seed = st->seed;
+  h->resume_pending = true;
+  return LP_OK;
+}
+
+int lp_get_state(lp_handle* h, lp_state* st, double* x, double* y, double* s, double* dy_prev,
+                 int32_t io_on_device) {
+  return guarded(h ? &h->err : nullptr,
+                 [&] { return get_state_impl(h, st, x, y, s, dy_prev, io_on_device); });
+}
+
+int lp_set_state(lp_handle* h, const lp_state* st, const double* x, const double* y, const double* s,
+                 const double* dy_prev, int32_t io_on_device) {
+  return guarded(h ? &h->err : nullptr,
+                 [&] { return set_state_impl(h, st, x, y, s, dy_prev, io_on_device); });
+}
+
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st) {
   if (!h || !st) return LP_ERR_ARG;
   if (cudaStreamSynchronize(h->st) != cudaSuccess) return LP_ERR_CUDA;
@@ -1934,37 +1990,50 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
   const auto t_start = std::chrono::steady_clock::now();
   const bool feasible = mode == LP_FEASIBLE;
   h->history.clear();
-  h->ratio_ref = 0.0;
-  h->ws_have_prev = false;
+  const bool resume = h->resume_pending;
+  h->resume_pending = false;
+  h->state_valid = false;
+  if (resume) {
+    if (x0 || y0 || s0) return h->fail(LP_ERR_ARG, "a resumed solve starts from its state: x0, y0, s0 must be null");
+    if (mode != h->resume.mode) return h->fail(LP_ERR_ARG, "the state is from a solve in the other mode");
+    if (h->resume.k > h->opt.k_max) return h->fail(LP_ERR_ARG, "the state's k exceeds k_max");
+  }
+  h->ratio_ref = resume ? h->resume.ratio_ref : 0.0;
+  h->ws_have_prev = resume && h->resume.has_dy_prev != 0;
   lp_result res;
   std::memset(&res, 0, sizeof res);
   const long long n = h->n;
   const int m = h->m;
-  // start point
-  if (x0) RET(copy_in(h, h->x, x0, n, io_on_device));
-  else CK(launch_fill(n, h->x, 1.0, h->num_sms, h->st));
-  if (s0) RET(copy_in(h, h->s, s0, n, io_on_device));
-  else CK(launch_fill(n, h->s, 1.0, h->num_sms, h->st));
-  if (y0) RET(copy_in(h, h->y, y0, m, io_on_device));
-  else CK(cudaMemsetAsync(h->y, 0, sizeof(double) * m, h->st));
-  if (feasible && (!x0 || !y0 || !s0))
+  // start point (a resumed solve finds its iterate in x, y, s already)
+  if (!resume) {
+    if (x0) RET(copy_in(h, h->x, x0, n, io_on_device));
+    else CK(launch_fill(n, h->x, 1.0, h->num_sms, h->st));
+    if (s0) RET(copy_in(h, h->s, s0, n, io_on_device));
+    else CK(launch_fill(n, h->s, 1.0, h->num_sms, h->st));
+    if (y0) RET(copy_in(h, h->y, y0, m, io_on_device));
+    else CK(cudaMemsetAsync(h->y, 0, sizeof(double) * m, h->st));
+  }
+  if (feasible && !resume && (!x0 || !y0 || !s0))
     return h->fail(LP_ERR_NOT_FEASIBLE, "feasible mode needs x0, y0, s0");
   CK(cudaMemsetAsync(&h->sc->err, 0, sizeof(int), h->st));
   RET(compute_mu(h));
   CK(launch_min_prod(n, h->x, h->s, h->vpart, h->tickets + 5, &h->sc->pad[3], h->num_sms, h->st));
   RET(sync_read(h));
-  const double mu0 = h->hsc->mu;
-  if (!(mu0 > 0) || !(h->hsc->pad[3] > 0)) return h->fail(LP_ERR_ARG, "start needs x0 > 0 and s0 > 0");
-  if (feasible && h->hsc->pad[3] < (1.0 - h->opt.gamma) * mu0 * (1.0 - 1e-9))
+  const double mu_start = h->hsc->mu;
+  if (!(mu_start > 0) || !(h->hsc->pad[3] > 0)) return h->fail(LP_ERR_ARG, "start needs x0 > 0 and s0 > 0");
+  if (feasible && h->hsc->pad[3] < (1.0 - h->opt.gamma) * mu_start * (1.0 - 1e-9))
     return h->fail(LP_ERR_NOT_FEASIBLE, "start is not in N(gamma)");
-  double r0 = 0.0;
+  // mu_0 and ||r^0|| belong to the start of the whole solve, also when resumed
+  const double mu0 = resume ? h->resume.mu0 : mu_start;
+  double r0 = resume ? h->resume.r0 : 0.0;
+  const int k_start = resume ? h->resume.k : 0;
   int status = LP_STATUS_MAX_ITER;
   double ms_res = 0, ms_sk = 0, ms_fac = 0, ms_in = 0, ms_cor = 0, ms_step = 0;
   auto now = [] { return std::chrono::steady_clock::now(); };
   auto ms_since = [](std::chrono::steady_clock::time_point t) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
   };
-  for (int k = 0; k <= h->opt.k_max; ++k) {
+  for (int k = k_start; k <= h->opt.k_max; ++k) {
     auto t0 = now();
     // ---- step 3: residuals, mu, right-hand side, d^2 ----
     RET(residual_pass(h, feasible, h->opt.sigma_rule == 1 ? 0.0 : -1.0));
@@ -1974,7 +2043,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     const double rp = sqrt(S.rp2), rd = sqrt(S.rd2);
     const StopMeasures sm = stop_measures(S.cx, S.by, S.rp2, S.rd2, h->bnorm, h->cnorm);
     const double gap = sm.gap, rp_rel = sm.rp_rel, rd_rel = sm.rd_rel;
-    if (k > 0 && !h->history.empty()) {
+    if (k > k_start && !h->history.empty()) {
       h->history.back().alpha_max = S.alpha_max;
       h->history.back().alpha_bar = S.alpha_bar;
     }
@@ -1990,7 +2059,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
       r0 = sqrt(S.rp2 + S.rd2);
       if (feasible && (rp_rel > 1e-8 || rd_rel > 1e-8))
         return h->fail(LP_ERR_NOT_FEASIBLE, "start is not feasible (rel residuals %.2e, %.2e)", rp_rel, rd_rel);
-    } else if (S.alpha_bar <= 0.0) {
+    } else if (k > k_start && S.alpha_bar <= 0.0) {
       status = LP_STATUS_STALLED;
       res.outer_iterations = k;
       break;
@@ -2115,6 +2184,15 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
   if (y) RET(copy_out(h, y, h->y, m, io_on_device));
   if (s) RET(copy_out(h, s, h->s, n, io_on_device));
   CK(cudaStreamSynchronize(h->st));
+  h->last_state.k = res.outer_iterations;
+  h->last_state.mode = mode;
+  h->last_state.has_dy_prev = h->ws_have_prev ? 1 : 0;
+  h->last_state.reserved = 0;
+  h->last_state.mu0 = mu0;
+  h->last_state.r0 = r0;
+  h->last_state.ratio_ref = h->ratio_ref;
+  h->last_state.seed = h->opt.seed;
+  h->state_valid = true;
   res.status = status;
   res.ms_total = ms_since(t_start);
   res.ms_residual = ms_res;

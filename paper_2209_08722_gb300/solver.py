@@ -366,6 +366,30 @@ class LPSolver:
         self._lib.lp_get_history(self._h, recs, cnt)
         return [recs[i].as_dict() for i in range(cnt)]
 
+    def get_state(self) -> dict:
+        """lp_get_state: the state of the last solve as host arrays and scalars
+        (a checkpoint: pass it to set_state on this or a fresh solver of the
+        same LP to resume the outer iteration where it stopped)."""
+        st = nat.LpState()
+        x, y, s, dy = np.empty(self.n), np.empty(self.m), np.empty(self.n), np.empty(self.m)
+        self._check(self._lib.lp_get_state(self._h, ctypes.byref(st), _ptr(x), _ptr(y), _ptr(s), _ptr(dy), 0))
+        out = st.as_dict()
+        out.update(x=x, y=y, s=s, dy_prev=dy)
+        return out
+
+    def set_state(self, state: dict):
+        """lp_set_state: the next solve() (with no start point) resumes from
+        `state` (a dict as returned by get_state)."""
+        st = nat.LpState(int(state["k"]), int(state["mode"]), int(state["has_dy_prev"]), 0,
+                         float(state["mu0"]), float(state["r0"]), float(state["ratio_ref"]), int(state["seed"]))
+        arrs = {}
+        for name, count in (("x", self.n), ("y", self.m), ("s", self.n), ("dy_prev", self.m)):
+            v = np.ascontiguousarray(state[name], dtype=np.float64)
+            _need(v, count, name)
+            arrs[name] = v
+        self._check(self._lib.lp_set_state(self._h, ctypes.byref(st), _ptr(arrs["x"]), _ptr(arrs["y"]),
+                                           _ptr(arrs["s"]), _ptr(arrs["dy_prev"]), 0))
+
     def kernel_stats(self) -> dict:
         st = nat.LpKernelStats()
         self._check(self._lib.lp_get_kernel_stats(self._h, ctypes.byref(st)))
