@@ -61,7 +61,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
         objs = list(ex.map(compile_one, srcs))
     out = lib_path()
     tmp = out + ".tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcusolver", "-lcublas"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcusolver", "-lcublas", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

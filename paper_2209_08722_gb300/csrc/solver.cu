@@ -17,6 +17,7 @@
 // check, inner-solve chunks); everything else is stream-ordered.
 #include <cublas_v2.h>
 #include <cusolverDn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <cmath>
@@ -1981,12 +1982,30 @@ static int normal_solve_impl(lp_handle* h, const double* D, const double* p, con
 // ---------------------------------------------------------------------------
 // the IPM (Algorithm 2 / Algorithm 3)
 // ---------------------------------------------------------------------------
+// NVTX ranges naming the phases of an outer iteration (shown by Nsight tools;
+// without a tool attached a push or pop is a no-op)
+struct PhaseRange {
+  bool open = false;
+  void next(const char* name) {
+    end();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  void end() {
+    if (open) nvtxRangePop();
+    open = false;
+  }
+  ~PhaseRange() { end(); }
+};
+
 static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, const double* y0,
              const double* s0, int32_t io_on_device, double* x, double* y, double* s,
              lp_result* info) {
   if (!h || !(tol > 0)) return LP_ERR_ARG;
   if (mode != LP_FEASIBLE && mode != LP_INFEASIBLE) return LP_ERR_ARG;
   h->err.clear();
+  PhaseRange solve_range, phase;
+  solve_range.next("lp_solve");
   const auto t_start = std::chrono::steady_clock::now();
   const bool feasible = mode == LP_FEASIBLE;
   h->history.clear();
@@ -2035,6 +2054,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
   };
   for (int k = k_start; k <= h->opt.k_max; ++k) {
     auto t0 = now();
+    phase.next("residuals");
     // ---- step 3: residuals, mu, right-hand side, d^2 ----
     RET(residual_pass(h, feasible, h->opt.sigma_rule == 1 ? 0.0 : -1.0));
     RET(sync_read(h));
@@ -2090,12 +2110,14 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     // ---- step 2 + Algorithm 1 steps 1-2: sketch and factor ----
     t0 = now();
     int retry = 0;
+    phase.next("sketch_factor");
     RET(sketch_and_factor(h, h->d2d, 1, k, &retry));
     res.sketch_retries += retry;
     const int retry0 = retry;
     const SketchRef skr{h->d2d, 1, (long long)k, &retry};
     ms_fac += ms_since(t0);
     // ---- Algorithm 1 step 3: inner solve to the Lemma 4.4 level ----
+    phase.next("inner_solve");
     t0 = now();
     const bool adaptive = h->opt.sigma_rule == 1;
     const double sig_lo = 0.1, sig_hi = 0.75;  // inside the analysis range (0, 4/5)
@@ -2116,6 +2138,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
       ms_in += ms_since(t0);
       // ---- step 5: correction v, directions ----
       t0 = now();
+      phase.next("correction");
       RET(correction(h, h->x, h->s, k, retry));
       RET(direction_pass(h, feasible));
     } else {
@@ -2140,6 +2163,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
       ist = std::max(ist, ist2);
       ms_in += ms_since(t0);
       t0 = now();
+      phase.next("directions");
       // affine direction (sigma = 0) and its largest positivity-keeping step
       CK(cudaMemcpyAsync(h->dy, h->dy_aff, mb, cudaMemcpyDeviceToDevice, h->st));
       CK(cudaMemcpyAsync(h->v, h->v_aff, nbytes, cudaMemcpyDeviceToDevice, h->st));
@@ -2172,6 +2196,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     CK(cudaStreamSynchronize(h->st));
     ms_cor += ms_since(t0);
     // ---- steps 6-8: step lengths and update ----
+    phase.next("step");
     t0 = now();
     CK(launch_step(n, h->x, h->s, h->dx, h->ds, h->opt.gamma, feasible ? 1 : 0, res_ratio, mu0,
                    h->vpart, h->tickets + 4, h->sc, h->num_sms, h->st));
@@ -2180,6 +2205,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     CK(cudaStreamSynchronize(h->st));
     ms_step += ms_since(t0);
   }
+  phase.end();
   if (x) RET(copy_out(h, x, h->x, n, io_on_device));
   if (y) RET(copy_out(h, y, h->y, m, io_on_device));
   if (s) RET(copy_out(h, s, h->s, n, io_on_device));
