@@ -126,6 +126,11 @@ typedef struct {
                               later handles of that shape reuse it untimed; the choice changes
                               the product's summation order (results agree with autotune = 0 to
                               rounding); 0 */
+    int32_t guard;         /* 1: every device workspace buffer of the handle is allocated with a
+                              256-byte guard region before and after it, filled with the byte
+                              0xA5; lp_check_guards reports regions that changed (a write past
+                              a buffer's ends: the stand-in for a device memory checker).  The
+                              results are the same as with guard = 0; 0 */
 } lp_options;
 
 /* ---- results -------------------------------------------------------------- */
@@ -487,6 +492,13 @@ int lp_get_warm_start_stats(lp_handle* h, int64_t* recorded, int64_t* proposals,
 /* Statistics of the hot product kernel (requires opt.profile = 1; the timed
  * launches are the sample described at lp_options.profile). */
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);
+
+/* Compares every guard region of a handle created with lp_options.guard = 1
+ * with its fill pattern (after the handle's stream is idle).  *checked = the
+ * number of regions compared (2 per buffer; 0 without the option), *damaged =
+ * how many differ; lp_last_error names the first damaged buffer (its index in
+ * allocation order and size).  LP_ERR_ARG for null pointers. */
+int lp_check_guards(lp_handle* h, int64_t* checked, int64_t* damaged);
 int lp_reset_kernel_stats(lp_handle* h);
 
 #ifdef __cplusplus

@@ -54,7 +54,7 @@ class LpOptions(ctypes.Structure):
                 ("profile", c_int32), ("w_factor", c_double), ("w", c_int64),
                 ("seed", c_uint64), ("stream", c_void_p), ("tensor_sketch", c_int32),
                 ("precondition", c_int32), ("sigma_rule", c_int32), ("graphs", c_int32),
-                ("autotune", c_int32)]
+                ("autotune", c_int32), ("guard", c_int32)]
 
 
 class LpResult(ctypes.Structure):
@@ -150,6 +150,7 @@ SIGNATURES = {
     "lp_set_warm_start": (c_int32, [P, c_int32, P, P, P, c_int32]),
     "lp_get_warm_start_stats": (c_int32, [P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
+    "lp_check_guards": (c_int32, [P, POINTER(c_int64), POINTER(c_int64)]),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }
 

@@ -235,18 +235,34 @@ struct lp_handle {
     err = buf;
     return code;
   }
+  // opt.guard: guard regions of kGuard bytes of kGuardByte on both sides of
+  // every buffer (the user part stays 256-byte aligned)
+  static constexpr size_t kGuard = 256;
+  static constexpr unsigned char kGuardByte = 0xA5;
+  struct GuardedBuf {
+    char* base;
+    size_t bytes;
+  };
+  std::vector<GuardedBuf> guarded_bufs;
   template <typename T>
   int alloc(T** ptr, size_t count) {
     void* p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    const size_t pad = opt.guard ? kGuard : 0;
+    if (cudaMalloc(&p, bytes + 2 * pad) != cudaSuccess) {
       cudaGetLastError();
       *ptr = nullptr;
-      return fail(LP_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
+      return fail(LP_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes + 2 * pad);
     }
     allocs.push_back(p);
-    cudaMemsetAsync(p, 0, bytes, st);
-    *ptr = static_cast<T*>(p);
+    char* user = static_cast<char*>(p) + pad;
+    if (pad) {
+      guarded_bufs.push_back({static_cast<char*>(p), bytes});
+      cudaMemsetAsync(p, kGuardByte, pad, st);
+      cudaMemsetAsync(user + bytes, kGuardByte, pad, st);
+    }
+    cudaMemsetAsync(user, 0, bytes, st);
+    *ptr = reinterpret_cast<T*>(user);
     return LP_OK;
   }
   cudaStream_t stream() const { return st; }
@@ -1197,6 +1213,7 @@ void options_check(const lp_options* o, std::string* why) {
   else if (o->w == 0 && !(o->w_factor > 0 && o->w_factor <= 1e6)) *why = "w_factor must be in (0, 1e6] when w = 0";
   else if (o->graphs != 0 && o->graphs != 1) *why = "graphs must be 0 or 1";
   else if (o->autotune != 0 && o->autotune != 1) *why = "autotune must be 0 or 1";
+  else if (o->guard != 0 && o->guard != 1) *why = "guard must be 0 or 1";
 }
 
 }  // namespace
@@ -1252,6 +1269,7 @@ void lp_options_default(lp_options* o) {
   o->sigma_rule = 0;
   o->graphs = 1;
   o->autotune = 0;
+  o->guard = 0;
 }
 
 const char* lp_create_error(void) { return g_create_error.c_str(); }
@@ -1910,6 +1928,33 @@ int lp_set_state(lp_handle* h, const lp_state* st, const double* x, const double
                  const double* dy_prev, int32_t io_on_device) {
   return guarded(h ? &h->err : nullptr,
                  [&] { return set_state_impl(h, st, x, y, s, dy_prev, io_on_device); });
+}
+
+static int check_guards_impl(lp_handle* h, int64_t* checked, int64_t* damaged) {
+  if (!h || !checked || !damaged) return LP_ERR_ARG;
+  h->err.clear();
+  CK(cudaStreamSynchronize(h->st));
+  std::vector<unsigned char> buf(lp_handle::kGuard);
+  int64_t nchk = 0, nbad = 0;
+  for (size_t i = 0; i < h->guarded_bufs.size(); ++i) {
+    const lp_handle::GuardedBuf& g = h->guarded_bufs[i];
+    for (int side = 0; side < 2; ++side) {
+      const char* src = side ? g.base + lp_handle::kGuard + g.bytes : g.base;
+      CK(cudaMemcpy(buf.data(), src, lp_handle::kGuard, cudaMemcpyDeviceToHost));
+      ++nchk;
+      bool ok = true;
+      for (unsigned char c : buf) ok = ok && c == lp_handle::kGuardByte;
+      if (!ok && nbad++ == 0)
+        h->fail(LP_OK, "guard %s buffer %zu (%zu bytes) was overwritten", side ? "after" : "before", i, g.bytes);
+    }
+  }
+  *checked = nchk;
+  *damaged = nbad;
+  return LP_OK;
+}
+
+int lp_check_guards(lp_handle* h, int64_t* checked, int64_t* damaged) {
+  return guarded(h ? &h->err : nullptr, [&] { return check_guards_impl(h, checked, damaged); });
 }
 
 int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st) {

@@ -390,6 +390,14 @@ class LPSolver:
         self._check(self._lib.lp_set_state(self._h, ctypes.byref(st), _ptr(arrs["x"]), _ptr(arrs["y"]),
                                            _ptr(arrs["s"]), _ptr(arrs["dy_prev"]), 0))
 
+    def check_guards(self):
+        """lp_check_guards: (regions checked, regions damaged, message) for a
+        solver created with guard=1."""
+        checked, damaged = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.lp_check_guards(self._h, ctypes.byref(checked), ctypes.byref(damaged)))
+        msg = self._lib.lp_last_error(self._h).decode() if damaged.value else ""
+        return checked.value, damaged.value, msg
+
     def kernel_stats(self) -> dict:
         st = nat.LpKernelStats()
         self._check(self._lib.lp_get_kernel_stats(self._h, ctypes.byref(st)))

@@ -23,8 +23,24 @@ def host(t):
 
 
 def solver_for(lp, **opts):
+    """A solver for a planted LP, created with guard regions around its device
+    buffers (unless guard=0 is asked for); closing it fails the test when a
+    kernel wrote past the end of a buffer."""
     from paper_2209_08722_gb300 import from_planted
-    return from_planted(lp, **opts)
+    opts.setdefault("guard", 1)
+    S = from_planted(lp, **opts)
+    if opts["guard"]:
+        close = S.close
+
+        def close_checked():
+            if S._h:
+                checked, damaged, msg = S.check_guards()
+                close()
+                assert checked > 0 and damaged == 0, msg
+            close()
+
+        S.close = close_checked
+    return S
 
 
 def adat_bound(A, d2, v):
