@@ -16,6 +16,8 @@
 #include "internal.h"
 #include "df.cuh"
 
+#include <atomic>
+
 namespace lpk {
 
 namespace {
@@ -147,13 +149,43 @@ size_t gram_df_scratch_floats(int m, int w, int num_sms) {
   return (size_t)2 * m * w + (size_t)2 * ks * ntiles * GT * GT;
 }
 
+// CTAs of k_gram_df resident per SM (occupancy query once per process; 3 if
+// the query fails)
+static int gram_ctas_per_sm() {
+  static std::atomic<int> cached{0};
+  int v = cached.load(std::memory_order_relaxed);
+  if (v == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gram_df, GTHREADS, 0) != cudaSuccess || b <= 0) {
+      cudaGetLastError();
+      b = 3;
+    }
+    v = b;
+    cached.store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+// Split of K = w into ks slices of kper (a multiple of GK, at least 128): the
+// run time goes as (waves of ntiles * ks CTAs over the resident slots) / ks,
+// so ks is the smallest that minimises it (a last, partly filled wave costs a
+// whole wave of CTAs that each do 1/ks of the work)
 void gram_df_split(int m, int w, int num_sms, int* ks_out, int* kper_out) {
   const int nt = (m + GT - 1) / GT;
-  const int ntiles = nt * (nt + 1) / 2;
-  int ks = std::max(1, std::min((w + 127) / 128, (2 * num_sms + ntiles - 1) / ntiles));
-  int kper = ((w + ks - 1) / ks + GK - 1) / GK * GK;
-  ks = (w + kper - 1) / kper;
-  *ks_out = ks;
+  const long long ntiles = (long long)nt * (nt + 1) / 2;
+  const long long slots = (long long)std::max(1, num_sms) * gram_ctas_per_sm();
+  const int ks_max = std::max(1, std::min(64, w / 128));
+  int best = 1;
+  double best_t = 0.0;
+  for (int ks = 1; ks <= ks_max; ++ks) {
+    const double t = (double)((ntiles * ks + slots - 1) / slots) / ks + 0.01 * ks;  // + reduction traffic
+    if (ks == 1 || t < best_t - 1e-12) {
+      best = ks;
+      best_t = t;
+    }
+  }
+  const int kper = ((w + best - 1) / best + GK - 1) / GK * GK;
+  *ks_out = (w + kper - 1) / kper;
   *kper_out = kper;
 }
 

@@ -13,9 +13,9 @@
 //   3. k_cs_scatter: the bucket lists, entry = j | sign << 31;
 //   4. k_cs_accum: one CTA per (bucket, 512-row slab) sorts its bucket's list by
 //      j, splits it into 8 contiguous ranges, and each warp streams its columns
-//      (coalesced 16-byte loads, the next column in flight while the current one
-//      is added) into double-float accumulators in registers; the 8 partial sums
-//      are combined in warp order.
+//      (coalesced 16-byte loads, a ring of the next columns in flight while the
+//      current one is added) into double-float accumulators in registers; the 8
+//      partial sums are combined in warp order.
 // A is read s times in total, by CTAs that sweep the columns in increasing j at
 // about the same pace, so the repeats mostly hit in L2.  FP32/BF16 storage sums
 // in double-float arithmetic (products formed exactly, relative error ~2^-44);
@@ -123,7 +123,7 @@ struct AccOf {  // double-float accumulators for FP32/BF16 storage, FP64 for FP6
 
 // one CTA per (bucket g, slab of 512 rows)
 template <typename TA>
-__global__ void __launch_bounds__(kAccThreads) k_cs_accum(const TA* __restrict__ A, int lda, int m, int w,
+__global__ void __launch_bounds__(kAccThreads, 2) k_cs_accum(const TA* __restrict__ A, int lda, int m, int w,
                                                           const int* __restrict__ base,
                                                           const int* __restrict__ list,
                                                           const double* __restrict__ sc64,
@@ -180,13 +180,15 @@ __global__ void __launch_bounds__(kAccThreads) k_cs_accum(const TA* __restrict__
 #pragma unroll
   for (int q = 0; q < (DF ? 1 : kEPL); ++q) acc[q] = 0.0;
 
-  // loaded elements: FP32 for FP32/BF16 storage (exact), FP64 for FP64
+  // loaded elements: FP32 for FP32/BF16 storage (exact), FP64 for FP64; a ring
+  // of D columns per lane keeps D - 1 to D column loads in flight per warp
   using LT = typename std::conditional<DF, float, double>::type;
-  LT cur[kEPL], nxt[kEPL];
-  int key_cur = 0, key_nxt = 0;
-  auto load = [&](int e, LT (&v)[kEPL], int& key) {
-    key = lst[e];
-    const long long j = key & 0x7FFFFFFF;
+  constexpr int D = DF ? 3 : 2;
+  LT buf[D][kEPL];
+  int key[D];
+  auto load = [&](int e, LT (&v)[kEPL], int& kk) {
+    kk = lst[e];
+    const long long j = kk & 0x7FFFFFFF;
     const TA* col = A + (size_t)j * lda + r0;
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
@@ -199,29 +201,33 @@ __global__ void __launch_bounds__(kAccThreads) k_cs_accum(const TA* __restrict__
       }
     }
   };
-  if (e0 < e1) load(e0, cur, key_cur);
-  for (int e = e0; e < e1; ++e) {
-    if (e + 1 < e1) load(e + 1, nxt, key_nxt);
-    const long long j = key_cur & 0x7FFFFFFF;
-    const bool neg = key_cur < 0;
-    if (DF) {
-      const float2 sc = scdf[j];
-      const float sh = neg ? -sc.x : sc.x, sl = neg ? -sc.y : sc.y;
 #pragma unroll
-      for (int q = 0; q < kEPL; ++q) df_fma((float)cur[q], sh, sl, hi[q], lo[q]);
-      // keep |lo| near ulp(hi): its own rounding then stays ~2^-48 |hi| per step
-      if (((e - e0) & 7) == 7) {
+  for (int u = 0; u < D; ++u)
+    if (e0 + u < e1) load(e0 + u, buf[u], key[u]);
+  for (int eb = e0; eb < e1; eb += D) {
 #pragma unroll
-        for (int q = 0; q < kEPL; ++q) df_renorm(hi[q], lo[q]);
+    for (int u = 0; u < D; ++u) {
+      const int e = eb + u;
+      if (e >= e1) break;
+      const long long j = key[u] & 0x7FFFFFFF;
+      const bool neg = key[u] < 0;
+      if (DF) {
+        const float2 sc = scdf[j];
+        const float sh = neg ? -sc.x : sc.x, sl = neg ? -sc.y : sc.y;
+#pragma unroll
+        for (int q = 0; q < kEPL; ++q) df_fma((float)buf[u][q], sh, sl, hi[q], lo[q]);
+        // keep |lo| near ulp(hi): its own rounding then stays ~2^-48 |hi| per step
+        if (((e - e0) & 7) == 7) {
+#pragma unroll
+          for (int q = 0; q < kEPL; ++q) df_renorm(hi[q], lo[q]);
+        }
+      } else {
+        const double sc = neg ? -sc64[j] : sc64[j];
+#pragma unroll
+        for (int q = 0; q < (DF ? 1 : kEPL); ++q) acc[q] = fma((double)buf[u][q], sc, acc[q]);
       }
-    } else {
-      const double sc = neg ? -sc64[j] : sc64[j];
-#pragma unroll
-      for (int q = 0; q < (DF ? 1 : kEPL); ++q) acc[q] = fma((double)cur[q], sc, acc[q]);
+      if (e + D < e1) load(e + D, buf[u], key[u]);
     }
-#pragma unroll
-    for (int q = 0; q < kEPL; ++q) cur[q] = nxt[q];
-    key_cur = key_nxt;
   }
 
   // ---- combine the warps' partial sums in warp order ----
