@@ -356,7 +356,10 @@ int lp_get_history(lp_handle* h, lp_iter_record* recs, int32_t max_records);
  *                the warm start's "previous" proposal, lp_set_warm_start)
  *   mu0, r0      mu and ||(r_p, r_d)|| at the solve's start point
  *   ratio_ref    the factor check's reference ratio max/min |R_ii| (0: none)
- *   seed         the sketch seed (lp_options.seed) of that solve */
+ *   seed         the sketch seed (lp_options.seed) of that solve
+ *   mu           mu of the iterate as the solve computed it (by the update's
+ *                own reduction, which may differ from x^T s / n summed afresh
+ *                in the last bit; the resumed solve takes this value) */
 typedef struct {
     int32_t k;
     int32_t mode;
@@ -366,6 +369,7 @@ typedef struct {
     double r0;
     double ratio_ref;
     uint64_t seed;
+    double mu;
 } lp_state;
 
 /* The state of the last lp_solve on `h` (whatever status >= 0 it returned):
@@ -382,8 +386,8 @@ int lp_get_state(lp_handle* h, lp_state* st, double* x, double* y, double* s, do
  * st->k from (x, y, s), counts k towards k_max, and takes mu_0, ||r^0||, the
  * factor reference and the sketch seed from the state (the handle's seed is
  * replaced by st->seed).  dy_prev is needed when st->has_dy_prev is 1.
- * LP_ERR_ARG for a null pointer, k < 0, an unknown mode, mu0 <= 0, a
- * negative or non-finite r0 or ratio_ref, or reserved != 0. */
+ * LP_ERR_ARG for a null pointer, k < 0, an unknown mode, mu0 <= 0 or
+ * mu <= 0, a negative or non-finite r0 or ratio_ref, or reserved != 0. */
 int lp_set_state(lp_handle* h, const lp_state* st, const double* x, const double* y,
                  const double* s, const double* dy_prev, int32_t io_on_device);
 

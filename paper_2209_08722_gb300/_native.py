@@ -100,7 +100,8 @@ class LpPhase1Info(ctypes.Structure):
 
 class LpState(ctypes.Structure):
     _fields_ = [("k", c_int32), ("mode", c_int32), ("has_dy_prev", c_int32), ("reserved", c_int32),
-                ("mu0", c_double), ("r0", c_double), ("ratio_ref", c_double), ("seed", c_uint64)]
+                ("mu0", c_double), ("r0", c_double), ("ratio_ref", c_double), ("seed", c_uint64),
+                ("mu", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -159,7 +159,7 @@ constexpr int kCsMaxW = 40960;  // the bucket histogram lives in shared memory
 cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
                                const double* dvec, int is_d2, uint64_t seed, long long k,
                                int retry, int s_blocks, int w, double* adw, const CsWork& ws,
-                               int num_sms, cudaStream_t st);
+                               int* err, int num_sms, cudaStream_t st);
 cudaError_t launch_v_gather(long long n, const double* x, const double* s, const double* u,
                             uint64_t seed, long long k, int retry, int s_blocks, int w, double scale,
                             double* v, int num_sms, cudaStream_t st);

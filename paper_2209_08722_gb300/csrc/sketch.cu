@@ -11,17 +11,20 @@
 //      scale d_j / sqrt(s), in FP64 and as a double-float pair;
 //   2. k_cs_scan: bucket offsets (exclusive scan);
 //   3. k_cs_scatter: the bucket lists, entry = j | sign << 31;
-//   4. k_cs_accum: one CTA per (bucket, 512-row slab) sorts its bucket's list by
-//      j, splits it into 8 contiguous ranges, and each warp streams its columns
-//      (coalesced 16-byte loads, a ring of the next columns in flight while the
-//      current one is added) into double-float accumulators in registers; the 8
-//      partial sums are combined in warp order.
-// A is read s times in total, by CTAs that sweep the columns in increasing j at
-// about the same pace, so the repeats mostly hit in L2.  FP32/BF16 storage sums
-// in double-float arithmetic (products formed exactly, relative error ~2^-44);
-// FP64 storage sums in FP64.  The summation order depends only on the hashes,
-// so the result is bitwise reproducible (for buckets of at most kSortCap
-// columns; larger buckets are summed in list order).
+//   4. k_cs_bucket: one CTA per bucket sorts its bucket's list by j in shared
+//      memory; one producer lane streams the listed columns, whole, with
+//      cp.async.bulk into a ring of shared-memory stages, and 512 consumer
+//      threads, each owning a few consecutive rows, add every staged column
+//      into double-float accumulators in registers (FP64 for FP64 storage).
+//      Columns of at most 512 or of more than 4096 rows (or more than the
+//      ring holds) take k_cs_accum: one CTA per (bucket, 512-row slab) whose
+//      8 warps load their share of the columns themselves and combine partial
+//      sums in warp order.
+// A is read s times in total (once per listed column).  FP32/BF16 storage
+// sums in double-float arithmetic (products formed exactly, relative error
+// ~2^-44); FP64 storage sums in FP64.  The summation order depends only on the
+// hashes, so the result is bitwise reproducible (for buckets of at most
+// kSortCap columns; larger buckets are summed in list order).
 #include "internal.h"
 #include "df.cuh"
 
@@ -261,6 +264,207 @@ __global__ void __launch_bounds__(kAccThreads, 2) k_cs_accum(const TA* __restric
   }
 }
 
+namespace {
+constexpr int kBkConsumers = 16;                      // consumer warps of k_cs_bucket
+constexpr int kBkThreads = (kBkConsumers + 1) * 32;   // + one producer warp
+constexpr int kBkRows = kBkConsumers * 32;            // threads that own rows
+constexpr int kBkRingBytes = 48 * 1024;               // column ring per CTA
+constexpr int kBkMaxStages = 32;
+constexpr int kBkSortCap = 4096;                      // bucket entries sorted (and scaled) in smem
+
+// RPT consecutive elements of a staged column, converted to FP32 (FP32/BF16
+// storage) or FP64
+template <typename TA, int RPT, typename LT>
+__device__ __forceinline__ void bk_load(const TA* p, LT (&v)[RPT]) {
+  if constexpr (sizeof(TA) == 2) {
+    static_assert(RPT % 2 == 0, "BF16 rows come in pairs");
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+#pragma unroll
+    for (int r = 0; r < RPT / 2; ++r) {
+      const uint32_t x = q[r];
+      v[2 * r] = (LT)__uint_as_float(x << 16);
+      v[2 * r + 1] = (LT)__uint_as_float(x & 0xFFFF0000u);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) v[r] = (LT)p[r];
+  }
+}
+}  // namespace
+
+// One CTA per bucket g, all rows: the bucket's list is sorted by column index
+// in shared memory and the signed scale of every listed column gathered next
+// to it; then one producer lane streams the listed columns (whole, lda
+// elements, contiguous in the column-major A) with cp.async.bulk into a ring
+// of shared-memory stages, and each of the 512 consumer threads adds its RPT
+// consecutive rows of every staged column, in list order, into double-float
+// accumulators in registers (FP64 for FP64 storage).  A is read once per
+// listed column, with up to `stages` columns in flight per CTA; the sum of
+// every output element runs over the bucket's columns in increasing j, so the
+// result is bitwise reproducible (buckets of at most kBkSortCap columns;
+// larger ones are summed in list order, their scales read from global
+// memory).  Waits are bounded; on a timeout the producer waits (bounded) for
+// its copies in flight and the bucket's column is written as zeros.
+template <typename TA, int RPT>
+__global__ void __launch_bounds__(kBkThreads, 2) k_cs_bucket(const TA* __restrict__ A, int lda, int m, int w,
+                                                             int stages, const int* __restrict__ base,
+                                                             const int* __restrict__ list,
+                                                             const double* __restrict__ sc64,
+                                                             const float2* __restrict__ scdf,
+                                                             double* __restrict__ adw, int* err) {
+  constexpr bool DF = sizeof(TA) != 8;
+  using LT = typename std::conditional<DF, float, double>::type;
+  extern __shared__ __align__(16) char smem[];
+  const int col_bytes = lda * (int)sizeof(TA);
+  char* ring = smem;                                                          // [stages][col_bytes]
+  int* keys = reinterpret_cast<int*>(smem + (size_t)stages * col_bytes);     // [kBkSortCap]
+  uint64_t* scs = reinterpret_cast<uint64_t*>(keys + kBkSortCap);           // [kBkSortCap] signed scales
+  uint64_t* full = scs + kBkSortCap;                                         // [stages]
+  uint64_t* empty = full + stages;                                           // [stages]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = blockIdx.x;
+  const int beg = base[g];
+  const int cnt = base[g + 1] - beg;
+
+  if (tid == 0) {
+    for (int st = 0; st < stages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kBkConsumers);
+    }
+    fence_mbar_init();
+  }
+  // ---- the bucket's list, sorted by column index (bitonic sort in smem) ----
+  const int* lst = list + beg;
+  const bool sorted = cnt <= kBkSortCap;
+  if (sorted) {
+    int p2 = 1;
+    while (p2 < cnt) p2 <<= 1;
+    for (int e = tid; e < p2; e += kBkThreads) keys[e] = e < cnt ? lst[e] : 0x7FFFFFFF;
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int e = tid; e < (p2 >> 1); e += kBkThreads) {
+          const int lo = 2 * e - (e & (stride - 1));
+          const int hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const int a = keys[lo], b = keys[hi];
+          const bool gt = (a & 0x7FFFFFFF) > (b & 0x7FFFFFFF);
+          if (gt == up) {
+            keys[lo] = b;
+            keys[hi] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    lst = keys;
+    // the signed scale of every listed column, gathered once (the loads of all
+    // entries in flight together) instead of once per column in the loop
+    for (int e = tid; e < cnt; e += kBkThreads) {
+      const int key = keys[e];
+      const long long j = key & 0x7FFFFFFF;
+      if constexpr (DF) {
+        float2 sc = scdf[j];
+        if (key < 0) sc = make_float2(-sc.x, -sc.y);
+        scs[e] = ((uint64_t)__float_as_uint(sc.y) << 32) | __float_as_uint(sc.x);
+      } else {
+        const double sc = key < 0 ? -sc64[j] : sc64[j];
+        scs[e] = (uint64_t)__double_as_longlong(sc);
+      }
+    }
+  }
+  __syncthreads();  // barriers initialised, keys sorted, scales gathered
+
+  if (warp == kBkConsumers) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int st = 0, issued = 0;
+      uint32_t parity = 1u;  // phase of empty[st] to wait for (the first pass waits for none)
+      bool aborted = false;
+      for (int e = 0; e < cnt; ++e) {
+        if (e >= stages && !mbar_wait(&empty[st], parity, err)) {
+          aborted = true;
+          break;
+        }
+        fence_proxy_async_smem();
+        const long long j = lst[e] & 0x7FFFFFFF;
+        mbar_arrive_expect_tx(&full[st], (uint32_t)col_bytes);
+        bulk_g2s(ring + (size_t)st * col_bytes, A + (size_t)j * lda, (uint32_t)col_bytes, &full[st]);
+        issued = e + 1;
+        if (++st == stages) {
+          st = 0;
+          parity ^= 1u;
+        }
+      }
+      if (aborted || *err != ERR_NONE)
+        for (int e = (issued > stages ? issued - stages : 0); e < issued; ++e)
+          mbar_wait(&full[e % stages], (uint32_t)((e / stages) & 1), err);
+    }
+    return;
+  }
+  // ---------------- consumers: rows r0 .. r0 + RPT - 1 ----------------
+  const int r0 = tid * RPT;
+  const bool rows_ok = r0 < lda;
+  float hi[RPT], lo[RPT];
+  double acc[DF ? 1 : RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) hi[r] = lo[r] = 0.0f;
+#pragma unroll
+  for (int r = 0; r < (DF ? 1 : RPT); ++r) acc[r] = 0.0;
+  bool ok = true;
+  int st = 0;
+  uint32_t parity = 0;
+  for (int e = 0; e < cnt; ++e) {
+    ok = mbar_wait(&full[st], parity, err);
+    if (!ok) break;
+    if (rows_ok) {
+      uint64_t sbits;
+      if (sorted) {
+        sbits = scs[e];
+      } else {
+        const int key = lst[e];
+        const long long j = key & 0x7FFFFFFF;
+        if constexpr (DF) {
+          float2 sc = scdf[j];
+          if (key < 0) sc = make_float2(-sc.x, -sc.y);
+          sbits = ((uint64_t)__float_as_uint(sc.y) << 32) | __float_as_uint(sc.x);
+        } else {
+          sbits = (uint64_t)__double_as_longlong(key < 0 ? -sc64[j] : sc64[j]);
+        }
+      }
+      LT v[RPT];
+      bk_load<TA, RPT, LT>(reinterpret_cast<const TA*>(ring + (size_t)st * col_bytes) + r0, v);
+      if constexpr (DF) {
+        const float sh = __uint_as_float((uint32_t)sbits), sl = __uint_as_float((uint32_t)(sbits >> 32));
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) df_fma(v[r], sh, sl, hi[r], lo[r]);
+        if ((e & 7) == 7) {
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) df_renorm(hi[r], lo[r]);
+        }
+      } else {
+        const double sc = __longlong_as_double((long long)sbits);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) acc[(DF ? 0 : r)] = fma((double)v[r], sc, acc[(DF ? 0 : r)]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if (++st == stages) {
+      st = 0;
+      parity ^= 1u;
+    }
+  }
+  if (!rows_ok) return;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int i = r0 + r;
+    if (i >= m) break;
+    double out = DF ? (double)hi[r] + (double)lo[r] : acc[DF ? 0 : r];
+    adw[(size_t)i * w + g] = ok ? out : 0.0;
+  }
+}
+
 // v_i = sqrt(x_i s_i) / sqrt(s) * sum_b sign_b(i) u[col_b(i)]   (eq. compv with u = (ADW)^+ r)
 __global__ void k_v_gather(long long n, const double* __restrict__ x, const double* __restrict__ s,
                            const double* __restrict__ u, uint64_t seed, long long k, int retry,
@@ -283,7 +487,7 @@ __global__ void k_v_gather(long long n, const double* __restrict__ x, const doub
 cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
                                const double* dvec, int is_d2, uint64_t seed, long long k,
                                int retry, int s_blocks, int w, double* adw, const CsWork& ws,
-                               int num_sms, cudaStream_t st) {
+                               int* err, int num_sms, cudaStream_t st) {
   const int wb = w / s_blocks;
   const double inv_sqrt_s = 1.0 / sqrt((double)s_blocks);
   cudaError_t e = cudaMemsetAsync(ws.count, 0, sizeof(int) * (size_t)w, st);
@@ -299,6 +503,46 @@ cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long lo
   k_cs_scan<<<1, 1024, 0, st>>>(w, ws.count, ws.base, ws.cursor);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_cs_scatter<<<grid_cols, 256, 0, st>>>(n, s_blocks, wb, seed, k, retry, ws.cursor, ws.list);
+  // the bucket kernel: whole columns through a ring of shared-memory stages
+  const int esz = dtype == 0 ? 8 : (dtype == 1 ? 4 : 2);
+  const int col_bytes = lda * esz;
+  int rpt = 1;
+  while (rpt * kBkRows < lda) rpt <<= 1;
+  if (esz == 2) rpt = std::max(rpt, 2);
+  const int stages = std::min(kBkMaxStages, kBkRingBytes / col_bytes);
+  // (columns of at most 512 rows go to the slab kernel, whose warps each take
+  // whole columns: one element per thread and column would leave the bucket
+  // kernel's consumers mostly waiting on the per-column handshake)
+  if (lda > kBkRows && rpt <= 8 && stages >= 2) {
+    const int bsmem = stages * col_bytes + kBkSortCap * (4 + 8) + 2 * stages * 8;
+    auto go = [&](auto kern, const auto* a) -> cudaError_t {
+      cudaError_t e2 = ensure_smem((const void*)kern, bsmem);
+      if (e2 != cudaSuccess) return e2;
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      kern<<<(unsigned)w, kBkThreads, bsmem, st>>>(a, lda, m, w, stages, ws.base, ws.list, ws.sc64, ws.scdf,
+                                                    adw, err);
+      return cudaGetLastError();
+    };
+    if (dtype == 0) {
+      const double* a = static_cast<const double*>(A);
+      if (rpt == 1) return go(k_cs_bucket<double, 1>, a);
+      if (rpt == 2) return go(k_cs_bucket<double, 2>, a);
+      if (rpt == 4) return go(k_cs_bucket<double, 4>, a);
+      return go(k_cs_bucket<double, 8>, a);
+    }
+    if (dtype == 1) {
+      const float* a = static_cast<const float*>(A);
+      if (rpt == 1) return go(k_cs_bucket<float, 1>, a);
+      if (rpt == 2) return go(k_cs_bucket<float, 2>, a);
+      if (rpt == 4) return go(k_cs_bucket<float, 4>, a);
+      return go(k_cs_bucket<float, 8>, a);
+    }
+    const bf16raw* a = static_cast<const bf16raw*>(A);
+    if (rpt == 2) return go(k_cs_bucket<bf16raw, 2>, a);
+    if (rpt == 4) return go(k_cs_bucket<bf16raw, 4>, a);
+    return go(k_cs_bucket<bf16raw, 8>, a);
+  }
+  // taller columns: one CTA per (bucket, 512-row slab), columns loaded by the warps
   // sorted keys + the warps' partial sums (FP64 or a double-float pair: 8 bytes)
   const int smem = kSortCap * (int)sizeof(int) + kAccWarps * kSlab * 8;
   dim3 grid((unsigned)w, (unsigned)((m + kSlab - 1) / kSlab));

@@ -568,7 +568,7 @@ cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t 
     return launch_sparse_sketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
                                 retry, h->s_blocks, h->w, h->adw, h->m, h->num_sms, h->st);
   return launch_countsketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, seed, k, retry,
-                            h->s_blocks, h->w, h->adw, h->cs, h->num_sms, h->st);
+                            h->s_blocks, h->w, h->adw, h->cs, &h->sc->err, h->num_sms, h->st);
 }
 
 // Largest jump of max/min |R_ii| (a lower bound on kappa(A D W)) over the
@@ -1901,7 +1901,8 @@ static int set_state_impl(lp_handle* h, const lp_state* st, const double* x, con
   if (!h || !st || !x || !y || !s) return LP_ERR_ARG;
   h->err.clear();
   if (st->k < 0 || (st->mode != LP_FEASIBLE && st->mode != LP_INFEASIBLE) || st->reserved != 0 ||
-      !(st->mu0 > 0) || !std::isfinite(st->mu0) || !(st->r0 >= 0) || !std::isfinite(st->r0) ||
+      !(st->mu0 > 0) || !std::isfinite(st->mu0) || !(st->mu > 0) || !std::isfinite(st->mu) ||
+      !(st->r0 >= 0) || !std::isfinite(st->r0) ||
       !(st->ratio_ref >= 0) || !std::isfinite(st->ratio_ref) || (st->has_dy_prev != 0 && st->has_dy_prev != 1) ||
       (st->has_dy_prev && !dy_prev))
     return h->fail(LP_ERR_ARG, "invalid state");
@@ -2091,6 +2092,9 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
   const double mu0 = resume ? h->resume.mu0 : mu_start;
   double r0 = resume ? h->resume.r0 : 0.0;
   const int k_start = resume ? h->resume.k : 0;
+  // a resumed solve continues with mu as the interrupted one had it (the
+  // update's reduction), not x^T s / n summed afresh
+  if (resume) CK(cudaMemcpyAsync(&h->sc->mu, &h->resume.mu, sizeof(double), cudaMemcpyHostToDevice, h->st));
   int status = LP_STATUS_MAX_ITER;
   double ms_res = 0, ms_sk = 0, ms_fac = 0, ms_in = 0, ms_cor = 0, ms_step = 0;
   auto now = [] { return std::chrono::steady_clock::now(); };
@@ -2263,6 +2267,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
   h->last_state.r0 = r0;
   h->last_state.ratio_ref = h->ratio_ref;
   h->last_state.seed = h->opt.seed;
+  h->last_state.mu = res.mu;
   h->state_valid = true;
   res.status = status;
   res.ms_total = ms_since(t_start);

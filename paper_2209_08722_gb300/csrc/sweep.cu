@@ -19,8 +19,9 @@
 //     pivots, one element per thread), one launch forms the panel
 //     U_I = A_{I,K} (-P^{-1}) of every row block once, and one launch over the
 //     upper-triangle 32 x 32 tiles writes the next iterate (each tile and its
-//     mirror: the iterate is symmetric); two buffers alternate, so no tile is
-//     read after it is overwritten.
+//     mirror: the iterate is symmetric; 128 threads per tile, a 2 x 4 block of
+//     outputs each); two buffers alternate, so no tile is read after it is
+//     overwritten.
 #include "internal.h"
 #include "df.cuh"
 
@@ -28,22 +29,25 @@ namespace lpk {
 
 namespace {
 constexpr int SB = 32;          // pivot block = tile
-constexpr int SW_THREADS = 256; // 8 x 32 threads per tile, 4 outputs each
-// Tiles per CTA of the tile kernel: two halves of 256 threads, each with its own
-// shared memory and named barrier, so the kernel occupies half as many SMs as
-// it has tiles and leaves SMs free for the pivot kernel running beside it.
-constexpr int kTilesPerCta = 2;
+constexpr int SW_THREADS = 256; // threads of the panel kernel: 4 outputs each
+// The tile kernel: ST_THREADS threads per 32 x 32 tile (2 x 4 outputs each),
+// kStepTiles tiles per CTA, each with its own shared memory and named barrier;
+// a CTA covers several tiles, so the kernel leaves SMs free for the pivot
+// kernel running beside it.
+constexpr int ST_THREADS = 128;
+constexpr int kStepTiles = 4;
 
-struct TileSmem {
-  float Ph[SB][SB + 1], Pl[SB][SB + 1];  // -P^{-1}
-  float Ch[SB][SB + 1], Cl[SB][SB + 1];  // panel rows of the other block: A_{J,K}
-  float Th[SB][SB + 1], Tl[SB][SB + 1];  // A_{X,K}, then U = A_{X,K} (-P^{-1})
+// the operands and the transposed tile of one tile of k_sweep_step, as (hi, lo) pairs
+struct StepSmem {
+  float2 P[SB][SB + 1];  // -P^{-1} or U_I
+  float2 C[SB][SB + 1];  // A_{J,K}
+  float2 T[SB][SB + 1];  // the tile, for the mirror
 };
 
-// barrier over the 256 threads of one half of the CTA (ids 1 and 2; 0 is
+// barrier over the `count` threads of one part of the CTA (ids >= 1; 0 is
 // __syncthreads')
-__device__ __forceinline__ void half_sync(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(SW_THREADS) : "memory");
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // (ah + al)(bh + bl) as a normalised pair
@@ -252,102 +256,122 @@ __device__ __forceinline__ void upper_tile(int t, int* I, int* J) {
 //   I = K:          P^{-1} A_KJ = -U_J^T
 //   otherwise:      A_IJ + U_I A_{J,K}^T
 // and each is written to (I, J) and, transposed through shared memory, to
-// (J, I); both writes are coalesced along rows.
-__global__ void __launch_bounds__(SW_THREADS* kTilesPerCta) k_sweep_step(const float* __restrict__ sh_, const float* __restrict__ sl_,
-                                                                         float* __restrict__ dh_, float* __restrict__ dl_,
-                                                                         int mp, int K, const float* __restrict__ qh,
-                                                                         const float* __restrict__ ql,
-                                                                         const float* __restrict__ uh_,
-                                                                         const float* __restrict__ ul_) {
+// (J, I); both writes are coalesced 16-byte stores along rows.  A tile takes
+// ST_THREADS threads, each forming a 2 x 4 block of outputs from operands held
+// in shared memory as (hi, lo) pairs, so one 8-byte load brings both halves
+// and every operand loaded serves four or two multiply-adds; kStepTiles tiles
+// share a CTA, each with its own named barrier.  Every output is formed by the
+// same operations in the same order as before this blocking (and as the pivot
+// kernel forms the next pivot block), so the results are unchanged.
+__global__ void __launch_bounds__(ST_THREADS* kStepTiles) k_sweep_step(const float* __restrict__ sh_, const float* __restrict__ sl_,
+                                                                       float* __restrict__ dh_, float* __restrict__ dl_,
+                                                                       int mp, int K, const float* __restrict__ qh,
+                                                                       const float* __restrict__ ql,
+                                                                       const float* __restrict__ uh_,
+                                                                       const float* __restrict__ ul_) {
   extern __shared__ __align__(16) char sw_smem[];
-  const int half = threadIdx.x / SW_THREADS;
-  TileSmem& S = reinterpret_cast<TileSmem*>(sw_smem)[half];
+  const int part = threadIdx.x / ST_THREADS;
+  StepSmem& S = reinterpret_cast<StepSmem*>(sw_smem)[part];
   const int nt = mp / SB;
-  const int tile = blockIdx.x * kTilesPerCta + half;
-  if (tile >= nt * (nt + 1) / 2) return;  // no tile for this half; the other half's barrier counts its own threads
+  const int tile = blockIdx.x * kStepTiles + part;
+  if (tile >= nt * (nt + 1) / 2) return;  // no tile for this part; the others' barriers count their own threads
   int I, J;
   upper_tile(tile, &I, &J);
   const int k0 = K * SB;
-  const int tid = threadIdx.x % SW_THREADS;
-  const int bar = 1 + half;
-  const int r = tid >> 3, c4 = (tid & 7) * 4;  // this thread's outputs: row r, columns c4..c4+3
+  const int tid = threadIdx.x % ST_THREADS;
+  const int bar = 1 + part;
+  const int r2 = (tid >> 3) * 2, c4 = (tid & 7) * 4;  // outputs: rows r2, r2 + 1; columns c4 .. c4 + 3
 
-  // ---- operands: Ph/Pl <- -P^{-1} or U_I, Th/Tl <- A_{J,K} or U_J ----
-  for (int e = tid; e < SB * SB; e += SW_THREADS) {
+  // ---- operands: P <- -P^{-1} or U_I, C <- A_{J,K} ----
+  for (int e = tid; e < SB * SB; e += ST_THREADS) {
     const int a = e / SB, b = e % SB;
     if (I == K && J == K) {
-      S.Ph[a][b] = qh[e];
-      S.Pl[a][b] = ql[e];
+      S.P[a][b] = make_float2(qh[e], ql[e]);
     } else if (J == K) {
-      S.Ph[a][b] = uh_[(size_t)I * SB * SB + e];
-      S.Pl[a][b] = ul_[(size_t)I * SB * SB + e];
+      S.P[a][b] = make_float2(uh_[(size_t)I * SB * SB + e], ul_[(size_t)I * SB * SB + e]);
     } else if (I == K) {
-      S.Ph[a][b] = uh_[(size_t)J * SB * SB + e];
-      S.Pl[a][b] = ul_[(size_t)J * SB * SB + e];
+      S.P[a][b] = make_float2(uh_[(size_t)J * SB * SB + e], ul_[(size_t)J * SB * SB + e]);
     } else {
-      S.Ph[a][b] = uh_[(size_t)I * SB * SB + e];
-      S.Pl[a][b] = ul_[(size_t)I * SB * SB + e];
+      S.P[a][b] = make_float2(uh_[(size_t)I * SB * SB + e], ul_[(size_t)I * SB * SB + e]);
       const size_t src = (size_t)(J * SB + a) * mp + k0 + b;
-      S.Ch[a][b] = sh_[src];
-      S.Cl[a][b] = sl_[src];
+      S.C[a][b] = make_float2(sh_[src], sl_[src]);
     }
   }
-  half_sync(bar);
+  named_sync(bar, ST_THREADS);
 
-  // ---- this thread's four outputs ----
-  float oh[4], ol[4];
+  // ---- this thread's 2 x 4 outputs ----
+  float oh[2][4], ol[2][4];
   if (I == K && J == K) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      oh[q] = S.Ph[r][c4 + q];
-      ol[q] = S.Pl[r][c4 + q];
-    }
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 v = S.P[r2 + a][c4 + q];
+        oh[a][q] = v.x;
+        ol[a][q] = v.y;
+      }
   } else if (J == K) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      oh[q] = -S.Ph[r][c4 + q];
-      ol[q] = -S.Pl[r][c4 + q];
-    }
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 v = S.P[r2 + a][c4 + q];
+        oh[a][q] = -v.x;
+        ol[a][q] = -v.y;
+      }
   } else if (I == K) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      oh[q] = -S.Ph[c4 + q][r];
-      ol[q] = -S.Pl[c4 + q][r];
-    }
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 v = S.P[c4 + q][r2 + a];
+        oh[a][q] = -v.x;
+        ol[a][q] = -v.y;
+      }
   } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const size_t src = (size_t)(I * SB + r) * mp + J * SB + c4 + q;
-      oh[q] = sh_[src];
-      ol[q] = sl_[src];
+    for (int a = 0; a < 2; ++a) {
+      const size_t src = (size_t)(I * SB + r2 + a) * mp + J * SB + c4;
+      const float4 h4 = *reinterpret_cast<const float4*>(sh_ + src);
+      const float4 l4 = *reinterpret_cast<const float4*>(sl_ + src);
+      oh[a][0] = h4.x; oh[a][1] = h4.y; oh[a][2] = h4.z; oh[a][3] = h4.w;
+      ol[a][0] = l4.x; ol[a][1] = l4.y; ol[a][2] = l4.z; ol[a][3] = l4.w;
     }
     for (int b = 0; b < SB; ++b) {
-      const float th = S.Ph[r][b], tl = S.Pl[r][b];
+      const float2 t0 = S.P[r2][b], t1 = S.P[r2 + 1][b];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) df_mac(th, tl, S.Ch[c4 + q][b], S.Cl[c4 + q][b], oh[q], ol[q]);
+      for (int q = 0; q < 4; ++q) {
+        const float2 cv = S.C[c4 + q][b];
+        df_mac(t0.x, t0.y, cv.x, cv.y, oh[0][q], ol[0][q]);
+        df_mac(t1.x, t1.y, cv.x, cv.y, oh[1][q], ol[1][q]);
+      }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) df_renorm(oh[q], ol[q]);
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) df_renorm(oh[a][q], ol[a][q]);
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const size_t dst = (size_t)(I * SB + r) * mp + J * SB + c4 + q;
-    dh_[dst] = oh[q];
-    dl_[dst] = ol[q];
+  for (int a = 0; a < 2; ++a) {
+    const size_t dst = (size_t)(I * SB + r2 + a) * mp + J * SB + c4;
+    *reinterpret_cast<float4*>(dh_ + dst) = make_float4(oh[a][0], oh[a][1], oh[a][2], oh[a][3]);
+    *reinterpret_cast<float4*>(dl_ + dst) = make_float4(ol[a][0], ol[a][1], ol[a][2], ol[a][3]);
   }
   if (I == J) return;
-  // the mirror (J, I) = tile^T, through shared memory (Th/Tl are free)
+  // the mirror (J, I) = tile^T, through shared memory
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    S.Th[r][c4 + q] = oh[q];
-    S.Tl[r][c4 + q] = ol[q];
-  }
-  half_sync(bar);
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const size_t dst = (size_t)(J * SB + r) * mp + I * SB + c4 + q;
-    dh_[dst] = S.Th[c4 + q][r];
-    dl_[dst] = S.Tl[c4 + q][r];
+    for (int q = 0; q < 4; ++q) S.T[r2 + a][c4 + q] = make_float2(oh[a][q], ol[a][q]);
+  named_sync(bar, ST_THREADS);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = S.T[c4 + q][r2 + a];
+    const size_t dst = (size_t)(J * SB + r2 + a) * mp + I * SB + c4;
+    *reinterpret_cast<float4*>(dh_ + dst) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+    *reinterpret_cast<float4*>(dl_ + dst) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
   }
 }
 
@@ -420,7 +444,7 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sweep_init<<<g1, 256, 0, st>>>(g, m, mp, a0h, a0l, scale_buf);
   const int nt = mp / SB;
-  const int tile_smem = (int)(sizeof(TileSmem) * kTilesPerCta);
+  const int tile_smem = (int)(sizeof(StepSmem) * kStepTiles);
   {
     const cudaError_t es = ensure_smem((const void*)k_sweep_step, tile_smem);
     if (es != cudaSuccess) return es;
@@ -449,7 +473,7 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
     g_launches.fetch_add(2, std::memory_order_relaxed);
     k_sweep_panel<<<nt, SW_THREADS, 0, st>>>(sh, sl, mp, K, qh[K & 1], ql[K & 1], uh, ul);
     const int ntiles = nt * (nt + 1) / 2;
-    k_sweep_step<<<(ntiles + kTilesPerCta - 1) / kTilesPerCta, SW_THREADS * kTilesPerCta, tile_smem, st>>>(
+    k_sweep_step<<<(ntiles + kStepTiles - 1) / kStepTiles, ST_THREADS * kStepTiles, tile_smem, st>>>(
         sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1], uh, ul);
     if (two) {
       if ((e = cudaEventRecord(ev_x, st)) != cudaSuccess) return e;

@@ -381,7 +381,8 @@ class LPSolver:
         """lp_set_state: the next solve() (with no start point) resumes from
         `state` (a dict as returned by get_state)."""
         st = nat.LpState(int(state["k"]), int(state["mode"]), int(state["has_dy_prev"]), 0,
-                         float(state["mu0"]), float(state["r0"]), float(state["ratio_ref"]), int(state["seed"]))
+                         float(state["mu0"]), float(state["r0"]), float(state["ratio_ref"]), int(state["seed"]),
+                         float(state["mu"]))
         arrs = {}
         for name, count in (("x", self.n), ("y", self.m), ("s", self.n), ("dy_prev", self.m)):
             v = np.ascontiguousarray(state[name], dtype=np.float64)

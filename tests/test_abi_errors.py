@@ -189,7 +189,7 @@ def test_null_handles_are_argument_errors(lib):
     assert lib.lp_reset_kernel_stats(None) == nat.LP_ERR_ARG
     assert lib.lp_set_warm_start(None, 0, None, None, None, 0) == nat.LP_ERR_ARG
     assert lib.lp_get_warm_start_stats(None, None, None, None) == nat.LP_ERR_ARG
-    st = nat.LpState(3, 1, 0, 0, 1.0, 1.0, 0.0, 0)
+    st = nat.LpState(3, 1, 0, 0, 1.0, 1.0, 0.0, 0, 1.0)
     assert lib.lp_get_state(None, ctypes.byref(st), p, p, p, None, 0) == nat.LP_ERR_ARG
     assert lib.lp_set_state(None, ctypes.byref(st), p, p, p, None, 0) == nat.LP_ERR_ARG
     hs = (ctypes.c_void_p * 1)(None)

@@ -115,6 +115,10 @@ DF_U = 2.0 ** -48
 @pytest.mark.parametrize("m,n,storage,s_blocks,w", [
     (64, 4099, "f64", 2, 0), (512, 20011, "f32", 4, 0), (30, 1500, "bf16", 3, 0), (8, 100, "f32", 1, 0),
     (600, 5003, "f32", 2, 0), (520, 3001, "bf16", 2, 0), (130, 2000, "f64", 2, 0),
+    # several rows per thread of the bucket kernel (4 BF16, 8 FP32, 4 FP64), and
+    # columns above its 4096 rows (the slab kernel)
+    (2048, 9001, "bf16", 4, 0), (2100, 4001, "f32", 2, 0), (1100, 3001, "f64", 2, 0),
+    (4500, 5003, "bf16", 2, 0),
     # buckets of ~10^4 columns: above the in-CTA sort capacity
     (4, 40000, "f32", 1, 4), (6, 30000, "f64", 2, 6)])
 def test_countsketch_matches_oracle(m, n, storage, s_blocks, w):

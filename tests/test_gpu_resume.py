@@ -60,7 +60,7 @@ def test_state_misuse_is_rejected():
         S.set_state(st)
         with pytest.raises(LPError):  # a resumed solve takes no start point
             S.solve(tol=1e-8, x0=st["x"], y0=st["y"], s0=st["s"])
-        for key, bad in (("k", -1), ("mu0", 0.0), ("r0", float("nan")), ("mode", 7)):
+        for key, bad in (("k", -1), ("mu0", 0.0), ("mu", -1.0), ("r0", float("nan")), ("mode", 7)):
             with pytest.raises(LPError):
                 S.set_state(dict(st, **{key: bad}))
         S.set_state(dict(st, k=3))
