@@ -160,6 +160,13 @@ cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long lo
                                const double* dvec, int is_d2, uint64_t seed, long long k,
                                int retry, int s_blocks, int w, double* adw, const CsWork& ws,
                                int* err, int num_sms, cudaStream_t st);
+// CountSketch of a CSC A summed per bucket in a fixed order (bitwise
+// reproducible); needs the CsWork lists, w <= kCsMaxW and m <= kSpMaxRows
+constexpr int kSpMaxRows = 1 << 20;
+cudaError_t launch_sparse_countsketch(int dtype, const long long* cp, const int* ri, const void* val,
+                                      long long n, const double* dvec, int is_d2, uint64_t seed, long long k,
+                                      int retry, int s_blocks, int w, double* adw, int m, const CsWork& ws,
+                                      int num_sms, cudaStream_t st);
 cudaError_t launch_v_gather(long long n, const double* x, const double* s, const double* u,
                             uint64_t seed, long long k, int retry, int s_blocks, int w, double scale,
                             double* v, int num_sms, cudaStream_t st);

@@ -411,46 +411,63 @@ __global__ void __launch_bounds__(kBkThreads, 2) k_cs_bucket(const TA* __restric
   for (int r = 0; r < RPT; ++r) hi[r] = lo[r] = 0.0f;
 #pragma unroll
   for (int r = 0; r < (DF ? 1 : RPT); ++r) acc[r] = 0.0;
+  // columns are taken in pairs (stages is even, so a pair's two stages share
+  // their phase): one wait and one release per stage as before, but half the
+  // loop overhead per column and two independent columns in flight per row
   bool ok = true;
   int st = 0;
   uint32_t parity = 0;
-  for (int e = 0; e < cnt; ++e) {
+  auto scale_of = [&](int e) -> uint64_t {
+    if (sorted) return scs[e];
+    const int key = lst[e];
+    const long long j = key & 0x7FFFFFFF;
+    if constexpr (DF) {
+      float2 sc = scdf[j];
+      if (key < 0) sc = make_float2(-sc.x, -sc.y);
+      return ((uint64_t)__float_as_uint(sc.y) << 32) | __float_as_uint(sc.x);
+    } else {
+      return (uint64_t)__double_as_longlong(key < 0 ? -sc64[j] : sc64[j]);
+    }
+  };
+  for (int e = 0; e < cnt; e += 2) {
+    const bool two = e + 1 < cnt;
     ok = mbar_wait(&full[st], parity, err);
+    if (ok && two) ok = mbar_wait(&full[st + 1], parity, err);
     if (!ok) break;
     if (rows_ok) {
-      uint64_t sbits;
-      if (sorted) {
-        sbits = scs[e];
-      } else {
-        const int key = lst[e];
-        const long long j = key & 0x7FFFFFFF;
-        if constexpr (DF) {
-          float2 sc = scdf[j];
-          if (key < 0) sc = make_float2(-sc.x, -sc.y);
-          sbits = ((uint64_t)__float_as_uint(sc.y) << 32) | __float_as_uint(sc.x);
-        } else {
-          sbits = (uint64_t)__double_as_longlong(key < 0 ? -sc64[j] : sc64[j]);
-        }
-      }
-      LT v[RPT];
-      bk_load<TA, RPT, LT>(reinterpret_cast<const TA*>(ring + (size_t)st * col_bytes) + r0, v);
+      LT v0[RPT], v1[RPT];
+      const uint64_t b0 = scale_of(e);
+      const uint64_t b1 = two ? scale_of(e + 1) : 0ull;
+      bk_load<TA, RPT, LT>(reinterpret_cast<const TA*>(ring + (size_t)st * col_bytes) + r0, v0);
+      if (two) bk_load<TA, RPT, LT>(reinterpret_cast<const TA*>(ring + (size_t)(st + 1) * col_bytes) + r0, v1);
       if constexpr (DF) {
-        const float sh = __uint_as_float((uint32_t)sbits), sl = __uint_as_float((uint32_t)(sbits >> 32));
+        const float h0 = __uint_as_float((uint32_t)b0), l0 = __uint_as_float((uint32_t)(b0 >> 32));
+        const float h1 = __uint_as_float((uint32_t)b1), l1 = __uint_as_float((uint32_t)(b1 >> 32));
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) df_fma(v[r], sh, sl, hi[r], lo[r]);
-        if ((e & 7) == 7) {
+        for (int r = 0; r < RPT; ++r) {
+          df_fma(v0[r], h0, l0, hi[r], lo[r]);
+          if (two) df_fma(v1[r], h1, l1, hi[r], lo[r]);
+        }
+        if ((e & 7) == 6) {  // after column e + 1 = 7 (mod 8)
 #pragma unroll
           for (int r = 0; r < RPT; ++r) df_renorm(hi[r], lo[r]);
         }
       } else {
-        const double sc = __longlong_as_double((long long)sbits);
+        const double c0 = __longlong_as_double((long long)b0), c1 = __longlong_as_double((long long)b1);
 #pragma unroll
-        for (int r = 0; r < RPT; ++r) acc[(DF ? 0 : r)] = fma((double)v[r], sc, acc[(DF ? 0 : r)]);
+        for (int r = 0; r < RPT; ++r) {
+          acc[(DF ? 0 : r)] = fma((double)v0[r], c0, acc[(DF ? 0 : r)]);
+          if (two) acc[(DF ? 0 : r)] = fma((double)v1[r], c1, acc[(DF ? 0 : r)]);
+        }
       }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
-    if (++st == stages) {
+    if (lane == 0) {
+      mbar_arrive(&empty[st]);
+      if (two) mbar_arrive(&empty[st + 1]);
+    }
+    st += 2;
+    if (st == stages) {
       st = 0;
       parity ^= 1u;
     }
@@ -484,10 +501,9 @@ __global__ void k_v_gather(long long n, const double* __restrict__ x, const doub
   }
 }
 
-cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
-                               const double* dvec, int is_d2, uint64_t seed, long long k,
-                               int retry, int s_blocks, int w, double* adw, const CsWork& ws,
-                               int* err, int num_sms, cudaStream_t st) {
+// the bucket sizes, offsets and lists and the per-column scales (passes 1-3)
+static cudaError_t cs_lists(long long n, const double* dvec, int is_d2, uint64_t seed, long long k, int retry,
+                            int s_blocks, int w, const CsWork& ws, int num_sms, cudaStream_t st) {
   const int wb = w / s_blocks;
   const double inv_sqrt_s = 1.0 / sqrt((double)s_blocks);
   cudaError_t e = cudaMemsetAsync(ws.count, 0, sizeof(int) * (size_t)w, st);
@@ -503,13 +519,196 @@ cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long lo
   k_cs_scan<<<1, 1024, 0, st>>>(w, ws.count, ws.base, ws.cursor);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_cs_scatter<<<grid_cols, 256, 0, st>>>(n, s_blocks, wb, seed, k, retry, ws.cursor, ws.list);
+  return cudaGetLastError();
+}
+
+// One CTA per bucket g of the sketch of a CSC A: the bucket's column list is
+// sorted by j; the entries of the listed columns are gathered into shared
+// memory in that order (value times the column's signed scale, in FP64) and
+// sorted by (row, gather position); each row's run is then summed in that
+// order by one thread and written to ADW (every row of the bucket's column
+// that no entry reaches keeps the zero the caller wrote).  So the sum of every
+// element runs over its terms in increasing j, whatever the scheduling: the
+// result is bitwise reproducible.  A bucket with more than kSpCap entries (or
+// a longer list than kBkSortCap) is summed with FP64 atomics instead.
+namespace {
+constexpr int kSpThreads = 256;
+constexpr int kSpCap = 4096;       // gathered entries per bucket
+constexpr int kSpPosBits = 12;     // gather position bits of a sort key (kSpCap = 2^12)
+}  // namespace
+
+template <typename TV>
+__global__ void __launch_bounds__(kSpThreads) k_sp_bucket(const long long* __restrict__ cp, const int* __restrict__ ri,
+                                                          const TV* __restrict__ val, int w,
+                                                          const int* __restrict__ base, const int* __restrict__ list,
+                                                          const double* __restrict__ sc64, double* __restrict__ adw) {
+  extern __shared__ __align__(16) char smem[];
+  int* keys = reinterpret_cast<int*>(smem);                         // [kBkSortCap] the sorted list
+  int* offs = keys + kBkSortCap;                                     // [kBkSortCap + 1] gather offsets
+  uint32_t* ek = reinterpret_cast<uint32_t*>(offs + kBkSortCap + 1); // [kSpCap] (row, position) keys
+  double* ev = reinterpret_cast<double*>(smem + (size_t)(2 * kBkSortCap + 1 + kSpCap) * 4 + 4);  // [kSpCap]
+  __shared__ int s_total;
+  const int tid = threadIdx.x;
+  const int g = blockIdx.x;
+  const int beg = base[g];
+  const int cnt = base[g + 1] - beg;
+  const int* lst = list + beg;
+  if (cnt > kBkSortCap) {  // (very large buckets) FP64 atomics
+    for (int e = tid; e < cnt; e += kSpThreads) {
+      const int key = lst[e];
+      const long long j = key & 0x7FFFFFFF;
+      const double sc = key < 0 ? -sc64[j] : sc64[j];
+      for (long long q = cp[j]; q < cp[j + 1]; ++q) atomicAdd(&adw[(size_t)ri[q] * w + g], (double)val[q] * sc);
+    }
+    return;
+  }
+  // ---- the list, sorted by j ----
+  int p2 = 1;
+  while (p2 < cnt) p2 <<= 1;
+  for (int e = tid; e < p2; e += kSpThreads) keys[e] = e < cnt ? lst[e] : 0x7FFFFFFF;
+  __syncthreads();
+  for (int size = 2; size <= p2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int e = tid; e < (p2 >> 1); e += kSpThreads) {
+        const int lo = 2 * e - (e & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const int a = keys[lo], b = keys[hi];
+        const bool gt = (a & 0x7FFFFFFF) > (b & 0x7FFFFFFF);
+        if (gt == up) {
+          keys[lo] = b;
+          keys[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- gather offsets: exclusive scan of the listed columns' entry counts
+  // (loaded in parallel; each thread scans a contiguous chunk, one thread the
+  // chunk totals) ----
+  __shared__ int chunk[kSpThreads];
+  for (int e = tid; e < cnt; e += kSpThreads) {
+    const long long j = keys[e] & 0x7FFFFFFF;
+    const long long len = cp[j + 1] - cp[j];
+    offs[e] = (int)std::min<long long>(len, kSpCap + 1);  // larger counts only need to exceed the cap
+  }
+  __syncthreads();
+  const int per = (cnt + kSpThreads - 1) / kSpThreads;
+  const int c0 = tid * per, c1 = std::min(cnt, c0 + per);
+  int run = 0;
+  for (int e = c0; e < c1; ++e) run += offs[e];
+  chunk[tid] = run;
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int t = 0; t < kSpThreads; ++t) {
+      const int v = chunk[t];
+      chunk[t] = acc;
+      acc = std::min(acc + v, kSpCap + 1);
+    }
+    s_total = acc;
+  }
+  __syncthreads();
+  run = chunk[tid];
+  for (int e = c0; e < c1; ++e) {
+    const int v = offs[e];
+    offs[e] = run;
+    run += v;
+  }
+  if (tid == 0) offs[cnt] = s_total;
+  __syncthreads();
+  const int total = s_total;
+  if (total > kSpCap) {  // too many entries to sort here: FP64 atomics
+    for (int e = tid; e < cnt; e += kSpThreads) {
+      const int key = keys[e];
+      const long long j = key & 0x7FFFFFFF;
+      const double sc = key < 0 ? -sc64[j] : sc64[j];
+      for (long long q = cp[j]; q < cp[j + 1]; ++q) atomicAdd(&adw[(size_t)ri[q] * w + g], (double)val[q] * sc);
+    }
+    return;
+  }
+  // ---- gather: entry q of listed column e at position offs[e] + (q - cp[j]) ----
+  for (int e = tid; e < cnt; e += kSpThreads) {
+    const int key = keys[e];
+    const long long j = key & 0x7FFFFFFF;
+    const double sc = key < 0 ? -sc64[j] : sc64[j];
+    const long long q0 = cp[j];
+    const int o = offs[e], len = offs[e + 1] - o;
+#pragma unroll 4
+    for (int t = 0; t < len; ++t) {
+      ek[o + t] = ((uint32_t)ri[q0 + t] << kSpPosBits) | (uint32_t)(o + t);
+      ev[o + t] = (double)val[q0 + t] * sc;
+    }
+  }
+  int t2 = 1;
+  while (t2 < total) t2 <<= 1;
+  for (int e = total + tid; e < t2; e += kSpThreads) ek[e] = 0xFFFFFFFFu;
+  __syncthreads();
+  // ---- sort by (row, gather position) ----
+  for (int size = 2; size <= t2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int e = tid; e < (t2 >> 1); e += kSpThreads) {
+        const int lo = 2 * e - (e & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint32_t a = ek[lo], b = ek[hi];
+        if ((a > b) == up) {
+          ek[lo] = b;
+          ek[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- each row's run summed in gather order by the thread at its start ----
+  for (int i = tid; i < total; i += kSpThreads) {
+    const uint32_t row = ek[i] >> kSpPosBits;
+    if (i > 0 && (ek[i - 1] >> kSpPosBits) == row) continue;
+    double sum = 0.0;
+    for (int q = i; q < total && (ek[q] >> kSpPosBits) == row; ++q) sum += ev[ek[q] & ((1u << kSpPosBits) - 1)];
+    adw[(size_t)row * w + g] = sum;
+  }
+}
+
+int sparse_cs_smem() { return (2 * kBkSortCap + 1 + kSpCap) * 4 + 4 + kSpCap * 8; }
+
+cudaError_t launch_sparse_countsketch(int dtype, const long long* cp, const int* ri, const void* val,
+                                      long long n, const double* dvec, int is_d2, uint64_t seed, long long k,
+                                      int retry, int s_blocks, int w, double* adw, int m, const CsWork& ws,
+                                      int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(adw, 0, sizeof(double) * (size_t)m * w, st);
+  if (e != cudaSuccess) return e;
+  e = cs_lists(n, dvec, is_d2, seed, k, retry, s_blocks, w, ws, num_sms, st);
+  if (e != cudaSuccess) return e;
+  const int smem = sparse_cs_smem();
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (dtype == 0) {
+    e = ensure_smem((const void*)k_sp_bucket<double>, smem);
+    if (e != cudaSuccess) return e;
+    k_sp_bucket<double><<<(unsigned)w, kSpThreads, smem, st>>>(cp, ri, static_cast<const double*>(val), w, ws.base,
+                                                               ws.list, ws.sc64, adw);
+  } else {
+    e = ensure_smem((const void*)k_sp_bucket<float>, smem);
+    if (e != cudaSuccess) return e;
+    k_sp_bucket<float><<<(unsigned)w, kSpThreads, smem, st>>>(cp, ri, static_cast<const float*>(val), w, ws.base,
+                                                              ws.list, ws.sc64, adw);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_countsketch(int dtype, const void* A, int lda, int m, long long n,
+                               const double* dvec, int is_d2, uint64_t seed, long long k,
+                               int retry, int s_blocks, int w, double* adw, const CsWork& ws,
+                               int* err, int num_sms, cudaStream_t st) {
+  cudaError_t e = cs_lists(n, dvec, is_d2, seed, k, retry, s_blocks, w, ws, num_sms, st);
+  if (e != cudaSuccess) return e;
   // the bucket kernel: whole columns through a ring of shared-memory stages
   const int esz = dtype == 0 ? 8 : (dtype == 1 ? 4 : 2);
   const int col_bytes = lda * esz;
   int rpt = 1;
   while (rpt * kBkRows < lda) rpt <<= 1;
   if (esz == 2) rpt = std::max(rpt, 2);
-  const int stages = std::min(kBkMaxStages, kBkRingBytes / col_bytes);
+  const int stages = std::min(kBkMaxStages, kBkRingBytes / col_bytes) / 2 * 2;  // even: columns go in pairs
   // (columns of at most 512 rows go to the slab kernel, whose warps each take
   // whole columns: one element per thread and column would leave the bucket
   // kernel's consumers mostly waiting on the per-column handshake)

@@ -136,7 +136,7 @@ struct lp_handle {
   double* qinv = nullptr;
   bool qinv_df_ok = false;  // ... and as FP32 pairs (the sweep's output), for the double-float GEMV
   float2* qinv_df = nullptr;
-  CsWork cs;             // dense CountSketch scratch
+  CsWork cs;             // CountSketch bucket lists and scales (dense, and sparse where they fit)
   float* gram_scratch = nullptr;  // double-float Gram: split ADW + split-K partials
   float* sweep_scratch = nullptr; // double-float sweep: two m x m iterates + pivots
   long long sweep_fallbacks = 0;
@@ -564,6 +564,9 @@ cudaError_t launch_sketch(lp_handle* h, const double* dvec, int is_d2, uint64_t 
   if (h->opt.sketch == LP_SKETCH_GAUSS)
     return launch_gauss_sketch(h->dtype, h->A, h->lda, h->m, h->n, dvec, is_d2, seed, k, retry, h->w,
                                h->adw, h->opt.tensor_sketch, &h->sc->err, h->num_sms, h->st);
+  if (h->sparse && h->cs.list)
+    return launch_sparse_countsketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
+                                     retry, h->s_blocks, h->w, h->adw, h->m, h->cs, h->num_sms, h->st);
   if (h->sparse)
     return launch_sparse_sketch(h->dtype, h->colptr, h->rowidx, h->spval, h->n, dvec, is_d2, seed, k,
                                 retry, h->s_blocks, h->w, h->adw, h->m, h->num_sms, h->st);
@@ -1608,6 +1611,16 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
       CK(cudaMemcpyAsync(h->spval, A->val, (size_t)h->esz * h->nnz, kind, h->st));
     }
     RET(build_rows(h, A));
+    // the bucket lists of the reproducible sparse CountSketch (else FP64 atomics)
+    if (h->opt.sketch == LP_SKETCH_COUNT && h->w <= kCsMaxW && (long long)h->n * h->s_blocks < (1LL << 31) &&
+        h->m <= kSpMaxRows) {
+      RET(h->alloc(&h->cs.count, (size_t)h->w + 1));
+      RET(h->alloc(&h->cs.base, (size_t)h->w + 1));
+      RET(h->alloc(&h->cs.cursor, (size_t)h->w + 1));
+      RET(h->alloc(&h->cs.list, (size_t)h->n * h->s_blocks));
+      RET(h->alloc(&h->cs.sc64, (size_t)h->n));
+      RET(h->alloc(&h->cs.scdf, (size_t)h->n));
+    }
   } else {
     if (h->opt.sketch == LP_SKETCH_COUNT) {
       if (h->w > kCsMaxW)

@@ -168,9 +168,8 @@ def test_c3_full_size_solve_from_csr_reaches_the_planted_objective():
     # lp_create sorts it into exactly the CSC the generator built (checked on
     # the host with the same sort), and the solve reaches the planted
     # objective; A_B may be singular (empty rows), so only the objective and
-    # the residuals are compared (several optimal x may exist).  The sparse
-    # kernels scatter with shared-memory atomics, so the CSR and CSC solves
-    # agree to rounding, not bitwise.
+    # the residuals are compared (several optimal x may exist).  Every sparse
+    # kernel sums in a fixed order, so the CSR and CSC solves agree bit for bit.
     torch_cuda()
     import scipy.sparse as sp
     from paper_2209_08722_gb300 import LPSolver, csr_to_csc
@@ -189,6 +188,6 @@ def test_c3_full_size_solve_from_csr_reaches_the_planted_objective():
     assert abs(float(lp.b @ y) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
     assert np.all(x > 0) and np.all(s > 0)
     with solver_for(lp, **opts) as S:
-        x2, _, _, info2 = S.solve(tol=1e-8)
+        x2, y2, _, info2 = S.solve(tol=1e-8)
     assert info2["status"] == 0
-    assert abs(float(lp.c @ x2) - float(lp.c @ x)) <= 1e-8 * (1 + abs(lp.objective))
+    assert np.array_equal(x2, x) and np.array_equal(y2, y)

@@ -1,8 +1,7 @@
 """Guard regions around every device buffer of a handle (lp_options.guard):
 the stand-in for a device memory checker.  Solves over the storage formats,
 sketches and inner solvers leave every guard intact, and the guarded handle's
-results equal the unguarded one's (bit for bit for dense A; to rounding for
-CSC, whose sketch sums with FP64 atomics)."""
+results equal the unguarded one's bit for bit."""
 
 import numpy as np
 import pytest
@@ -36,12 +35,8 @@ def test_guards_stay_intact_and_results_are_unchanged(name, make, opts):
         assert checked >= 40 and checked % 2 == 0
         assert damaged == 0, msg
     assert info["status"] == i0["status"] == 0
-    if lp.sparse:
-        # the sparse sketch sums with FP64 atomics: equal to rounding, not bitwise
-        assert abs(float(lp.c @ x) - float(lp.c @ x0)) <= 1e-9 * (1 + abs(float(lp.c @ x0)))
-    else:
-        assert info["inner_total"] == i0["inner_total"]
-        assert np.array_equal(x, x0) and np.array_equal(y, y0)
+    assert info["inner_total"] == i0["inner_total"]
+    assert np.array_equal(x, x0) and np.array_equal(y, y0)
 
 
 def test_unguarded_handle_checks_nothing():

@@ -2,8 +2,9 @@
 
 Same rows as tests/test_gpu_kernels.py for a CSC A with a fixed number of
 nonzeros per column and heavy-tailed row counts (20% Zipf(1.2) rows).  The
-per-CTA sums of the sparse kernels are accumulated with shared-memory atomics,
-so tolerances are the forward-error bounds of the same sums in any order.
+tolerances are the forward-error bounds of the sums in any order; the sums
+themselves run in a fixed order (two-pass product, sketch summed per bucket),
+so repeated calls and CSR/CSC input agree bit for bit.
 """
 
 import numpy as np
@@ -76,20 +77,46 @@ def test_sparse_residual_rhs_and_directions(mode):
     assert np.all(np.abs(dx - dx_ref) <= 32 * k * EPS64 * (x + 0.5 * mu / s + (x / s) * ds_bound + np.abs(v) / s))
 
 
-def test_sparse_countsketch():
+@pytest.mark.parametrize("m,n,k,s_blocks,w_factor", [
+    (64, 5000, 8, 2, 4.0), (300, 20011, 8, 3, 4.0),
+    # buckets of ~10^4 entries: above the per-bucket sort capacity (FP64 atomics)
+    (16, 20000, 8, 1, 1.0)])
+def test_sparse_countsketch(m, n, k, s_blocks, w_factor):
     torch = torch_cuda()
-    m, n, k = 64, 5000, 8
     lp = _lp(m, n, k, seed=4)
     rng = np.random.default_rng(5)
     D = np.exp(rng.uniform(-3, 3, n))
-    with solver_for(lp, s=2) as S:
+    with solver_for(lp, s=s_blocks, w_factor=w_factor) as S:
         w = S.sketch_width
         adw = host(S.sketch(dev(torch, D), 99, 3, 0))
-    W = sketch.countsketch_matrix(99, 3, 0, n, w, 2)
+        again = host(S.sketch(dev(torch, D), 99, 3, 0))
+    W = sketch.countsketch_matrix(99, 3, 0, n, w, s_blocks)
     AD = lp.scipy_csc().multiply(D[None, :]).tocsc()
     ref = (AD @ W).toarray()
     bound = (abs(AD) @ abs(W)).toarray()
     assert np.all(np.abs(adw - ref) <= 16 * n * EPS64 * bound + 1e-300)
+    if w_factor > 1.0:
+        # buckets within the sort capacity are summed in a fixed order
+        assert np.array_equal(adw.view(np.uint64), again.view(np.uint64))
+
+
+def test_sparse_solve_from_csr_equals_csc_bit_for_bit():
+    # the CSR input is sorted into the CSC the generator built, and every
+    # sparse kernel (products, passes, sketch) sums in a fixed order
+    torch_cuda()
+    import scipy.sparse as sp
+    from paper_2209_08722_gb300 import LPSolver
+    lp = _lp(128, 30011, 8, seed=9)
+    vals = lp.val.astype(np.float32)
+    csr = sp.csc_matrix((vals, lp.row_idx, lp.col_ptr), shape=(lp.m, lp.n)).tocsr()
+    rp, ci = csr.indptr.astype(np.int64), csr.indices.astype(np.int32)
+    with LPSolver(None, lp.b, lp.c, lp.m, lp.n, dtype="f32", csr=(rp, ci, csr.data), s=2) as S:
+        x1, y1, _, i1 = S.solve(tol=1e-8)
+    with solver_for(lp, s=2) as S:
+        x2, y2, _, i2 = S.solve(tol=1e-8)
+    assert i1["status"] == i2["status"] == 0
+    assert i1["inner_total"] == i2["inner_total"]
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
 
 
 def test_sparse_normal_solve_matches_cholesky():
