@@ -101,30 +101,59 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
       }
     }
     __syncthreads();
+    // (qh + ql)(vh + vl) into (sh, sl): exact product of the high parts plus
+    // the cross terms
+    auto mac = [](float2 q, float2 v, float& sh, float& sl) {
+      const float pr = __fmul_rn(q.x, v.x);
+      float e = fmaf(q.x, v.x, -pr);
+      e = fmaf(q.x, v.y, e);
+      e = fmaf(q.y, v.x, e);
+      float t, c;
+      two_sum(sh, pr, t, c);
+      sh = t;
+      sl = __fadd_rn(sl, __fadd_rn(c, e));
+    };
+    const bool even = (a.m & 1) == 0;  // rows of pairs start 16-byte aligned
     for (int i = gw; i < a.m; i += nw) {
       const float2* row = a.Mdf + (size_t)i * a.m;
       float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
-      // 8 row entries per lane in flight at once: the row loads are the latency
-      for (int j0 = 0; j0 < a.m; j0 += 8 * 32) {
-        float2 q[8];
+      if (even) {
+        // 16-byte loads of two adjacent entries, 8 per lane in flight at once
+        // (the row loads are the latency)
+        const float4* row4 = reinterpret_cast<const float4*>(row);
+        const int m2 = a.m >> 1;
+        const float4* xs4 = reinterpret_cast<const float4*>(xs);
+        int j0 = 0;
+        for (; j0 + 8 * 32 <= m2; j0 += 8 * 32) {  // whole chunks: no bounds checks
+          float4 q[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int j = j0 + k * 32 + lane;
-          q[k] = j < a.m ? __ldg(row + j) : make_float2(0.0f, 0.0f);
+          for (int k = 0; k < 8; ++k) q[k] = __ldg(row4 + j0 + k * 32 + lane);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float4 v = xs4[j0 + k * 32 + lane];
+            mac(make_float2(q[k].x, q[k].y), make_float2(v.x, v.y), sh[0], sl[0]);
+            mac(make_float2(q[k].z, q[k].w), make_float2(v.z, v.w), sh[1], sl[1]);
+          }
         }
+        for (int j = j0 + lane; j < m2; j += 32) {  // the ragged end
+          const float4 q = __ldg(row4 + j), v = xs4[j];
+          mac(make_float2(q.x, q.y), make_float2(v.x, v.y), sh[0], sl[0]);
+          mac(make_float2(q.z, q.w), make_float2(v.z, v.w), sh[1], sl[1]);
+        }
+      } else {
+        for (int j0 = 0; j0 < a.m; j0 += 8 * 32) {
+          float2 q[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int j = j0 + k * 32 + lane;
-          const float2 v = j < a.m ? xs[j] : make_float2(0.0f, 0.0f);
-          // (qh + ql)(vh + vl): exact product of the high parts plus the cross terms
-          const float pr = __fmul_rn(q[k].x, v.x);
-          float e = fmaf(q[k].x, v.x, -pr);
-          e = fmaf(q[k].x, v.y, e);
-          e = fmaf(q[k].y, v.x, e);
-          float t, c;
-          two_sum(sh[k & 1], pr, t, c);
-          sh[k & 1] = t;
-          sl[k & 1] = __fadd_rn(sl[k & 1], __fadd_rn(c, e));
+          for (int k = 0; k < 8; ++k) {
+            const int j = j0 + k * 32 + lane;
+            q[k] = j < a.m ? __ldg(row + j) : make_float2(0.0f, 0.0f);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int j = j0 + k * 32 + lane;
+            const float2 v = j < a.m ? xs[j] : make_float2(0.0f, 0.0f);
+            mac(q[k], v, sh[k & 1], sl[k & 1]);
+          }
         }
       }
       df_add(sh[0], sl[0], sh[1], sl[1]);
