@@ -57,18 +57,18 @@ ORACLE_RECORDS = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
 # the workloads the bench times; sizes and solver options as in lpgen.CONFIGS
 BENCH = {
     "c4": dict(
-        m=2048, n=524288, dtype="bf16", s=4, w_factor=4.0, whole_oracle=False,
+        m=2048, n=524288, dtype="bf16", s=4, w_factor=4.0, refine_every=12, whole_oracle=False,
         workload=("planted dense LP m=2048 n=524288 BF16 storage, N(0,1) entries, "
                   "infeasible start x0=s0=1 y0=0, CountSketch w=8192 s=4"),
         l2="inputs larger than L2 (A = 2.15 GB BF16)",
         dtype_detail=("A stored BF16; inner-loop products in FP32 with FP32 accumulation; residual "
-                      "refresh, residuals, directions, sketch sums and factor in double-float "
-                      "(FP64-class); FP64 vectors, dots and step lengths"),
+                      "refresh (every 12 CG steps), residuals, directions, sketch sums and factor in "
+                      "double-float (FP64-class); FP64 vectors, dots and step lengths"),
         kernel="k_rows (A diag(d2) A^T v, BF16 storage, FP32 arithmetic, row-split)",
         sources=("stream_rows.cu", "stream_dev.cuh", "stream.cuh", "common.cuh", "df.cuh"),
         traffic="traffic_k_rows_m2048_n524288_bf16.json"),
     "c2": dict(
-        m=512, n=131072, dtype="f32", s=4, w_factor=4.0, whole_oracle=True,
+        m=512, n=131072, dtype="f32", s=4, w_factor=4.0, refine_every=8, whole_oracle=True,
         workload=("planted dense LP m=512 n=131072 FP32 storage, columns scaled 10^U(-2,2), "
                   "infeasible start x0=s0=1 y0=0, CountSketch w=2048 s=4"),
         l2="inputs larger than L2 (A = 268 MB FP32)",
@@ -660,7 +660,7 @@ def main():
         torch.cuda.synchronize()
 
     lp = make_lp(args.config, replica_seed(rank))
-    opts = dict(dtype=cfg["dtype"], s=cfg["s"], w_factor=cfg["w_factor"])
+    opts = dict(dtype=cfg["dtype"], s=cfg["s"], w_factor=cfg["w_factor"], refine_every=cfg["refine_every"])
     stream = torch.cuda.current_stream()
     solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, profile=1, stream=stream.cuda_stream,
                       **opts)
