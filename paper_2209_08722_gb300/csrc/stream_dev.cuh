@@ -27,8 +27,7 @@ __device__ __forceinline__ void issue_tile(const StreamArgs& a, const SmemLayout
     total += cvb[q];
   }
   mbar_arrive_expect_tx(&bars[stage], total);
-  bulk_g2s(st, static_cast<const char*>(a.A) + (size_t)j0 * a.lda * sizeof(TA), abytes,
-           &bars[stage]);
+  bulk_g2s_stream(st, static_cast<const char*>(a.A) + (size_t)j0 * a.lda * sizeof(TA), abytes, &bars[stage]);
 #pragma unroll
   for (int q = 0; q < kMaxColVecs; ++q)
     if (q < a.ncv)
