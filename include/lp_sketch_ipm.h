@@ -147,6 +147,11 @@ typedef struct {
     double rd_rel;              /* ||A^T y + s - c|| / (1 + ||c||) */
     double mu;                  /* final x^T s / n */
     double ms_total;            /* wall time of the call */
+    /* time per phase, summed over the outer iterations: residual, correction
+     * (with the directions) and step are the device time between stream
+     * events around their kernels; sketch + factor and the inner solve are
+     * host wall time (they end with host decisions); ms_sketch is 0 (the
+     * sketch is inside ms_factor) */
     double ms_residual, ms_sketch, ms_factor, ms_inner, ms_correction, ms_step;
 } lp_result;
 

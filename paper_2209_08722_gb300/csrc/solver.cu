@@ -102,6 +102,10 @@ struct lp_handle {
   // second stream and events for the factor's overlapped pivot kernels (sweep.cu)
   cudaStream_t st_aux = nullptr;
   cudaEvent_t ev_x = nullptr, ev_p = nullptr;
+  // phase timing without host synchronisation: the correction and step phases
+  // of an outer iteration are bracketed by these, read after the next
+  // synchronisation
+  cudaEvent_t ev_cor = nullptr, ev_step = nullptr, ev_end = nullptr, ev_res = nullptr, ev_res_end = nullptr;
   cusolverDnHandle_t sol = nullptr;
   cublasHandle_t blas = nullptr;
   int lwork_potrf = 0;
@@ -1301,6 +1305,11 @@ int lp_destroy(lp_handle* h) {
   }
   if (h->ev_x) cudaEventDestroy(h->ev_x);
   if (h->ev_p) cudaEventDestroy(h->ev_p);
+  if (h->ev_cor) cudaEventDestroy(h->ev_cor);
+  if (h->ev_step) cudaEventDestroy(h->ev_step);
+  if (h->ev_end) cudaEventDestroy(h->ev_end);
+  if (h->ev_res) cudaEventDestroy(h->ev_res);
+  if (h->ev_res_end) cudaEventDestroy(h->ev_res_end);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
   return LP_OK;
@@ -1558,6 +1567,11 @@ static int create_impl(lp_handle* h, const lp_matrix* A, const double* b, const 
   CK(cudaStreamCreateWithFlags(&h->st_aux, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev_x, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_p, cudaEventDisableTiming));
+  CK(cudaEventCreate(&h->ev_cor));
+  CK(cudaEventCreate(&h->ev_step));
+  CK(cudaEventCreate(&h->ev_end));
+  CK(cudaEventCreate(&h->ev_res));
+  CK(cudaEventCreate(&h->ev_res_end));
   h->m = A->m;
   h->n = A->n;
   h->dtype = A->dtype;
@@ -2120,13 +2134,31 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
   auto ms_since = [](std::chrono::steady_clock::time_point t) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
   };
+  bool pending = false;  // the last iteration's correction and step events are still to be read
+  auto read_pending = [&]() -> int {
+    if (!pending) return LP_OK;
+    float a = 0.0f, b = 0.0f;
+    CK(cudaEventElapsedTime(&a, h->ev_cor, h->ev_step));
+    CK(cudaEventElapsedTime(&b, h->ev_step, h->ev_end));
+    ms_cor += a;
+    ms_step += b;
+    pending = false;
+    return LP_OK;
+  };
   for (int k = k_start; k <= h->opt.k_max; ++k) {
-    auto t0 = now();
     phase.next("residuals");
     // ---- step 3: residuals, mu, right-hand side, d^2 ----
+    CK(cudaEventRecord(h->ev_res, h->st));  // after the previous step's kernels in stream order
     RET(residual_pass(h, feasible, h->opt.sigma_rule == 1 ? 0.0 : -1.0));
+    CK(cudaEventRecord(h->ev_res_end, h->st));
     RET(sync_read(h));
-    ms_res += ms_since(t0);
+    RET(read_pending());
+    {
+      float r = 0.0f;
+      CK(cudaEventElapsedTime(&r, h->ev_res, h->ev_res_end));
+      ms_res += r;
+    }
+    auto t0 = now();
     const DevScalars& S = *h->hsc;
     const double rp = sqrt(S.rp2), rd = sqrt(S.rd2);
     const StopMeasures sm = stop_measures(S.cx, S.by, S.rp2, S.rd2, h->bnorm, h->cnorm);
@@ -2205,7 +2237,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
       RET(warm_start_finish(h));
       ms_in += ms_since(t0);
       // ---- step 5: correction v, directions ----
-      t0 = now();
+      CK(cudaEventRecord(h->ev_cor, h->st));
       phase.next("correction");
       RET(correction(h, h->x, h->s, k, retry));
       RET(direction_pass(h, feasible));
@@ -2230,7 +2262,7 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
       iters += it2;
       ist = std::max(ist, ist2);
       ms_in += ms_since(t0);
-      t0 = now();
+      CK(cudaEventRecord(h->ev_cor, h->st));
       phase.next("directions");
       // affine direction (sigma = 0) and its largest positivity-keeping step
       CK(cudaMemcpyAsync(h->dy, h->dy_aff, mb, cudaMemcpyDeviceToDevice, h->st));
@@ -2261,19 +2293,19 @@ static int solve_impl(lp_handle* h, double tol, int32_t mode, const double* x0, 
     }
     res.inner_total += iters;
     res.inner_max = std::max(res.inner_max, iters);
-    CK(cudaStreamSynchronize(h->st));
-    ms_cor += ms_since(t0);
     // ---- steps 6-8: step lengths and update ----
     phase.next("step");
-    t0 = now();
+    CK(cudaEventRecord(h->ev_step, h->st));
     CK(launch_step(n, h->x, h->s, h->dx, h->ds, h->opt.gamma, feasible ? 1 : 0, res_ratio, mu0,
                    h->vpart, h->tickets + 4, h->sc, h->num_sms, h->st));
     CK(launch_update(n, m, h->x, h->s, h->y, h->dx, h->ds, h->dy, h->sc, h->vpart, h->tickets + 6,
                      h->num_sms, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    ms_step += ms_since(t0);
+    CK(cudaEventRecord(h->ev_end, h->st));
+    pending = true;
   }
   phase.end();
+  CK(cudaStreamSynchronize(h->st));
+  RET(read_pending());
   if (x) RET(copy_out(h, x, h->x, n, io_on_device));
   if (y) RET(copy_out(h, y, h->y, m, io_on_device));
   if (s) RET(copy_out(h, s, h->s, n, io_on_device));

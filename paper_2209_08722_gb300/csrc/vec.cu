@@ -86,15 +86,16 @@ __global__ void __launch_bounds__(256) k_gemv_tri(const GemvArgs a) {
     // full rows in double-float on the FP32 pipe: x split into pairs in shared
     // memory once per CTA, each warp one row, FP64 only for the row result
     extern __shared__ float2 xs[];
-    for (int j0 = 0; j0 < a.m; j0 += 4 * (int)blockDim.x) {
-      double v[4];
+    // 16 loads per thread in flight at once (m <= 2048 in one round at 128 threads)
+    for (int j0 = 0; j0 < a.m; j0 += 16 * (int)blockDim.x) {
+      double v[16];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 16; ++k) {
         const int j = j0 + k * (int)blockDim.x + (int)threadIdx.x;
         v[k] = j < a.m ? a.x[j] : 0.0;
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 16; ++k) {
         const int j = j0 + k * (int)blockDim.x + (int)threadIdx.x;
         const float h = (float)v[k];
         if (j < a.m) xs[j] = make_float2(h, (float)(v[k] - (double)h));

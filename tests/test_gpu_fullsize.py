@@ -163,6 +163,63 @@ def test_c4_full_size_solve_reaches_the_planted_optimum(c4_lp):
     assert set(np.argsort(-x)[:lp.m]) == set(basis)
 
 
+def test_c3_full_size_sparse_countsketch_sampled_columns():
+    # the reproducible sparse sketch (entries of each bucket gathered in column
+    # order, sorted by row, summed per row) at 4096 x 2,000,000, w = 3m, s = 2:
+    # sampled buckets against the oracle's hash, and two calls bit for bit
+    torch = torch_cuda()
+    lp = lpgen.config_small("c3", 1)
+    A = lp.scipy_csc()
+    rng = np.random.default_rng(16)
+    D = np.exp(rng.uniform(-3, 3, lp.n))
+    seed, k, retry, s_blocks = 3, 4, 0, 2
+    with solver_for(lp, s=s_blocks, w_factor=3.0) as S:
+        w = S.sketch_width
+        adw = host(S.sketch(dev(torch, D), seed, k, retry))
+        again = host(S.sketch(dev(torch, D), seed, k, retry))
+    assert np.array_equal(adw.view(np.uint64), again.view(np.uint64))
+    cols, signs = sketch.countsketch_hash(seed, k, retry, lp.n, w, s_blocks)
+    for bucket in rng.choice(w, 16, replace=False):
+        b = bucket // (w // s_blocks)
+        members = np.nonzero(cols[b] == bucket)[0]
+        scale = signs[b, members] * D[members] / np.sqrt(s_blocks)
+        sub = A[:, members]
+        ref = sub @ scale
+        bound = abs(sub) @ np.abs(scale)
+        nnz_col = int(np.diff(A.indptr)[members].max()) if len(members) else 1
+        eps = 4 * (len(members) * nnz_col + 8) * EPS64
+        assert np.all(np.abs(adw[:, bucket] - ref) <= eps * bound + 1e-300), bucket
+
+
+def test_c4_full_size_countsketch_sampled_columns(c4_lp):
+    # the bucket kernel (whole 2048-row BF16 columns by bulk copy, double-float
+    # sums) at 2048 x 524288, w = 4m, s = 4: sampled buckets against the
+    # oracle's hash; two calls bit for bit
+    torch = torch_cuda()
+    lp = c4_lp
+    cfg = lpgen.CONFIGS["c4"]
+    rng = np.random.default_rng(17)
+    D = np.exp(rng.uniform(-3, 3, lp.n))
+    seed, k, retry = 0, 6, 0
+    with solver_for(lp, s=cfg["s"], w_factor=cfg["w_factor"]) as S:
+        w = S.sketch_width
+        adw = host(S.sketch(dev(torch, D), seed, k, retry))
+        again = host(S.sketch(dev(torch, D), seed, k, retry))
+    assert adw.shape == (lp.m, w)
+    assert np.array_equal(adw.view(np.uint64), again.view(np.uint64))
+    cols, signs = sketch.countsketch_hash(seed, k, retry, lp.n, w, cfg["s"])
+    store = lp.storage_array()
+    eps = max(8 * lp.n * EPS64, (32 * lp.n * cfg["s"] / w + 64) * DF_U)
+    for bucket in rng.choice(w, 12, replace=False):
+        b = bucket // (w // cfg["s"])
+        members = np.nonzero(cols[b] == bucket)[0]
+        blk = (store[members].astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)  # (cols, m)
+        scale = signs[b, members] * D[members] / np.sqrt(cfg["s"])
+        ref = blk.T @ scale
+        bound = np.abs(blk).T @ np.abs(scale)
+        assert np.all(np.abs(adw[:, bucket] - ref) <= eps * bound + 1e-300), bucket
+
+
 def test_c3_full_size_solve_from_csr_reaches_the_planted_objective():
     # 4096 x 2,000,000 with 16 M nonzeros, given as CSR (the configured format):
     # lp_create sorts it into exactly the CSC the generator built (checked on
