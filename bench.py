@@ -114,7 +114,8 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+             "clocks.mem,temperature.gpu,temperature.memory")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
@@ -132,6 +133,7 @@ class ClockSampler:
             self.p.kill()
         self.f.seek(0)
         sm, mx, reasons = [], [], set()
+        mem, tg, tm = [], [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().splitlines():
             parts = [t.strip() for t in line.split(",")]
@@ -145,10 +147,22 @@ class ClockSampler:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(nm)
+            for lst, k in ((mem, 9), (tg, 10), (tm, 11)):
+                try:
+                    lst.append(float(parts[k]))
+                except (IndexError, ValueError):
+                    pass
         os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None,
+               "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if mem:
+            out["mem_mhz"] = statistics.median(mem)
+        if tg:
+            out["gpu_temp_c_max"] = max(tg)
+        if tm:
+            out["mem_temp_c_max"] = max(tm)
+        return out
 
 
 def make_lp(name: str, seed: int):
