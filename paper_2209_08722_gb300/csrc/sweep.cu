@@ -268,12 +268,13 @@ __global__ void __launch_bounds__(ST_THREADS* kStepTiles) k_sweep_step(const flo
                                                                        int mp, int K, const float* __restrict__ qh,
                                                                        const float* __restrict__ ql,
                                                                        const float* __restrict__ uh_,
-                                                                       const float* __restrict__ ul_) {
+                                                                       const float* __restrict__ ul_,
+                                                                       int tiles_per_cta) {
   extern __shared__ __align__(16) char sw_smem[];
   const int part = threadIdx.x / ST_THREADS;
   StepSmem& S = reinterpret_cast<StepSmem*>(sw_smem)[part];
   const int nt = mp / SB;
-  const int tile = blockIdx.x * kStepTiles + part;
+  const int tile = blockIdx.x * tiles_per_cta + part;
   if (tile >= nt * (nt + 1) / 2) return;  // no tile for this part; the others' barriers count their own threads
   int I, J;
   upper_tile(tile, &I, &J);
@@ -444,7 +445,11 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sweep_init<<<g1, 256, 0, st>>>(g, m, mp, a0h, a0l, scale_buf);
   const int nt = mp / SB;
-  const int tile_smem = (int)(sizeof(StepSmem) * kStepTiles);
+  // tiles per CTA: as many as keep every SM busy (4 when there are tiles for
+  // two waves of 4-tile CTAs, fewer for small matrices, down to one per CTA)
+  const int ntiles_all = nt * (nt + 1) / 2;
+  const int tpc = ntiles_all >= 8 * num_sms ? kStepTiles : (ntiles_all >= 2 * num_sms ? 2 : 1);
+  const int tile_smem = (int)(sizeof(StepSmem) * tpc);
   {
     const cudaError_t es = ensure_smem((const void*)k_sweep_step, tile_smem);
     if (es != cudaSuccess) return es;
@@ -473,8 +478,8 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
     g_launches.fetch_add(2, std::memory_order_relaxed);
     k_sweep_panel<<<nt, SW_THREADS, 0, st>>>(sh, sl, mp, K, qh[K & 1], ql[K & 1], uh, ul);
     const int ntiles = nt * (nt + 1) / 2;
-    k_sweep_step<<<(ntiles + kStepTiles - 1) / kStepTiles, ST_THREADS * kStepTiles, tile_smem, st>>>(
-        sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1], uh, ul);
+    k_sweep_step<<<(ntiles + tpc - 1) / tpc, ST_THREADS * tpc, tile_smem, st>>>(
+        sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1], uh, ul, tpc);
     if (two) {
       if ((e = cudaEventRecord(ev_x, st)) != cudaSuccess) return e;
       if (K + 1 < nt && (e = cudaEventRecord(ev_p, st_aux)) != cudaSuccess) return e;
