@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       ok = mbar_wait(&empty[c & 1], (uint32_t)((c >> 1) & 1), err);
     staged = ok ? staged : -1;
   }
-  // every thread's verdict: the stagers' waits and the MMA lane's
+  // every thread's outcome: the stagers' waits and the MMA lane's
   const bool all_ok = __syncthreads_and(staged >= 0 && mma_ok_s != 0) != 0;
   tc_fence_after();
   if (all_ok && nchunks > 0 && warp < TC_STAGERS / 32) {

@@ -119,6 +119,9 @@ DF_U = 2.0 ** -48
     # columns above its 4096 rows (the slab kernel)
     (2048, 9001, "bf16", 4, 0), (2100, 4001, "f32", 2, 0), (1100, 3001, "f64", 2, 0),
     (4500, 5003, "bf16", 2, 0),
+    # more buckets than columns: most buckets of the bucket kernel are empty,
+    # the others hold an odd or even number of columns
+    (600, 701, "f32", 1, 0), (1030, 1100, "bf16", 1, 0),
     # buckets of ~10^4 columns: above the in-CTA sort capacity
     (4, 40000, "f32", 1, 4), (6, 30000, "f64", 2, 6)])
 def test_countsketch_matches_oracle(m, n, storage, s_blocks, w):
