@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(SB* SB) k_sweep_pivot(const float* __restrict_
 __global__ void __launch_bounds__(SW_THREADS) k_sweep_panel(const float* __restrict__ sh_, const float* __restrict__ sl_,
                                                             int mp, int K, const float* __restrict__ qh,
                                                             const float* __restrict__ ql, float* __restrict__ uh_,
-                                                            float* __restrict__ ul_) {
+                                                            float* __restrict__ ul_, float* __restrict__ uth_,
+                                                            float* __restrict__ utl_) {
   __shared__ float Ph[SB][SB + 1], Pl[SB][SB + 1];
   __shared__ float Th[SB][SB + 1], Tl[SB][SB + 1];
   const int I = blockIdx.x;
@@ -236,6 +237,10 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep_panel(const float* __restr
     df_renorm(uh4[q], ul4[q]);
     uh_[(size_t)I * SB * SB + r * SB + c4 + q] = uh4[q];
     ul_[(size_t)I * SB * SB + r * SB + c4 + q] = ul4[q];
+    if (uth_) {  // U_I^T as well, for the 64 x 64 block kernel's coalesced staging
+      uth_[(size_t)I * SB * SB + (c4 + q) * SB + r] = uh4[q];
+      utl_[(size_t)I * SB * SB + (c4 + q) * SB + r] = ul4[q];
+    }
   }
 }
 
@@ -376,6 +381,157 @@ __global__ void __launch_bounds__(ST_THREADS* kStepTiles) k_sweep_step(const flo
   }
 }
 
+// The same pivot step for large matrices, on 64 x 64 blocks of the upper
+// triangle (2 x 2 tiles of 32) with 256 threads, each forming a 4 x 4 block
+// of outputs.  The operands of an interior tile, U of the block's two row
+// tiles and A_{J,K} of its two column tiles, are held transposed in shared
+// memory ([k][row] pairs), so a thread's four rows and four columns come in
+// two 16-byte loads each and every loaded pair serves four multiply-adds.
+// Every output is formed by the same operations in the same order as in
+// k_sweep_step.  Tiles of row or column K are copied from the pivot block or
+// the panel; a diagonal block forms its upper-right tile and mirrors it into
+// the lower-left one, an off-diagonal block is mirrored whole, through shared
+// memory.  One 64 x 64 block per CTA: about one wave of CTAs for the
+// 2048-row factor, where the 32 x 32 tiles take two.
+namespace {
+constexpr int SB2 = 2 * SB;        // 64
+constexpr int S64_THREADS = 256;   // 16 x 16 threads, 4 x 4 outputs each
+struct Step64Smem {
+  union {
+    struct {
+      float2 U[SB][SB2];   // [k][row]: U of row tiles 2 I2, 2 I2 + 1
+      float2 C[SB][SB2];   // [k][col]: A_{J,K} of column tiles 2 J2, 2 J2 + 1
+    } op;
+    float2 T[SB2][SB2 + 1];  // the block, for the mirror
+  };
+};
+}  // namespace
+
+__global__ void __launch_bounds__(S64_THREADS, 4) k_sweep_step64(const float* __restrict__ sh_, const float* __restrict__ sl_,
+                                                                 float* __restrict__ dh_, float* __restrict__ dl_,
+                                                                 int mp, int K, const float* __restrict__ qh,
+                                                                 const float* __restrict__ ql,
+                                                                 const float* __restrict__ uh_,
+                                                                 const float* __restrict__ ul_,
+                                                                 const float* __restrict__ uth_,
+                                                                 const float* __restrict__ utl_) {
+  extern __shared__ __align__(16) char s64_smem[];
+  Step64Smem& S = *reinterpret_cast<Step64Smem*>(s64_smem);
+  const int nt = mp / SB, nb = nt / 2;
+  int I2, J2;
+  upper_tile(blockIdx.x, &I2, &J2);
+  if (I2 >= nb || J2 >= nb) return;
+  const int k0 = K * SB;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int r4 = ty * 4, c4 = tx * 4;            // rows / columns within the 64 x 64 block
+  const int qa = r4 >> 5, qb = c4 >> 5;          // this thread's quadrant
+  const int I = 2 * I2 + qa, J = 2 * J2 + qb;    // its tile
+  const int r = r4 & (SB - 1), c = c4 & (SB - 1);  // rows / columns within the tile
+  const bool lower_of_diag = I2 == J2 && qa > qb;  // formed as the mirror of the upper-right tile
+
+  // ---- operands of the interior tiles, transposed: U from the panel's
+  // transposed copy, A_{J,K}^T as the iterate's row block K (the iterate is
+  // stored symmetric: off-diagonal tiles are written with their mirror), so
+  // consecutive threads read consecutive addresses and store to consecutive
+  // banks ----
+  for (int e = tid; e < SB2 * SB; e += S64_THREADS) {
+    const int k = e / SB2, row = e % SB2;  // k in [0, 32), row of the block's row (column) pair
+    const int ti = 2 * I2 + row / SB, tj = 2 * J2 + row / SB;
+    const size_t ue = (size_t)ti * SB * SB + (size_t)k * SB + (row % SB);
+    S.op.U[k][row] = ti == K ? make_float2(0.0f, 0.0f) : make_float2(uth_[ue], utl_[ue]);
+    const size_t ce = (size_t)(k0 + k) * mp + tj * SB + (row % SB);
+    S.op.C[k][row] = make_float2(sh_[ce], sl_[ce]);
+  }
+  __syncthreads();
+
+  float oh[4][4], ol[4][4];
+  if (!lower_of_diag) {
+    if (I == K && J == K) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4 h4 = *reinterpret_cast<const float4*>(qh + (r + a) * SB + c);
+        const float4 l4 = *reinterpret_cast<const float4*>(ql + (r + a) * SB + c);
+        oh[a][0] = h4.x; oh[a][1] = h4.y; oh[a][2] = h4.z; oh[a][3] = h4.w;
+        ol[a][0] = l4.x; ol[a][1] = l4.y; ol[a][2] = l4.z; ol[a][3] = l4.w;
+      }
+    } else if (J == K) {  // -U_I
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const size_t u = (size_t)I * SB * SB + (size_t)(r + a) * SB + c;
+        const float4 h4 = *reinterpret_cast<const float4*>(uh_ + u);
+        const float4 l4 = *reinterpret_cast<const float4*>(ul_ + u);
+        oh[a][0] = -h4.x; oh[a][1] = -h4.y; oh[a][2] = -h4.z; oh[a][3] = -h4.w;
+        ol[a][0] = -l4.x; ol[a][1] = -l4.y; ol[a][2] = -l4.z; ol[a][3] = -l4.w;
+      }
+    } else if (I == K) {  // -U_J^T
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const size_t u = (size_t)J * SB * SB + (size_t)(c + q) * SB + (r + a);
+          oh[a][q] = -uh_[u];
+          ol[a][q] = -ul_[u];
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const size_t src = (size_t)(I * SB + r + a) * mp + J * SB + c;
+        const float4 h4 = *reinterpret_cast<const float4*>(sh_ + src);
+        const float4 l4 = *reinterpret_cast<const float4*>(sl_ + src);
+        oh[a][0] = h4.x; oh[a][1] = h4.y; oh[a][2] = h4.z; oh[a][3] = h4.w;
+        ol[a][0] = l4.x; ol[a][1] = l4.y; ol[a][2] = l4.z; ol[a][3] = l4.w;
+      }
+      for (int b = 0; b < SB; ++b) {
+        const float4 u01 = *reinterpret_cast<const float4*>(&S.op.U[b][r4]);
+        const float4 u23 = *reinterpret_cast<const float4*>(&S.op.U[b][r4 + 2]);
+        const float4 c01 = *reinterpret_cast<const float4*>(&S.op.C[b][c4]);
+        const float4 c23 = *reinterpret_cast<const float4*>(&S.op.C[b][c4 + 2]);
+        const float uhv[4] = {u01.x, u01.z, u23.x, u23.z}, ulv[4] = {u01.y, u01.w, u23.y, u23.w};
+        const float chv[4] = {c01.x, c01.z, c23.x, c23.z}, clv[4] = {c01.y, c01.w, c23.y, c23.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) df_mac(uhv[a], ulv[a], chv[q], clv[q], oh[a][q], ol[a][q]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) df_renorm(oh[a][q], ol[a][q]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const size_t dst = (size_t)(I * SB + r + a) * mp + J * SB + c;
+      *reinterpret_cast<float4*>(dh_ + dst) = make_float4(oh[a][0], oh[a][1], oh[a][2], oh[a][3]);
+      *reinterpret_cast<float4*>(dl_ + dst) = make_float4(ol[a][0], ol[a][1], ol[a][2], ol[a][3]);
+    }
+  }
+  // ---- mirrors: the whole block (off-diagonal) or its upper-right tile ----
+  __syncthreads();  // every read of the operands is done; T reuses their space
+  if (!lower_of_diag) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) S.T[r4 + a][c4 + q] = make_float2(oh[a][q], ol[a][q]);
+  }
+  __syncthreads();
+  // the thread at (r4, c4) of the mirror block writes mirror rows r4.., columns
+  // c4.., i.e. the block's entries (c4 + q, r4 + a)
+  const bool write_mirror = I2 != J2 || lower_of_diag;
+  if (write_mirror) {
+    // mirror position: block (J2, I2), its tile rows come from the block's columns
+    const int MI = 2 * J2 + qa, MJ = 2 * I2 + qb;  // tile of the mirror entry
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = S.T[c4 + q][r4 + a];
+      const size_t dst = (size_t)(MI * SB + r + a) * mp + MJ * SB + c;
+      *reinterpret_cast<float4*>(dh_ + dst) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+      *reinterpret_cast<float4*>(dl_ + dst) = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+    }
+  }
+}
+
 // Q^{-1} = -2^-e A_final (FP64, m x m, both triangles) and the rank check on
 // the pivots (|R_ii| = sqrt(pivot_i))
 __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ ah, const float* __restrict__ al,
@@ -418,7 +574,7 @@ __global__ void __launch_bounds__(256) k_sweep_finish(const float* __restrict__ 
 
 size_t sweep_scratch_floats(int m) {
   const size_t mp = (size_t)(m + SB - 1) / SB * SB;
-  return 4 * mp * mp + mp + 8 + 4 * SB * SB + 2 * mp * SB;
+  return 4 * mp * mp + mp + 8 + 4 * SB * SB + 4 * mp * SB;  // + U^T for the block kernel
 }
 
 // G: upper triangle of the column-major m x m Gram; qinv: m x m output
@@ -441,6 +597,8 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   // the panels U_I of the current step: [nt][SB][SB] pairs
   float* uh = qbase + 4 * SB * SB;
   float* ul = uh + (size_t)mp * SB;
+  float* uth = ul + (size_t)mp * SB;  // the panels transposed ([nt][k][row] pairs)
+  float* utl = uth + (size_t)mp * SB;
   const int g1 = (int)std::max<long long>(1, std::min<long long>(((long long)mm + 255) / 256, (long long)num_sms * 4));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_sweep_init<<<g1, 256, 0, st>>>(g, m, mp, a0h, a0l, scale_buf);
@@ -452,6 +610,15 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
   const int tile_smem = (int)(sizeof(StepSmem) * tpc);
   {
     const cudaError_t es = ensure_smem((const void*)k_sweep_step, tile_smem);
+    if (es != cudaSuccess) return es;
+  }
+  // 64 x 64 blocks where the 32 x 32 tiles would take more than one wave of
+  // 4-tile CTAs (an even number of tiles per row)
+  const bool use64 = (nt % 2) == 0 && ntiles_all >= 8 * num_sms;
+  const int nblk64 = (nt / 2) * (nt / 2 + 1) / 2;
+  const int smem64 = (int)sizeof(Step64Smem);
+  if (use64) {
+    const cudaError_t es = ensure_smem((const void*)k_sweep_step64, smem64);
     if (es != cudaSuccess) return es;
   }
   // The pivot kernel of step K + 1 needs the iterate that step K reads and
@@ -476,10 +643,15 @@ cudaError_t launch_sweep_inverse(const double* g, int m, float* scratch, double*
     }
     if (two && K >= 1 && (e = cudaStreamWaitEvent(st, ev_p, 0)) != cudaSuccess) return e;
     g_launches.fetch_add(2, std::memory_order_relaxed);
-    k_sweep_panel<<<nt, SW_THREADS, 0, st>>>(sh, sl, mp, K, qh[K & 1], ql[K & 1], uh, ul);
+    k_sweep_panel<<<nt, SW_THREADS, 0, st>>>(sh, sl, mp, K, qh[K & 1], ql[K & 1], uh, ul,
+                                             use64 ? uth : nullptr, use64 ? utl : nullptr);
     const int ntiles = nt * (nt + 1) / 2;
-    k_sweep_step<<<(ntiles + tpc - 1) / tpc, ST_THREADS * tpc, tile_smem, st>>>(
-        sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1], uh, ul, tpc);
+    if (use64)
+      k_sweep_step64<<<nblk64, S64_THREADS, smem64, st>>>(sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K,
+                                                          qh[K & 1], ql[K & 1], uh, ul, uth, utl);
+    else
+      k_sweep_step<<<(ntiles + tpc - 1) / tpc, ST_THREADS * tpc, tile_smem, st>>>(
+          sh, sl, even ? a1h : a0h, even ? a1l : a0l, mp, K, qh[K & 1], ql[K & 1], uh, ul, tpc);
     if (two) {
       if ((e = cudaEventRecord(ev_x, st)) != cudaSuccess) return e;
       if (K + 1 < nt && (e = cudaEventRecord(ev_p, st_aux)) != cudaSuccess) return e;
