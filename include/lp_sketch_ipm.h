@@ -508,6 +508,17 @@ int lp_get_kernel_stats(lp_handle* h, lp_kernel_stats* st);
  * how many differ; lp_last_error names the first damaged buffer (its index in
  * allocation order and size).  LP_ERR_ARG for null pointers. */
 int lp_check_guards(lp_handle* h, int64_t* checked, int64_t* damaged);
+
+/* Device memory of destroyed handles is kept by the library (per device and
+ * block size, up to 16 GiB in all) and reused by the next handles, so that
+ * creating and destroying handles of one shape again and again (a service
+ * solving a stream of LPs) makes no cudaMalloc or cudaFree calls after the
+ * first.  A cudaMalloc that fails empties the cache and is retried.  This
+ * call returns every cached block to the driver; call it with no handle's
+ * work in flight on a block being freed (blocks enter the cache only after
+ * their handle's streams were synchronised).  Always LP_OK.  (Not a method
+ * of the paper: memory management of the library.) */
+int lp_release_cached_memory(void);
 int lp_reset_kernel_stats(lp_handle* h);
 
 #ifdef __cplusplus

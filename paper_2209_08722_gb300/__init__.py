@@ -10,7 +10,8 @@ from .build_native import build, lib_path  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("LPSolver", "LPError", "from_planted", "phase1_start", "solve_batch", "Mlp", "csr_to_csc"):
+    if name in ("LPSolver", "LPError", "from_planted", "phase1_start", "solve_batch", "Mlp", "csr_to_csc",
+                "release_cached_memory"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -152,6 +152,7 @@ SIGNATURES = {
     "lp_get_warm_start_stats": (c_int32, [P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64)]),
     "lp_get_kernel_stats": (c_int32, [P, POINTER(LpKernelStats)]),
     "lp_check_guards": (c_int32, [P, POINTER(c_int64), POINTER(c_int64)]),
+    "lp_release_cached_memory": (c_int32, []),
     "lp_reset_kernel_stats": (c_int32, [P]),
 }
 

@@ -88,6 +88,48 @@ std::string csr_to_csc(int m, long long n, long long nnz, const int64_t* rp, con
 }
 }  // namespace
 
+// Device blocks freed by destroyed handles are kept for the next handles
+// (keyed by device and size), up to kPoolCap bytes: a handle of a shape
+// solved before is then created without cudaMalloc and destroyed without
+// cudaFree, which for large A is most of its creation and destruction time.
+// A failed cudaMalloc empties the cache and retries; lp_release_cached_memory
+// returns the cache to the driver.
+namespace {
+constexpr size_t kPoolCap = size_t(16) << 30;
+std::mutex g_pool_mu;
+std::multimap<std::pair<int, size_t>, void*> g_pool;
+size_t g_pool_bytes = 0;
+
+void* pool_take(int dev, size_t bytes) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  auto it = g_pool.find({dev, bytes});
+  if (it == g_pool.end()) return nullptr;
+  void* p = it->second;
+  g_pool.erase(it);
+  g_pool_bytes -= bytes;
+  return p;
+}
+
+void pool_give(int dev, size_t bytes, void* p) {
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool_bytes + bytes <= kPoolCap) {
+      g_pool.insert({{dev, bytes}, p});
+      g_pool_bytes += bytes;
+      return;
+    }
+  }
+  cudaFree(p);
+}
+
+void pool_release() {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  for (auto& kv : g_pool) cudaFree(kv.second);
+  g_pool.clear();
+  g_pool_bytes = 0;
+}
+}  // namespace
+
 struct lp_handle {
   int dev = 0, num_sms = 1;
   int m = 0;
@@ -222,7 +264,7 @@ struct lp_handle {
   unsigned long long k1_sample = 0;  // product launches seen by the profiling sampler
   long long launch_base = 0;
   std::vector<lp_iter_record> history;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;  // device blocks and their sizes
   // checkpoint / resume: the state of the last solve (valid while x, y, s
   // still hold its iterate) and a state loaded for the next solve
   bool state_valid = false;
@@ -250,15 +292,20 @@ struct lp_handle {
   std::vector<GuardedBuf> guarded_bufs;
   template <typename T>
   int alloc(T** ptr, size_t count) {
-    void* p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
     const size_t pad = opt.guard ? kGuard : 0;
-    if (cudaMalloc(&p, bytes + 2 * pad) != cudaSuccess) {
+    const size_t total = bytes + 2 * pad;
+    void* p = pool_take(dev, total);
+    if (!p && cudaMalloc(&p, total) != cudaSuccess) {
       cudaGetLastError();
-      *ptr = nullptr;
-      return fail(LP_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes + 2 * pad);
+      pool_release();  // the cached blocks may be what the device is short of
+      if (cudaMalloc(&p, total) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(LP_ERR_OOM, "cudaMalloc of %zu bytes failed", total);
+      }
     }
-    allocs.push_back(p);
+    allocs.push_back({p, total});
     char* user = static_cast<char*>(p) + pad;
     if (pad) {
       guarded_bufs.push_back({static_cast<char*>(p), bytes});
@@ -1290,7 +1337,8 @@ int lp_destroy(lp_handle* h) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
   }
-  for (void* p : h->allocs) cudaFree(p);
+  if (h->st_aux) cudaStreamSynchronize(h->st_aux);  // no kernel of this handle uses a block any more
+  for (auto& a : h->allocs) pool_give(h->dev, a.second, a.first);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hinfo) cudaFreeHost(h->hinfo);
   if (h->hval) cudaFreeHost(h->hval);
@@ -1984,6 +2032,11 @@ static int check_guards_impl(lp_handle* h, int64_t* checked, int64_t* damaged) {
   }
   *checked = nchk;
   *damaged = nbad;
+  return LP_OK;
+}
+
+int lp_release_cached_memory(void) {
+  pool_release();
   return LP_OK;
 }
 

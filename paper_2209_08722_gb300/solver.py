@@ -409,6 +409,12 @@ class LPSolver:
         self._check(self._lib.lp_reset_kernel_stats(self._h))
 
 
+def release_cached_memory():
+    """lp_release_cached_memory: return the device blocks the library keeps
+    from destroyed solvers to the driver."""
+    nat.load().lp_release_cached_memory()
+
+
 def from_planted(lp, device: bool = False, **options) -> LPSolver:
     """An LPSolver for an ``lpgen.PlantedLP`` (dense or CSC)."""
     if lp.sparse:

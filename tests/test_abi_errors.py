@@ -175,6 +175,7 @@ def test_null_handles_are_argument_errors(lib):
     d = np.ones(N)
     p = d.ctypes.data
     assert lib.lp_destroy(None) == nat.LP_OK
+    assert lib.lp_release_cached_memory() == nat.LP_OK  # an empty cache: nothing to free
     assert lib.lp_last_error(None) == b""
     assert lib.lp_adat(None, p, p, p, 0) == nat.LP_ERR_ARG
     assert lib.lp_residual_rhs(None, p, p, p, 1, None, None, None, None) == nat.LP_ERR_ARG

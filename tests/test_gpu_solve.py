@@ -265,3 +265,27 @@ def test_lp_whose_sketches_collapsed_near_the_optimum_is_solved():
         assert info["rel_gap"] <= 1e-8
         assert abs(lp.c @ x - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
         assert info["inner_max"] <= 200, info
+
+
+def test_handles_reuse_cached_device_memory():
+    # a destroyed handle's device blocks go to the library's cache and the next
+    # handle of the same shape takes them (zeroed again): the solves agree bit
+    # for bit, a guarded handle (other block sizes) keeps intact guards, and
+    # releasing the cache leaves the library usable
+    torch_cuda()
+    from paper_2209_08722_gb300 import release_cached_memory
+    lp = lpgen.planted_dense(96, 6001, seed=31, storage="f32")
+    with solver_for(lp, s=2, guard=0) as S:
+        x1, y1, _, i1 = S.solve(tol=1e-8)
+    with solver_for(lp, s=2, guard=0) as S:
+        x2, y2, _, i2 = S.solve(tol=1e-8)
+    assert i1["status"] == i2["status"] == 0
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+    with solver_for(lp, s=2, guard=1) as S:
+        x3, _, _, _ = S.solve(tol=1e-8)
+        assert S.check_guards()[1] == 0
+    assert np.array_equal(x1, x3)
+    release_cached_memory()
+    with solver_for(lp, s=2, guard=0) as S:
+        x4, _, _, _ = S.solve(tol=1e-8)
+    assert np.array_equal(x1, x4)
