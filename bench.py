@@ -573,7 +573,7 @@ def run_warm_start(args):
 
 
 def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk,
-              oracle=None, cfg=None, e2e_clk=None):
+              oracle=None, cfg=None, e2e_extra=None):
     """The JSON line of the default run: the metric and its run keys plus roofline,
     cpu_baseline, e2e, gpu_launches, clocks, the solve's counts and the
     comparison with the oracle's objective.  Pure host code (reads the
@@ -605,7 +605,7 @@ def ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, cl
                      "mean_launch_ms": k_ms},
         "cpu_baseline": cpu,
         "e2e": dict({"value": e2e / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d,
-                     "d2h_bytes_per_step": d2h}, **({"clocks": e2e_clk} if e2e_clk else {})),
+                     "d2h_bytes_per_step": d2h}, **(e2e_extra or {})),
         "gpu_launches": gpu_launches,
         "clocks": clk,
         "solve": {"outer_iterations": infos[-1]["outer_iterations"],
@@ -723,21 +723,31 @@ def main():
     solver.close()
     # one untimed round, then up to 5 timed ones: the loop follows the timed
     # solves under load, so it is kept short and its clocks are recorded too
-    e2e_ms = []
+    e2e_ms, e2e_parts = [], []
     e2e_steps = min(args.steps, 5)
     e2e_clocks = ClockSampler(local)
     for it in range(1 + e2e_steps):
         barrier()
         t0 = time.perf_counter()
         sv = LPSolver(pinA, pinb, pinc, lp.m, lp.n, stream=stream.cuda_stream, **opts)
+        t1 = time.perf_counter()
         _, _, _, inf2 = sv.solve(tol=TOL, out=outs)
+        t2 = time.perf_counter()
         sv.close()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) * 1000.0
+        t3 = time.perf_counter()
+        dt = (t3 - t0) * 1000.0
         assert inf2["status"] == 0
         if it >= 1:
             e2e_ms.append(dt)
+            e2e_parts.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3, (t3 - t2) * 1e3, inf2["ms_total"]))
     e2e_clk = e2e_clocks.stop()
+    e2e_extra = {"clocks": e2e_clk}
+    if e2e_parts:  # where the end-to-end time goes (host clock; the copy of A runs asynchronously into the solve)
+        e2e_extra["parts_ms"] = {"create": float(np.mean([p[0] for p in e2e_parts])),
+                                 "solve_call": float(np.mean([p[1] for p in e2e_parts])),
+                                 "destroy": float(np.mean([p[2] for p in e2e_parts])),
+                                 "solve_reported": float(np.mean([p[3] for p in e2e_parts]))}
     e2e = max_over_ranks(float(np.mean(e2e_ms)), dist, "cuda")
     del pinA
 
@@ -770,7 +780,7 @@ def main():
                           "source": "recorded whole solve (tests/golden/oracle_solves.json)",
                           "gpu_objective_rel_diff": abs(obj - rec["objective"]) / (1 + abs(rec["objective"]))}
     line = ours_line(args, world, ms_per_step, stats, infos, obj_err, e2e, h2d, d2h, clk, cpu, cpu_sk,
-                     oracle, cfg, e2e_clk=e2e_clk)
+                     oracle, cfg, e2e_extra=e2e_extra)
     line["solve"]["error_vs_fp64"] = err_fp64
     print(json.dumps(line), flush=True)
     if dist is not None:
