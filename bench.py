@@ -9,6 +9,10 @@ y0 = 0), chosen with --config:
   c2            planted dense LP, m = 512, n = 131072, N(0,1) entries with
                 every column scaled by 10**U(-2, 2), stored in FP32 (268 MB);
                 CountSketch w = 2048, s = 4
+  c3            planted sparse LP, m = 4096, n = 2,000,000, 8 nonzeros per
+                column (16 M), given as CSR with FP32 values; CountSketch
+                w = 3m = 12288, s = 2 (the oracle forms A densely, 65.5 GB in
+                FP64 here, so this line has no CPU baseline)
 
 Printed JSON line (rank 0):
   value       device-timed seconds per LP solve (inputs resident in HBM); with
@@ -77,7 +81,39 @@ BENCH = {
         kernel="k_adat_fused (A diag(d2) A^T v, FP32)",
         sources=("stream.cu", "stream_dev.cuh", "stream.cuh", "common.cuh", "df.cuh"),
         traffic="traffic_k_adat_fused_m512_n131072.json"),
+    "c3": dict(
+        m=4096, n=2_000_000, dtype="f32", s=2, w_factor=3.0, refine_every=8, whole_oracle=False,
+        sparse=True,
+        workload=("planted sparse LP m=4096 n=2,000,000, 8 nonzeros per column (16 M; 20 % of them in "
+                  "Zipf(1.2)-ranked rows), N(0,1) values in FP32, given as CSR, infeasible start "
+                  "x0=s0=1 y0=0, CountSketch w=12288 s=2"),
+        l2=("inputs larger than L2 (A = 144 MB as CSC with FP32 values and int32 indices; every "
+            "product streams it and its row-ordered copy, 272 MB)"),
+        dtype_detail=("A stored sparse with FP32 values (CSC, sorted from the CSR input, plus a "
+                      "row-ordered copy); inner-loop products FP32 with FP32 accumulation in two "
+                      "deterministic passes; residual refresh, residuals, directions and sketch sums "
+                      "in FP64; factor in double-float; FP64 vectors, dots and step lengths"),
+        kernel=("k_spc + k_spr + k_spe (A diag(d2) A^T v, sparse FP32: column pass, row-segment "
+                "pass, row epilogue)"),
+        sources=("sparse.cu", "stream.cuh", "common.cuh"),
+        traffic=None),
 }
+
+
+def csr_of(lp):
+    """The sparse workload's A as CSR (row_ptr int64, col_idx int32, FP32
+    values), the format it is given in; lp_create sorts it into CSC."""
+    import scipy.sparse as sp
+    a = sp.csc_matrix((lp.val.astype(np.float32), lp.row_idx, lp.col_ptr), shape=(lp.m, lp.n)).tocsr()
+    return a.indptr.astype(np.int64), a.indices.astype(np.int32), a.data.astype(np.float32)
+
+
+def solver_input(lp, cfg):
+    """(A, keyword arguments) for LPSolver: the dense storage array, or the
+    CSR triple of the sparse workload."""
+    if cfg.get("sparse"):
+        return None, {"csr": csr_of(lp)}
+    return lp.storage_array(), {}
 
 
 def load_peaks():
@@ -100,6 +136,8 @@ def hot_kernel_source_hash(sources) -> str:
 def traffic_record(cfg):
     """Per-launch DRAM bytes of the hot kernel from the committed ncu summary,
     valid only while the kernel's sources are unchanged."""
+    if not cfg.get("traffic"):
+        return None
     p = os.path.join(ROOT, "profiles", cfg["traffic"])
     if not os.path.exists(p):
         return None
@@ -291,6 +329,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = BENCH[args.config]
+    if cfg.get("sparse"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle forms A densely: the "
+                          "4096 x 2,000,000 sparse LP would take 65.5 GB in FP64"}))
+        return 0
     lp = make_lp(args.config, 0)
     cores = os.cpu_count()
     if cfg["whole_oracle"]:
@@ -339,8 +381,9 @@ def run_kernel(args):
     else:
         lp = make_lp(args.config, 0)
     stream = torch.cuda.current_stream()
-    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, dtype=cfg["dtype"], s=cfg["s"],
-                      w_factor=cfg["w_factor"], profile=1, stream=stream.cuda_stream)
+    A0, akw = solver_input(lp, cfg)
+    solver = LPSolver(A0, lp.b, lp.c, lp.m, lp.n, dtype=cfg["dtype"], s=cfg["s"],
+                      w_factor=cfg["w_factor"], profile=1, stream=stream.cuda_stream, **akw)
     rng = np.random.default_rng(0)
     d2 = torch.from_numpy(np.exp(rng.uniform(-5, 5, lp.n))).cuda()
     v = torch.from_numpy(rng.standard_normal(lp.m)).cuda()
@@ -371,6 +414,8 @@ def run_gauss_kernel(args):
     from paper_2209_08722_gb300 import LPSolver
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     cfg = BENCH[args.config]
+    if cfg.get("sparse"):
+        raise SystemExit("the Gaussian sketch kernels take a dense A; --config c3 is sparse")
     lp = make_lp(args.config, 0)
     stream = torch.cuda.current_stream()
     tensor = 1 if args.kernel == "gauss" else 0
@@ -676,8 +721,8 @@ def main():
     lp = make_lp(args.config, replica_seed(rank))
     opts = dict(dtype=cfg["dtype"], s=cfg["s"], w_factor=cfg["w_factor"], refine_every=cfg["refine_every"])
     stream = torch.cuda.current_stream()
-    solver = LPSolver(lp.storage_array(), lp.b, lp.c, lp.m, lp.n, profile=1, stream=stream.cuda_stream,
-                      **opts)
+    A0, akw = solver_input(lp, cfg)
+    solver = LPSolver(A0, lp.b, lp.c, lp.m, lp.n, profile=1, stream=stream.cuda_stream, **akw, **opts)
     info = None
     for _ in range(args.warmup):
         x, y, s, info = solver.solve(tol=TOL)
@@ -710,15 +755,25 @@ def main():
                 "y": float(np.linalg.norm(y - lp.y_star) / np.linalg.norm(lp.y_star)),
                 "s": float(np.linalg.norm(s - lp.s_star) / np.linalg.norm(lp.s_star)),
                 "reference": "planted optimum (x*, y*, s*), relative 2-norm errors"}
+    if cfg.get("sparse"):
+        err_fp64["note"] = ("the sparse LP's optimal x and y need not be unique (A_B can be singular): "
+                            "the objective is the compared quantity")
 
     # ---- end to end through the C ABI with host buffers ----
-    pinA = torch.from_numpy(lp.storage_array()).pin_memory()
+    if cfg.get("sparse"):
+        pinA = None
+        e2e_akw = {"csr": tuple(torch.from_numpy(t).pin_memory() for t in akw["csr"])}
+        a_bytes = sum(t.numel() * t.element_size() for t in e2e_akw["csr"])
+    else:
+        pinA = torch.from_numpy(A0).pin_memory()
+        e2e_akw = {}
+        a_bytes = pinA.numel() * pinA.element_size()
     pinb = torch.from_numpy(np.ascontiguousarray(lp.b)).pin_memory()
     pinc = torch.from_numpy(np.ascontiguousarray(lp.c)).pin_memory()
     outs = (torch.empty(lp.n, dtype=torch.float64).pin_memory(),
             torch.empty(lp.m, dtype=torch.float64).pin_memory(),
             torch.empty(lp.n, dtype=torch.float64).pin_memory())
-    h2d = pinA.numel() * pinA.element_size() + (lp.m + lp.n) * 8
+    h2d = a_bytes + (lp.m + lp.n) * 8
     d2h = (2 * lp.n + lp.m) * 8
     solver.close()
     # one untimed round, then up to 5 timed ones: the loop follows the timed
@@ -729,7 +784,7 @@ def main():
     for it in range(1 + e2e_steps):
         barrier()
         t0 = time.perf_counter()
-        sv = LPSolver(pinA, pinb, pinc, lp.m, lp.n, stream=stream.cuda_stream, **opts)
+        sv = LPSolver(pinA, pinb, pinc, lp.m, lp.n, stream=stream.cuda_stream, **e2e_akw, **opts)
         t1 = time.perf_counter()
         _, _, _, inf2 = sv.solve(tol=TOL, out=outs)
         t2 = time.perf_counter()
@@ -749,14 +804,17 @@ def main():
                                  "destroy": float(np.mean([p[2] for p in e2e_parts])),
                                  "solve_reported": float(np.mean([p[3] for p in e2e_parts]))}
     e2e = max_over_ranks(float(np.mean(e2e_ms)), dist, "cuda")
-    del pinA
+    del pinA, e2e_akw
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
     cpu = cpu_sk = oracle = None
-    if not args.no_cpu_baseline and world == 1:
+    if cfg.get("sparse"):
+        cpu = {"value": None, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "not run: the oracle forms A densely (4096 x 2,000,000 in FP64 is 65.5 GB)"}
+    elif not args.no_cpu_baseline and world == 1:
         if cfg["whole_oracle"]:
             secs, its, o_obj = oracle_whole_solve(lp)
             cpu = {"value": secs, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",

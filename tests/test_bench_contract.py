@@ -154,3 +154,43 @@ def test_oracle_record_matches_only_the_same_lp(tmp_path, monkeypatch):
     other = lpgen.planted_dense(8, 64, seed=1, storage="f32")
     assert bench.oracle_record("c2", other) is None          # another planted optimum
     assert bench.oracle_record("c4", lp) is None             # no record
+
+
+def test_sparse_workload_is_given_as_csr_of_the_same_matrix():
+    import lpgen
+    import numpy as np
+    lp = lpgen.planted_sparse(40, 300, nnz_per_col=4, seed=3)
+    rp, ci, vals = bench.csr_of(lp)
+    assert rp.dtype == np.int64 and ci.dtype == np.int32 and vals.dtype == np.float32
+    assert rp[0] == 0 and rp[-1] == len(ci) == len(vals) == lp.col_ptr[-1]
+    dense = np.zeros((lp.m, lp.n))
+    for i in range(lp.m):
+        for k in range(rp[i], rp[i + 1]):
+            dense[i, ci[k]] += vals[k]
+    ref = np.zeros((lp.m, lp.n))
+    for j in range(lp.n):
+        for k in range(lp.col_ptr[j], lp.col_ptr[j + 1]):
+            ref[lp.row_idx[k], j] += np.float32(lp.val[k])
+    assert np.array_equal(dense, ref)
+    A0, kw = bench.solver_input(lp, bench.BENCH["c3"])
+    assert A0 is None and set(kw) == {"csr"}
+
+
+def test_sparse_workload_line_has_every_contract_key():
+    cfg = bench.BENCH["c3"]
+    assert bench.traffic_record(cfg) is None
+    args = argparse.Namespace(steps=3, warmup=3, config="c3")
+    stats = {"launches": 21, "ms": 2.1, "bytes_per_launch": 152_000_000, "all_launches": 900}
+    cpu = {"value": None, "unit": "s", "cores": 16, "kind": "oracle", "sample": "not run"}
+    line = bench.ours_line(args, 1, 6600.0, stats, [_info()], 5e-9, 7000.0, 200_000_000, 1, {}, cpu, None,
+                           None, cfg)
+    _check_common(line)
+    assert line["dtype"] == "f32" and "sparse" in line["config"]["workload"]
+    assert line["roofline"]["traffic"] is None and line["roofline"]["frac"] > 0
+
+
+def test_reference_arm_is_unavailable_for_the_sparse_workload(monkeypatch, capsys):
+    monkeypatch.delenv("RANK", raising=False)
+    assert bench.run_reference(argparse.Namespace(steps=2, warmup=1, gpus=1, config="c3")) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "densely" in line["unavailable"]
