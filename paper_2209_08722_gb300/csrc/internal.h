@@ -112,8 +112,6 @@ int sparse_grid(int num_sms);
 constexpr int kSegNnz = 4096;  // CSR entries per row segment at most
 int sparse2_col_grid(long long n, int num_sms);
 cudaError_t launch_sparse2(int dtype, bool fp64, int mode, const StreamArgs& a, int num_sms, cudaStream_t st);
-cudaError_t launch_sparse(int dtype, bool fp64, int mode, const StreamArgs& a, int grid,
-                          cudaStream_t st);
 cudaError_t launch_sparse_sketch(int dtype, const long long* cp, const int* ri, const void* val,
                                  long long n, const double* dvec, int is_d2, uint64_t seed,
                                  long long k, int retry, int s_blocks, int w, double* adw, int m,
