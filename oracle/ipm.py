@@ -31,6 +31,7 @@ from typing import List, Optional
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse as sps
 
 from . import correction, pcg, sketch
 
@@ -109,7 +110,10 @@ def rhs(A, x, s, r_p, r_d, sigma, mu, feasible: bool):
 
 
 def normal_matrix(A, d2):
-    """M = A D^2 A^T (eq. normal), formed densely (oracle only)."""
+    """M = A D^2 A^T (eq. normal), formed densely (oracle only).  A sparse A
+    (scipy.sparse) gives the same matrix through a sparse product."""
+    if sps.issparse(A):
+        return (A @ sps.diags(d2) @ A.T).toarray()
     return (A * d2) @ A.T
 
 
@@ -402,9 +406,16 @@ def solve(A, b, c, opt: Options, x0=None, y0=None, s0=None) -> Result:
     """Algorithm 2 (``opt.mode == "feasible"``) or 3 (``"infeasible"``).
 
     Default start (infeasible): x0 = s0 = 1, y0 = 0.  The feasible mode needs
-    a strictly feasible start in N(gamma) from the caller.
+    a strictly feasible start in N(gamma) from the caller.  A may be a
+    scipy.sparse matrix with the exact solver (fixed sigma): every step then
+    uses A only in products with vectors and in eq. normal's A D^2 A^T.
     """
-    A = np.asarray(A, dtype=np.float64)
+    if sps.issparse(A):
+        if opt.solver != "exact" or opt.sigma_rule == "adaptive":
+            raise ValueError("a sparse A is taken by the exact solver with fixed sigma only")
+        A = sps.csr_matrix(A, dtype=np.float64)
+    else:
+        A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
     feasible = opt.mode == "feasible"
     x = np.ones(n) if x0 is None else np.array(x0, dtype=float)

@@ -74,6 +74,49 @@ def test_planted_tiny_matches_vertex_enumeration():
 
 
 # ---------------------------------------------------------------------------
+# sparse A: the exact solver takes a scipy.sparse matrix (eq. normal's
+# A D^2 A^T by a sparse product)
+# ---------------------------------------------------------------------------
+
+def _csc(lp):
+    import scipy.sparse as sps
+    return sps.csc_matrix((lp.val, lp.row_idx, lp.col_ptr), shape=(lp.m, lp.n))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_sparse_input_reaches_the_planted_optimum(seed):
+    # the planted (x*, y*, s*) of a sparse LP fixes its optimal value in
+    # closed form; the solve from the infeasible start must reach it
+    lp = lpgen.planted_sparse(24, 900, nnz_per_col=4, seed=seed)
+    A = _csc(lp)
+    res = ipm.solve(A, lp.b, lp.c, ipm.Options(mode="infeasible", solver="exact"))
+    assert res.status == "optimal"
+    obj = lp.c @ res.x
+    assert abs(obj - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    assert abs(obj - lp.b @ res.y) <= 1e-8 * (1 + abs(obj))
+    assert np.linalg.norm(A @ res.x - lp.b) <= 1e-8 * (1 + np.linalg.norm(lp.b))
+    assert np.all(res.x > 0) and np.all(res.s > 0)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sparse_input_matches_vertex_enumeration(seed):
+    # brute force over every basis of a tiny sparse LP: the optimal value
+    # the oracle reaches from the sparse matrix is the best vertex
+    lp = lpgen.planted_sparse(3, 12, nnz_per_col=2, seed=seed)
+    best, _, count = vertex.enumerate_vertices(lp.dense(), lp.b, lp.c)
+    assert count > 0 and best == pytest.approx(lp.objective, rel=1e-9, abs=1e-9)
+    res = ipm.solve(_csc(lp), lp.b, lp.c, ipm.Options(mode="infeasible", solver="exact"))
+    assert res.status == "optimal"
+    assert abs(lp.c @ res.x - best) <= 1e-7 * (1 + abs(best))
+
+
+def test_sparse_input_is_refused_by_the_sketched_solver():
+    lp = lpgen.planted_sparse(8, 100, nnz_per_col=3, seed=0)
+    with pytest.raises(ValueError):
+        ipm.solve(_csc(lp), lp.b, lp.c, ipm.Options(mode="infeasible", solver="sketch"))
+
+
+# ---------------------------------------------------------------------------
 # per-step identities and invariants
 # ---------------------------------------------------------------------------
 

@@ -65,6 +65,8 @@ PINS = {
     "planted_sketch": ("test_oracle_ipm", "test_planted_optimum_reached", {"solver": "sketch", "seed": 0}),
     "feasible_planted": ("test_oracle_ipm", "test_feasible_mode_planted", {}),
     "vertices": ("test_oracle_ipm", "test_vertex_enumeration_and_highs_agree_with_oracle", {"seed": 0}),
+    "planted_sparse": ("test_oracle_ipm", "test_sparse_input_reaches_the_planted_optimum", {"seed": 0}),
+    "vertices_sparse": ("test_oracle_ipm", "test_sparse_input_matches_vertex_enumeration", {"seed": 0}),
     "lemma45_feas": ("test_oracle_ipm", "test_lemma_4_5_identities", {"mode": "feasible"}),
     "lemma45_infeas": ("test_oracle_ipm", "test_lemma_4_5_identities", {"mode": "infeasible"}),
     "feasible_stays": ("test_oracle_ipm", "test_feasible_iterates_stay_feasible_and_in_neighbourhood", {}),
@@ -163,6 +165,10 @@ MUTANTS = [
      ["lemma45_feas", "feasible_planted"]),
     ("normal_matrix_d_not_d2", "ipm", "normal_matrix", "(A * d2) @ A.T", "(A * np.sqrt(d2)) @ A.T",
      ["planted_exact", "vertices"]),
+    ("normal_matrix_sparse_d_not_d2", "ipm", "normal_matrix", "A @ sps.diags(d2) @ A.T",
+     "A @ sps.diags(np.sqrt(d2)) @ A.T", ["planted_sparse", "vertices_sparse"]),
+    ("normal_matrix_sparse_weights_reversed", "ipm", "normal_matrix", "A @ sps.diags(d2) @ A.T",
+     "A @ sps.diags(d2[::-1]) @ A.T", ["planted_sparse", "vertices_sparse"]),
     ("direction_v_dropped", "ipm", "directions", " - v / s", "", ["lemma45_feas", "lemma45_infeas"]),
     ("direction_d2_inverted", "ipm", "directions", "(x / s) * ds", "(s / x) * ds",
      ["lemma45_feas", "lemma45_infeas"]),
