@@ -9,7 +9,7 @@ run times single outer iterations of the oracle live and scales them by the
 outer-iteration count recorded here for the same LP; the bench also checks the
 GPU objective against the objective recorded here.
 
-    python tests/golden/make_oracle_records.py c4 [c2 ...]
+    python tests/golden/make_oracle_records.py c4 [c2 c3 ...]
 """
 
 import json
@@ -32,7 +32,11 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_solves.js
 def record(name: str) -> dict:
     cfg = lpgen.CONFIGS[name]
     lp = lpgen.make(cfg)
-    A = lp.dense()
+    if lp.sparse:  # the oracle's exact solver takes the sparse matrix as it is
+        import scipy.sparse as sps
+        A = sps.csc_matrix((lp.val, lp.row_idx, lp.col_ptr), shape=(lp.m, lp.n))
+    else:
+        A = lp.dense()
     t0 = time.perf_counter()
     res = ipm.solve(A, lp.b, lp.c, ipm.Options(mode="infeasible", solver="exact", tol=1e-8))
     secs = time.perf_counter() - t0

@@ -189,8 +189,13 @@ def test_sparse_workload_line_has_every_contract_key():
     assert line["roofline"]["traffic"] is None and line["roofline"]["frac"] > 0
 
 
-def test_reference_arm_is_unavailable_for_the_sparse_workload(monkeypatch, capsys):
-    monkeypatch.delenv("RANK", raising=False)
-    assert bench.run_reference(argparse.Namespace(steps=2, warmup=1, gpus=1, config="c3")) == 0
-    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
-    assert line["impl"] == "reference" and "densely" in line["unavailable"]
+def test_oracle_takes_the_sparse_workload_as_a_sparse_matrix():
+    import lpgen
+    import numpy as np
+    import scipy.sparse as sps
+    lp = lpgen.planted_sparse(12, 200, nnz_per_col=3, seed=1)
+    A = bench.oracle_matrix(lp)
+    assert sps.issparse(A) and A.shape == (lp.m, lp.n)
+    assert np.array_equal(A.toarray(), lp.dense())
+    st = bench.OracleStepper(lp)
+    assert st.step() > 0 and st.state[0].shape == (lp.n,)
