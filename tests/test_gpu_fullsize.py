@@ -12,6 +12,9 @@ the double-float product to 8 (m + n) 2^-53 times the same bound, the
 double-float sketch to (32 n s / w + 64) 2^-48 times |A D| |W|.
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -23,6 +26,16 @@ pytestmark = pytest.mark.gpu
 
 M, N, S_BLOCKS, W_FACTOR = 512, 131072, 4, 4.0
 DF_U = 2.0 ** -48
+
+
+def _oracle_objective(name, lp):
+    """The objective of the CPU oracle's own whole solve of this very LP,
+    written by tests/golden/make_oracle_records.py (which calls only the
+    oracle)."""
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_solves.json")))[name]
+    assert (rec["m"], rec["n"], rec["seed"]) == (lp.m, lp.n, 0)
+    assert abs(rec["planted_objective"] - lp.objective) <= 1e-9 * (1 + abs(lp.objective))
+    return rec["objective"]
 
 
 @pytest.fixture(scope="module")
@@ -77,6 +90,8 @@ def test_full_size_solve_reaches_the_planted_optimum(bench_lp):
     assert info["status"] == 0, info
     assert info["rel_gap"] <= 1e-8 and info["rp_rel"] <= 1e-8 and info["rd_rel"] <= 1e-8
     assert abs(float(lp.c @ x) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    o = _oracle_objective("c2", lp)
+    assert abs(float(lp.c @ x) - o) <= 1e-7 * (1 + abs(o))
     assert np.all(x > 0) and np.all(s > 0)
     # the planted support is identified: the m largest x_j are the basic columns
     basis = np.nonzero(lp.x_star > 0)[0]
@@ -158,6 +173,8 @@ def test_c4_full_size_solve_reaches_the_planted_optimum(c4_lp):
     assert info["rel_gap"] <= 1e-8 and info["rp_rel"] <= 1e-8 and info["rd_rel"] <= 1e-8
     assert abs(float(lp.c @ x) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
     assert abs(float(lp.b @ y) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    o = _oracle_objective("c4", lp)
+    assert abs(float(lp.c @ x) - o) <= 1e-7 * (1 + abs(o))
     assert np.all(x > 0) and np.all(s > 0)
     basis = np.nonzero(lp.x_star > 0)[0]
     assert set(np.argsort(-x)[:lp.m]) == set(basis)
@@ -243,6 +260,8 @@ def test_c3_full_size_solve_from_csr_reaches_the_planted_objective():
     assert info["rel_gap"] <= 1e-8 and info["rp_rel"] <= 1e-8 and info["rd_rel"] <= 1e-8
     assert abs(float(lp.c @ x) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
     assert abs(float(lp.b @ y) - lp.objective) <= 1e-7 * (1 + abs(lp.objective))
+    o = _oracle_objective("c3", lp)
+    assert abs(float(lp.c @ x) - o) <= 1e-7 * (1 + abs(o))
     assert np.all(x > 0) and np.all(s > 0)
     with solver_for(lp, **opts) as S:
         x2, y2, _, info2 = S.solve(tol=1e-8)
