@@ -22,10 +22,10 @@ import textwrap
 import numpy as np
 import pytest
 
-from oracle import correction, ipm, mlp, pcg, phase1, sketch
+from oracle import correction, ipm, mlp, pcg, phase1, sketch, vertex
 
 MODULES = {"sketch": sketch, "pcg": pcg, "correction": correction, "ipm": ipm,
-           "phase1": phase1, "mlp": mlp}
+           "phase1": phase1, "mlp": mlp, "vertex": vertex}
 
 
 def _pin(test_module, name, **kwargs):
@@ -40,6 +40,8 @@ PINS = {
     # oracle.sketch
     "splitmix_golden": ("test_oracle_sketch", "test_splitmix64_reference_outputs", {}),
     "counter_draw": ("test_oracle_sketch", "test_counter_draw_equals_stream_position", {}),
+    "cs_redraw": ("test_oracle_sketch", "test_countsketch_redraw_changes_hash", {}),
+    "cs_blocks": ("test_oracle_sketch", "test_countsketch_blocks_hash_independently", {}),
     "cs_structure": ("test_oracle_sketch", "test_countsketch_structure", {"w": 128, "s": 4}),
     "cs_gram": ("test_oracle_sketch", "test_sparse_embedding_approximates_gram", {}),
     "gauss_moments": ("test_oracle_sketch", "test_gaussian_sketch_moments", {}),
@@ -65,6 +67,7 @@ PINS = {
     "planted_sketch": ("test_oracle_ipm", "test_planted_optimum_reached", {"solver": "sketch", "seed": 0}),
     "feasible_planted": ("test_oracle_ipm", "test_feasible_mode_planted", {}),
     "vertices": ("test_oracle_ipm", "test_vertex_enumeration_and_highs_agree_with_oracle", {"seed": 0}),
+    "planted_tiny_vertices": ("test_oracle_ipm", "test_planted_tiny_matches_vertex_enumeration", {}),
     "planted_sparse": ("test_oracle_ipm", "test_sparse_input_reaches_the_planted_optimum", {"seed": 0}),
     "vertices_sparse": ("test_oracle_ipm", "test_sparse_input_matches_vertex_enumeration", {"seed": 0}),
     "lemma45_feas": ("test_oracle_ipm", "test_lemma_4_5_identities", {"mode": "feasible"}),
@@ -109,6 +112,18 @@ MUTANTS = [
     ("mix64_shift", "sketch", "mix64", "(z >> _U64(30))", "(z >> _U64(29))", ["splitmix_golden"]),
     ("mix64_multiplier", "sketch", "mix64", "0x94D049BB133111EB", "0x94D049BB133111EF", ["splitmix_golden"]),
     ("draw_off_by_one", "sketch", "draw", "(ctr + _U64(1))", "ctr", ["counter_draw"]),
+    ("stream_off_by_one", "sketch", "splitmix64_stream", "np.arange(1, count + 1", "np.arange(0, count",
+     ["splitmix_golden"]),
+    ("counter_block_dropped", "sketch", "countsketch_counter", "* MAX_BLOCKS + block)", "* MAX_BLOCKS)",
+     ["cs_blocks"]),
+    ("counter_retry_dropped", "sketch", "countsketch_counter", "(k * MAX_RETRY + retry)", "(k * MAX_RETRY)",
+     ["cs_redraw"]),
+    ("counter_outer_dropped", "sketch", "countsketch_counter", "(k * MAX_RETRY + retry)", "(retry)",
+     ["cs_redraw"]),
+    ("cg_coeffs_beta_inverted", "ipm", "_cg_coeffs", "beta = rr_new / rr", "beta = rr / rr_new", ["lanczos"]),
+    ("flatten_row_major", "mlp", "flatten", "p.T.reshape(-1)", "p.reshape(-1)", ["mlp_layout"]),
+    ("vertex_feasibility_sign", "vertex", "enumerate_vertices", "(xB < -feas_tol).any()",
+     "(xB > feas_tol).any()", ["planted_tiny_vertices", "vertices"]),
     ("cs_block_offset_dropped", "sketch", "countsketch_hash",
      "cols[b] = b * wb + h.astype(np.int64)", "cols[b] = h.astype(np.int64)", ["cs_structure"]),
     ("cs_scale_dropped", "sketch", "countsketch_matrix", "(signs / np.sqrt(s))", "signs",

@@ -86,6 +86,18 @@ def test_countsketch_redraw_changes_hash():
     assert (a != b).mean() > 0.8 and (a != c).mean() > 0.8
 
 
+def test_countsketch_blocks_hash_independently():
+    # the s blocks of one draw are independent hashes (each row has one
+    # nonzero per block, at a bucket and sign of its own): two blocks put a
+    # row in the same in-block bucket with probability 1/(w/s) and give it
+    # the same sign half of the time
+    n, w, s = 20000, 128, 2
+    cols, signs = sketch.countsketch_hash(5, 2, 0, n, w, s)
+    h0, h1 = cols[0], cols[1] - w // s
+    assert abs((h0 == h1).mean() - 1.0 / (w // s)) < 0.01
+    assert abs((signs[0] == signs[1]).mean() - 0.5) < 0.03
+
+
 def test_sparse_embedding_approximates_gram():
     # eq. pdprec with Z = V^T (orthonormal rows): ||Z W W^T Z^T - I|| small for large w
     rng = np.random.default_rng(0)
