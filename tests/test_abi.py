@@ -53,7 +53,8 @@ def test_struct_layouts_match_c():
     from paper_2209_08722_gb300 import _native as nat
     structs = {"lp_matrix": nat.LpMatrix, "lp_options": nat.LpOptions, "lp_result": nat.LpResult,
                "lp_nsolve_info": nat.LpNsolveInfo, "lp_kernel_stats": nat.LpKernelStats,
-               "lp_iter_record": nat.LpIterRecord, "lp_phase1_info": nat.LpPhase1Info}
+               "lp_iter_record": nat.LpIterRecord, "lp_phase1_info": nat.LpPhase1Info,
+               "lp_state": nat.LpState}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
