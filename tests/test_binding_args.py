@@ -143,3 +143,20 @@ def test_phase1_and_batch_arguments():
     _reaches_library(lambda: phase1_start(A, np.ones(M), M, N, tol=0.0))   # tol must be > 0
     with pytest.raises(ValueError, match="mode"):
         solve_batch([], mode="both")
+
+
+def test_state_arguments():
+    # a checkpoint's vectors must have the LP's sizes before any pointer
+    # reaches lp_set_state, which copies exactly n / m values from each
+    S = _bare_solver()
+    good = {"k": 3, "mode": 1, "has_dy_prev": 0, "mu0": 1.0, "r0": 1.0, "ratio_ref": 0.0, "seed": 0,
+            "mu": 0.5, "x": np.ones(N), "y": np.zeros(M), "s": np.ones(N), "dy_prev": np.zeros(M)}
+    for key, bad in (("x", np.ones(N - 1)), ("y", np.zeros(M + 1)), ("s", np.ones(M)),
+                     ("dy_prev", np.zeros(N))):
+        with pytest.raises(ValueError, match=f"{key} must have"):
+            S.set_state(dict(good, **{key: bad}))
+    with pytest.raises(KeyError):
+        S.set_state({k: v for k, v in good.items() if k != "mu"})
+    _reaches_library(lambda: S.set_state(good))
+    _reaches_library(lambda: S.get_state())
+    _reaches_library(lambda: S.check_guards())
