@@ -19,6 +19,7 @@
 #include <cusolverDn.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -59,11 +60,87 @@ struct EvPair {
 // only on the matrix).  Returns an empty string, or the structural error found
 // in the CSR arrays (row pointers not starting at 0, decreasing, or not ending
 // at nnz; a column index outside [0, n)).
+//
+// Large matrices are sorted in parts: the rows are split into contiguous
+// ranges of about equal entry counts, each part counts its own entries per
+// column, and within a column the parts take their slots in row order, so the
+// result is the serial sort's, bit for bit, whatever the number of parts.
 struct CscCopy {
   std::vector<int64_t> ptr;
   std::vector<int32_t> idx;
   std::vector<char> val;
 };
+
+// f(t) for t in [0, parts): parts 1.. on worker threads, part 0 (and any part
+// whose thread cannot be started) on the calling thread.  f must not throw.
+template <typename F>
+void run_parts(int parts, const F& f) {
+  std::vector<std::thread> workers;
+  workers.reserve((size_t)parts);
+  std::vector<int> here;
+  here.reserve((size_t)parts);
+  for (int t = 1; t < parts; ++t) {
+    try {
+      workers.emplace_back(f, t);
+    } catch (...) {
+      here.push_back(t);
+    }
+  }
+  f(0);
+  for (int t : here) f(t);
+  for (auto& w : workers) w.join();
+}
+
+// V: an unsigned integer of the element's size (values are moved bit for bit)
+template <typename V>
+void csr_to_csc_fill(int m, long long n, long long nnz, const int64_t* rp, const int32_t* ci, const V* v,
+                     CscCopy* out) {
+  // parts: at most 8 and the host's threads, none for small matrices, and at
+  // most 256 MB of per-part column slots
+  int parts = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+  if (nnz < (1LL << 20) || m < 2 * parts) parts = 1;
+  while (parts > 1 && (double)parts * (double)n * sizeof(int64_t) > 256e6) --parts;
+  std::vector<int> rb((size_t)parts + 1);
+  rb[0] = 0;
+  rb[parts] = m;
+  for (int t = 1; t < parts; ++t) {
+    const long long target = nnz / parts * t;
+    rb[t] = std::max(rb[t - 1], (int)(std::lower_bound(rp, rp + m + 1, (int64_t)target) - rp));
+    rb[t] = std::min(rb[t], m);
+  }
+  // slot[t][j]: part t's count in column j, then its next free slot there
+  std::vector<int64_t> slot((size_t)parts * n, 0);
+  run_parts(parts, [&](int t) {
+    int64_t* c = slot.data() + (size_t)t * n;
+    for (long long q = rp[rb[t]]; q < rp[rb[t + 1]]; ++q) ++c[ci[q]];
+  });
+  out->ptr.assign((size_t)n + 1, 0);
+  int64_t run = 0;
+  for (long long j = 0; j < n; ++j) {
+    out->ptr[j] = run;
+    for (int t = 0; t < parts; ++t) {
+      int64_t& c = slot[(size_t)t * n + j];
+      const int64_t k = c;
+      c = run;
+      run += k;
+    }
+  }
+  out->ptr[n] = run;
+  out->idx.resize((size_t)std::max<long long>(nnz, 1));
+  out->val.resize((size_t)std::max<long long>(nnz, 1) * sizeof(V));
+  int32_t* idx = out->idx.data();
+  V* val = reinterpret_cast<V*>(out->val.data());
+  run_parts(parts, [&](int t) {
+    int64_t* c = slot.data() + (size_t)t * n;
+    for (int i = rb[t]; i < rb[t + 1]; ++i)
+      for (long long q = rp[i]; q < rp[i + 1]; ++q) {
+        const int64_t dst = c[ci[q]]++;
+        idx[dst] = i;
+        val[dst] = v[q];
+      }
+  });
+}
+
 std::string csr_to_csc(int m, long long n, long long nnz, const int64_t* rp, const int32_t* ci,
                        const void* val, int esz, CscCopy* out) {
   if (rp[0] != 0 || rp[m] != nnz) return "CSR ptr[0] != 0 or ptr[m] != nnz";
@@ -71,19 +148,9 @@ std::string csr_to_csc(int m, long long n, long long nnz, const int64_t* rp, con
     if (rp[i + 1] < rp[i]) return "CSR row pointers not monotone";
   for (long long q = 0; q < nnz; ++q)
     if (ci[q] < 0 || ci[q] >= n) return "CSR column index out of range";
-  out->ptr.assign((size_t)n + 1, 0);
-  for (long long q = 0; q < nnz; ++q) ++out->ptr[(size_t)ci[q] + 1];
-  for (long long j = 0; j < n; ++j) out->ptr[j + 1] += out->ptr[j];
-  std::vector<int64_t> cursor(out->ptr.begin(), out->ptr.end() - 1);
-  out->idx.resize((size_t)std::max<long long>(nnz, 1));
-  out->val.resize((size_t)std::max<long long>(nnz, 1) * esz);
-  const char* v = static_cast<const char*>(val);
-  for (int i = 0; i < m; ++i)
-    for (long long q = rp[i]; q < rp[i + 1]; ++q) {
-      const int64_t dst = cursor[ci[q]]++;
-      out->idx[dst] = i;
-      std::memcpy(out->val.data() + (size_t)dst * esz, v + (size_t)q * esz, esz);
-    }
+  if (esz == 8) csr_to_csc_fill(m, n, nnz, rp, ci, static_cast<const uint64_t*>(val), out);
+  else if (esz == 4) csr_to_csc_fill(m, n, nnz, rp, ci, static_cast<const uint32_t*>(val), out);
+  else csr_to_csc_fill(m, n, nnz, rp, ci, static_cast<const uint16_t*>(val), out);
   return std::string();
 }
 }  // namespace

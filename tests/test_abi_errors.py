@@ -313,3 +313,36 @@ def test_csr_to_csc_is_a_stable_column_sort(lib):
     with pytest.raises(LPError):
         csr_to_csc(rp, bad, val, m, n, "f64")
     assert lib.lp_csr_to_csc(m, n, 0, None, None, None, nat.LP_F64, None, None, None) == nat.LP_ERR_ARG
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_csr_to_csc_in_parts_equals_scipy_bit_for_bit(lib, dtype):
+    # above a million entries the sort runs in parts on host threads; the
+    # result must still be the stable sort, bit for bit: empty rows, rows
+    # of very different lengths, duplicate column indices, and the reverse
+    # direction (CSC -> CSR, as lp_create builds the row copy) too
+    sp = pytest.importorskip("scipy.sparse")
+    from paper_2209_08722_gb300.solver import csr_to_csc
+    rng = np.random.default_rng(11)
+    m, n = 3001, 40000
+    counts = rng.integers(0, 800, size=m)
+    counts[rng.choice(m, 50, replace=False)] = 0
+    counts[rng.choice(m, 5, replace=False)] = 20000
+    rp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    nnz = int(rp[-1])
+    assert nnz >= 1 << 20
+    ci = rng.integers(0, n, size=nnz).astype(np.int32)
+    bits = rng.integers(0, 1 << 16, size=nnz, dtype=np.uint16)
+    vals = {"f64": rng.standard_normal(nnz), "f32": rng.standard_normal(nnz).astype(np.float32),
+            "bf16": bits}[dtype]
+    keys = np.arange(nnz, dtype=np.int64)  # SciPy carries the entry's position through its own sort
+    ref = sp.csr_matrix((keys + 1, ci, rp), shape=(m, n)).tocsc()
+    cp, ri, vo = csr_to_csc(rp, ci, vals, m, n, dtype)
+    assert np.array_equal(cp, ref.indptr) and np.array_equal(ri, ref.indices)
+    assert np.array_equal(vo.view(np.uint8), vals[ref.data - 1].view(np.uint8))
+    # the reverse direction: the CSC read as the CSR of the transpose
+    rp2, ci2, vo2 = csr_to_csc(cp, ri, vo, n, m, dtype)
+    assert np.array_equal(rp2, rp)
+    back = sp.csc_matrix((np.arange(nnz) + 1, ri, cp), shape=(m, n)).tocsr()
+    assert np.array_equal(ci2, back.indices)
+    assert np.array_equal(vo2.view(np.uint8), vo[back.data - 1].view(np.uint8))
